@@ -1,0 +1,17 @@
+"""FP64 CPU oracle for the cue field and growth-cone step.
+
+Test infrastructure only: the test suite, the smoke check and the CPU-baseline
+leg of ``bench.py`` may import this package; the product library never does.
+"""
+from .oracle import (  # noqa: F401
+    Grid,
+    Cone,
+    build,
+    philox4x32_10,
+    noise,
+    node_gradient,
+    gradient_at,
+    field_step,
+    cone_step,
+    run,
+)

@@ -1,0 +1,360 @@
+/*
+ * cue_oracle.c -- plain FP64 CPU oracle for the guidance-cue field and the
+ * growth-cone step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * restatement of the model that the CUDA path is checked against.  Only the
+ * test suite, the smoke check and the CPU-baseline leg of the benchmark may
+ * build, load or call it; the product library never links it, and it shares
+ * no code, header, table or constant with the CUDA sources.
+ *
+ * The model (Mihut, Morgan & Kaiser, "GPU Simulation of Axon Growth and
+ * Guidance through Cue Diffusion"):
+ *   - the cue lives on a fixed Eulerian grid (Sec. 5.2), diffuses at a
+ *     per-cue rate and is emitted by sources placed pseudo-randomly
+ *     (Sec. 4.3); its influence falls off with distance from the source
+ *     (Sec. 3.5, "Diffusion of guidance molecules").  Written as an explicit
+ *     update  C' = C + dt (D lap(C) - lambda C) + S  on nodes x = i h with
+ *     no-flux walls;
+ *   - each growth cone advances a fixed distance per step along its
+ *     direction, which is steered by vector addition of the current
+ *     direction and the cue direction it senses across its width
+ *     (Sec. 3.5, "Growth cone steering mechanisms", Eq. 6-7), plus a
+ *     Gaussian term (Sec. 3.5, the N(SNR,1) decision) drawn from a
+ *     stateless per-thread counter-based generator (Sec. 5.1) through the
+ *     Box-Muller transform (Sec. 3.2, normal-deviate method);
+ *   - a cone stops when it leaves the simulation bounds (Sec. 3.4) or, when
+ *     enabled, when it comes within a radius of a cue source, tested on
+ *     squared distances (Sec. 3.3).
+ *
+ * Readings where the paper is silent (all listed in the design notes):
+ *   - nodes at x = i h, domain [0,(N-1)h] per axis;
+ *   - no-flux wall = a missing neighbour contributes no flux term
+ *     (equivalently a ghost node equal to the edge node);
+ *   - the per-step emission e_k is added to the source node after the
+ *     stencil, unscaled by dt; a dense rate map M enters as dt*M;
+ *   - cones and field both read the state of step n;
+ *   - node gradient = central difference with ghost = edge; the gradient at
+ *     a point is the bilinear (2D) / trilinear (3D) interpolation of the node
+ *     gradients;
+ *   - ghat = g/|g| if |g|^2 > eps^2 else 0; v = w_p d + w_g ghat + w_n xi;
+ *     d' = v/|v| unless |v|^2 <= 1e-30 (then d' = d); p' = p + l d';
+ *   - noise: Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
+ *     key = (seed lo, seed hi), counter = (axon, step, 0, 0); uniforms
+ *     u1 = ((x0>>8)+1) 2^-24 in (0,1], u2 = (x1>>8) 2^-24 in [0,1), and the
+ *     same for (x2, x3); Box-Muller gives xi0, xi1 from (u1,u2), xi2 from
+ *     (u3,u4);
+ *   - wall mode 0 (stop): if p' leaves the domain the cone becomes inactive
+ *     and keeps p, d of step n; wall mode 1 (clamp): each coordinate of p' is
+ *     clamped to the domain and d' is kept;
+ *   - source stop: after the move, inactive if |p' - x_k|^2 <= r^2 for some
+ *     source node x_k.
+ *
+ * Pins (tests that do not re-type this code): hand-enumerated single steps,
+ * exact mass conservation, the exact FTCS variance growth, the heat kernel,
+ * the pure-decay closed form, the DCT-II steady-state solve, mirror and
+ * transpose symmetry, self-adjointness of the no-flux Laplacian, exact
+ * gradients of linear and quadratic fields, the scalar heading recurrence,
+ * straight lines, the normal law of the noise, and Philox against an
+ * independent implementation.  Whole-run trajectories (hundreds of coupled
+ * steps) are parity unpinned by design: they are chaotic with respect to
+ * rounding and are compared only as endpoint statistics.
+ *
+ * Layout: fields are dense row-major arrays with x fastest,
+ * index = i + nx (j + ny k).  Cone state is structure-of-arrays:
+ * pos[c*n + a] is coordinate c of cone a (same for dir).
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int nx, ny, nz;     /* nodes per axis (nz = 1 in 2D) */
+    double h, D, lambda, dt;
+} orc_grid;
+
+typedef struct {
+    double w_prev, w_grad, w_noise, step_len;
+    double stop_radius; /* <= 0: off */
+    double grad_eps;
+    int wall_mode;      /* 0 = stop at the wall, 1 = clamp to the wall */
+    uint64_t seed;
+} orc_cone;
+
+static int64_t nodes_of(const orc_grid *g)
+{
+    return (int64_t)g->nx * g->ny * (g->dim == 3 ? g->nz : 1);
+}
+
+static int extent(const orc_grid *g, int axis)
+{
+    return axis == 0 ? g->nx : axis == 1 ? g->ny : g->nz;
+}
+
+/* ------------------------------------------------------------------------
+ * Philox-4x32-10, written from the SC'11 definition: each round multiplies
+ * counter words 0 and 2 by the two round constants, forms the 64-bit
+ * products' high and low halves, and mixes the high halves with the other
+ * two words and the round key; the key is bumped by the two Weyl constants
+ * between rounds.
+ * ---------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in (0,1]: the top 24 bits plus one, times 2^-24. */
+static double unit_open0(uint32_t x) { return ((double)(x >> 8) + 1.0) * (1.0 / 16777216.0); }
+/* Uniform in [0,1): the top 24 bits times 2^-24. */
+static double unit_open1(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+/* Gaussian noise vector of cone `axon` at step `step` (Box-Muller on the
+ * four Philox words); xi[0..dim-1] are i.i.d. N(0,1). */
+void orc_noise(uint64_t seed, uint32_t axon, uint32_t step, int dim, double xi[3])
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    uint32_t ctr[4] = {axon, step, 0u, 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    double u1 = unit_open0(x[0]), u2 = unit_open1(x[1]);
+    double r = sqrt(-2.0 * log(u1));
+    xi[0] = r * cos(two_pi * u2);
+    xi[1] = r * sin(two_pi * u2);
+    xi[2] = 0.0;
+    if (dim == 3) {
+        double u3 = unit_open0(x[2]), u4 = unit_open1(x[3]);
+        double r2 = sqrt(-2.0 * log(u3));
+        xi[2] = r2 * cos(two_pi * u4);
+    }
+}
+
+void orc_noise_many(uint64_t seed, int n, const uint32_t *axon, const uint32_t *step,
+                    int dim, double *xi /* [n][3] */)
+{
+    for (int a = 0; a < n; ++a)
+        orc_noise(seed, axon[a], step[a], dim, xi + 3 * (size_t)a);
+}
+
+void orc_philox_many(int n, const uint32_t *ctr /* [n][4] */, const uint32_t *key /* [n][2] */,
+                     uint32_t *out /* [n][4] */)
+{
+    for (int a = 0; a < n; ++a)
+        orc_philox4x32_10(ctr + 4 * (size_t)a, key + 2 * (size_t)a, out + 4 * (size_t)a);
+}
+
+/* ------------------------------------------------------------------------
+ * Field: one explicit step.  For every node, each existing axis neighbour j
+ * contributes alpha (C_j - C_i); missing neighbours (walls) contribute
+ * nothing; decay removes lambda dt C_i.  Then the point sources add their
+ * per-step emission, then a dense rate map adds dt M_i.
+ * ---------------------------------------------------------------------- */
+void orc_field_step(const orc_grid *g, const double *C, double *Cn,
+                    const int32_t *src_cell, const double *src_emit, int n_src,
+                    const double *src_map)
+{
+    const double alpha = g->D * g->dt / (g->h * g->h);
+    const double decay = g->lambda * g->dt;
+    const int nx = g->nx, ny = g->ny, nz = (g->dim == 3) ? g->nz : 1;
+    const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t c = i * sx + j * sy + k * sz;
+                double ci = C[c];
+                double flux = 0.0;
+                if (i > 0)      flux += C[c - sx] - ci;
+                if (i < nx - 1) flux += C[c + sx] - ci;
+                if (j > 0)      flux += C[c - sy] - ci;
+                if (j < ny - 1) flux += C[c + sy] - ci;
+                if (g->dim == 3) {
+                    if (k > 0)      flux += C[c - sz] - ci;
+                    if (k < nz - 1) flux += C[c + sz] - ci;
+                }
+                Cn[c] = ci + alpha * flux - decay * ci;
+            }
+    for (int s = 0; s < n_src; ++s)
+        Cn[src_cell[s]] += src_emit[s];
+    if (src_map) {
+        int64_t n = nodes_of(g);
+        for (int64_t c = 0; c < n; ++c)
+            Cn[c] += g->dt * src_map[c];
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Gradient.  Node gradient: central differences, a missing neighbour
+ * replaced by the node itself (ghost = edge), so on a wall node the
+ * one-sided difference is halved.  Point gradient: bilinear / trilinear
+ * interpolation of the node gradients of the cell that holds p, the cell's
+ * lower corner clamped to [0, N-2] on each axis.
+ * ---------------------------------------------------------------------- */
+static double node_value(const orc_grid *g, const double *C, int i, int j, int k)
+{
+    return C[(int64_t)i + (int64_t)g->nx * ((int64_t)j + (int64_t)g->ny * k)];
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+void orc_node_gradient(const orc_grid *g, const double *C, int i, int j, int k, double out[3])
+{
+    const double inv2h = 1.0 / (2.0 * g->h);
+    int nz = (g->dim == 3) ? g->nz : 1;
+    out[0] = (node_value(g, C, clampi(i + 1, 0, g->nx - 1), j, k) -
+              node_value(g, C, clampi(i - 1, 0, g->nx - 1), j, k)) * inv2h;
+    out[1] = (node_value(g, C, i, clampi(j + 1, 0, g->ny - 1), k) -
+              node_value(g, C, i, clampi(j - 1, 0, g->ny - 1), k)) * inv2h;
+    out[2] = 0.0;
+    if (g->dim == 3)
+        out[2] = (node_value(g, C, i, j, clampi(k + 1, 0, nz - 1)) -
+                  node_value(g, C, i, j, clampi(k - 1, 0, nz - 1))) * inv2h;
+}
+
+void orc_gradient_at(const orc_grid *g, const double *C, const double p[3], double out[3])
+{
+    int lo[3] = {0, 0, 0};
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int ax = 0; ax < g->dim; ++ax) {
+        double s = p[ax] / g->h;
+        int i0 = (int)floor(s);
+        i0 = clampi(i0, 0, extent(g, ax) - 2);
+        lo[ax] = i0;
+        f[ax] = s - (double)i0;
+    }
+    out[0] = out[1] = out[2] = 0.0;
+    int kcorners = (g->dim == 3) ? 2 : 1;
+    for (int dk = 0; dk < kcorners; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                double w = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]);
+                if (g->dim == 3) w *= (dk ? f[2] : 1.0 - f[2]);
+                double gn[3];
+                orc_node_gradient(g, C, lo[0] + di, lo[1] + dj, lo[2] + dk, gn);
+                out[0] += w * gn[0];
+                out[1] += w * gn[1];
+                out[2] += w * gn[2];
+            }
+}
+
+void orc_gradient_many(const orc_grid *g, const double *C, int n, const double *p /* [n][3] */,
+                       double *out /* [n][3] */)
+{
+    for (int a = 0; a < n; ++a)
+        orc_gradient_at(g, C, p + 3 * (size_t)a, out + 3 * (size_t)a);
+}
+
+/* ------------------------------------------------------------------------
+ * Growth cones: one step of every active cone on the field C of this step.
+ * pos/dir are SoA [dim][n]; active is 0/1.
+ * ---------------------------------------------------------------------- */
+void orc_cone_step(const orc_grid *g, const orc_cone *cp, const double *C, uint32_t step,
+                   int n, double *pos, double *dir, uint8_t *active,
+                   const int32_t *src_cell, int n_src)
+{
+    const int dim = g->dim;
+    const double eps2 = cp->grad_eps * cp->grad_eps;
+    const double r2 = cp->stop_radius * cp->stop_radius;
+    for (int a = 0; a < n; ++a) {
+        if (!active[a]) continue;
+        double p[3] = {0, 0, 0}, d[3] = {0, 0, 0};
+        for (int c = 0; c < dim; ++c) {
+            p[c] = pos[(size_t)c * n + a];
+            d[c] = dir[(size_t)c * n + a];
+        }
+        /* sensed cue direction */
+        double gr[3];
+        orc_gradient_at(g, C, p, gr);
+        double gn2 = 0.0;
+        for (int c = 0; c < dim; ++c) gn2 += gr[c] * gr[c];
+        double ghat[3] = {0, 0, 0};
+        if (gn2 > eps2) {
+            double inv = 1.0 / sqrt(gn2);
+            for (int c = 0; c < dim; ++c) ghat[c] = gr[c] * inv;
+        }
+        /* noise */
+        double xi[3];
+        orc_noise(cp->seed, (uint32_t)a, step, dim, xi);
+        /* vector addition of previous direction, cue direction and noise */
+        double v[3] = {0, 0, 0}, vn2 = 0.0;
+        for (int c = 0; c < dim; ++c) {
+            v[c] = cp->w_prev * d[c] + cp->w_grad * ghat[c] + cp->w_noise * xi[c];
+            vn2 += v[c] * v[c];
+        }
+        double dn[3] = {d[0], d[1], d[2]};
+        if (vn2 > 1e-30) {
+            double inv = 1.0 / sqrt(vn2);
+            for (int c = 0; c < dim; ++c) dn[c] = v[c] * inv;
+        }
+        double pn[3] = {0, 0, 0};
+        for (int c = 0; c < dim; ++c) pn[c] = p[c] + cp->step_len * dn[c];
+        /* walls */
+        int outside = 0;
+        for (int c = 0; c < dim; ++c) {
+            double hi = (extent(g, c) - 1) * g->h;
+            if (pn[c] < 0.0 || pn[c] > hi) {
+                outside = 1;
+                if (cp->wall_mode == 1) pn[c] = pn[c] < 0.0 ? 0.0 : hi;
+            }
+        }
+        if (outside && cp->wall_mode == 0) {
+            active[a] = 0;          /* stays at p, d of this step */
+            continue;
+        }
+        for (int c = 0; c < dim; ++c) {
+            pos[(size_t)c * n + a] = pn[c];
+            dir[(size_t)c * n + a] = dn[c];
+        }
+        /* source proximity, squared-distance test */
+        if (cp->stop_radius > 0.0) {
+            for (int s = 0; s < n_src; ++s) {
+                int64_t cell = src_cell[s];
+                double xs[3];
+                xs[0] = (double)(cell % g->nx) * g->h;
+                xs[1] = (double)((cell / g->nx) % g->ny) * g->h;
+                xs[2] = (dim == 3) ? (double)(cell / ((int64_t)g->nx * g->ny)) * g->h : 0.0;
+                double d2 = 0.0;
+                for (int c = 0; c < dim; ++c) d2 += (pn[c] - xs[c]) * (pn[c] - xs[c]);
+                if (d2 <= r2) { active[a] = 0; break; }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * nsteps of the coupled model starting at step `step0`: the cones step on
+ * C^n, then the field advances to C^{n+1}.  C holds the field on entry and
+ * exit; work is a scratch field of the same size.
+ * ---------------------------------------------------------------------- */
+void orc_run(const orc_grid *g, const orc_cone *cp, double *C, double *work,
+             uint32_t step0, int nsteps,
+             const int32_t *src_cell, const double *src_emit, int n_src, const double *src_map,
+             int n, double *pos, double *dir, uint8_t *active)
+{
+    int64_t nn = nodes_of(g);
+    for (int s = 0; s < nsteps; ++s) {
+        uint32_t step = step0 + (uint32_t)s;
+        if (n > 0)
+            orc_cone_step(g, cp, C, step, n, pos, dir, active, src_cell, n_src);
+        orc_field_step(g, C, work, src_cell, src_emit, n_src, src_map);
+        memcpy(C, work, (size_t)nn * sizeof(double));
+    }
+}

@@ -1,0 +1,217 @@
+"""ctypes front end of the FP64 oracle in ``cue_oracle.c``.
+
+Test infrastructure only (see the package docstring).  Every function takes
+and returns numpy arrays; fields are shaped (ny, nx) in 2D and (nz, ny, nx) in
+3D (C order, x fastest); cone state is structure-of-arrays, pos/dir shaped
+(dim, n), active shaped (n,) uint8.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cue_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class _Grid(ct.Structure):
+    _fields_ = [("dim", ct.c_int), ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+                ("h", ct.c_double), ("D", ct.c_double), ("lam", ct.c_double), ("dt", ct.c_double)]
+
+
+class _Cone(ct.Structure):
+    _fields_ = [("w_prev", ct.c_double), ("w_grad", ct.c_double), ("w_noise", ct.c_double),
+                ("step_len", ct.c_double), ("stop_radius", ct.c_double), ("grad_eps", ct.c_double),
+                ("wall_mode", ct.c_int), ("seed", ct.c_uint64)]
+
+
+@dataclasses.dataclass
+class Grid:
+    """Grid and field physics: node i of an axis sits at x = i*h."""
+    dim: int
+    nx: int
+    ny: int
+    nz: int = 1
+    h: float = 1.0
+    D: float = 1.0
+    lam: float = 0.0
+    dt: float = 0.2
+
+    def _c(self) -> _Grid:
+        return _Grid(self.dim, self.nx, self.ny, self.nz if self.dim == 3 else 1,
+                     self.h, self.D, self.lam, self.dt)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx) if self.dim == 3 else (self.ny, self.nx)
+
+    @property
+    def extents(self):
+        return (self.nx, self.ny, self.nz)[: self.dim]
+
+
+@dataclasses.dataclass
+class Cone:
+    """Growth-cone steering parameters."""
+    w_prev: float = 0.5
+    w_grad: float = 0.4
+    w_noise: float = 0.1
+    step_len: float = 0.5
+    stop_radius: float = 0.0
+    grad_eps: float = 1e-15
+    wall_mode: int = 0
+    seed: int = 0
+
+    def _c(self) -> _Cone:
+        return _Cone(self.w_prev, self.w_grad, self.w_noise, self.step_len, self.stop_radius,
+                     self.grad_eps, self.wall_mode, self.seed & 0xFFFFFFFFFFFFFFFF)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, FP contraction off) and return the .so path."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ct.CDLL(build())
+            P = ct.c_void_p
+            lib.orc_philox_many.argtypes = [ct.c_int, P, P, P]
+            lib.orc_noise_many.argtypes = [ct.c_uint64, ct.c_int, P, P, ct.c_int, P]
+            lib.orc_node_gradient.argtypes = [ct.POINTER(_Grid), P, ct.c_int, ct.c_int, ct.c_int, P]
+            lib.orc_gradient_many.argtypes = [ct.POINTER(_Grid), P, ct.c_int, P, P]
+            lib.orc_field_step.argtypes = [ct.POINTER(_Grid), P, P, P, P, ct.c_int, P]
+            lib.orc_cone_step.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, ct.c_uint32,
+                                          ct.c_int, P, P, P, P, ct.c_int]
+            lib.orc_run.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, ct.c_uint32,
+                                    ct.c_int, P, P, ct.c_int, P, ct.c_int, P, P, P]
+            for f in ("orc_philox_many", "orc_noise_many", "orc_node_gradient",
+                      "orc_gradient_many", "orc_field_step", "orc_cone_step", "orc_run"):
+                getattr(lib, f).restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _src(src_cell, src_emit):
+    cell = np.ascontiguousarray(np.asarray(src_cell, dtype=np.int32).reshape(-1))
+    emit = None if src_emit is None else _f64(np.asarray(src_emit).reshape(-1))
+    return cell, emit
+
+
+def philox4x32_10(ctr, key):
+    """Philox-4x32-10 of counters ``ctr`` (n,4) under keys ``key`` (n,2) -> (n,4) uint32."""
+    ctr = np.ascontiguousarray(np.atleast_2d(ctr), dtype=np.uint32)
+    key = np.ascontiguousarray(np.atleast_2d(key), dtype=np.uint32)
+    key = np.ascontiguousarray(np.broadcast_to(key, (ctr.shape[0], 2)))
+    out = np.empty_like(ctr)
+    _load().orc_philox_many(ctr.shape[0], _ptr(ctr), _ptr(key), _ptr(out))
+    return out
+
+
+def noise(seed, axon, step, dim):
+    """Box-Muller Gaussian vectors for cones ``axon`` at steps ``step`` -> (n,3) (unused tail 0)."""
+    axon = np.ascontiguousarray(np.atleast_1d(axon), dtype=np.uint32)
+    step = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(step), axon.shape), dtype=np.uint32)
+    out = np.zeros((axon.shape[0], 3))
+    _load().orc_noise_many(int(seed) & 0xFFFFFFFFFFFFFFFF, axon.shape[0], _ptr(axon), _ptr(step),
+                           dim, _ptr(out))
+    return out
+
+
+def node_gradient(grid: Grid, C, i, j, k=0):
+    C = _f64(C)
+    out = np.zeros(3)
+    g = grid._c()
+    _load().orc_node_gradient(ct.byref(g), _ptr(C), i, j, k, _ptr(out))
+    return out
+
+
+def gradient_at(grid: Grid, C, p):
+    """Interpolated gradient at points ``p`` (n, dim) -> (n, 3)."""
+    C = _f64(C)
+    p = np.atleast_2d(np.asarray(p, dtype=np.float64))
+    pp = np.zeros((p.shape[0], 3))
+    pp[:, : p.shape[1]] = p
+    out = np.zeros((p.shape[0], 3))
+    g = grid._c()
+    _load().orc_gradient_many(ct.byref(g), _ptr(C), p.shape[0], _ptr(pp), _ptr(out))
+    return out
+
+
+def field_step(grid: Grid, C, src_cell=(), src_emit=(), src_map=None):
+    """One explicit field step; returns C^{n+1} (float64, same shape as C)."""
+    C = _f64(C)
+    out = np.empty_like(C)
+    cell, emit = _src(src_cell, src_emit)
+    smap = None if src_map is None else _f64(src_map)
+    g = grid._c()
+    _load().orc_field_step(ct.byref(g), _ptr(C), _ptr(out), _ptr(cell), _ptr(emit),
+                           cell.shape[0], _ptr(smap))
+    return out
+
+
+def cone_step(grid: Grid, cone: Cone, C, step, pos, dir, active, src_cell=()):
+    """One cone step on field C at step index ``step``; returns new (pos, dir, active)."""
+    C = _f64(C)
+    pos = _f64(pos).copy()
+    dirs = _f64(dir).copy()
+    act = np.ascontiguousarray(active, dtype=np.uint8).copy()
+    cell, _ = _src(src_cell, None)
+    g, c = grid._c(), cone._c()
+    _load().orc_cone_step(ct.byref(g), ct.byref(c), _ptr(C), int(step), act.shape[0],
+                          _ptr(pos), _ptr(dirs), _ptr(act), _ptr(cell), cell.shape[0])
+    return pos, dirs, act
+
+
+def run(grid: Grid, cone: Cone, C, step0, nsteps, src_cell=(), src_emit=(), src_map=None,
+        pos=None, dir=None, active=None):
+    """``nsteps`` coupled steps from step index ``step0``: cones on C^n, then C^n -> C^{n+1}.
+
+    Returns (C, pos, dir, active) as new arrays."""
+    C = _f64(C).copy()
+    work = np.empty_like(C)
+    cell, emit = _src(src_cell, src_emit)
+    smap = None if src_map is None else _f64(src_map)
+    if pos is None:
+        n = 0
+        pos = np.zeros((grid.dim, 0))
+        dirs = np.zeros((grid.dim, 0))
+        act = np.zeros(0, np.uint8)
+    else:
+        pos = _f64(pos).copy()
+        dirs = _f64(dir).copy()
+        act = np.ascontiguousarray(active, dtype=np.uint8).copy()
+        n = act.shape[0]
+    g, c = grid._c(), cone._c()
+    _load().orc_run(ct.byref(g), ct.byref(c), _ptr(C), _ptr(work), int(step0), int(nsteps),
+                    _ptr(cell), _ptr(emit), cell.shape[0], _ptr(smap), n,
+                    _ptr(pos), _ptr(dirs), _ptr(act))
+    return C, pos, dirs, act
