@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark of the cue-field + growth-cone hot path on one GB300 per rank.
+
+Default workload: 2D 2048^2 grid, D = 1, lambda = 0.005, dt = 0.2, no-flux
+walls, 64 sources (emission ~ U[0.5, 2]), 16,384 cones that stop within
+radius 2 of a source or at the walls, 5,000 coupled steps.  One benchmark
+step is one whole simulation of that workload from its initial state (all
+field and cone rows of every time step); the state reset and an L2 flush
+(a 512 MiB write) sit between timed steps, outside the timed events.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cue cell-updates/s + axon-steps/s, %HBM roofline; adjoint & batched vs plain"
+UNIT = "cell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cue", "reference"], default="cue")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"])
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "fused"])
+    ap.add_argument("--depth", type=int, default=0, help="temporal depth on the fused path (0 = auto)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    return ap.parse_args()
+
+
+def workload(name, rank=0):
+    from paper_1405_3331_gb300 import workloads as W
+    if name == "c1":
+        return W.config_c1(seed=0 + 100 * rank)
+    if name == "c2":
+        return W.config_c2(seed=1 + 100 * rank)
+    if name == "c3":
+        return W.config_c3(seed=2 + 100 * rank)
+    if name == "c5":
+        return W.config_c5(seed=4 + 100 * rank)
+    raise KeyError(name)
+
+
+def describe(w):
+    dims = f"{w.nx}x{w.ny}" + (f"x{w.nz}" if w.dim == 3 else "")
+    return {
+        "workload": f"{w.dim}D {dims} cue field + {w.n_axons} growth cones, {w.nsteps} steps",
+        "grid": dims, "n_src": w.n_src, "n_axons": w.n_axons, "steps_per_run": w.nsteps,
+        "D": w.D, "lambda": w.lam, "dt": w.dt, "stop_radius": w.stop_radius,
+        "wall_mode": "clamp" if w.wall_mode else "stop", "source_map": w.src_map is not None,
+        "l2": "flushed between timed steps (512 MiB write)",
+    }
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for(device_index):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",")]
+        if device_index < len(ids):
+            return ids[device_index]
+    return device_index
+
+
+# ------------------------------------------------------------------ traffic
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1405_3331_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, work):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[f"{kernel}@{work}"]
+        if e.get("source_digest") != source_digest():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(w, budget_s):
+    """Time the FP64 oracle (single thread, as it stands) on the first steps of the workload."""
+    import numpy as np
+    import oracle
+    g = oracle.Grid(w.dim, w.nx, w.ny, w.nz if w.dim == 3 else 1, h=w.h, D=w.D, lam=w.lam, dt=w.dt)
+    c = oracle.Cone(w.w_prev, w.w_grad, w.w_noise, w.step_len, w.stop_radius, w.grad_eps, w.wall_mode,
+                    w.seed)
+    C = w.field0().astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.run(g, c, C, 0, 1, w.src_cell, w.src_emit, w.src_map, w.pos, w.dir, w.active)
+    one = time.perf_counter() - t0
+    nsteps = max(1, min(w.nsteps, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    _, _, _, act = oracle.run(g, c, C, 0, nsteps, w.src_cell, w.src_emit, w.src_map, w.pos, w.dir,
+                              w.active)
+    dt = time.perf_counter() - t0
+    return nsteps, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    import numpy as np
+    import oracle
+    g = oracle.Grid(w.dim, w.nx, w.ny, w.nz if w.dim == 3 else 1, h=w.h, D=w.D, lam=w.lam, dt=w.dt)
+    c = oracle.Cone(w.w_prev, w.w_grad, w.w_noise, w.step_len, w.stop_radius, w.grad_eps, w.wall_mode,
+                    w.seed)
+    C0 = w.field0().astype(np.float64)
+    # each reference step: a bounded sample (the first S time steps) of the workload
+    t0 = time.perf_counter()
+    oracle.run(g, c, C0, 0, 1, w.src_cell, w.src_emit, w.src_map, w.pos, w.dir, w.active)
+    one = time.perf_counter() - t0
+    total_budget = 150.0
+    S = max(1, min(w.nsteps, int(total_budget / max(1, args.steps + args.warmup) / max(one, 1e-6))))
+    for _ in range(args.warmup):
+        oracle.run(g, c, C0, 0, S, w.src_cell, w.src_emit, w.src_map, w.pos, w.dir, w.active)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(g, c, C0, 0, S, w.src_cell, w.src_emit, w.src_map, w.pos, w.dir, w.active)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = w.n_cells * S * args.steps / total
+    sample = f"first {S} of {w.nsteps} time steps of the workload per step (field + cones), from C0"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": describe(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_1405_3331_gb300 import build as cue_build
+    cue_build.build()
+    from paper_1405_3331_gb300 import cue
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    w = workload(args.workload, rank)
+    path = {"auto": cue.CUE_PATH_AUTO, "plain": cue.CUE_PATH_PLAIN, "fused": cue.CUE_PATH_FUSED}[args.path]
+    sim = cue.Simulation(w, device=dev, path=path)
+    if args.depth:
+        sim.set_option(cue.CUE_OPT_TEMPORAL_DEPTH, args.depth)
+    stream = sim.stream
+    C0 = sim.fields[0].clone()
+    pos0, dir0, act0 = sim.pos.clone(), sim.dir.clone(), sim.active.clone()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def reset():
+        with torch.cuda.stream(stream):
+            sim.fields[0].copy_(C0)
+            sim.pos.copy_(pos0)
+            sim.dir.copy_(dir0)
+            sim.active.copy_(act0)
+        cue._check(cue.cue_set_state(sim.h, 0, 0, 0), "cue_set_state")
+
+    # warm-up (also counts the cone updates of one run: every run is identical)
+    for i in range(max(args.warmup, 3)):
+        reset()
+        if i == max(args.warmup, 3) - 1:
+            sim.cone_updates()
+        sim.sim_run(w.nsteps)
+    sim.check()
+    cone_updates_per_run = sim.cone_updates()
+
+    # timed region
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_id_for(local))
+    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 1)
+    sim.kernel_time()
+    barrier()
+    sampler.start()
+    launches0 = sim.launches()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        reset()
+        evs[k][0].record(stream)
+        sim.sim_run(w.nsteps)
+        evs[k][1].record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = sim.launches() - launches0
+    kern_ms, kern_n = sim.kernel_time()
+    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 0)
+    sim.check()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cells_per_run = w.n_cells * w.nsteps
+    value = world * cells_per_run * args.steps / (total_ms / 1e3)
+    axon_steps = world * cone_updates_per_run * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel
+    hbm, peak_kind = peaks()
+    fused = kern_n > 0 and sim_path_used(sim) == "fused"
+    bytes_per_cell = 12 if w.src_map is not None else 8
+    if kern_n:
+        steps_per_launch = (w.nsteps * args.steps) / kern_n
+        alg_bytes = bytes_per_cell * w.n_cells          # compulsory field traffic of one launch
+        avg_s = kern_ms / kern_n / 1e3
+        achieved = alg_bytes / avg_s / 1e9
+    else:
+        steps_per_launch, alg_bytes, avg_s, achieved = 0, 0, 0, 0.0
+    kname = "fused" if fused else "field"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm if hbm else None,
+                "traffic": recorded_traffic(kname, args.workload),
+                "kernel": kname, "peak_kind": peak_kind, "launches": kern_n,
+                "avg_launch_us": avg_s * 1e6, "steps_per_launch": steps_per_launch,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "effective_gbs": bytes_per_cell * w.n_cells * steps_per_launch / avg_s / 1e9 if avg_s else 0}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(describe(w), parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       path=sim_path_used(sim)),
+        "axon_steps_per_s": axon_steps, "cone_updates_per_run": cone_updates_per_run,
+        "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+    }
+
+    # end to end through the public API from pinned host buffers
+    if not args.no_e2e:
+        Ch = w.field0()
+        host = [torch.from_numpy(a).pin_memory() for a in (Ch, w.pos, w.dir, w.active)]
+        out = tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in host)
+        sim.run_host(*host, w.nsteps, out=out)     # warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 3))
+        barrier()
+        tot = 0.0
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0.record(stream)
+            sim.run_host(*host, w.nsteps, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        h2d = sum(t.numel() * t.element_size() for t in host)
+        d2h = sum(t.numel() * t.element_size() for t in out)
+        line["e2e"] = {"value": world * cells_per_run * reps / (tot / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": tot / reps}
+
+    # HBM probe: plain field kernel on 2D 8192^2 (256 MiB per buffer), never L2-resident
+    if not args.no_probe and rank == 0:
+        line["hbm_probe"] = hbm_probe(cue, torch, dev, hbm)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nsteps, secs = oracle_sample(w, args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": w.n_cells * nsteps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {nsteps} of {w.nsteps} time steps of the same workload (FP64, one thread)",
+            "seconds": secs}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def sim_path_used(sim):
+    from paper_1405_3331_gb300 import cue
+    return "fused" if getattr(sim, "fused_active", lambda: False)() else "plain"
+
+
+def hbm_probe(cue, torch, dev, hbm):
+    from paper_1405_3331_gb300 import workloads as W
+    w = W.hbm_probe_2d()
+    sim = cue.Simulation(w, device=dev, path=cue.CUE_PATH_PLAIN)
+    sim.cue_step(5)
+    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 1)
+    sim.kernel_time()
+    n = 20
+    sim.cue_step(n)
+    ms, k = sim.kernel_time()
+    sim.check()
+    sim.close()
+    gbs = 8 * w.n_cells * k / (ms / 1e3) / 1e9
+    return {"workload": "2D 8192x8192 field only (256 MiB per buffer), plain field kernel",
+            "cell_updates_per_s": w.n_cells * k / (ms / 1e3), "achieved_gbs": gbs, "peak_gbs": hbm,
+            "frac": gbs / hbm, "launches": k, "avg_launch_us": ms / k * 1e3}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

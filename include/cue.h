@@ -1,0 +1,189 @@
+/*
+ * cue.h -- C ABI of libcue.so: GB300 (sm_103a) cue-field diffusion and
+ * growth-cone steering.
+ *
+ * The model follows Mihut, Morgan & Kaiser, "GPU Simulation of Axon Growth
+ * and Guidance through Cue Diffusion": guidance cues live on a fixed
+ * Eulerian grid (Sec. 5.2) and are emitted by sources placed pseudo-randomly
+ * with their own diffusion rates (Sec. 4.3); each axon's growth cone advances
+ * a fixed distance per step along a direction that is steered by vector
+ * addition of its current direction and the cue direction it senses
+ * (Sec. 3.5, Eq. 6-7), with Gaussian noise from a stateless per-thread
+ * counter-based generator (Sec. 5.1, Sec. 3.2 Box-Muller); cones stop when
+ * they leave the simulation bounds (Sec. 3.4) or come within a radius of a
+ * source, tested on squared distances (Sec. 3.3).
+ *
+ * One time step n -> n+1:
+ *   cones (read C^n):  g   = multilinear interpolation at p of the node
+ *                            central-difference gradients of C^n
+ *                      v   = w_prev d + w_grad g/|g| + w_noise xi
+ *                      d'  = v/|v|;  p' = p + step_len d'
+ *                      stop if p' leaves [0,(N-1)h]^dim (or clamp), or if
+ *                      |p' - x_k|^2 <= stop_radius^2 for a source node x_k
+ *   field:             C^{n+1}_i = C^n_i + alpha sum_{axis nbrs j}(C_j - C_i)
+ *                                  - lambda dt C^n_i  (+ e_k at source k)
+ *                                  (+ dt M_i for a dense rate map M)
+ *                      alpha = D dt / h^2, missing neighbours at the walls
+ *                      contribute nothing (no-flux).
+ *   noise:             Philox-4x32-10, key = (seed lo, seed hi),
+ *                      counter = (axon, step, 0, 0), Box-Muller on the words.
+ *
+ * Conventions for every call below.
+ *   - Layout: fields are dense FP32 arrays, x fastest:
+ *     index = i + nx (j + ny k), node (i,j,k) at (i h, j h, k h).
+ *     Cone state is structure-of-arrays: pos[c*n_axons + a] is coordinate c
+ *     of cone a (same for dir); active[a] is 0 or 1.
+ *   - Ownership: every buffer is allocated and owned by the caller (for
+ *     example with PyTorch) and must stay valid until cue_destroy.  The
+ *     library allocates no device memory: all its scratch lives in the
+ *     caller's workspace (cue_workspace_bytes).  The handle is host memory
+ *     owned by the library and freed by cue_destroy.
+ *   - Streams: every call is asynchronous on the stream given to cue_init
+ *     (or cue_set_stream); only cue_status synchronises.
+ *   - Errors: calls return CUE_OK (0) or a negative CUE_ERR_* code and never
+ *     throw.  Device-side problems (non-finite values, out-of-range source
+ *     cells, a bounded wait that ran out) are recorded in a status word in
+ *     the workspace and reported by cue_status.
+ */
+#ifndef CUE_H
+#define CUE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define CUE_OK               0
+#define CUE_ERR_ARG         -1  /* invalid argument (null pointer, bad size, bad enum)      */
+#define CUE_ERR_UNSTABLE    -2  /* D dt / h^2 > 1/(2 dim) or lambda dt outside [0, 1]     */
+#define CUE_ERR_CUDA        -3  /* a CUDA runtime call failed                               */
+#define CUE_ERR_NONFINITE   -4  /* a kernel produced a NaN or Inf                           */
+#define CUE_ERR_TIMEOUT     -5  /* a bounded device-side wait gave up                       */
+#define CUE_ERR_BOUNDS      -6  /* a source cell index outside the grid was skipped         */
+#define CUE_ERR_WORKSPACE   -7  /* workspace missing, too small or misaligned               */
+#define CUE_ERR_STATE       -8  /* call order violated (e.g. sim_run with cone/field steps
+                                   out of step)                                             */
+
+/* ---- parameters -------------------------------------------------------- */
+typedef struct {
+    int32_t dim;            /* 2 or 3                                                  */
+    int32_t nx, ny, nz;     /* nodes per axis, each >= 2 (nz ignored when dim == 2)    */
+    float h;                /* node spacing, > 0                                       */
+    float D;                /* diffusion coefficient, >= 0                             */
+    float lambda;           /* decay rate, >= 0                                        */
+    float dt;               /* time step, > 0                                          */
+    int32_t boundary;       /* 0 = no-flux walls (the only value accepted)             */
+} cue_params;
+
+typedef struct {
+    float w_prev;           /* weight of the previous direction                        */
+    float w_grad;           /* weight of the normalised sensed gradient                */
+    float w_noise;          /* weight of the Gaussian noise vector                     */
+    float step_len;         /* distance advanced per step (same units as h)           */
+    float stop_radius;      /* stop within this distance of a source node; <= 0: off   */
+    float grad_eps;         /* |g| <= grad_eps counts as no gradient (default 1e-15)   */
+    int32_t wall_mode;      /* 0 = stop when leaving the domain, 1 = clamp to it       */
+    int32_t reserved;       /* must be 0                                               */
+    uint64_t seed;          /* Philox key (low word, high word)                        */
+} cone_params;
+
+typedef struct cue_sim cue_sim;   /* opaque, host-side */
+
+/* ---- options (cue_set_option) ------------------------------------------ */
+#define CUE_OPT_PATH            1  /* value: CUE_PATH_*                                    */
+#define CUE_OPT_TEMPORAL_DEPTH  2  /* value: steps fused per launch on the fused path (1..16),
+                                      0 = library choice                                    */
+#define CUE_OPT_ROWS_PER_THREAD 3  /* value: rows streamed per thread by the plain 2D field
+                                      kernel (1..64), 0 = library choice                    */
+#define CUE_OPT_TIME_KERNEL     4  /* value 1: bracket every launch of the dominant field
+                                      kernel with CUDA events on the handle's stream, read
+                                      back by cue_kernel_time; 0: off (default)             */
+#define CUE_PATH_AUTO   0          /* library picks (fused when supported)                 */
+#define CUE_PATH_PLAIN  1          /* one launch per half-step: cone kernel, field kernel  */
+#define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel       */
+
+/* Bytes of device workspace the simulation needs (256-byte aligned). */
+size_t cue_workspace_bytes(const cue_params *params, int32_t n_src, int32_t n_axons);
+
+/*
+ * Create a simulation handle over caller-owned device buffers.
+ *   d_field_a   : C^n on entry (current buffer 0), nx*ny(*nz) floats
+ *   d_field_b   : second field buffer of the same size (contents ignored)
+ *   d_src_cell  : n_src int32 node indices (duplicates allowed; out-of-range
+ *                 indices are skipped and reported as CUE_ERR_BOUNDS)
+ *   d_src_emit  : n_src floats, emission added to the node every step
+ *   d_src_map   : nullable; nx*ny(*nz) floats, rate map M (adds dt*M_i)
+ *   d_pos,d_dir : dim*n_axons floats each (SoA), d_active: n_axons bytes
+ *   d_workspace : >= cue_workspace_bytes(...) bytes, 256-byte aligned
+ *   stream      : cudaStream_t (NULL = legacy default stream)
+ * Returns CUE_OK, CUE_ERR_ARG, CUE_ERR_UNSTABLE, CUE_ERR_WORKSPACE or
+ * CUE_ERR_CUDA.  On error *out is set to NULL.  Field and cone step
+ * counters start at 0.
+ */
+int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone,
+             float *d_field_a, float *d_field_b,
+             const int32_t *d_src_cell, const float *d_src_emit, int32_t n_src,
+             const float *d_src_map,
+             float *d_pos, float *d_dir, uint8_t *d_active, int32_t n_axons,
+             void *d_workspace, size_t ws_bytes, void *stream);
+
+/* Advance the field only (rows a1, a2), nsteps >= 0 times; increments the
+ * field step counter and flips the current buffer once per step. */
+int cue_step(cue_sim *sim, int32_t nsteps);
+
+/* Advance the cones only (rows a3-a6) nsteps times on the current field,
+ * which is held fixed; step k uses Philox counter step = cone counter + k.
+ * Increments the cone step counter.  cone_step(1) followed by cue_step(1)
+ * equals sim_run(1). */
+int cone_step(cue_sim *sim, int32_t nsteps);
+
+/* Advance cones and field together nsteps times (rows a1-a6): at each step
+ * the cones read C^n and the field becomes C^{n+1}.  Requires the cone and
+ * field counters to be equal (else CUE_ERR_STATE); advances both. */
+int sim_run(cue_sim *sim, int32_t nsteps);
+
+/* Step counters and the index (0 = d_field_a, 1 = d_field_b) of the buffer
+ * that holds the current field. */
+int cue_get_state(const cue_sim *sim, int64_t *field_step, int64_t *cone_step_out,
+                  int32_t *cur_buffer);
+
+/* Restore counters and the current-buffer index (for snapshots/resume). */
+int cue_set_state(cue_sim *sim, int64_t field_step, int64_t cone_step_in, int32_t cur_buffer);
+
+/* Re-target the stream used by later calls. */
+int cue_set_stream(cue_sim *sim, void *stream);
+
+/* Set an option (CUE_OPT_*). */
+int cue_set_option(cue_sim *sim, int32_t option, int64_t value);
+
+/* Number of kernels this handle has launched so far. */
+uint64_t cue_launch_count(const cue_sim *sim);
+
+/* With CUE_OPT_TIME_KERNEL on: synchronise the stream and return the summed
+ * device time (ms, from CUDA events on the handle's stream) and the number of
+ * launches of the dominant field kernel (the fused kernel on the fused path,
+ * the field stencil on the plain path) since the previous call; resets both. */
+int cue_kernel_time(cue_sim *sim, double *total_ms, uint64_t *launches);
+
+/* Synchronise the stream and return the number of cone updates (active
+ * cone x step pairs) performed since the previous call; resets the count. */
+int cue_cone_updates(cue_sim *sim, uint64_t *count);
+
+/* Synchronise the stream, then return and clear the device status word:
+ * CUE_OK, CUE_ERR_NONFINITE, CUE_ERR_BOUNDS, CUE_ERR_TIMEOUT or CUE_ERR_CUDA. */
+int cue_status(cue_sim *sim);
+
+/* Free the handle (never the caller's buffers).  NULL is accepted. */
+void cue_destroy(cue_sim *sim);
+
+/* Static description of a status code. */
+const char *cue_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUE_H */

@@ -1,0 +1,380 @@
+// cue_api.cu -- the C ABI of libcue.so (declared in include/cue.h): argument
+// checking, the handle, step bookkeeping and dispatch to the kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "cue_internal.h"
+
+namespace cue {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons)
+{
+    WorkspaceLayout w;
+    size_t off = 0;
+    w.status_off = off;
+    off += 256;
+    w.src_xyz_off = off;
+    off += align256(sizeof(float) * 3 * (size_t)(n_src > 0 ? n_src : 0));
+    w.n_tiles = fused_tile_count(p);
+    w.bin_count_off = off;
+    off += align256(sizeof(int32_t) * 2 * (size_t)(w.n_tiles > 0 ? w.n_tiles : 1));
+    w.bin_list_off = off;
+    off += align256(sizeof(int32_t) * (size_t)(n_axons > 0 ? n_axons : 1));
+    w.bin_slot_off = off;
+    off += align256(sizeof(int32_t) * (size_t)(n_axons > 0 ? n_axons : 1));
+    w.total = off;
+    return w;
+}
+
+static constexpr size_t kEventRing = 512;
+
+static void timing_collect(Sim &s, size_t slot)
+{
+    float ms = 0.f;
+    if (cudaEventSynchronize(s.ev_stop[slot]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, s.ev_start[slot], s.ev_stop[slot]) == cudaSuccess) {
+        s.timed_ms += ms;
+        s.timed_launches++;
+    }
+}
+
+void timing_begin(Sim &s)
+{
+    if (!s.time_kernel) return;
+    if (s.ev_start.empty()) {
+        s.ev_start.resize(kEventRing);
+        s.ev_stop.resize(kEventRing);
+        for (size_t i = 0; i < kEventRing; ++i) {
+            cudaEventCreate(&s.ev_start[i]);
+            cudaEventCreate(&s.ev_stop[i]);
+        }
+    }
+    if (s.ev_live == kEventRing) {          // reuse the oldest pair: fold its time in first
+        timing_collect(s, s.ev_next);
+        s.ev_live--;
+    }
+    cudaEventRecord(s.ev_start[s.ev_next], s.stream);
+}
+
+void timing_end(Sim &s)
+{
+    if (!s.time_kernel) return;
+    cudaEventRecord(s.ev_stop[s.ev_next], s.stream);
+    s.ev_next = (s.ev_next + 1) % kEventRing;
+    s.ev_live++;
+}
+
+static void timing_drain(Sim &s)
+{
+    size_t first = (s.ev_next + kEventRing - s.ev_live) % kEventRing;
+    for (size_t i = 0; i < s.ev_live; ++i) timing_collect(s, (first + i) % kEventRing);
+    s.ev_live = 0;
+}
+
+static void timing_free(Sim &s)
+{
+    for (size_t i = 0; i < s.ev_start.size(); ++i) {
+        cudaEventDestroy(s.ev_start[i]);
+        cudaEventDestroy(s.ev_stop[i]);
+    }
+    s.ev_start.clear();
+    s.ev_stop.clear();
+}
+
+}  // namespace cue
+
+using namespace cue;
+
+struct cue_sim : public cue::Sim {};
+
+namespace {
+
+bool params_ok(const cue_params *p)
+{
+    if (!p) return false;
+    if (p->dim != 2 && p->dim != 3) return false;
+    if (p->nx < 2 || p->ny < 2 || (p->dim == 3 && p->nz < 2)) return false;
+    long long n = (long long)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
+    if (n > (1LL << 31) - 1) return false;
+    if (!(p->h > 0.f) || !(p->dt > 0.f) || !(p->D >= 0.f) || !(p->lambda >= 0.f)) return false;
+    if (!std::isfinite(p->h) || !std::isfinite(p->dt) || !std::isfinite(p->D) || !std::isfinite(p->lambda))
+        return false;
+    if (p->boundary != 0) return false;
+    return true;
+}
+
+bool cone_ok(const cone_params *c)
+{
+    if (!c) return false;
+    if (c->wall_mode != 0 && c->wall_mode != 1) return false;
+    if (c->reserved != 0) return false;
+    const float v[] = {c->w_prev, c->w_grad, c->w_noise, c->step_len, c->stop_radius, c->grad_eps};
+    for (float x : v)
+        if (!std::isfinite(x)) return false;
+    if (c->step_len < 0.f || c->grad_eps < 0.f) return false;
+    return true;
+}
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? CUE_OK : CUE_ERR_CUDA; }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+size_t cue_workspace_bytes(const cue_params *params, int32_t n_src, int32_t n_axons)
+{
+    if (!params_ok(params) || n_src < 0 || n_axons < 0) return 0;
+    return workspace_layout(*params, n_src, n_axons).total;
+}
+
+int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone, float *d_field_a,
+             float *d_field_b, const int32_t *d_src_cell, const float *d_src_emit, int32_t n_src,
+             const float *d_src_map, float *d_pos, float *d_dir, uint8_t *d_active, int32_t n_axons,
+             void *d_workspace, size_t ws_bytes, void *stream)
+{
+    if (!out) return CUE_ERR_ARG;
+    *out = nullptr;
+    if (!params_ok(params) || !cone_ok(cone)) return CUE_ERR_ARG;
+    if (!d_field_a || !d_field_b || d_field_a == d_field_b) return CUE_ERR_ARG;
+    if (n_src < 0 || n_axons < 0) return CUE_ERR_ARG;
+    if (n_src > 0 && (!d_src_cell || !d_src_emit)) return CUE_ERR_ARG;
+    if (n_axons > 0 && (!d_pos || !d_dir || !d_active)) return CUE_ERR_ARG;
+    const int dim = params->dim;
+    const float alpha = params->D * params->dt / (params->h * params->h);
+    const float decay = params->lambda * params->dt;
+    if (alpha > 1.0f / (2.0f * dim) * (1.0f + 1e-6f) || decay > 1.0f) return CUE_ERR_UNSTABLE;
+    WorkspaceLayout wl = workspace_layout(*params, n_src, n_axons);
+    if (!d_workspace || ws_bytes < wl.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
+        return CUE_ERR_WORKSPACE;
+
+    cue_sim *s = new (std::nothrow) cue_sim();
+    if (!s) return CUE_ERR_ARG;
+    s->params = *params;
+    if (dim == 2) s->params.nz = 1;
+    s->cone = *cone;
+    FieldDesc &f = s->fd;
+    f.dim = dim;
+    f.nx = params->nx;
+    f.ny = params->ny;
+    f.nz = dim == 3 ? params->nz : 1;
+    f.h = params->h;
+    f.alpha = alpha;
+    f.decay = decay;
+    f.dt = params->dt;
+    ConeDesc &c = s->cd;
+    c.w_prev = cone->w_prev;
+    c.w_grad = cone->w_grad;
+    c.w_noise = cone->w_noise;
+    c.step_len = cone->step_len;
+    c.stop_r2 = cone->stop_radius > 0.f ? cone->stop_radius * cone->stop_radius : -1.0f;
+    c.eps2 = cone->grad_eps * cone->grad_eps;
+    c.inv2h = 1.0f / (2.0f * params->h);
+    c.hi0 = (float)(f.nx - 1) * f.h;
+    c.hi1 = (float)(f.ny - 1) * f.h;
+    c.hi2 = (float)(f.nz - 1) * f.h;
+    c.wall_mode = cone->wall_mode;
+    c.key0 = (uint32_t)(cone->seed & 0xFFFFFFFFull);
+    c.key1 = (uint32_t)(cone->seed >> 32);
+    s->field[0] = d_field_a;
+    s->field[1] = d_field_b;
+    s->src_cell = d_src_cell;
+    s->src_emit = d_src_emit;
+    s->n_src = n_src;
+    s->src_map = d_src_map;
+    s->pos = d_pos;
+    s->dir = d_dir;
+    s->active = d_active;
+    s->n_axons = n_axons;
+    s->ws = static_cast<unsigned char *>(d_workspace);
+    s->ws_bytes = ws_bytes;
+    s->wl = wl;
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->vec4 = (f.nx % 4 == 0) && aligned16(d_field_a) && aligned16(d_field_b) &&
+              (!d_src_map || aligned16(d_src_map));
+    cudaError_t e = cudaMemsetAsync(s->ws, 0, 256, s->stream);
+    if (e == cudaSuccess) e = launch_src_xyz(*s);
+    if (e != cudaSuccess) {
+        delete s;
+        return CUE_ERR_CUDA;
+    }
+    *out = s;
+    return CUE_OK;
+}
+
+int cue_step(cue_sim *s, int32_t nsteps)
+{
+    if (!s || nsteps < 0) return CUE_ERR_ARG;
+    if (s->field_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
+    for (int k = 0; k < nsteps; ++k) {
+        float *in = s->field[s->cur], *out = s->field[s->cur ^ 1];
+        cudaError_t e = launch_field_step(*s, in, out);
+        if (e == cudaSuccess) e = launch_sources(*s, out);
+        if (e != cudaSuccess) return CUE_ERR_CUDA;
+        s->cur ^= 1;
+        s->field_step++;
+    }
+    return CUE_OK;
+}
+
+int cone_step(cue_sim *s, int32_t nsteps)
+{
+    if (!s || nsteps < 0) return CUE_ERR_ARG;
+    if (s->cone_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
+    for (int k = 0; k < nsteps; ++k) {
+        cudaError_t e = launch_cone_step(*s, s->field[s->cur], (uint32_t)s->cone_step);
+        if (e != cudaSuccess) return CUE_ERR_CUDA;
+        s->cone_step++;
+    }
+    return CUE_OK;
+}
+
+int sim_run(cue_sim *s, int32_t nsteps)
+{
+    if (!s || nsteps < 0) return CUE_ERR_ARG;
+    if (s->cone_step != s->field_step) return CUE_ERR_STATE;
+    if (s->field_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
+    int rc = run_fused_if_supported(*s, nsteps);
+    if (rc != 1) return rc;       // handled (0 = ok, < 0 = error)
+    for (int k = 0; k < nsteps; ++k) {
+        float *in = s->field[s->cur], *out = s->field[s->cur ^ 1];
+        cudaError_t e = launch_cone_step(*s, in, (uint32_t)s->cone_step);
+        if (e == cudaSuccess) e = launch_field_step(*s, in, out);
+        if (e == cudaSuccess) e = launch_sources(*s, out);
+        if (e != cudaSuccess) return CUE_ERR_CUDA;
+        s->cur ^= 1;
+        s->field_step++;
+        s->cone_step++;
+    }
+    return CUE_OK;
+}
+
+int cue_get_state(const cue_sim *s, int64_t *field_step, int64_t *cone_step_out, int32_t *cur_buffer)
+{
+    if (!s) return CUE_ERR_ARG;
+    if (field_step) *field_step = s->field_step;
+    if (cone_step_out) *cone_step_out = s->cone_step;
+    if (cur_buffer) *cur_buffer = s->cur;
+    return CUE_OK;
+}
+
+int cue_set_state(cue_sim *s, int64_t field_step, int64_t cone_step_in, int32_t cur_buffer)
+{
+    if (!s || field_step < 0 || cone_step_in < 0 || field_step > 0xFFFFFFFFLL ||
+        cone_step_in > 0xFFFFFFFFLL || (cur_buffer != 0 && cur_buffer != 1))
+        return CUE_ERR_ARG;
+    s->field_step = field_step;
+    s->cone_step = cone_step_in;
+    s->cur = cur_buffer;
+    return CUE_OK;
+}
+
+int cue_set_stream(cue_sim *s, void *stream)
+{
+    if (!s) return CUE_ERR_ARG;
+    s->stream = static_cast<cudaStream_t>(stream);
+    return CUE_OK;
+}
+
+int cue_set_option(cue_sim *s, int32_t option, int64_t value)
+{
+    if (!s) return CUE_ERR_ARG;
+    switch (option) {
+    case CUE_OPT_PATH:
+        if (value != CUE_PATH_AUTO && value != CUE_PATH_PLAIN && value != CUE_PATH_FUSED) return CUE_ERR_ARG;
+        if (value == CUE_PATH_FUSED && !fused_supported(*s)) return CUE_ERR_ARG;
+        s->path = (int)value;
+        return CUE_OK;
+    case CUE_OPT_TEMPORAL_DEPTH:
+        if (value < 0 || value > kMaxTemporalDepth) return CUE_ERR_ARG;
+        s->temporal_depth = (int)value;
+        return CUE_OK;
+    case CUE_OPT_ROWS_PER_THREAD:
+        if (value < 0 || value > 64) return CUE_ERR_ARG;
+        s->rows_per_thread = (int)value;
+        return CUE_OK;
+    case CUE_OPT_TIME_KERNEL:
+        if (value != 0 && value != 1) return CUE_ERR_ARG;
+        if (!value && s->time_kernel) timing_drain(*s);
+        s->time_kernel = value != 0;
+        return CUE_OK;
+    default:
+        return CUE_ERR_ARG;
+    }
+}
+
+int cue_kernel_time(cue_sim *s, double *total_ms, uint64_t *launches)
+{
+    if (!s) return CUE_ERR_ARG;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return CUE_ERR_CUDA;
+    timing_drain(*s);
+    if (total_ms) *total_ms = s->timed_ms;
+    if (launches) *launches = s->timed_launches;
+    s->timed_ms = 0.0;
+    s->timed_launches = 0;
+    return CUE_OK;
+}
+
+uint64_t cue_launch_count(const cue_sim *s) { return s ? s->launches : 0; }
+
+int cue_cone_updates(cue_sim *s, uint64_t *count)
+{
+    if (!s || !count) return CUE_ERR_ARG;
+    unsigned long long v = 0;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return CUE_ERR_CUDA;
+    if (cudaMemcpy(&v, s->cone_counter(), sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return CUE_ERR_CUDA;
+    if (cudaMemset(s->cone_counter(), 0, sizeof(v)) != cudaSuccess) return CUE_ERR_CUDA;
+    *count = v;
+    return CUE_OK;
+}
+
+int cue_status(cue_sim *s)
+{
+    if (!s) return CUE_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return CUE_ERR_CUDA;
+    unsigned word = 0;
+    e = cudaMemcpy(&word, s->status(), sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return CUE_ERR_CUDA;
+    if (word) {
+        e = cudaMemset(s->status(), 0, sizeof(unsigned));
+        if (e != cudaSuccess) return CUE_ERR_CUDA;
+    }
+    if (word & kStatusNonFinite) return CUE_ERR_NONFINITE;
+    if (word & kStatusTimeout) return CUE_ERR_TIMEOUT;
+    if (word & kStatusBounds) return CUE_ERR_BOUNDS;
+    e = cudaGetLastError();
+    return cuda_err(e);
+}
+
+void cue_destroy(cue_sim *s)
+{
+    if (!s) return;
+    if (!s->ev_start.empty()) {
+        cudaStreamSynchronize(s->stream);
+        timing_free(*s);
+    }
+    delete s;
+}
+
+const char *cue_strerror(int code)
+{
+    switch (code) {
+    case CUE_OK: return "ok";
+    case CUE_ERR_ARG: return "invalid argument";
+    case CUE_ERR_UNSTABLE: return "unstable parameters: D dt / h^2 > 1/(2 dim) or lambda dt > 1";
+    case CUE_ERR_CUDA: return "CUDA runtime error";
+    case CUE_ERR_NONFINITE: return "non-finite value produced on the device";
+    case CUE_ERR_TIMEOUT: return "bounded device-side wait timed out";
+    case CUE_ERR_BOUNDS: return "source cell index outside the grid (skipped)";
+    case CUE_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+    case CUE_ERR_STATE: return "call order violated (cone and field step counters differ)";
+    default: return "unknown status code";
+    }
+}
+
+}  // extern "C"

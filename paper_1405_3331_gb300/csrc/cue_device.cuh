@@ -1,0 +1,242 @@
+// cue_device.cuh -- device-side building blocks shared by the CUDA kernels of
+// libcue.so: parameter blocks, the Philox-4x32-10 counter generator, the
+// Box-Muller noise, multilinear gradient sampling and the growth-cone update.
+//
+// Model: Mihut, Morgan & Kaiser, cue diffusion on an Eulerian grid (Sec. 5.2)
+// steering growth cones by vector addition of the current direction and the
+// sensed cue direction (Sec. 3.5, Eq. 6-7), with Gaussian noise from a
+// stateless per-thread counter-based generator (Sec. 5.1) through Box-Muller
+// (Sec. 3.2), and stop tests on the simulation bounds (Sec. 3.4) and on
+// squared distances to the sources (Sec. 3.3).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cue {
+
+// Field physics, precomputed on the host in FP32.
+struct FieldDesc {
+    int dim;
+    int nx, ny, nz;     // nz == 1 in 2D
+    float h;
+    float alpha;        // D dt / h^2
+    float decay;        // lambda dt
+    float dt;
+};
+
+// Cone parameters, precomputed on the host in FP32.
+struct ConeDesc {
+    float w_prev, w_grad, w_noise, step_len;
+    float stop_r2;      // stop_radius^2; < 0 disables the source stop
+    float eps2;         // grad_eps^2
+    float inv2h;        // 1 / (2 h)
+    float hi0, hi1, hi2; // domain upper bound per axis: (N - 1) h
+    int wall_mode;      // 0 stop, 1 clamp
+    uint32_t key0, key1;
+};
+
+// Bits of the device status word.
+enum : unsigned {
+    kStatusNonFinite = 1u,
+    kStatusBounds = 2u,
+    kStatusTimeout = 4u,
+};
+
+__device__ __forceinline__ void flag_status(unsigned *status, unsigned bits)
+{
+    if (status) atomicOr(status, bits);
+}
+
+// Warp-aggregated count of active cones into a 64-bit counter (one atomic per
+// warp).  Must be called by all lanes of a converged warp.
+__device__ __forceinline__ void count_active(unsigned long long *counter, bool active)
+{
+    unsigned m = __ballot_sync(0xffffffffu, active);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(counter, (unsigned long long)__popc(m));
+}
+
+// --------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds; a round
+// takes the two 64-bit products of counter words 0 and 2 with the round
+// multipliers, XORs their high halves with words 1 and 3 and the two key
+// words, and bumps the key by the Weyl increments.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
+                                              uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = 0xD2511F53u, b = 0xCD9E8D57u;
+        uint32_t hi_a = __umulhi(a, c0), lo_a = a * c0;
+        uint32_t hi_b = __umulhi(b, c2), lo_b = b * c2;
+        uint32_t n0 = hi_b ^ c1 ^ k0;
+        uint32_t n2 = hi_a ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo_b;
+        c2 = n2;
+        c3 = lo_a;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Gaussian vector of cone `axon` at `step`: uniforms from the top 24 bits of
+// the Philox words (u1, u3 in (0,1]; u2, u4 in [0,1)), Box-Muller on
+// (u1,u2) for components 0,1 and on (u3,u4) for component 2.
+template <int DIM>
+__device__ __forceinline__ void cone_noise(uint32_t k0, uint32_t k1, uint32_t axon, uint32_t step,
+                                           float xi[DIM])
+{
+    uint32_t w0 = axon, w1 = step, w2 = 0u, w3 = 0u;
+    philox4x32_10(w0, w1, w2, w3, k0, k1);
+    const float two_m24 = 5.9604644775390625e-8f;   // 2^-24
+    float u1 = (float)((w0 >> 8) + 1u) * two_m24;
+    float u2 = (float)(w1 >> 8) * two_m24;
+    float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    xi[0] = r * c;
+    xi[1] = r * s;
+    if constexpr (DIM == 3) {
+        float u3 = (float)((w2 >> 8) + 1u) * two_m24;
+        float u4 = (float)(w3 >> 8) * two_m24;
+        float r2 = sqrtf(-2.0f * logf(u3));
+        xi[2] = r2 * cospif(2.0f * u4);
+    }
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// --------------------------------------------------------------------------
+// Gradient at point p: multilinear interpolation of node central differences
+// (a missing neighbour at a wall is replaced by the node itself).  `ld(i,j,k)`
+// returns C at a node inside the grid.
+// --------------------------------------------------------------------------
+template <int DIM, class Load>
+__device__ __forceinline__ void sample_gradient(const FieldDesc &f, const ConeDesc &c, const float *p,
+                                                const Load &ld, float *g)
+{
+    const int ext[3] = {f.nx, f.ny, f.nz};
+    int lo[3] = {0, 0, 0};
+    float fr[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+        float s = p[ax] / f.h;
+        int i0 = clampi((int)floorf(s), 0, ext[ax] - 2);
+        lo[ax] = i0;
+        fr[ax] = s - (float)i0;
+    }
+    const int xm = max(lo[0] - 1, 0), x0 = lo[0], x1 = lo[0] + 1, xp = min(lo[0] + 2, f.nx - 1);
+    const int ym = max(lo[1] - 1, 0), y0 = lo[1], y1 = lo[1] + 1, yp = min(lo[1] + 2, f.ny - 1);
+    const float wx[2] = {1.0f - fr[0], fr[0]};
+    const float wy[2] = {1.0f - fr[1], fr[1]};
+    if constexpr (DIM == 2) {
+        // rows y0, y1 across x = xm..xp; columns x0, x1 across y = ym..yp
+        float r0m = ld(xm, y0, 0), r00 = ld(x0, y0, 0), r01 = ld(x1, y0, 0), r0p = ld(xp, y0, 0);
+        float r1m = ld(xm, y1, 0), r10 = ld(x0, y1, 0), r11 = ld(x1, y1, 0), r1p = ld(xp, y1, 0);
+        float cm0 = ld(x0, ym, 0), cm1 = ld(x1, ym, 0);
+        float cp0 = ld(x0, yp, 0), cp1 = ld(x1, yp, 0);
+        // node gradients at the four corners (x index a, y index b)
+        float gx00 = (r01 - r0m) * c.inv2h, gx10 = (r0p - r00) * c.inv2h;
+        float gx01 = (r11 - r1m) * c.inv2h, gx11 = (r1p - r10) * c.inv2h;
+        float gy00 = (r10 - cm0) * c.inv2h, gy10 = (r11 - cm1) * c.inv2h;
+        float gy01 = (cp0 - r00) * c.inv2h, gy11 = (cp1 - r01) * c.inv2h;
+        float w00 = wx[0] * wy[0], w10 = wx[1] * wy[0], w01 = wx[0] * wy[1], w11 = wx[1] * wy[1];
+        g[0] = w00 * gx00 + w10 * gx10 + w01 * gx01 + w11 * gx11;
+        g[1] = w00 * gy00 + w10 * gy10 + w01 * gy01 + w11 * gy11;
+    } else {
+        const int zm = max(lo[2] - 1, 0), z0 = lo[2], z1 = lo[2] + 1, zp = min(lo[2] + 2, f.nz - 1);
+        const float wz[2] = {1.0f - fr[2], fr[2]};
+        const int xs[2] = {x0, x1}, ys[2] = {y0, y1}, zs[2] = {z0, z1};
+        const int xl[2] = {xm, x0}, xr[2] = {x1, xp};
+        const int yl[2] = {ym, y0}, yr[2] = {y1, yp};
+        const int zl[2] = {zm, z0}, zr[2] = {z1, zp};
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    float w = wx[a] * wy[e] * wz[b];
+                    float nx_ = (ld(xr[a], ys[e], zs[b]) - ld(xl[a], ys[e], zs[b])) * c.inv2h;
+                    float ny_ = (ld(xs[a], yr[e], zs[b]) - ld(xs[a], yl[e], zs[b])) * c.inv2h;
+                    float nz_ = (ld(xs[a], ys[e], zr[b]) - ld(xs[a], ys[e], zl[b])) * c.inv2h;
+                    gx += w * nx_;
+                    gy += w * ny_;
+                    gz += w * nz_;
+                }
+        g[0] = gx;
+        g[1] = gy;
+        g[2] = gz;
+    }
+}
+
+// --------------------------------------------------------------------------
+// One growth-cone step.  p, d are updated in place; returns false when the
+// cone stops at this step.  src_xyz holds the source node coordinates as
+// [3][n_src] (x row, y row, z row).
+// --------------------------------------------------------------------------
+template <int DIM, class Load>
+__device__ __forceinline__ bool cone_update(const FieldDesc &f, const ConeDesc &c, const Load &ld,
+                                            uint32_t axon, uint32_t step, float *p, float *d,
+                                            const float *src_xyz, int src_stride, int n_src)
+{
+    float g[DIM];
+    sample_gradient<DIM>(f, c, p, ld, g);
+    float gn2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) gn2 = fmaf(g[i], g[i], gn2);
+    float ginv = (gn2 > c.eps2) ? 1.0f / sqrtf(gn2) : 0.0f;
+
+    float xi[DIM];
+    cone_noise<DIM>(c.key0, c.key1, axon, step, xi);
+
+    float v[DIM], vn2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        v[i] = c.w_prev * d[i] + c.w_grad * (g[i] * ginv) + c.w_noise * xi[i];
+        vn2 = fmaf(v[i], v[i], vn2);
+    }
+    float dn[DIM];
+    if (vn2 > 1e-30f) {
+        float vinv = 1.0f / sqrtf(vn2);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) dn[i] = v[i] * vinv;
+    } else {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) dn[i] = d[i];
+    }
+    const float hi[3] = {c.hi0, c.hi1, c.hi2};
+    float pn[DIM];
+    bool outside = false;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        pn[i] = fmaf(c.step_len, dn[i], p[i]);
+        if (pn[i] < 0.0f || pn[i] > hi[i]) {
+            outside = true;
+            pn[i] = pn[i] < 0.0f ? 0.0f : hi[i];
+        }
+    }
+    if (outside && c.wall_mode == 0) return false;   // keeps p, d of this step
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        p[i] = pn[i];
+        d[i] = dn[i];
+    }
+    if (c.stop_r2 >= 0.0f) {
+        for (int s = 0; s < n_src; ++s) {
+            float d2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                float e = pn[i] - src_xyz[i * src_stride + s];
+                d2 = fmaf(e, e, d2);
+            }
+            if (d2 <= c.stop_r2) return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace cue

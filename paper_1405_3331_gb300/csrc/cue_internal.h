@@ -1,0 +1,90 @@
+// cue_internal.h -- host-side definitions shared by the translation units of
+// libcue.so (handle layout, workspace layout, kernel launchers).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <vector>
+
+#include "cue.h"
+#include "cue_device.cuh"
+
+namespace cue {
+
+// Workspace layout (all offsets 256-byte aligned):
+//   [0,   256)  status word (unsigned) at 0, cone-update counter (u64) at 8
+//   [256, ...)  source coordinates, FP32 [3][n_src]
+//   [...]       fused-path scratch: per-tile counters and axon bins
+struct WorkspaceLayout {
+    size_t status_off = 0;
+    size_t src_xyz_off = 0;
+    size_t bin_count_off = 0;    // 2 x n_tiles int32 (double-buffered counts)
+    size_t bin_list_off = 0;     // n_axons int32 (axon ids grouped by tile)
+    size_t bin_slot_off = 0;     // n_axons int32 (tile id of each axon, -1 = none)
+    size_t total = 0;
+    int n_tiles = 0;
+};
+
+WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons);
+
+struct Sim {
+    cue_params params;
+    cone_params cone;
+    FieldDesc fd;
+    ConeDesc cd;
+    float *field[2];
+    const int32_t *src_cell;
+    const float *src_emit;
+    int n_src;
+    const float *src_map;
+    float *pos, *dir;
+    uint8_t *active;
+    int n_axons;
+    unsigned char *ws;
+    size_t ws_bytes;
+    WorkspaceLayout wl;
+    cudaStream_t stream;
+    int64_t field_step = 0, cone_step = 0;
+    int cur = 0;
+    int path = CUE_PATH_AUTO;
+    int temporal_depth = 0;
+    int rows_per_thread = 0;     // plain 2D field kernel; 0 = heuristic
+    uint64_t launches = 0;
+    bool vec4 = false;           // nx % 4 == 0 and 16-byte aligned buffers
+    bool src_xyz_ready = false;
+
+    // dominant-kernel timing (CUE_OPT_TIME_KERNEL): a ring of event pairs
+    bool time_kernel = false;
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+    size_t ev_next = 0, ev_live = 0;
+    double timed_ms = 0.0;
+    uint64_t timed_launches = 0;
+
+    unsigned *status() const { return reinterpret_cast<unsigned *>(ws + wl.status_off); }
+    unsigned long long *cone_counter() const
+    {
+        return reinterpret_cast<unsigned long long *>(ws + wl.status_off + 8);
+    }
+    float *src_xyz() const { return reinterpret_cast<float *>(ws + wl.src_xyz_off); }
+};
+
+// ---- fused, temporally blocked path (k_fused.cu) ----
+constexpr int kMaxTemporalDepth = 16;
+int fused_tile_count(const cue_params &p);   // tiles of the fused path (0 if unsupported)
+bool fused_supported(const Sim &s);
+// Runs nsteps on the fused path when selected and supported: returns CUE_OK or
+// a negative error when it ran, 1 when the caller should use the plain path.
+int run_fused_if_supported(Sim &s, int nsteps);
+
+// Bracket a launch of the dominant kernel with timing events (no-ops when off).
+void timing_begin(Sim &s);
+void timing_end(Sim &s);
+
+// ---- launchers (each returns cudaGetLastError() after its launches) ----
+cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout);
+cudaError_t launch_sources(Sim &s, float *Cout);
+cudaError_t launch_src_xyz(Sim &s);
+cudaError_t launch_cone_step(Sim &s, const float *C, uint32_t step);
+
+}  // namespace cue

@@ -1,0 +1,76 @@
+// k_cone.cu -- one growth-cone step for every active cone (rows a3-a6) on
+// the field of the current step, one thread per cone.  The field is read
+// through the read-only path; source node coordinates for the stop test are
+// staged in shared memory per block.
+//
+// Steering (Sec. 3.5, "Growth cone steering mechanisms", Eq. 6-7): vector
+// addition of the previous direction, the normalised sensed cue gradient and
+// Philox/Box-Muller noise (Sec. 5.1, Sec. 3.2); advance by a fixed length;
+// stop outside the domain (Sec. 3.4) or near a source (Sec. 3.3).
+#include "cue_internal.h"
+
+namespace cue {
+namespace {
+
+constexpr int kMaxSmemSources = 2048;   // [3][2048] floats = 24 KiB
+
+template <int DIM>
+__global__ void __launch_bounds__(256) cone_plain(FieldDesc f, ConeDesc c, const float *__restrict__ C,
+                                                  uint32_t step, int n, float *__restrict__ pos,
+                                                  float *__restrict__ dir, uint8_t *__restrict__ active,
+                                                  const float *__restrict__ src_xyz, int n_src,
+                                                  unsigned *status, unsigned long long *counter)
+{
+    __shared__ float s_src[3 * kMaxSmemSources];
+    const bool use_stop = c.stop_r2 >= 0.0f && n_src > 0;
+    const bool in_smem = n_src <= kMaxSmemSources;
+    if (use_stop && in_smem) {
+        for (int i = threadIdx.x; i < DIM * n_src; i += blockDim.x) {
+            int ax = i / n_src, s = i - ax * n_src;
+            s_src[ax * kMaxSmemSources + s] = src_xyz[ax * n_src + s];
+        }
+    }
+    __syncthreads();
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = a < n && active[a];
+    count_active(counter, live);
+    if (!live) return;
+    float p[DIM], d[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        p[i] = pos[(size_t)i * n + a];
+        d[i] = dir[(size_t)i * n + a];
+    }
+    const size_t sy = f.nx, sz = (size_t)f.nx * f.ny;
+    auto ld = [&](int i, int j, int k) { return __ldg(C + (size_t)i + sy * j + sz * k); };
+    const float *src = in_smem ? s_src : src_xyz;
+    const int stride = in_smem ? kMaxSmemSources : n_src;
+    bool alive = cone_update<DIM>(f, c, ld, (uint32_t)a, step, p, d, src, stride, use_stop ? n_src : 0);
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        pos[(size_t)i * n + a] = p[i];
+        dir[(size_t)i * n + a] = d[i];
+        bad |= !(fabsf(p[i]) <= 3.402823466e38f) || !(fabsf(d[i]) <= 3.402823466e38f);
+    }
+    if (!alive) active[a] = 0;
+    if (bad) flag_status(status, kStatusNonFinite);
+}
+
+}  // namespace
+
+cudaError_t launch_cone_step(Sim &s, const float *C, uint32_t step)
+{
+    if (s.n_axons == 0) return cudaSuccess;
+    const int blocks = (s.n_axons + 255) / 256;
+    if (s.fd.dim == 2)
+        cone_plain<2><<<blocks, 256, 0, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, s.pos, s.dir, s.active,
+                                                    s.src_xyz(), s.n_src, s.status(), s.cone_counter());
+    else
+        cone_plain<3><<<blocks, 256, 0, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, s.pos, s.dir, s.active,
+                                                    s.src_xyz(), s.n_src, s.status(), s.cone_counter());
+    s.launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace cue
