@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    ap.add_argument("--run-steps", type=int, default=0,
+                    help="time steps per benchmark step (0 = the workload's own count); for profiling")
     return ap.parse_args()
 
 
@@ -259,6 +261,8 @@ def main():
         torch.cuda.synchronize(dev)
 
     w = workload(args.workload, rank)
+    if args.run_steps:
+        w.nsteps = args.run_steps
     path = {"auto": cue.CUE_PATH_AUTO, "plain": cue.CUE_PATH_PLAIN, "fused": cue.CUE_PATH_FUSED}[args.path]
     sim = cue.Simulation(w, device=dev, path=path)
     if args.depth:
@@ -389,8 +393,7 @@ def main():
 
 
 def sim_path_used(sim):
-    from paper_1405_3331_gb300 import cue
-    return "fused" if getattr(sim, "fused_active", lambda: False)() else "plain"
+    return "fused" if sim.fused_active() else "plain"
 
 
 def hbm_probe(cue, torch, dev, hbm):

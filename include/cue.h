@@ -101,6 +101,10 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
 #define CUE_OPT_TIME_KERNEL     4  /* value 1: bracket every launch of the dominant field
                                       kernel with CUDA events on the handle's stream, read
                                       back by cue_kernel_time; 0: off (default)             */
+/* read-only values for cue_get_option */
+#define CUE_INFO_LAST_PATH     16  /* CUE_PATH_PLAIN or CUE_PATH_FUSED: path of the last step */
+#define CUE_INFO_TILE          17  /* fused tile interior: TX | TY << 16 (0 if not prepared) */
+#define CUE_INFO_DEPTH         18  /* temporal depth the fused path runs with                 */
 #define CUE_PATH_AUTO   0          /* library picks (fused when supported)                 */
 #define CUE_PATH_PLAIN  1          /* one launch per half-step: cone kernel, field kernel  */
 #define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel       */
@@ -158,6 +162,9 @@ int cue_set_stream(cue_sim *sim, void *stream);
 
 /* Set an option (CUE_OPT_*). */
 int cue_set_option(cue_sim *sim, int32_t option, int64_t value);
+
+/* Read an option (CUE_OPT_*) or an informational value (CUE_INFO_*). */
+int cue_get_option(const cue_sim *sim, int32_t option, int64_t *value);
 
 /* Number of kernels this handle has launched so far. */
 uint64_t cue_launch_count(const cue_sim *sim);

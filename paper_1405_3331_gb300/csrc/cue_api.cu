@@ -19,12 +19,18 @@ WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons)
     w.src_xyz_off = off;
     off += align256(sizeof(float) * 3 * (size_t)(n_src > 0 ? n_src : 0));
     w.n_tiles = fused_tile_count(p);
+    const size_t nt = (size_t)(w.n_tiles > 0 ? w.n_tiles : 1);
+    const size_t na = (size_t)(n_axons > 0 ? n_axons : 1);
     w.bin_count_off = off;
-    off += align256(sizeof(int32_t) * 2 * (size_t)(w.n_tiles > 0 ? w.n_tiles : 1));
+    off += align256(sizeof(int32_t) * 2 * nt);
+    w.bin_off_off = off;
+    off += align256(sizeof(int32_t) * (nt + 1));
     w.bin_list_off = off;
-    off += align256(sizeof(int32_t) * (size_t)(n_axons > 0 ? n_axons : 1));
-    w.bin_slot_off = off;
-    off += align256(sizeof(int32_t) * (size_t)(n_axons > 0 ? n_axons : 1));
+    off += align256(sizeof(int32_t) * na);
+    w.cone_tile_off = off;
+    off += align256(sizeof(int32_t) * na);
+    w.cone_slot_off = off;
+    off += align256(sizeof(int32_t) * na);
     w.total = off;
     return w;
 }
@@ -166,6 +172,7 @@ int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone, f
     f.alpha = alpha;
     f.decay = decay;
     f.dt = params->dt;
+    f.beta = (float)(1.0 - 2.0 * dim * (double)alpha - (double)decay);
     ConeDesc &c = s->cd;
     c.w_prev = cone->w_prev;
     c.w_grad = cone->w_grad;
@@ -197,6 +204,8 @@ int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone, f
     s->vec4 = (f.nx % 4 == 0) && aligned16(d_field_a) && aligned16(d_field_b) &&
               (!d_src_map || aligned16(d_src_map));
     cudaError_t e = cudaMemsetAsync(s->ws, 0, 256, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->ws + wl.bin_count_off, 0, wl.bin_off_off - wl.bin_count_off, s->stream);
     if (e == cudaSuccess) e = launch_src_xyz(*s);
     if (e != cudaSuccess) {
         delete s;
@@ -210,6 +219,9 @@ int cue_step(cue_sim *s, int32_t nsteps)
 {
     if (!s || nsteps < 0) return CUE_ERR_ARG;
     if (s->field_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
+    int rc = field_fused_if_supported(*s, nsteps);
+    if (rc != 1) return rc;
+    s->fused_used = false;
     for (int k = 0; k < nsteps; ++k) {
         float *in = s->field[s->cur], *out = s->field[s->cur ^ 1];
         cudaError_t e = launch_field_step(*s, in, out);
@@ -240,6 +252,7 @@ int sim_run(cue_sim *s, int32_t nsteps)
     if (s->field_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
     int rc = run_fused_if_supported(*s, nsteps);
     if (rc != 1) return rc;       // handled (0 = ok, < 0 = error)
+    s->fused_used = false;
     for (int k = 0; k < nsteps; ++k) {
         float *in = s->field[s->cur], *out = s->field[s->cur ^ 1];
         cudaError_t e = launch_cone_step(*s, in, (uint32_t)s->cone_step);
@@ -292,6 +305,7 @@ int cue_set_option(cue_sim *s, int32_t option, int64_t value)
     case CUE_OPT_TEMPORAL_DEPTH:
         if (value < 0 || value > kMaxTemporalDepth) return CUE_ERR_ARG;
         s->temporal_depth = (int)value;
+        s->geom_ready = false;
         return CUE_OK;
     case CUE_OPT_ROWS_PER_THREAD:
         if (value < 0 || value > 64) return CUE_ERR_ARG;
@@ -317,6 +331,21 @@ int cue_kernel_time(cue_sim *s, double *total_ms, uint64_t *launches)
     s->timed_ms = 0.0;
     s->timed_launches = 0;
     return CUE_OK;
+}
+
+int cue_get_option(const cue_sim *s, int32_t option, int64_t *value)
+{
+    if (!s || !value) return CUE_ERR_ARG;
+    switch (option) {
+    case CUE_OPT_PATH: *value = s->path; return CUE_OK;
+    case CUE_OPT_TEMPORAL_DEPTH: *value = s->temporal_depth; return CUE_OK;
+    case CUE_OPT_ROWS_PER_THREAD: *value = s->rows_per_thread; return CUE_OK;
+    case CUE_OPT_TIME_KERNEL: *value = s->time_kernel ? 1 : 0; return CUE_OK;
+    case CUE_INFO_LAST_PATH: *value = s->fused_used ? CUE_PATH_FUSED : CUE_PATH_PLAIN; return CUE_OK;
+    case CUE_INFO_TILE: *value = s->geom_ready ? (int64_t)s->geom.TX | ((int64_t)s->geom.TY << 16) : 0; return CUE_OK;
+    case CUE_INFO_DEPTH: *value = s->geom_ready ? s->geom.K : 0; return CUE_OK;
+    default: return CUE_ERR_ARG;
+    }
 }
 
 uint64_t cue_launch_count(const cue_sim *s) { return s ? s->launches : 0; }

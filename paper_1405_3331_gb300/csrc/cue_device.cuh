@@ -23,7 +23,26 @@ struct FieldDesc {
     float alpha;        // D dt / h^2
     float decay;        // lambda dt
     float dt;
+    float beta;         // 1 - 2 dim alpha - lambda dt
 };
+
+// The node update used by every field kernel:
+//   C' = beta C + alpha (sum of the axis neighbours),
+// where a neighbour missing at a wall is replaced by the node itself, so its
+// flux term alpha (C_j - C_i) vanishes (no-flux).  Neighbours are summed as
+// ((x- + x+) + (y- + y+)) [+ (z- + z+)] in every kernel so that all paths
+// round identically.
+__device__ __forceinline__ float node_update2(float c, float xm, float xp, float ym, float yp,
+                                              float alpha, float beta)
+{
+    return fmaf(alpha, (xm + xp) + (ym + yp), beta * c);
+}
+
+__device__ __forceinline__ float node_update3(float c, float xm, float xp, float ym, float yp,
+                                              float zm, float zp, float alpha, float beta)
+{
+    return fmaf(alpha, ((xm + xp) + (ym + yp)) + (zm + zp), beta * c);
+}
 
 // Cone parameters, precomputed on the host in FP32.
 struct ConeDesc {

@@ -15,15 +15,29 @@ namespace cue {
 // Workspace layout (all offsets 256-byte aligned):
 //   [0,   256)  status word (unsigned) at 0, cone-update counter (u64) at 8
 //   [256, ...)  source coordinates, FP32 [3][n_src]
-//   [...]       fused-path scratch: per-tile counters and axon bins
+//   [...]       fused-path scratch: per-tile cone counts (two rounds), bin
+//               offsets, the cone ids grouped by tile, each cone's tile and
+//               slot.  n_tiles is an upper bound over every tile geometry.
 struct WorkspaceLayout {
     size_t status_off = 0;
     size_t src_xyz_off = 0;
     size_t bin_count_off = 0;    // 2 x n_tiles int32 (double-buffered counts)
-    size_t bin_list_off = 0;     // n_axons int32 (axon ids grouped by tile)
-    size_t bin_slot_off = 0;     // n_axons int32 (tile id of each axon, -1 = none)
+    size_t bin_off_off = 0;      // n_tiles + 1 int32
+    size_t bin_list_off = 0;     // n_axons int32 (cone ids grouped by tile)
+    size_t cone_tile_off = 0;    // n_axons int32 (tile of each cone, -1 = inactive)
+    size_t cone_slot_off = 0;    // n_axons int32 (slot within its tile)
     size_t total = 0;
     int n_tiles = 0;
+};
+
+// Tile geometry of the fused path.
+struct FusedGeom {
+    int W, R;            // loaded columns, rows
+    int HX, HY;          // halo columns (multiple of 4), rows
+    int TX, TY;          // interior columns, rows
+    int ntx, nty;        // tiles per axis
+    int K;               // temporal depth
+    int ctas_per_sm;
 };
 
 WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons);
@@ -61,6 +75,18 @@ struct Sim {
     double timed_ms = 0.0;
     uint64_t timed_launches = 0;
 
+    // fused path
+    FusedGeom geom{};
+    bool geom_ready = false;
+    bool fused_used = false;
+    long long bin_round = 0;
+    alignas(64) unsigned char tmap[2][128];   // CUtensorMap per field buffer (as TMA source)
+
+    int *bin_count() const { return reinterpret_cast<int *>(ws + wl.bin_count_off); }
+    int *bin_off() const { return reinterpret_cast<int *>(ws + wl.bin_off_off); }
+    int *bin_list() const { return reinterpret_cast<int *>(ws + wl.bin_list_off); }
+    int *cone_tile() const { return reinterpret_cast<int *>(ws + wl.cone_tile_off); }
+    int *cone_slot() const { return reinterpret_cast<int *>(ws + wl.cone_slot_off); }
     unsigned *status() const { return reinterpret_cast<unsigned *>(ws + wl.status_off); }
     unsigned long long *cone_counter() const
     {
@@ -76,6 +102,8 @@ bool fused_supported(const Sim &s);
 // Runs nsteps on the fused path when selected and supported: returns CUE_OK or
 // a negative error when it ran, 1 when the caller should use the plain path.
 int run_fused_if_supported(Sim &s, int nsteps);
+// Same for field-only steps (cue_step).
+int field_fused_if_supported(Sim &s, int nsteps);
 
 // Bracket a launch of the dominant kernel with timing events (no-ops when off).
 void timing_begin(Sim &s);

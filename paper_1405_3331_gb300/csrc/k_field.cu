@@ -6,29 +6,14 @@
 // Update (Sec. 5.2 Eulerian grid, Sec. 4.3 sources with their own rates):
 //   C'_i = C_i + alpha * sum_{existing axis nbrs j} (C_j - C_i) - decay * C_i
 //          [+ dt * M_i] [+ e_k at source nodes]
-// A missing neighbour (wall) is replaced by the node itself, so its
-// difference is exactly zero.
+// evaluated as beta C_i + alpha sum_j C_j with a missing neighbour (wall)
+// replaced by the node itself (node_update2/3).
 #include "cue_internal.h"
 
 namespace cue {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ float node_update(float c, float l, float r, float u, float d,
-                                             float alpha, float decay)
-{
-    float flux = (l - c) + (r - c) + (u - c) + (d - c);
-    return fmaf(alpha, flux, fmaf(-decay, c, c));
-}
-
-// Same with the two z neighbours (3D, 7-point).
-__device__ __forceinline__ float node_update6(float c, float l, float r, float u, float d, float b,
-                                              float a, float alpha, float decay)
-{
-    float flux = (l - c) + (r - c) + (u - c) + (d - c) + (b - c) + (a - c);
-    return fmaf(alpha, flux, fmaf(-decay, c, c));
-}
 
 __device__ __forceinline__ bool finite4(const float4 &v)
 {
@@ -74,10 +59,10 @@ __global__ void __launch_bounds__(256) field2d_vec4(FieldDesc f, const float *__
         if (!has_r) r = cur.w;
         if (xin) {
             float4 o;
-            o.x = node_update(cur.x, l, cur.y, up.x, dn.x, f.alpha, f.decay);
-            o.y = node_update(cur.y, cur.x, cur.z, up.y, dn.y, f.alpha, f.decay);
-            o.z = node_update(cur.z, cur.y, cur.w, up.z, dn.z, f.alpha, f.decay);
-            o.w = node_update(cur.w, cur.z, r, up.w, dn.w, f.alpha, f.decay);
+            o.x = node_update2(cur.x, l, cur.y, up.x, dn.x, f.alpha, f.beta);
+            o.y = node_update2(cur.y, cur.x, cur.z, up.y, dn.y, f.alpha, f.beta);
+            o.z = node_update2(cur.z, cur.y, cur.w, up.z, dn.z, f.alpha, f.beta);
+            o.w = node_update2(cur.w, cur.z, r, up.w, dn.w, f.alpha, f.beta);
             if constexpr (MAP) {
                 float4 m = __ldg(m4 + (size_t)y * nx4 + x4);
                 o.x = fmaf(f.dt, m.x, o.x);
@@ -142,10 +127,10 @@ __global__ void __launch_bounds__(32 * BY) field3d_vec4(FieldDesc f, const float
         if (!has_r) r = cur.w;
         if (act) {
             float4 o;
-            o.x = node_update6(cur.x, l, cur.y, s.x, n.x, below.x, above.x, f.alpha, f.decay);
-            o.y = node_update6(cur.y, cur.x, cur.z, s.y, n.y, below.y, above.y, f.alpha, f.decay);
-            o.z = node_update6(cur.z, cur.y, cur.w, s.z, n.z, below.z, above.z, f.alpha, f.decay);
-            o.w = node_update6(cur.w, cur.z, r, s.w, n.w, below.w, above.w, f.alpha, f.decay);
+            o.x = node_update3(cur.x, l, cur.y, s.x, n.x, below.x, above.x, f.alpha, f.beta);
+            o.y = node_update3(cur.y, cur.x, cur.z, s.y, n.y, below.y, above.y, f.alpha, f.beta);
+            o.z = node_update3(cur.z, cur.y, cur.w, s.z, n.z, below.z, above.z, f.alpha, f.beta);
+            o.w = node_update3(cur.w, cur.z, r, s.w, n.w, below.w, above.w, f.alpha, f.beta);
             if constexpr (MAP) {
                 float4 m = __ldg(m4 + at(y, z));
                 o.x = fmaf(f.dt, m.x, o.x);
@@ -180,16 +165,18 @@ __global__ void __launch_bounds__(256) field_scalar(FieldDesc f, const float *__
         const int j = (int)((c / f.nx) % f.ny);
         const int k = (int)(c / sz);
         const float ci = __ldg(Cin + c);
-        float flux = 0.f;
-        flux += (i > 0 ? __ldg(Cin + c - 1) : ci) - ci;
-        flux += (i < f.nx - 1 ? __ldg(Cin + c + 1) : ci) - ci;
-        flux += (j > 0 ? __ldg(Cin + c - sy) : ci) - ci;
-        flux += (j < f.ny - 1 ? __ldg(Cin + c + sy) : ci) - ci;
+        const float xm = i > 0 ? __ldg(Cin + c - 1) : ci;
+        const float xp = i < f.nx - 1 ? __ldg(Cin + c + 1) : ci;
+        const float ym = j > 0 ? __ldg(Cin + c - sy) : ci;
+        const float yp = j < f.ny - 1 ? __ldg(Cin + c + sy) : ci;
+        float o;
         if (f.dim == 3) {
-            flux += (k > 0 ? __ldg(Cin + c - sz) : ci) - ci;
-            flux += (k < f.nz - 1 ? __ldg(Cin + c + sz) : ci) - ci;
+            const float zm = k > 0 ? __ldg(Cin + c - sz) : ci;
+            const float zp = k < f.nz - 1 ? __ldg(Cin + c + sz) : ci;
+            o = node_update3(ci, xm, xp, ym, yp, zm, zp, f.alpha, f.beta);
+        } else {
+            o = node_update2(ci, xm, xp, ym, yp, f.alpha, f.beta);
         }
-        float o = fmaf(f.alpha, flux, fmaf(-f.decay, ci, ci));
         if constexpr (MAP) o = fmaf(f.dt, __ldg(M + c), o);
         bad |= !(fabsf(o) <= 3.402823466e38f);
         Cout[c] = o;

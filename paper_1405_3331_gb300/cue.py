@@ -29,13 +29,16 @@ CUE_OPT_PATH = 1
 CUE_OPT_TEMPORAL_DEPTH = 2
 CUE_OPT_ROWS_PER_THREAD = 3
 CUE_OPT_TIME_KERNEL = 4
+CUE_INFO_LAST_PATH = 16
+CUE_INFO_TILE = 17
+CUE_INFO_DEPTH = 18
 CUE_PATH_AUTO = 0
 CUE_PATH_PLAIN = 1
 CUE_PATH_FUSED = 2
 
 EXPORTED = ("cue_workspace_bytes", "cue_init", "cue_step", "cone_step", "sim_run", "cue_get_state",
             "cue_set_state", "cue_set_stream", "cue_set_option", "cue_launch_count", "cue_status",
-            "cue_destroy", "cue_strerror", "cue_kernel_time", "cue_cone_updates")
+            "cue_destroy", "cue_strerror", "cue_kernel_time", "cue_cone_updates", "cue_get_option")
 
 
 class cue_params(ct.Structure):
@@ -85,6 +88,7 @@ def lib():
             L.cue_set_state.argtypes = [P, I64, I64, I32]
             L.cue_set_stream.argtypes = [P, P]
             L.cue_set_option.argtypes = [P, I32, I64]
+            L.cue_get_option.argtypes = [P, I32, ct.POINTER(I64)]
             L.cue_launch_count.argtypes = [P]
             L.cue_launch_count.restype = ct.c_uint64
             L.cue_status.argtypes = [P]
@@ -96,7 +100,7 @@ def lib():
             L.cue_strerror.restype = ct.c_char_p
             for f in ("cue_init", "cue_step", "cone_step", "sim_run", "cue_get_state", "cue_set_state",
                       "cue_set_stream", "cue_set_option", "cue_status", "cue_kernel_time",
-                      "cue_cone_updates"):
+                      "cue_cone_updates", "cue_get_option"):
                 getattr(L, f).restype = ct.c_int
             _lib = L
     return _lib
@@ -150,6 +154,13 @@ def cue_set_stream(h, stream: int) -> int:
 
 def cue_set_option(h, option: int, value: int) -> int:
     return lib().cue_set_option(h, option, value)
+
+
+def cue_get_option(h, option: int):
+    """Returns (status, value)."""
+    v = ct.c_int64()
+    rc = lib().cue_get_option(h, option, ct.byref(v))
+    return rc, v.value
 
 
 def cue_launch_count(h) -> int:
@@ -251,6 +262,15 @@ class Simulation:
 
     def set_option(self, option: int, value: int):
         _check(cue_set_option(self.h, option, value), "cue_set_option")
+
+    def get_option(self, option: int) -> int:
+        rc, v = cue_get_option(self.h, option)
+        _check(rc, "cue_get_option")
+        return v
+
+    def fused_active(self) -> bool:
+        """True when the last stepping call ran on the fused, temporally blocked path."""
+        return self.get_option(CUE_INFO_LAST_PATH) == CUE_PATH_FUSED
 
     def launches(self) -> int:
         return cue_launch_count(self.h)
