@@ -38,6 +38,7 @@ struct FusedGeom {
     int ntx, nty;        // tiles per axis
     int K;               // temporal depth
     int ctas_per_sm;
+    int local_stop;      // 1: the halo covers the source-stop radius, test tile sources only
 };
 
 WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons);

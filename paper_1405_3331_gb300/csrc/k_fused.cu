@@ -40,6 +40,8 @@ constexpr int kThreads = 256;         // 8 warps
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxTileSrc = 256;      // sources per tile (and in total on this path)
 constexpr long long kWaitLimit = 1LL << 22;
+constexpr int kBand = 12;             // rows swept by each warp per sub-step
+constexpr int kRows = kWarps * kBand; // loaded rows per tile (96)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -101,38 +103,115 @@ __device__ __forceinline__ void st_row(float4 *S4, int r, int lane, const Row &v
     S4[r * (kW / 4) + 32 + lane] = v.b;
 }
 
+// New values of a 4-node group from its old values and neighbours, with the
+// arithmetic of node_update2: horizontal pairs summed as scalars, the rest two
+// nodes at a time with the packed FP32x2 instructions (each lane of a pair
+// rounds exactly like the scalar form).
+__device__ __forceinline__ float4 update4(float L, const float4 &c, float R, const float4 &u, const float4 &d,
+                                          float2 alpha2, float2 beta2)
+{
+    float2 h01 = make_float2(L + c.y, c.x + c.z);
+    float2 h23 = make_float2(c.y + c.w, c.z + R);
+    float2 s01 = __fadd2_rn(h01, __fadd2_rn(make_float2(u.x, u.y), make_float2(d.x, d.y)));
+    float2 s23 = __fadd2_rn(h23, __fadd2_rn(make_float2(u.z, u.w), make_float2(d.z, d.w)));
+    float2 o01 = __ffma2_rn(alpha2, s01, __fmul2_rn(beta2, make_float2(c.x, c.y)));
+    float2 o23 = __ffma2_rn(alpha2, s23, __fmul2_rn(beta2, make_float2(c.z, c.w)));
+    return make_float4(o01.x, o01.y, o23.x, o23.y);
+}
+
+// Per-lane wall flags: the x walls (global x = 0 and nx-1) fall on the first /
+// last component of one of the lane's two float4 groups.
+struct LaneWalls {
+    bool l_a, r_a, l_b, r_b;
+};
+
 // New values of row `cur` from the old rows above/at/below.  x neighbours come
-// from adjacent lanes; the tile's outer columns (invalid rim) use the node
-// itself; the walls (global x = 0 and x = nx-1) use the node itself.
+// from adjacent lanes.  The tile's two outermost columns take whatever the
+// shuffle wraps around (they are outside the valid region after the first
+// sub-step anyway); a node on an x wall uses itself as its missing neighbour.
 __device__ __forceinline__ Row update_row(const Row &up, const Row &cur, const Row &dn, int lane,
-                                          bool wl_a, bool wr_a, bool wl_b, bool wr_b, float alpha, float beta)
+                                          const LaneWalls &w, float2 alpha2, float2 beta2)
 {
     float aL = __shfl_sync(kFull, cur.a.w, (lane + 31) & 31);
     float aR = __shfl_sync(kFull, lane == 0 ? cur.b.x : cur.a.x, (lane + 1) & 31);
     float bL = __shfl_sync(kFull, lane == 31 ? cur.a.w : cur.b.w, (lane + 31) & 31);
     float bR = __shfl_sync(kFull, cur.b.x, (lane + 1) & 31);
-    if (lane == 0 || wl_a) aL = cur.a.x;
-    if (wr_a) aR = cur.a.w;
-    if (wl_b) bL = cur.b.x;
-    if (lane == 31 || wr_b) bR = cur.b.w;
+    aL = w.l_a ? cur.a.x : aL;
+    aR = w.r_a ? cur.a.w : aR;
+    bL = w.l_b ? cur.b.x : bL;
+    bR = w.r_b ? cur.b.w : bR;
     Row o;
-    o.a.x = node_update2(cur.a.x, aL, cur.a.y, up.a.x, dn.a.x, alpha, beta);
-    o.a.y = node_update2(cur.a.y, cur.a.x, cur.a.z, up.a.y, dn.a.y, alpha, beta);
-    o.a.z = node_update2(cur.a.z, cur.a.y, cur.a.w, up.a.z, dn.a.z, alpha, beta);
-    o.a.w = node_update2(cur.a.w, cur.a.z, aR, up.a.w, dn.a.w, alpha, beta);
-    o.b.x = node_update2(cur.b.x, bL, cur.b.y, up.b.x, dn.b.x, alpha, beta);
-    o.b.y = node_update2(cur.b.y, cur.b.x, cur.b.z, up.b.y, dn.b.y, alpha, beta);
-    o.b.z = node_update2(cur.b.z, cur.b.y, cur.b.w, up.b.z, dn.b.z, alpha, beta);
-    o.b.w = node_update2(cur.b.w, cur.b.z, bR, up.b.w, dn.b.w, alpha, beta);
+    o.a = update4(aL, cur.a, aR, up.a, dn.a, alpha2, beta2);
+    o.b = update4(bL, cur.b, bR, up.b, dn.b, alpha2, beta2);
     return o;
 }
 
-__device__ __forceinline__ void add_comp(float4 &v, int k, float e)
+__device__ __forceinline__ float comp(const float4 &v, int k)
 {
-    if (k == 0) v.x += e;
-    else if (k == 1) v.y += e;
-    else if (k == 2) v.z += e;
-    else v.w += e;
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ void set_comp(float4 &v, int k, float e)
+{
+    if (k == 0) v.x = e;
+    else if (k == 1) v.y = e;
+    else if (k == 2) v.z = e;
+    else v.w = e;
+}
+
+// Sources of one warp band, consumed in row order.
+struct BandSources {
+    const int *t_col, *t_row;
+    const float *t_e;
+    int begin, end;
+};
+
+// One sub-step of the in-place sweep over the warp's band of kBand rows
+// starting at r0.  `above` / `below` are the old rows just outside the band,
+// read before the CTA barrier that precedes the sweep.  On WALL tiles (a y
+// wall inside the loaded rows), rows outside the domain are not stored and the
+// ghost row beyond each y wall is rewritten with the new edge row, so the
+// next sub-step sees the edge node as its own missing neighbour.
+template <bool WALL>
+__device__ __forceinline__ void sweep_band(float4 *S4, int lane, int r0, const Row &above, const Row &below,
+                                           const LaneWalls &lw, float2 alpha2, float2 beta2,
+                                           const BandSources &src, int oy, int ny)
+{
+    int sp = src.begin;
+    int srow = sp < src.end ? src.t_row[sp] : 1 << 30;
+    Row up = above;
+    Row cur = ld_row(S4, r0, lane);
+    Row dn = ld_row(S4, r0 + 1, lane);
+#pragma unroll
+    for (int i = 0; i < kBand; ++i) {
+        const int r = r0 + i;
+        Row nxt;
+        if (i + 2 < kBand) nxt = ld_row(S4, r + 2, lane);
+        else if (i + 2 == kBand) nxt = below;
+        Row o = update_row(up, cur, dn, lane, lw, alpha2, beta2);
+        while (srow == r) {
+            const int col = src.t_col[sp];
+            const float e = src.t_e[sp];
+            const int q = col >> 2;
+            if ((q & 31) == lane) {
+                if (q < 32) set_comp(o.a, col & 3, comp(o.a, col & 3) + e);
+                else set_comp(o.b, col & 3, comp(o.b, col & 3) + e);
+            }
+            ++sp;
+            srow = sp < src.end ? src.t_row[sp] : 1 << 30;
+        }
+        if (WALL) {
+            const int gy = oy + r;
+            if (gy >= 0 && gy < ny) st_row(S4, r, lane, o);
+            if (gy == 0 && r > 0) st_row(S4, r - 1, lane, o);               // top ghost row
+            if (gy == ny - 1 && r + 1 < kRows) st_row(S4, r + 1, lane, o);  // bottom ghost row
+        } else {
+            st_row(S4, r, lane, o);
+        }
+        up = cur;
+        cur = dn;
+        dn = nxt;
+    }
 }
 
 struct FusedArgs {
@@ -147,6 +226,7 @@ struct FusedArgs {
     float *pos, *dir;
     uint8_t *active;
     const int *bin_off, *bin_list;
+    int *next_count, *cone_tile, *cone_slot;   // re-binning for the next launch
     const int32_t *src_cell;
     const float *src_emit;
     int n_src;
@@ -154,6 +234,15 @@ struct FusedArgs {
     unsigned *status;
     unsigned long long *counter;
 };
+
+constexpr int kConeSlots = 2;          // cones held in registers per thread
+
+__device__ __forceinline__ int tile_of(const FieldDesc &f, const FusedGeom &g, float px, float py)
+{
+    int ix = clampi((int)floorf(px / f.h), 0, f.nx - 1);
+    int iy = clampi((int)floorf(py / f.h), 0, f.ny - 1);
+    return (iy / g.TY) * g.ntx + ix / g.TX;
+}
 
 __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_constant__ CUtensorMap tmap,
                                                               const FusedArgs A)
@@ -165,34 +254,59 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     float *S = reinterpret_cast<float *>(smem_raw + 128);
     float4 *S4 = reinterpret_cast<float4 *>(smem_raw + 128);
-    int *row_start = reinterpret_cast<int *>(S + g.R * kW);    // R + 1
-    int *row_fill = row_start + (g.R + 1);                      // R
-    int *t_col = row_fill + g.R;                                // kMaxTileSrc
-    float *t_e = reinterpret_cast<float *>(t_col + kMaxTileSrc);
-    float *s_xy = t_e + kMaxTileSrc;                            // [2][kMaxTileSrc]
+    int *row_start = reinterpret_cast<int *>(S + kRows * kW);    // R + 1
+    int *row_fill = row_start + (kRows + 1);                      // R
+    int *t_col = row_fill + kRows;                                // kMaxTileSrc each:
+    int *t_row = t_col + kMaxTileSrc;
+    float *t_e = reinterpret_cast<float *>(t_row + kMaxTileSrc);
+    float *t_xy = t_e + kMaxTileSrc;                            // [2][kMaxTileSrc] tile sources
+    float *s_xy = t_xy + 2 * kMaxTileSrc;                       // [2][kMaxTileSrc] all sources
 
     const int t = blockIdx.x;
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int ox = tx * g.TX - g.HX, oy = ty * g.TY - g.HY;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = A.n_axons;
 
     if (tid == 0) mbar_init(bar, 1);
-    for (int r = tid; r < g.R; r += kThreads) row_fill[r] = 0;
+    for (int r = tid; r < kRows; r += kThreads) row_fill[r] = 0;
     __syncthreads();
     if (tid == 0) {
-        mbar_expect_tx(bar, (unsigned)(g.R * kW * sizeof(float)));
+        mbar_expect_tx(bar, (unsigned)(kRows * kW * sizeof(float)));
         tma_load_2d(S, &tmap, bar, ox, oy);
     }
 
-    // point sources inside the loaded region, grouped by tile row (overlaps the TMA load)
+    // this tile's cones into registers (overlaps the TMA load)
+    const int b0 = A.cones_on ? A.bin_off[t] : 0;
+    const int b1 = A.cones_on ? A.bin_off[t + 1] : 0;
+    int ca[kConeSlots];
+    bool cl[kConeSlots];
+    float cp[kConeSlots][2], cdir[kConeSlots][2];
+#pragma unroll
+    for (int q = 0; q < kConeSlots; ++q) {
+        int i = b0 + tid + q * kThreads;
+        ca[q] = i < b1 ? A.bin_list[i] : -1;
+        cl[q] = ca[q] >= 0;
+        if (cl[q]) {
+            cl[q] = A.active[ca[q]] != 0;
+            cp[q][0] = A.pos[ca[q]];
+            cp[q][1] = A.pos[n + ca[q]];
+            cdir[q][0] = A.dir[ca[q]];
+            cdir[q][1] = A.dir[n + ca[q]];
+        }
+    }
+
+    // point sources inside the loaded region, grouped by tile row
     const bool stop_on = A.cones_on && A.c.stop_r2 >= 0.0f && A.n_src > 0;
     for (int s = tid; s < A.n_src; s += kThreads) {
         int cell = A.src_cell[s];
         if (cell >= 0 && cell < f.nx * f.ny) {
             int gx = cell % f.nx, gy = cell / f.nx;
-            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + g.R) atomicAdd(&row_fill[gy - oy], 1);
+            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) atomicAdd(&row_fill[gy - oy], 1);
+        } else if (t == 0) {
+            flag_status(A.status, kStatusBounds);      // skipped, reported once per launch
         }
-        if (stop_on) {
+        if (stop_on && !g.local_stop) {
             s_xy[s] = A.src_xyz[s];
             s_xy[kMaxTileSrc + s] = A.src_xyz[A.n_src + s];
         }
@@ -200,38 +314,42 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     __syncthreads();
     if (warp == 0) {       // exclusive scan of the per-row counts
         int carry = 0;
-        for (int base = 0; base < g.R; base += 32) {
+        for (int base = 0; base < kRows; base += 32) {
             int r = base + lane;
-            int v = r < g.R ? row_fill[r] : 0;
+            int v = r < kRows ? row_fill[r] : 0;
             int x = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 int y = __shfl_up_sync(kFull, x, o);
                 if (lane >= o) x += y;
             }
-            if (r < g.R) row_start[r] = carry + x - v;
+            if (r < kRows) row_start[r] = carry + x - v;
             carry += __shfl_sync(kFull, x, 31);
         }
-        if (lane == 0) row_start[g.R] = carry;
+        if (lane == 0) row_start[kRows] = carry;
     }
     __syncthreads();
-    for (int r = tid; r < g.R; r += kThreads) row_fill[r] = 0;
+    for (int r = tid; r < kRows; r += kThreads) row_fill[r] = 0;
     __syncthreads();
     for (int s = tid; s < A.n_src; s += kThreads) {
         int cell = A.src_cell[s];
         if (cell >= 0 && cell < f.nx * f.ny) {
             int gx = cell % f.nx, gy = cell / f.nx;
-            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + g.R) {
+            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) {
                 int r = gy - oy;
                 int slot = row_start[r] + atomicAdd(&row_fill[r], 1);
                 t_col[slot] = gx - ox;
+                t_row[slot] = r;
                 t_e[slot] = A.src_emit[s];
+                t_xy[slot] = (float)gx * f.h;
+                t_xy[kMaxTileSrc + slot] = (float)gy * f.h;
             }
         }
     }
 
-    // wait for the tile (bounded)
-    bool ok = mbar_wait_bounded(bar, 0);
+    // wait for the tile: one thread polls (bounded), the rest wait at the barrier
+    bool ok = true;
+    if (tid == 0) ok = mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!ok)) {
         if (tid == 0) {
             flag_status(A.status, kStatusTimeout);
@@ -239,29 +357,58 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
         }
         return;
     }
+    mbar_wait_bounded(bar, 0);              // completed phase: returns at once, acquires the tile
 
-    const int b0 = A.cones_on ? A.bin_off[t] : 0;
-    const int b1 = A.cones_on ? A.bin_off[t + 1] : 0;
-    const int r0 = warp * g.R / kWarps, r1 = (warp + 1) * g.R / kWarps;
+    const int r0 = warp * kBand;
     const int colA = 4 * lane, colB = 128 + 4 * lane;
     const int gxA = ox + colA, gxB = ox + colB;
-    const bool wl_a = gxA == 0, wl_b = gxB == 0;
-    const bool wr_a = gxA + 3 == f.nx - 1, wr_b = gxB + 3 == f.nx - 1;
-    const int n = A.n_axons;
+    const float2 alpha2 = make_float2(f.alpha, f.alpha), beta2 = make_float2(f.beta, f.beta);
+    const BandSources bsrc{t_col, t_row, t_e, row_start[r0], row_start[r0 + kBand]};
+    const float *stop_xy = g.local_stop ? t_xy : s_xy;
+    const int n_stop = stop_on ? (g.local_stop ? row_start[kRows] : A.n_src) : 0;
+    // walls: x walls by per-lane flags; y walls by a ghost row inside the loaded rows
+    const LaneWalls lw{gxA == 0, gxA + 3 == f.nx - 1, gxB == 0, gxB + 3 == f.nx - 1};
+    const int gt = (oy <= -1) ? -oy - 1 : -1;                       // tile row of global y = -1
+    const int gb = (oy + kRows - 1 >= f.ny) ? f.ny - oy : -1;       // tile row of global y = ny
+    const bool wall = gt >= 0 || gb >= 0;
+    if (wall) {       // ghost rows take the edge rows before the first sub-step
+        if (gt >= 0)
+            for (int c = tid; c < kW; c += kThreads) S[gt * kW + c] = S[(gt + 1) * kW + c];
+        if (gb >= 0 && gb < kRows)
+            for (int c = tid; c < kW; c += kThreads) S[gb * kW + c] = S[(gb - 1) * kW + c];
+        __syncthreads();
+    }
 
     auto ld = [&](int i, int j, int) {
         int lx = i - ox, ly = j - oy;
-        if ((unsigned)lx >= (unsigned)kW || (unsigned)ly >= (unsigned)g.R) {
+        if ((unsigned)lx >= (unsigned)kW || (unsigned)ly >= (unsigned)kRows) {
             flag_status(A.status, kStatusBounds);
             lx = min(max(lx, 0), kW - 1);
-            ly = min(max(ly, 0), g.R - 1);
+            ly = min(max(ly, 0), kRows - 1);
         }
         return S[ly * kW + lx];
     };
 
+    bool stopped[kConeSlots];
+#pragma unroll
+    for (int q = 0; q < kConeSlots; ++q) stopped[q] = false;
+
     for (int j = 0; j < A.K; ++j) {
+        const uint32_t step = A.step0 + j;
         // ---- phase A: cones of this tile read C^{n+j}
-        for (int base = b0; base < b1; base += kThreads) {
+#pragma unroll
+        for (int q = 0; q < kConeSlots; ++q) {
+            count_active(A.counter, cl[q]);
+            if (cl[q]) {
+                bool alive = cone_update<2>(f, A.c, ld, (uint32_t)ca[q], step, cp[q], cdir[q], stop_xy,
+                                            kMaxTileSrc, n_stop);
+                if (!alive) {
+                    cl[q] = false;
+                    stopped[q] = true;
+                }
+            }
+        }
+        for (int base = b0 + kConeSlots * kThreads; base < b1; base += kThreads) {   // overflow
             int i = base + tid;
             int a = i < b1 ? A.bin_list[i] : -1;
             bool live = a >= 0 && A.active[a];
@@ -269,8 +416,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
             if (live) {
                 float p[2] = {A.pos[a], A.pos[n + a]};
                 float d[2] = {A.dir[a], A.dir[n + a]};
-                bool alive = cone_update<2>(f, A.c, ld, (uint32_t)a, A.step0 + j, p, d, s_xy, kMaxTileSrc,
-                                            stop_on ? A.n_src : 0);
+                bool alive = cone_update<2>(f, A.c, ld, (uint32_t)a, step, p, d, stop_xy, kMaxTileSrc, n_stop);
                 A.pos[a] = p[0];
                 A.pos[n + a] = p[1];
                 A.dir[a] = d[0];
@@ -279,31 +425,46 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
             }
         }
         // rows just outside this warp's band, read before anyone overwrites them
-        Row above, below;
-        const bool has_above = r0 > 0, has_below = r1 < g.R;
-        if (has_above) above = ld_row(S4, r0 - 1, lane);
-        if (has_below) below = ld_row(S4, r1, lane);
+        const Row above = ld_row(S4, r0 > 0 ? r0 - 1 : r0, lane);
+        const Row below = ld_row(S4, r0 + kBand < kRows ? r0 + kBand : r0 + kBand - 1, lane);
         __syncthreads();
         // ---- phase B: in-place sweep of the band to C^{n+j+1}
-        Row cur = ld_row(S4, r0, lane);
-        Row up = has_above ? above : cur;
-        for (int r = r0; r < r1; ++r) {
-            Row dn = (r + 1 < r1) ? ld_row(S4, r + 1, lane) : (has_below ? below : cur);
-            const int gy = oy + r;
-            const Row &u2 = (gy == 0) ? cur : up;
-            const Row &d2 = (gy == f.ny - 1) ? cur : dn;
-            Row o = update_row(u2, cur, d2, lane, wl_a, wr_a, wl_b, wr_b, f.alpha, f.beta);
-            for (int s = row_start[r], s1 = row_start[r + 1]; s < s1; ++s) {
-                int col = t_col[s];
-                float e = t_e[s];
-                if ((col >> 2) == lane) add_comp(o.a, col & 3, e);
-                else if (((col - 128) >> 2) == lane && col >= 128) add_comp(o.b, col & 3, e);
-            }
-            st_row(S4, r, lane, o);
-            up = cur;
-            cur = dn;
-        }
+        if (wall) sweep_band<true>(S4, lane, r0, above, below, lw, alpha2, beta2, bsrc, oy, f.ny);
+        else sweep_band<false>(S4, lane, r0, above, below, lw, alpha2, beta2, bsrc, oy, f.ny);
         __syncthreads();
+    }
+
+    // ---- cones back to global memory, binned for the next launch
+#pragma unroll
+    for (int q = 0; q < kConeSlots; ++q) {
+        const int a = ca[q];
+        if (a < 0) continue;
+        A.pos[a] = cp[q][0];
+        A.pos[n + a] = cp[q][1];
+        A.dir[a] = cdir[q][0];
+        A.dir[n + a] = cdir[q][1];
+        if (stopped[q]) A.active[a] = 0;
+        if (A.next_count) {
+            if (cl[q]) {
+                int tile = tile_of(f, g, cp[q][0], cp[q][1]);
+                A.cone_tile[a] = tile;
+                A.cone_slot[a] = atomicAdd(&A.next_count[tile], 1);
+            } else {
+                A.cone_tile[a] = -1;
+            }
+        }
+    }
+    if (A.next_count) {
+        for (int i = b0 + kConeSlots * kThreads + tid; i < b1; i += kThreads) {
+            int a = A.bin_list[i];
+            if (A.active[a]) {
+                int tile = tile_of(f, g, A.pos[a], A.pos[n + a]);
+                A.cone_tile[a] = tile;
+                A.cone_slot[a] = atomicAdd(&A.next_count[tile], 1);
+            } else {
+                A.cone_tile[a] = -1;
+            }
+        }
     }
 
     // ---- store the interior
@@ -338,9 +499,7 @@ __global__ void bin_count_kernel(FieldDesc f, FusedGeom g, int n, const float *_
         cone_tile[a] = -1;
         return;
     }
-    int ix = clampi((int)floorf(pos[a] / f.h), 0, f.nx - 1);
-    int iy = clampi((int)floorf(pos[n + a] / f.h), 0, f.ny - 1);
-    int tile = (iy / g.TY) * g.ntx + ix / g.TX;
+    int tile = tile_of(f, g, pos[a], pos[n + a]);
     cone_tile[a] = tile;
     cone_slot[a] = atomicAdd(&count[tile], 1);
 }
@@ -426,46 +585,45 @@ int device_sm_count()
 
 size_t fused_smem_bytes(int R)
 {
-    return 128 + (size_t)R * kW * sizeof(float) + sizeof(int) * (2 * R + 1) + sizeof(int) * kMaxTileSrc +
-           sizeof(float) * 3 * kMaxTileSrc;
+    return 128 + (size_t)R * kW * sizeof(float) + sizeof(int) * (2 * R + 1) + sizeof(int) * 2 * kMaxTileSrc +
+           sizeof(float) * 5 * kMaxTileSrc;
 }
 
 // Tile geometry for temporal depth K; returns false if the fused path cannot run.
-bool choose_geometry(const FieldDesc &f, float step_len, bool cones, int K, int sms, FusedGeom &g)
+bool choose_geometry(const FieldDesc &f, float step_len, float stop_r2, bool cones, int K, int sms, FusedGeom &g)
 {
     if (f.dim != 2 || K < 1 || K > kMaxTemporalDepth) return false;
-    double drift = cones ? std::ceil((K - 1) * (double)step_len / (double)f.h * (1.0 + 1e-5)) : 0.0;
+    const double tol = 1.0 + 1e-5;
+    double drift = cones ? std::ceil((K - 1) * (double)step_len / (double)f.h * tol) : 0.0;
     int H = cones ? (int)(K + 1 + drift) : K;
+    // a cone stays within K step_len of its tile; sources within the stop radius of it
+    // are then inside the loaded region when H >= ceil((K step_len + r) / h) + 1
+    int local_stop = 1;
+    if (cones && stop_r2 >= 0.0f) {
+        double r = std::sqrt((double)stop_r2);
+        int need = (int)std::ceil((K * (double)step_len + r) / (double)f.h * tol) + 1;
+        local_stop = need <= H ? 1 : 0;
+    }
     int HX = (H + 3) & ~3;
     if (kW - 2 * HX < 32) return false;
-    const int candidates[2][2] = {{100, 2}, {208, 1}};   // rows, CTAs per SM
-    double best = 1e300;
-    bool found = false;
-    for (auto &cand : candidates) {
-        int R = cand[0], cps = cand[1];
-        int TY = R - 2 * H;
-        if (TY < 8) continue;
-        int TX = kW - 2 * HX;
-        long long ntx = (f.nx + TX - 1) / TX, nty = (f.ny + TY - 1) / TY;
-        long long tiles = ntx * nty;
-        long long slots = (long long)sms * cps;
-        double waves = (double)((tiles + slots - 1) / slots);
-        double cost = waves * cps * R;
-        if (cost < best) {
-            best = cost;
-            g.W = kW;
-            g.R = R;
-            g.HX = HX;
-            g.HY = H;
-            g.TX = TX;
-            g.TY = TY;
-            g.ntx = (int)ntx;
-            g.nty = (int)nty;
-            g.K = K;
-            g.ctas_per_sm = cps;
-            found = true;
-        }
-    }
+    const int R = kRows, cps = 2;
+    int TY = R - 2 * H;
+    if (TY < 8) return false;
+    int TX = kW - 2 * HX;
+    if (TX < 32) return false;
+    g.W = kW;
+    g.R = R;
+    g.HX = HX;
+    g.HY = H;
+    g.TX = TX;
+    g.TY = TY;
+    g.ntx = (f.nx + TX - 1) / TX;
+    g.nty = (f.ny + TY - 1) / TY;
+    g.K = K;
+    g.ctas_per_sm = cps;
+    g.local_stop = local_stop;
+    (void)sms;
+    bool found = true;
     return found;
 }
 
@@ -487,7 +645,7 @@ bool fused_supported(const Sim &s)
     if (s.fd.dim != 2 || !s.vec4 || s.src_map || s.n_src > kMaxTileSrc) return false;
     if (!encode_fn()) return false;
     FusedGeom g;
-    if (!choose_geometry(s.fd, s.cd.step_len, s.n_axons > 0, default_depth(s), device_sm_count(), g))
+    if (!choose_geometry(s.fd, s.cd.step_len, s.cd.stop_r2, s.n_axons > 0, default_depth(s), device_sm_count(), g))
         return false;
     long long tiles = (long long)g.ntx * g.nty;
     if (tiles > s.wl.n_tiles || tiles + 1 > 16384) return false;
@@ -516,7 +674,8 @@ static int prepare(Sim &s)
     const int K = default_depth(s);
     if (s.geom_ready && s.geom.K == K) return CUE_OK;
     FusedGeom g;
-    if (!choose_geometry(s.fd, s.cd.step_len, s.n_axons > 0, K, device_sm_count(), g)) return CUE_ERR_ARG;
+    if (!choose_geometry(s.fd, s.cd.step_len, s.cd.stop_r2, s.n_axons > 0, K, device_sm_count(), g))
+        return CUE_ERR_ARG;
     s.geom = g;
     if (!make_maps(s)) return CUE_ERR_CUDA;
     size_t smem = fused_smem_bytes(g.R);
@@ -532,7 +691,22 @@ static int prepare(Sim &s)
     return CUE_OK;
 }
 
+// Count every active cone into its tile for the current round (start of a run).
+static cudaError_t launch_bin_count(Sim &s)
+{
+    int *cur_count = s.bin_count() + (s.bin_round & 1) * s.wl.n_tiles;
+    const int n_tiles = s.geom.ntx * s.geom.nty;
+    cudaError_t e = cudaMemsetAsync(cur_count, 0, sizeof(int) * n_tiles, s.stream);
+    if (e != cudaSuccess) return e;
+    bin_count_kernel<<<(s.n_axons + 255) / 256, 256, 0, s.stream>>>(s.fd, s.geom, s.n_axons, s.pos, s.active,
+                                                                     cur_count, s.cone_tile(), s.cone_slot());
+    s.launches++;
+    return cudaGetLastError();
+}
+
 // One launch of k <= K fused steps (cones on or off) from s.cur into s.cur^1.
+// With cones: scatter the current round's counts into bins first; the fused
+// kernel counts its cones into the next round as it finishes.
 static cudaError_t launch_fused(Sim &s, int k, bool cones)
 {
     const FusedGeom &g = s.geom;
@@ -540,10 +714,8 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     int *count = s.bin_count();
     int *cur_count = count + (s.bin_round & 1) * s.wl.n_tiles;
     int *next_count = count + ((s.bin_round + 1) & 1) * s.wl.n_tiles;
-    if (cones && s.n_axons > 0) {
-        bin_count_kernel<<<(s.n_axons + 255) / 256, 256, 0, s.stream>>>(s.fd, g, s.n_axons, s.pos, s.active, cur_count,
-                                                                         s.cone_tile(), s.cone_slot());
-        s.launches++;
+    const bool with_cones = cones && s.n_axons > 0;
+    if (with_cones) {
         int blocks = (s.n_axons + 1023) / 1024;
         size_t sm = sizeof(int) * (n_tiles + 1);
         bin_scatter_kernel<<<blocks, 1024, sm, s.stream>>>(n_tiles, s.n_axons, cur_count, next_count, s.bin_off(),
@@ -558,13 +730,16 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     A.Cout = s.field[s.cur ^ 1];
     A.K = k;
     A.step0 = (uint32_t)s.field_step;
-    A.cones_on = (cones && s.n_axons > 0) ? 1 : 0;
+    A.cones_on = with_cones ? 1 : 0;
     A.n_axons = s.n_axons;
     A.pos = s.pos;
     A.dir = s.dir;
     A.active = s.active;
     A.bin_off = s.bin_off();
     A.bin_list = s.bin_list();
+    A.next_count = with_cones ? next_count : nullptr;
+    A.cone_tile = s.cone_tile();
+    A.cone_slot = s.cone_slot();
     A.src_cell = s.src_cell;
     A.src_emit = s.src_emit;
     A.n_src = s.n_src;
@@ -588,6 +763,7 @@ int run_fused_if_supported(Sim &s, int nsteps)
     }
     int rc = prepare(s);
     if (rc != CUE_OK) return s.path == CUE_PATH_FUSED ? rc : 1;
+    if (nsteps > 0 && s.n_axons > 0 && launch_bin_count(s) != cudaSuccess) return CUE_ERR_CUDA;
     while (nsteps > 0) {
         int k = nsteps < s.geom.K ? nsteps : s.geom.K;
         if (launch_fused(s, k, true) != cudaSuccess) return CUE_ERR_CUDA;
