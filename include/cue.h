@@ -66,6 +66,8 @@ extern "C" {
 #define CUE_ERR_WORKSPACE   -7  /* workspace missing, too small or misaligned               */
 #define CUE_ERR_STATE       -8  /* call order violated (e.g. sim_run with cone/field steps
                                    out of step)                                             */
+#define CUE_ERR_SCRATCH     -9  /* the problem needs more scratch than sim_run_static's
+                                   fixed device array holds                                 */
 
 /* ---- parameters -------------------------------------------------------- */
 typedef struct {
@@ -185,6 +187,41 @@ int cue_status(cue_sim *sim);
 
 /* Free the handle (never the caller's buffers).  NULL is accepted. */
 void cue_destroy(cue_sim *sim);
+
+/*
+ * sim_run_static: the coupled run (as sim_run) for callers that cannot
+ * allocate device memory -- code that runs under another framework's
+ * allocator, a host that forbids cudaMalloc once it has started, or a caller
+ * that must not grow the process's device footprint per call.  The paper has
+ * no counterpart: this is an interface for such callers, not part of the
+ * model.
+ *
+ * Arguments are those of cue_init (minus the workspace) plus the starting
+ * step index step0 (both counters) and nsteps.  The fields, sources and cone
+ * buffers are the caller's, as with cue_init; d_field_a holds C at step0 and
+ * *cur_buffer_out receives the index of the buffer holding the result
+ * (0 = d_field_a, 1 = d_field_b).  Work is queued on `stream`; the call
+ * returns without synchronising.
+ *
+ * Scratch: one file-scope device array of cue_static_scratch_bytes()
+ * (4 MiB), held by every GPU that loads the library until the process exits.
+ * Problems needing more (cue_workspace_bytes) are rejected with
+ * CUE_ERR_SCRATCH.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents (the parts that must start at zero are
+ * cleared by each call); calls whose GPU work overlaps in time race on it.
+ * Device-side status (non-finite values, skipped sources) is recorded in the
+ * array but not reported by this call.
+ */
+int sim_run_static(const cue_params *params, const cone_params *cone, float *d_field_a, float *d_field_b,
+                   const int32_t *d_src_cell, const float *d_src_emit, int32_t n_src, const float *d_src_map,
+                   float *d_pos, float *d_dir, uint8_t *d_active, int32_t n_axons, int64_t step0, int32_t nsteps,
+                   void *stream, int32_t *cur_buffer_out);
+
+/* Size in bytes of sim_run_static's device scratch array. */
+size_t cue_static_scratch_bytes(void);
 
 /* Static description of a status code. */
 const char *cue_strerror(int code);

@@ -402,6 +402,7 @@ const char *cue_strerror(int code)
     case CUE_ERR_BOUNDS: return "source cell index outside the grid (skipped)";
     case CUE_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
     case CUE_ERR_STATE: return "call order violated (cone and field step counters differ)";
+    case CUE_ERR_SCRATCH: return "problem needs more scratch than sim_run_static's fixed 4 MiB device array";
     default: return "unknown status code";
     }
 }

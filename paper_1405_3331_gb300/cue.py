@@ -24,6 +24,7 @@ CUE_ERR_TIMEOUT = -5
 CUE_ERR_BOUNDS = -6
 CUE_ERR_WORKSPACE = -7
 CUE_ERR_STATE = -8
+CUE_ERR_SCRATCH = -9
 
 CUE_OPT_PATH = 1
 CUE_OPT_TEMPORAL_DEPTH = 2
@@ -38,7 +39,8 @@ CUE_PATH_FUSED = 2
 
 EXPORTED = ("cue_workspace_bytes", "cue_init", "cue_step", "cone_step", "sim_run", "cue_get_state",
             "cue_set_state", "cue_set_stream", "cue_set_option", "cue_launch_count", "cue_status",
-            "cue_destroy", "cue_strerror", "cue_kernel_time", "cue_cone_updates", "cue_get_option")
+            "cue_destroy", "cue_strerror", "cue_kernel_time", "cue_cone_updates", "cue_get_option", "sim_run_static",
+            "cue_static_scratch_bytes")
 
 
 class cue_params(ct.Structure):
@@ -89,6 +91,11 @@ def lib():
             L.cue_set_stream.argtypes = [P, P]
             L.cue_set_option.argtypes = [P, I32, I64]
             L.cue_get_option.argtypes = [P, I32, ct.POINTER(I64)]
+            L.sim_run_static.argtypes = [ct.POINTER(cue_params), ct.POINTER(cone_params), P, P, P, P, I32, P,
+                                         P, P, P, I32, I64, I32, P, ct.POINTER(I32)]
+            L.sim_run_static.restype = ct.c_int
+            L.cue_static_scratch_bytes.argtypes = []
+            L.cue_static_scratch_bytes.restype = SZ
             L.cue_launch_count.argtypes = [P]
             L.cue_launch_count.restype = ct.c_uint64
             L.cue_status.argtypes = [P]
@@ -183,6 +190,23 @@ def cue_cone_updates(h):
     n = ct.c_uint64()
     rc = lib().cue_cone_updates(h, ct.byref(n))
     return rc, n.value
+
+
+def sim_run_static(params: cue_params, cone: cone_params, field_a: int, field_b: int, src_cell: int,
+                   src_emit: int, n_src: int, src_map: int, pos: int, dir: int, active: int, n_axons: int,
+                   step0: int, nsteps: int, stream: int):
+    """The coupled run without a caller workspace (fixed device scratch array).
+
+    Returns (status, index of the buffer holding the result)."""
+    cur = ct.c_int32(-1)
+    rc = lib().sim_run_static(ct.byref(params), ct.byref(cone), field_a, field_b, src_cell, src_emit, n_src,
+                              src_map or None, pos, dir, active, n_axons, step0, nsteps, stream or None,
+                              ct.byref(cur))
+    return rc, cur.value
+
+
+def cue_static_scratch_bytes() -> int:
+    return int(lib().cue_static_scratch_bytes())
 
 
 def cue_destroy(h) -> None:

@@ -53,7 +53,7 @@ def test_library_exports_every_declared_symbol(cue):
 
 
 def test_strerror_covers_every_code(cue):
-    for code in range(0, -9, -1):
+    for code in range(0, -10, -1):
         s = cue.cue_strerror(code)
         assert s and s != "unknown status code"
     assert cue.cue_strerror(-99) == "unknown status code"
