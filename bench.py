@@ -233,6 +233,21 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ ranks
+def aggregate(local_ms, units_per_step, steps, world, dist=None, device=None):
+    """Whole-job figures: the slowest rank's time, and the units all ranks processed per second.
+
+    Each rank runs its own replica (no data-path collective); `local_ms` is this rank's summed
+    device time for `steps` steps.  Returns (max_ms, value)."""
+    t = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t, world * units_per_step * steps / (t / 1e3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse_args()
@@ -293,7 +308,7 @@ def main():
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     sampler = ClockSampler(gpu_id_for(local))
-    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 1)
+    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 16)     # events around every 16th launch
     sim.kernel_time()
     barrier()
     sampler.start()
@@ -311,13 +326,9 @@ def main():
     kern_ms, kern_n = sim.kernel_time()
     sim.set_option(cue.CUE_OPT_TIME_KERNEL, 0)
     sim.check()
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    local_ms = sum(a.elapsed_time(b) for a, b in evs)
     cells_per_run = w.n_cells * w.nsteps
-    value = world * cells_per_run * args.steps / (total_ms / 1e3)
+    total_ms, value = aggregate(local_ms, cells_per_run, args.steps, world, dist, dev)
     axon_steps = world * cone_updates_per_run * args.steps / (total_ms / 1e3)
 
     # roofline of the dominant kernel
@@ -325,7 +336,7 @@ def main():
     fused = kern_n > 0 and sim_path_used(sim) == "fused"
     bytes_per_cell = 12 if w.src_map is not None else 8
     if kern_n:
-        steps_per_launch = (w.nsteps * args.steps) / kern_n
+        steps_per_launch = (w.nsteps / (launches_per_run(sim, w)))
         alg_bytes = bytes_per_cell * w.n_cells          # compulsory field traffic of one launch
         avg_s = kern_ms / kern_n / 1e3
         achieved = alg_bytes / avg_s / 1e9
@@ -390,6 +401,15 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def launches_per_run(sim, w):
+    """Launches of the dominant kernel in one run (K steps per launch on the fused path)."""
+    from paper_1405_3331_gb300 import cue
+    if sim.fused_active():
+        K = sim.get_option(cue.CUE_INFO_DEPTH)
+        return (w.nsteps + K - 1) // K
+    return w.nsteps
 
 
 def sim_path_used(sim):

@@ -100,9 +100,9 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
                                       0 = library choice                                    */
 #define CUE_OPT_ROWS_PER_THREAD 3  /* value: rows streamed per thread by the plain 2D field
                                       kernel (1..64), 0 = library choice                    */
-#define CUE_OPT_TIME_KERNEL     4  /* value 1: bracket every launch of the dominant field
-                                      kernel with CUDA events on the handle's stream, read
-                                      back by cue_kernel_time; 0: off (default)             */
+#define CUE_OPT_TIME_KERNEL     4  /* value v >= 1: bracket every v-th launch of the dominant
+                                      field kernel with CUDA events on the handle's stream,
+                                      read back by cue_kernel_time; 0: off (default)        */
 /* read-only values for cue_get_option */
 #define CUE_INFO_LAST_PATH     16  /* CUE_PATH_PLAIN or CUE_PATH_FUSED: path of the last step */
 #define CUE_INFO_TILE          17  /* fused tile interior: TX | TY << 16 (0 if not prepared) */

@@ -49,7 +49,10 @@ static void timing_collect(Sim &s, size_t slot)
 
 void timing_begin(Sim &s)
 {
+    s.timing_now = false;
     if (!s.time_kernel) return;
+    if (s.time_seen++ % s.time_period != 0) return;
+    s.timing_now = true;
     if (s.ev_start.empty()) {
         s.ev_start.resize(kEventRing);
         s.ev_stop.resize(kEventRing);
@@ -67,7 +70,8 @@ void timing_begin(Sim &s)
 
 void timing_end(Sim &s)
 {
-    if (!s.time_kernel) return;
+    if (!s.time_kernel || !s.timing_now) return;
+    s.timing_now = false;
     cudaEventRecord(s.ev_stop[s.ev_next], s.stream);
     s.ev_next = (s.ev_next + 1) % kEventRing;
     s.ev_live++;
@@ -312,9 +316,11 @@ int cue_set_option(cue_sim *s, int32_t option, int64_t value)
         s->rows_per_thread = (int)value;
         return CUE_OK;
     case CUE_OPT_TIME_KERNEL:
-        if (value != 0 && value != 1) return CUE_ERR_ARG;
+        if (value < 0 || value > 1 << 20) return CUE_ERR_ARG;
         if (!value && s->time_kernel) timing_drain(*s);
         s->time_kernel = value != 0;
+        s->time_period = value > 0 ? (int)value : 1;
+        s->time_seen = 0;
         return CUE_OK;
     default:
         return CUE_ERR_ARG;
@@ -340,7 +346,7 @@ int cue_get_option(const cue_sim *s, int32_t option, int64_t *value)
     case CUE_OPT_PATH: *value = s->path; return CUE_OK;
     case CUE_OPT_TEMPORAL_DEPTH: *value = s->temporal_depth; return CUE_OK;
     case CUE_OPT_ROWS_PER_THREAD: *value = s->rows_per_thread; return CUE_OK;
-    case CUE_OPT_TIME_KERNEL: *value = s->time_kernel ? 1 : 0; return CUE_OK;
+    case CUE_OPT_TIME_KERNEL: *value = s->time_kernel ? s->time_period : 0; return CUE_OK;
     case CUE_INFO_LAST_PATH: *value = s->fused_used ? CUE_PATH_FUSED : CUE_PATH_PLAIN; return CUE_OK;
     case CUE_INFO_TILE: *value = s->geom_ready ? (int64_t)s->geom.TX | ((int64_t)s->geom.TY << 16) : 0; return CUE_OK;
     case CUE_INFO_DEPTH: *value = s->geom_ready ? s->geom.K : 0; return CUE_OK;

@@ -71,6 +71,9 @@ struct Sim {
 
     // dominant-kernel timing (CUE_OPT_TIME_KERNEL): a ring of event pairs
     bool time_kernel = false;
+    int time_period = 1;          // time every time_period-th launch
+    long long time_seen = 0;      // dominant-kernel launches seen while timing
+    bool timing_now = false;      // the current launch is bracketed
     std::vector<cudaEvent_t> ev_start, ev_stop;
     size_t ev_next = 0, ev_live = 0;
     double timed_ms = 0.0;
