@@ -177,6 +177,7 @@ int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone, f
     f.decay = decay;
     f.dt = params->dt;
     f.beta = (float)(1.0 - 2.0 * dim * (double)alpha - (double)decay);
+    f.inv_h = 1.0f / params->h;
     ConeDesc &c = s->cd;
     c.w_prev = cone->w_prev;
     c.w_grad = cone->w_grad;

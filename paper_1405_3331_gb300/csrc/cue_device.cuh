@@ -24,6 +24,7 @@ struct FieldDesc {
     float decay;        // lambda dt
     float dt;
     float beta;         // 1 - 2 dim alpha - lambda dt
+    float inv_h;        // 1 / h
 };
 
 // The node update used by every field kernel:
@@ -132,85 +133,130 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // (a missing neighbour at a wall is replaced by the node itself).  `ld(i,j,k)`
 // returns C at a node inside the grid.
 // --------------------------------------------------------------------------
-template <int DIM, class Load>
-__device__ __forceinline__ void sample_gradient(const FieldDesc &f, const ConeDesc &c, const float *p,
-                                                const Load &ld, float *g)
+
+// Cell of p (lower corner clamped to [0, N-2] per axis) and the fractional
+// position inside it.
+template <int DIM>
+__device__ __forceinline__ void cell_of(const FieldDesc &f, const float *p, int *lo, float *fr)
 {
     const int ext[3] = {f.nx, f.ny, f.nz};
-    int lo[3] = {0, 0, 0};
-    float fr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
-        float s = p[ax] / f.h;
+        float s = p[ax] * f.inv_h;
         int i0 = clampi((int)floorf(s), 0, ext[ax] - 2);
         lo[ax] = i0;
         fr[ax] = s - (float)i0;
     }
+}
+
+// The 12 nodes a 2D gradient sample reads, in a fixed order: rows y0 and y1
+// across x = i0-1 .. i0+2, then columns x0 and x1 at y = j0-1 and j0+2 (indices
+// clamped at the walls, i.e. the ghost node is the edge node).
+constexpr int kPatch2 = 12;
+
+template <class Load>
+__device__ __forceinline__ void gather2(const FieldDesc &f, const int *lo, const Load &ld, float *v)
+{
     const int xm = max(lo[0] - 1, 0), x0 = lo[0], x1 = lo[0] + 1, xp = min(lo[0] + 2, f.nx - 1);
     const int ym = max(lo[1] - 1, 0), y0 = lo[1], y1 = lo[1] + 1, yp = min(lo[1] + 2, f.ny - 1);
+    v[0] = ld(xm, y0, 0);
+    v[1] = ld(x0, y0, 0);
+    v[2] = ld(x1, y0, 0);
+    v[3] = ld(xp, y0, 0);
+    v[4] = ld(xm, y1, 0);
+    v[5] = ld(x0, y1, 0);
+    v[6] = ld(x1, y1, 0);
+    v[7] = ld(xp, y1, 0);
+    v[8] = ld(x0, ym, 0);
+    v[9] = ld(x1, ym, 0);
+    v[10] = ld(x0, yp, 0);
+    v[11] = ld(x1, yp, 0);
+}
+
+// 2D gradient from the gathered nodes and the fractional position.
+__device__ __forceinline__ void grad2(const ConeDesc &c, const float *v, const float *fr, float *g)
+{
+    const float r0m = v[0], r00 = v[1], r01 = v[2], r0p = v[3];
+    const float r1m = v[4], r10 = v[5], r11 = v[6], r1p = v[7];
+    const float cm0 = v[8], cm1 = v[9], cp0 = v[10], cp1 = v[11];
     const float wx[2] = {1.0f - fr[0], fr[0]};
     const float wy[2] = {1.0f - fr[1], fr[1]};
+    // node gradients at the four corners (x index a, y index b)
+    float gx00 = (r01 - r0m) * c.inv2h, gx10 = (r0p - r00) * c.inv2h;
+    float gx01 = (r11 - r1m) * c.inv2h, gx11 = (r1p - r10) * c.inv2h;
+    float gy00 = (r10 - cm0) * c.inv2h, gy10 = (r11 - cm1) * c.inv2h;
+    float gy01 = (cp0 - r00) * c.inv2h, gy11 = (cp1 - r01) * c.inv2h;
+    float w00 = wx[0] * wy[0], w10 = wx[1] * wy[0], w01 = wx[0] * wy[1], w11 = wx[1] * wy[1];
+    g[0] = w00 * gx00 + w10 * gx10 + w01 * gx01 + w11 * gx11;
+    g[1] = w00 * gy00 + w10 * gy10 + w01 * gy01 + w11 * gy11;
+}
+
+// 3D gradient: the 32 nodes of the trilinear footprint read through `ld`.
+template <class Load>
+__device__ __forceinline__ void grad3(const FieldDesc &f, const ConeDesc &c, const int *lo, const float *fr,
+                                      const Load &ld, float *g)
+{
+    const int xm = max(lo[0] - 1, 0), x0 = lo[0], x1 = lo[0] + 1, xp = min(lo[0] + 2, f.nx - 1);
+    const int ym = max(lo[1] - 1, 0), y0 = lo[1], y1 = lo[1] + 1, yp = min(lo[1] + 2, f.ny - 1);
+    const int zm = max(lo[2] - 1, 0), z0 = lo[2], z1 = lo[2] + 1, zp = min(lo[2] + 2, f.nz - 1);
+    const float wx[2] = {1.0f - fr[0], fr[0]};
+    const float wy[2] = {1.0f - fr[1], fr[1]};
+    const float wz[2] = {1.0f - fr[2], fr[2]};
+    const int xs[2] = {x0, x1}, ys[2] = {y0, y1}, zs[2] = {z0, z1};
+    const int xl[2] = {xm, x0}, xr[2] = {x1, xp};
+    const int yl[2] = {ym, y0}, yr[2] = {y1, yp};
+    const int zl[2] = {zm, z0}, zr[2] = {z1, zp};
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                float w = wx[a] * wy[e] * wz[b];
+                float nx_ = (ld(xr[a], ys[e], zs[b]) - ld(xl[a], ys[e], zs[b])) * c.inv2h;
+                float ny_ = (ld(xs[a], yr[e], zs[b]) - ld(xs[a], yl[e], zs[b])) * c.inv2h;
+                float nz_ = (ld(xs[a], ys[e], zr[b]) - ld(xs[a], ys[e], zl[b])) * c.inv2h;
+                gx += w * nx_;
+                gy += w * ny_;
+                gz += w * nz_;
+            }
+    g[0] = gx;
+    g[1] = gy;
+    g[2] = gz;
+}
+
+template <int DIM, class Load>
+__device__ __forceinline__ void sample_gradient(const FieldDesc &f, const ConeDesc &c, const float *p,
+                                                const Load &ld, float *g)
+{
+    int lo[3] = {0, 0, 0};
+    float fr[3] = {0.f, 0.f, 0.f};
+    cell_of<DIM>(f, p, lo, fr);
     if constexpr (DIM == 2) {
-        // rows y0, y1 across x = xm..xp; columns x0, x1 across y = ym..yp
-        float r0m = ld(xm, y0, 0), r00 = ld(x0, y0, 0), r01 = ld(x1, y0, 0), r0p = ld(xp, y0, 0);
-        float r1m = ld(xm, y1, 0), r10 = ld(x0, y1, 0), r11 = ld(x1, y1, 0), r1p = ld(xp, y1, 0);
-        float cm0 = ld(x0, ym, 0), cm1 = ld(x1, ym, 0);
-        float cp0 = ld(x0, yp, 0), cp1 = ld(x1, yp, 0);
-        // node gradients at the four corners (x index a, y index b)
-        float gx00 = (r01 - r0m) * c.inv2h, gx10 = (r0p - r00) * c.inv2h;
-        float gx01 = (r11 - r1m) * c.inv2h, gx11 = (r1p - r10) * c.inv2h;
-        float gy00 = (r10 - cm0) * c.inv2h, gy10 = (r11 - cm1) * c.inv2h;
-        float gy01 = (cp0 - r00) * c.inv2h, gy11 = (cp1 - r01) * c.inv2h;
-        float w00 = wx[0] * wy[0], w10 = wx[1] * wy[0], w01 = wx[0] * wy[1], w11 = wx[1] * wy[1];
-        g[0] = w00 * gx00 + w10 * gx10 + w01 * gx01 + w11 * gx11;
-        g[1] = w00 * gy00 + w10 * gy10 + w01 * gy01 + w11 * gy11;
+        float v[kPatch2];
+        gather2(f, lo, ld, v);
+        grad2(c, v, fr, g);
     } else {
-        const int zm = max(lo[2] - 1, 0), z0 = lo[2], z1 = lo[2] + 1, zp = min(lo[2] + 2, f.nz - 1);
-        const float wz[2] = {1.0f - fr[2], fr[2]};
-        const int xs[2] = {x0, x1}, ys[2] = {y0, y1}, zs[2] = {z0, z1};
-        const int xl[2] = {xm, x0}, xr[2] = {x1, xp};
-        const int yl[2] = {ym, y0}, yr[2] = {y1, yp};
-        const int zl[2] = {zm, z0}, zr[2] = {z1, zp};
-        float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int e = 0; e < 2; ++e)
-#pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    float w = wx[a] * wy[e] * wz[b];
-                    float nx_ = (ld(xr[a], ys[e], zs[b]) - ld(xl[a], ys[e], zs[b])) * c.inv2h;
-                    float ny_ = (ld(xs[a], yr[e], zs[b]) - ld(xs[a], yl[e], zs[b])) * c.inv2h;
-                    float nz_ = (ld(xs[a], ys[e], zr[b]) - ld(xs[a], ys[e], zl[b])) * c.inv2h;
-                    gx += w * nx_;
-                    gy += w * ny_;
-                    gz += w * nz_;
-                }
-        g[0] = gx;
-        g[1] = gy;
-        g[2] = gz;
+        grad3(f, c, lo, fr, ld, g);
     }
 }
 
 // --------------------------------------------------------------------------
-// One growth-cone step.  p, d are updated in place; returns false when the
-// cone stops at this step.  src_xyz holds the source node coordinates as
-// [3][n_src] (x row, y row, z row).
+// The rest of a growth-cone step once the gradient g at p and the noise xi are
+// known: vector addition, normalisation (reciprocal square roots), advance
+// and stop tests.  p, d are updated
+// in place; returns false when the cone stops at this step.  src_xyz holds
+// source node coordinates as rows of src_stride (x row, y row, z row).
 // --------------------------------------------------------------------------
-template <int DIM, class Load>
-__device__ __forceinline__ bool cone_update(const FieldDesc &f, const ConeDesc &c, const Load &ld,
-                                            uint32_t axon, uint32_t step, float *p, float *d,
-                                            const float *src_xyz, int src_stride, int n_src)
+template <int DIM>
+__device__ __forceinline__ bool cone_finish_xi(const ConeDesc &c, const float *g, const float *xi, float *p,
+                                               float *d, const float *src_xyz, int src_stride, int n_src)
 {
-    float g[DIM];
-    sample_gradient<DIM>(f, c, p, ld, g);
     float gn2 = 0.f;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) gn2 = fmaf(g[i], g[i], gn2);
-    float ginv = (gn2 > c.eps2) ? 1.0f / sqrtf(gn2) : 0.0f;
-
-    float xi[DIM];
-    cone_noise<DIM>(c.key0, c.key1, axon, step, xi);
+    float ginv = (gn2 > c.eps2) ? rsqrtf(gn2) : 0.0f;
 
     float v[DIM], vn2 = 0.f;
 #pragma unroll
@@ -220,7 +266,7 @@ __device__ __forceinline__ bool cone_update(const FieldDesc &f, const ConeDesc &
     }
     float dn[DIM];
     if (vn2 > 1e-30f) {
-        float vinv = 1.0f / sqrtf(vn2);
+        float vinv = rsqrtf(vn2);
 #pragma unroll
         for (int i = 0; i < DIM; ++i) dn[i] = v[i] * vinv;
     } else {
@@ -256,6 +302,27 @@ __device__ __forceinline__ bool cone_update(const FieldDesc &f, const ConeDesc &
         }
     }
     return true;
+}
+
+// cone_finish_xi with the noise of (axon, step) drawn here.
+template <int DIM>
+__device__ __forceinline__ bool cone_finish(const ConeDesc &c, const float *g, uint32_t axon, uint32_t step,
+                                            float *p, float *d, const float *src_xyz, int src_stride, int n_src)
+{
+    float xi[DIM];
+    cone_noise<DIM>(c.key0, c.key1, axon, step, xi);
+    return cone_finish_xi<DIM>(c, g, xi, p, d, src_xyz, src_stride, n_src);
+}
+
+// One whole growth-cone step (gradient, then cone_finish).
+template <int DIM, class Load>
+__device__ __forceinline__ bool cone_update(const FieldDesc &f, const ConeDesc &c, const Load &ld,
+                                            uint32_t axon, uint32_t step, float *p, float *d,
+                                            const float *src_xyz, int src_stride, int n_src)
+{
+    float g[DIM];
+    sample_gradient<DIM>(f, c, p, ld, g);
+    return cone_finish<DIM>(c, g, axon, step, p, d, src_xyz, src_stride, n_src);
 }
 
 }  // namespace cue

@@ -239,8 +239,8 @@ constexpr int kConeSlots = 2;          // cones held in registers per thread
 
 __device__ __forceinline__ int tile_of(const FieldDesc &f, const FusedGeom &g, float px, float py)
 {
-    int ix = clampi((int)floorf(px / f.h), 0, f.nx - 1);
-    int iy = clampi((int)floorf(py / f.h), 0, f.ny - 1);
+    int ix = clampi((int)floorf(px * f.inv_h), 0, f.nx - 1);
+    int iy = clampi((int)floorf(py * f.inv_h), 0, f.ny - 1);
     return (iy / g.TY) * g.ntx + ix / g.TX;
 }
 
@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     int *t_row = t_col + kMaxTileSrc;
     float *t_e = reinterpret_cast<float *>(t_row + kMaxTileSrc);
     float *t_xy = t_e + kMaxTileSrc;                            // [2][kMaxTileSrc] tile sources
-    float *s_xy = t_xy + 2 * kMaxTileSrc;                       // [2][kMaxTileSrc] all sources
+    int *cid = reinterpret_cast<int *>(t_xy + 2 * kMaxTileSrc);   // [kThreads] slot-0 cone ids
+    float *nzb = reinterpret_cast<float *>(cid + kThreads);       // [2 parity][2][kThreads] noise
 
     const int t = blockIdx.x;
     const int tx = t % g.ntx, ty = t / g.ntx;
@@ -295,6 +296,19 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
             cdir[q][1] = A.dir[n + ca[q]];
         }
     }
+    // Noise of the slot-0 cones is drawn one sub-step ahead by the threads that
+    // hold no cone (it does not depend on the cone state), unless the tile is so
+    // full that few threads are free; the first sub-step's noise is drawn here,
+    // while the tile copy is in flight.
+    const int cnt0 = min(b1 - b0, kThreads);
+    const bool pre_noise = cnt0 > 0 && cnt0 <= kThreads - 64;
+    cid[tid] = ca[0];
+    if (pre_noise && ca[0] >= 0) {
+        float xi[2];
+        cone_noise<2>(A.c.key0, A.c.key1, (uint32_t)ca[0], A.step0, xi);
+        nzb[tid] = xi[0];
+        nzb[kThreads + tid] = xi[1];
+    }
 
     // point sources inside the loaded region, grouped by tile row
     const bool stop_on = A.cones_on && A.c.stop_r2 >= 0.0f && A.n_src > 0;
@@ -305,10 +319,6 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
             if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) atomicAdd(&row_fill[gy - oy], 1);
         } else if (t == 0) {
             flag_status(A.status, kStatusBounds);      // skipped, reported once per launch
-        }
-        if (stop_on && !g.local_stop) {
-            s_xy[s] = A.src_xyz[s];
-            s_xy[kMaxTileSrc + s] = A.src_xyz[A.n_src + s];
         }
     }
     __syncthreads();
@@ -364,7 +374,9 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     const int gxA = ox + colA, gxB = ox + colB;
     const float2 alpha2 = make_float2(f.alpha, f.alpha), beta2 = make_float2(f.beta, f.beta);
     const BandSources bsrc{t_col, t_row, t_e, row_start[r0], row_start[r0 + kBand]};
-    const float *stop_xy = g.local_stop ? t_xy : s_xy;
+    // source-stop list: this tile's sources when the halo covers the stop radius, else all
+    const float *stop_xy = g.local_stop ? t_xy : A.src_xyz;
+    const int stop_stride = g.local_stop ? kMaxTileSrc : A.n_src;
     const int n_stop = stop_on ? (g.local_stop ? row_start[kRows] : A.n_src) : 0;
     // walls: x walls by per-lane flags; y walls by a ghost row inside the loaded rows
     const LaneWalls lw{gxA == 0, gxA + 3 == f.nx - 1, gxB == 0, gxB + 3 == f.nx - 1};
@@ -389,6 +401,26 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
         return S[ly * kW + lx];
     };
 
+    auto ld_fast = [&](int i, int j, int) { return S[(j - oy) * kW + (i - ox)]; };
+    // one cone step on the shared-memory field (the plain kernel's arithmetic)
+    auto step_cone = [&](uint32_t a, uint32_t stp, float *p, float *d, const float *xi_in) {
+        int lo[2];
+        float fr[2], v[kPatch2], gr[2], xi[2];
+        cell_of<2>(f, p, lo, fr);
+        const bool inside = max(lo[0] - 1, 0) - ox >= 0 && min(lo[0] + 2, f.nx - 1) - ox < kW &&
+                            max(lo[1] - 1, 0) - oy >= 0 && min(lo[1] + 2, f.ny - 1) - oy < kRows;
+        if (inside) gather2(f, lo, ld_fast, v);
+        else gather2(f, lo, ld, v);
+        grad2(A.c, v, fr, gr);
+        if (xi_in) {
+            xi[0] = xi_in[0];
+            xi[1] = xi_in[1];
+        } else {
+            cone_noise<2>(A.c.key0, A.c.key1, a, stp, xi);
+        }
+        return cone_finish_xi<2>(A.c, gr, xi, p, d, stop_xy, stop_stride, n_stop);
+    };
+
     bool stopped[kConeSlots];
 #pragma unroll
     for (int q = 0; q < kConeSlots; ++q) stopped[q] = false;
@@ -396,12 +428,28 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     for (int j = 0; j < A.K; ++j) {
         const uint32_t step = A.step0 + j;
         // ---- phase A: cones of this tile read C^{n+j}
+        if (pre_noise && tid >= cnt0 && j + 1 < A.K) {     // free threads: next sub-step's noise
+            float *nz_next = nzb + ((j + 1) & 1) * 2 * kThreads;
+            for (int i = tid - cnt0; i < cnt0; i += kThreads - cnt0) {
+                float xi[2];
+                cone_noise<2>(A.c.key0, A.c.key1, (uint32_t)cid[i], step + 1, xi);
+                nz_next[i] = xi[0];
+                nz_next[kThreads + i] = xi[1];
+            }
+        }
 #pragma unroll
         for (int q = 0; q < kConeSlots; ++q) {
             count_active(A.counter, cl[q]);
             if (cl[q]) {
-                bool alive = cone_update<2>(f, A.c, ld, (uint32_t)ca[q], step, cp[q], cdir[q], stop_xy,
-                                            kMaxTileSrc, n_stop);
+                float xi_pre[2];
+                const float *xi_in = nullptr;
+                if (q == 0 && pre_noise) {
+                    const float *nz = nzb + (j & 1) * 2 * kThreads;
+                    xi_pre[0] = nz[tid];
+                    xi_pre[1] = nz[kThreads + tid];
+                    xi_in = xi_pre;
+                }
+                bool alive = step_cone((uint32_t)ca[q], step, cp[q], cdir[q], xi_in);
                 if (!alive) {
                     cl[q] = false;
                     stopped[q] = true;
@@ -416,7 +464,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
             if (live) {
                 float p[2] = {A.pos[a], A.pos[n + a]};
                 float d[2] = {A.dir[a], A.dir[n + a]};
-                bool alive = cone_update<2>(f, A.c, ld, (uint32_t)a, step, p, d, stop_xy, kMaxTileSrc, n_stop);
+                bool alive = step_cone((uint32_t)a, step, p, d, nullptr);
                 A.pos[a] = p[0];
                 A.pos[n + a] = p[1];
                 A.dir[a] = d[0];
@@ -586,7 +634,7 @@ int device_sm_count()
 size_t fused_smem_bytes(int R)
 {
     return 128 + (size_t)R * kW * sizeof(float) + sizeof(int) * (2 * R + 1) + sizeof(int) * 2 * kMaxTileSrc +
-           sizeof(float) * 5 * kMaxTileSrc;
+           sizeof(float) * 3 * kMaxTileSrc + sizeof(int) * kThreads + sizeof(float) * 4 * kThreads;
 }
 
 // Tile geometry for temporal depth K; returns false if the fused path cannot run.
