@@ -85,6 +85,8 @@ struct Sim {
     bool fused_used = false;
     long long bin_round = 0;
     alignas(64) unsigned char tmap[2][128];   // CUtensorMap per field buffer (as TMA source)
+    alignas(64) unsigned char tmap3[2][128];  // 3D plane maps of the field buffers
+    bool tmap3_ready = false;
 
     int *bin_count() const { return reinterpret_cast<int *>(ws + wl.bin_count_off); }
     int *bin_off() const { return reinterpret_cast<int *>(ws + wl.bin_off_off); }
@@ -118,5 +120,8 @@ cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout);
 cudaError_t launch_sources(Sim &s, float *Cout);
 cudaError_t launch_src_xyz(Sim &s);
 cudaError_t launch_cone_step(Sim &s, const float *C, uint32_t step);
+// 3D field step through the TMA plane pipeline (k_field3d.cu)
+bool field3d_tma_prepare(Sim &s);
+cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout);
 
 }  // namespace cue

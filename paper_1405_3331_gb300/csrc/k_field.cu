@@ -250,6 +250,11 @@ cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout)
         dim3 block(32, BY);
         if (map) field2d_vec4<true><<<grid, block, 0, s.stream>>>(f, Cin, Cout, s.src_map, rows, s.status());
         else field2d_vec4<false><<<grid, block, 0, s.stream>>>(f, Cin, Cout, nullptr, rows, s.status());
+    } else if (s.vec4 && f.dim == 3 && (Cin == s.field[0] || Cin == s.field[1]) && field3d_tma_prepare(s)) {
+        cudaError_t e = launch_field3d_tma(s, Cin == s.field[0] ? 0 : 1, Cout);
+        timing_end(s);
+        s.launches++;
+        return e;
     } else if (s.vec4 && f.dim == 3) {
         constexpr int BY = 8;
         const int nx4 = f.nx / 4;

@@ -10,6 +10,8 @@ from __future__ import annotations
 
 import ctypes as ct
 import os
+
+import numpy as np
 import threading
 from typing import Optional
 
@@ -224,10 +226,14 @@ class Simulation:
 
     ``workload`` is a :class:`paper_1405_3331_gb300.workloads.Workload` (or
     anything with the same attributes).  All buffers live on ``device``; the
-    library runs on ``stream`` (default: the current torch stream).
+    library runs on ``stream`` (default: the current torch stream).  ``field_offset``
+    places the two field buffers that many floats into their allocations; an offset
+    that is not a multiple of 4 breaks 16-byte alignment and so selects the any-size
+    kernels (used by the tests to compare kernels bit for bit).
     """
 
-    def __init__(self, workload, device="cuda:0", stream=None, path: int = CUE_PATH_AUTO):
+    def __init__(self, workload, device="cuda:0", stream=None, path: int = CUE_PATH_AUTO,
+                 field_offset: int = 0):
         import torch
         self.torch = torch
         self.w = workload
@@ -241,8 +247,11 @@ class Simulation:
                                 wl.grad_eps, wl.wall_mode, 0, wl.seed & 0xFFFFFFFFFFFFFFFF)
         dev = self.device
         with torch.cuda.device(dev):
-            self.fields = [torch.as_tensor(wl.field0(), device=dev).contiguous(),
-                           torch.empty(shape, dtype=torch.float32, device=dev)]
+            n_cells = int(np.prod(shape))
+            self._field_store = [torch.empty(n_cells + field_offset, dtype=torch.float32, device=dev)
+                                 for _ in range(2)]
+            self.fields = [st[field_offset:].view(shape) for st in self._field_store]
+            self.fields[0].copy_(torch.as_tensor(wl.field0()))
             self.src_cell = torch.as_tensor(wl.src_cell, dtype=torch.int32, device=dev)
             self.src_emit = torch.as_tensor(wl.src_emit, dtype=torch.float32, device=dev)
             self.src_map = (None if wl.src_map is None else
