@@ -14,4 +14,6 @@ from .oracle import (  # noqa: F401
     field_step,
     cone_step,
     run,
+    endpoint_loss,
+    adjoint,
 )

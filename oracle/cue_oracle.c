@@ -67,6 +67,7 @@
 #include <math.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 typedef struct {
@@ -357,4 +358,263 @@ void orc_run(const orc_grid *g, const orc_cone *cp, double *C, double *work,
         orc_field_step(g, C, work, src_cell, src_emit, n_src, src_map);
         memcpy(C, work, (size_t)nn * sizeof(double));
     }
+}
+
+/* ------------------------------------------------------------------------
+ * Adjoint of the endpoint loss  L = (1/n) sum_a |p_a^T - t_a|^2  with respect
+ * to D, lambda, the per-step emissions e_k and the rate map M, for the
+ * no-stopping workload (wall mode 1 = clamp, no source stop).  The field does
+ * not depend on the cones; the cones read C^n through the gradient sample.
+ *
+ * Forward, stored: C^n and (p^n, d^n) for n = 0..T.
+ * Backward, n = T-1 .. 0, with pbar/dbar = dL/dp^{n+1}, dL/dd^{n+1} and
+ * mu = dL/dC^{n+1} on entry:
+ *   parameter terms of C^{n+1} = C^n + alpha lap(C^n) - lambda dt C^n + s:
+ *     dL/dD      += (dt/h^2) <mu, lap(C^n)>
+ *     dL/dlambda -= dt <mu, C^n>
+ *     dL/de_k    += mu[cell_k]
+ *     dL/dM_i    += dt mu_i
+ *   field:  mu <- A mu   (A = I + alpha lap - lambda dt, symmetric)
+ *   cones:  back through p' = clamp(p + l d'), d' = v/|v|,
+ *           v = w_p d + w_g g/|g| + w_n xi, g = grad C^n (p); the sampled
+ *           gradient is linear in C^n, so its adjoint adds into mu (now
+ *           dL/dC^n), and bilinear in p, so it adds into pbar.
+ * Written from the derivation above; pinned by central finite differences of
+ * the forward loss (tests).
+ * ---------------------------------------------------------------------- */
+static void lap_apply(const orc_grid *g, const double *x, double *out)
+{
+    const int nx = g->nx, ny = g->ny, nz = (g->dim == 3) ? g->nz : 1;
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t c = i + j * sy + k * sz;
+                double xi = x[c], s = 0.0;
+                if (i > 0) s += x[c - 1] - xi;
+                if (i < nx - 1) s += x[c + 1] - xi;
+                if (j > 0) s += x[c - sy] - xi;
+                if (j < ny - 1) s += x[c + sy] - xi;
+                if (g->dim == 3) {
+                    if (k > 0) s += x[c - sz] - xi;
+                    if (k < nz - 1) s += x[c + sz] - xi;
+                }
+                out[c] = s;
+            }
+}
+
+/* Backward through one clamp-mode cone step of cone a (2D or 3D). */
+static void cone_step_adjoint(const orc_grid *g, const orc_cone *cp, const double *C, uint32_t step,
+                              uint32_t a, const double *p, const double *d, double *pbar, double *dbar,
+                              double *mu)
+{
+    const int dim = g->dim;
+    const double eps2 = cp->grad_eps * cp->grad_eps;
+    /* recompute the forward step */
+    int lo[3] = {0, 0, 0};
+    double f[3] = {0, 0, 0};
+    for (int ax = 0; ax < dim; ++ax) {
+        double s = p[ax] / g->h;
+        int i0 = (int)floor(s);
+        i0 = clampi(i0, 0, extent(g, ax) - 2);
+        lo[ax] = i0;
+        f[ax] = s - (double)i0;
+    }
+    const int kc = (dim == 3) ? 2 : 1;
+    double gn[8][3], w[8], dw[8][3];
+    int corner[8][3];
+    int nc = 0;
+    double gr[3] = {0, 0, 0};
+    for (int dk = 0; dk < kc; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                double wx = di ? f[0] : 1.0 - f[0], wy = dj ? f[1] : 1.0 - f[1];
+                double wz = (dim == 3) ? (dk ? f[2] : 1.0 - f[2]) : 1.0;
+                double sx = di ? 1.0 : -1.0, sy = dj ? 1.0 : -1.0, sz = dk ? 1.0 : -1.0;
+                corner[nc][0] = lo[0] + di;
+                corner[nc][1] = lo[1] + dj;
+                corner[nc][2] = lo[2] + dk;
+                orc_node_gradient(g, C, corner[nc][0], corner[nc][1], corner[nc][2], gn[nc]);
+                w[nc] = wx * wy * wz;
+                dw[nc][0] = sx * wy * wz / g->h;      /* d w / d p_x */
+                dw[nc][1] = wx * sy * wz / g->h;
+                dw[nc][2] = (dim == 3) ? wx * wy * sz / g->h : 0.0;
+                for (int k = 0; k < 3; ++k) gr[k] += w[nc] * gn[nc][k];
+                ++nc;
+            }
+    double gn2 = 0.0;
+    for (int k = 0; k < dim; ++k) gn2 += gr[k] * gr[k];
+    double gnorm = sqrt(gn2), ghat[3] = {0, 0, 0};
+    int has_g = gn2 > eps2;
+    if (has_g)
+        for (int k = 0; k < dim; ++k) ghat[k] = gr[k] / gnorm;
+    double xi[3];
+    orc_noise(cp->seed, a, step, dim, xi);
+    double v[3] = {0, 0, 0}, vn2 = 0.0;
+    for (int k = 0; k < dim; ++k) {
+        v[k] = cp->w_prev * d[k] + cp->w_grad * ghat[k] + cp->w_noise * xi[k];
+        vn2 += v[k] * v[k];
+    }
+    double vn = sqrt(vn2), dn[3] = {d[0], d[1], d[2]};
+    int has_v = vn2 > 1e-30;
+    if (has_v)
+        for (int k = 0; k < dim; ++k) dn[k] = v[k] / vn;
+    double qbar[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+        double q = p[k] + cp->step_len * dn[k];
+        double hi = (extent(g, k) - 1) * g->h;
+        qbar[k] = (q < 0.0 || q > hi) ? 0.0 : pbar[k];
+    }
+    /* back through d' = v/|v| (or d' = d) */
+    double dnbar[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) dnbar[k] = dbar[k] + cp->step_len * qbar[k];
+    double vbar[3] = {0, 0, 0}, dbar_out[3] = {0, 0, 0};
+    if (has_v) {
+        double dot = 0.0;
+        for (int k = 0; k < dim; ++k) dot += dn[k] * dnbar[k];
+        for (int k = 0; k < dim; ++k) vbar[k] = (dnbar[k] - dn[k] * dot) / vn;
+        for (int k = 0; k < dim; ++k) dbar_out[k] = cp->w_prev * vbar[k];
+    } else {
+        for (int k = 0; k < dim; ++k) dbar_out[k] = dnbar[k];
+    }
+    /* back through ghat = g/|g| */
+    double gbar[3] = {0, 0, 0};
+    if (has_g) {
+        double dot = 0.0;
+        for (int k = 0; k < dim; ++k) dot += ghat[k] * cp->w_grad * vbar[k];
+        for (int k = 0; k < dim; ++k) gbar[k] = (cp->w_grad * vbar[k] - ghat[k] * dot) / gnorm;
+    }
+    /* back through the sample: position (bilinear weights) and field (node differences) */
+    double pbar_out[3] = {qbar[0], qbar[1], qbar[2]};
+    const double inv2h = 1.0 / (2.0 * g->h);
+    int nz = (dim == 3) ? g->nz : 1;
+    for (int c = 0; c < nc; ++c) {
+        for (int m = 0; m < dim; ++m)
+            for (int k = 0; k < dim; ++k) pbar_out[m] += gbar[k] * dw[c][m] * gn[c][k];
+        int i = corner[c][0], j = corner[c][1], kk = corner[c][2];
+        for (int k = 0; k < dim; ++k) {
+            double coef = gbar[k] * w[c] * inv2h;
+            int ip[3] = {i, j, kk}, im[3] = {i, j, kk};
+            int ext = extent(g, k);
+            if (k == 2) ext = nz;
+            ip[k] = clampi(ip[k] + 1, 0, ext - 1);
+            im[k] = clampi(im[k] - 1, 0, ext - 1);
+            mu[(int64_t)ip[0] + (int64_t)g->nx * ((int64_t)ip[1] + (int64_t)g->ny * ip[2])] += coef;
+            mu[(int64_t)im[0] + (int64_t)g->nx * ((int64_t)im[1] + (int64_t)g->ny * im[2])] -= coef;
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        pbar[k] = (k < dim) ? pbar_out[k] : 0.0;
+        dbar[k] = (k < dim) ? dbar_out[k] : 0.0;
+    }
+}
+
+/* Forward T clamp-mode steps from (C0, pos0, dir0), then the adjoint.
+ * Returns the loss; writes dL/dD, dL/dlambda, dL/de_k (n_src), dL/dM (cells).
+ * pos0/dir0/targets are SoA [dim][n].  Memory: (T+1) fields and cone states. */
+double orc_adjoint(const orc_grid *g, const orc_cone *cp, const double *C0,
+                   const int32_t *src_cell, const double *src_emit, int n_src, const double *src_map,
+                   int n, const double *pos0, const double *dir0, const double *targets, int T,
+                   double *gD, double *glam, double *gsrc, double *gmap, double *Cs, double *Ps, double *Ds,
+                   double *work)
+{
+    const int dim = g->dim;
+    const int64_t nn = nodes_of(g);
+    const size_t cs = (size_t)dim * n;
+    uint8_t *act = (uint8_t *)work;                  /* n bytes (all stay active) */
+    double *mu = (double *)((uint8_t *)work + ((n + 15) / 16) * 16);
+    double *mu2 = mu + nn, *lapC = mu2 + nn;
+    /* forward, storing every state */
+    memcpy(Cs, C0, (size_t)nn * sizeof(double));
+    memcpy(Ps, pos0, cs * sizeof(double));
+    memcpy(Ds, dir0, cs * sizeof(double));
+    for (int a = 0; a < n; ++a) act[a] = 1;
+    for (int s = 0; s < T; ++s) {
+        memcpy(Ps + (size_t)(s + 1) * cs, Ps + (size_t)s * cs, cs * sizeof(double));
+        memcpy(Ds + (size_t)(s + 1) * cs, Ds + (size_t)s * cs, cs * sizeof(double));
+        orc_cone_step(g, cp, Cs + (size_t)s * nn, (uint32_t)s, n, Ps + (size_t)(s + 1) * cs,
+                      Ds + (size_t)(s + 1) * cs, act, src_cell, n_src);
+        orc_field_step(g, Cs + (size_t)s * nn, Cs + (size_t)(s + 1) * nn, src_cell, src_emit, n_src, src_map);
+    }
+    /* loss and its adjoint at T */
+    double loss = 0.0;
+    const double *PT = Ps + (size_t)T * cs;
+    double *pbar = (double *)malloc(cs * sizeof(double)), *dbar = (double *)malloc(cs * sizeof(double));
+    for (int a = 0; a < n; ++a)
+        for (int k = 0; k < dim; ++k) {
+            double e = PT[(size_t)k * n + a] - targets[(size_t)k * n + a];
+            loss += e * e;
+            pbar[(size_t)k * n + a] = 2.0 * e / n;
+            dbar[(size_t)k * n + a] = 0.0;
+        }
+    loss /= n;
+    const double alpha_dD = g->dt / (g->h * g->h);
+    *gD = 0.0;
+    *glam = 0.0;
+    for (int s = 0; s < n_src; ++s) gsrc[s] = 0.0;
+    for (int64_t c = 0; c < nn; ++c) gmap[c] = 0.0;
+    for (int64_t c = 0; c < nn; ++c) mu[c] = 0.0;          /* dL/dC^T = 0 */
+    const double alpha = g->D * g->dt / (g->h * g->h), decay = g->lambda * g->dt;
+    for (int s = T - 1; s >= 0; --s) {
+        const double *Cn = Cs + (size_t)s * nn;
+        /* parameter terms with mu = dL/dC^{s+1} */
+        lap_apply(g, Cn, lapC);
+        double sD = 0.0, sL = 0.0;
+        for (int64_t c = 0; c < nn; ++c) {
+            sD += mu[c] * lapC[c];
+            sL += mu[c] * Cn[c];
+            gmap[c] += g->dt * mu[c];
+        }
+        *gD += alpha_dD * sD;
+        *glam -= g->dt * sL;
+        for (int k = 0; k < n_src; ++k) gsrc[k] += mu[src_cell[k]];
+        /* field: mu <- A mu */
+        lap_apply(g, mu, mu2);
+        for (int64_t c = 0; c < nn; ++c) mu2[c] = mu[c] + alpha * mu2[c] - decay * mu[c];
+        memcpy(mu, mu2, (size_t)nn * sizeof(double));
+        /* cones of step s: pbar/dbar from step s+1 to step s, and dL/dC^s */
+        const double *P = Ps + (size_t)s * cs, *Dd = Ds + (size_t)s * cs;
+        for (int a = 0; a < n; ++a) {
+            double p[3] = {0, 0, 0}, d[3] = {0, 0, 0}, pb[3] = {0, 0, 0}, db[3] = {0, 0, 0};
+            for (int k = 0; k < dim; ++k) {
+                p[k] = P[(size_t)k * n + a];
+                d[k] = Dd[(size_t)k * n + a];
+                pb[k] = pbar[(size_t)k * n + a];
+                db[k] = dbar[(size_t)k * n + a];
+            }
+            cone_step_adjoint(g, cp, Cn, (uint32_t)s, (uint32_t)a, p, d, pb, db, mu);
+            for (int k = 0; k < dim; ++k) {
+                pbar[(size_t)k * n + a] = pb[k];
+                dbar[(size_t)k * n + a] = db[k];
+            }
+        }
+    }
+    free(pbar);
+    free(dbar);
+    return loss;
+}
+
+/* Loss of the forward run alone (for finite differences). */
+double orc_endpoint_loss(const orc_grid *g, const orc_cone *cp, const double *C0,
+                         const int32_t *src_cell, const double *src_emit, int n_src, const double *src_map,
+                         int n, const double *pos0, const double *dir0, const double *targets, int T)
+{
+    const int dim = g->dim;
+    const int64_t nn = nodes_of(g);
+    double *C = (double *)malloc((size_t)nn * sizeof(double)), *W = (double *)malloc((size_t)nn * sizeof(double));
+    double *P = (double *)malloc((size_t)dim * n * sizeof(double)), *D = (double *)malloc((size_t)dim * n * sizeof(double));
+    uint8_t *act = (uint8_t *)malloc((size_t)n + 1);
+    memcpy(C, C0, (size_t)nn * sizeof(double));
+    memcpy(P, pos0, (size_t)dim * n * sizeof(double));
+    memcpy(D, dir0, (size_t)dim * n * sizeof(double));
+    for (int a = 0; a < n; ++a) act[a] = 1;
+    orc_run(g, cp, C, W, 0, T, src_cell, src_emit, n_src, src_map, n, P, D, act);
+    double loss = 0.0;
+    for (int a = 0; a < n; ++a)
+        for (int k = 0; k < dim; ++k) {
+            double e = P[(size_t)k * n + a] - targets[(size_t)k * n + a];
+            loss += e * e;
+        }
+    free(C); free(W); free(P); free(D); free(act);
+    return loss / n;
 }

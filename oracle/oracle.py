@@ -105,6 +105,12 @@ def _load():
                                           ct.c_int, P, P, P, P, ct.c_int]
             lib.orc_run.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, ct.c_uint32,
                                     ct.c_int, P, P, ct.c_int, P, ct.c_int, P, P, P]
+            lib.orc_adjoint.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, P, ct.c_int, P, ct.c_int,
+                                        P, P, P, ct.c_int, P, P, P, P, P, P, P, P]
+            lib.orc_adjoint.restype = ct.c_double
+            lib.orc_endpoint_loss.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, P, ct.c_int, P,
+                                              ct.c_int, P, P, P, ct.c_int]
+            lib.orc_endpoint_loss.restype = ct.c_double
             for f in ("orc_philox_many", "orc_noise_many", "orc_node_gradient",
                       "orc_gradient_many", "orc_field_step", "orc_cone_step", "orc_run"):
                 getattr(lib, f).restype = None
@@ -215,3 +221,39 @@ def run(grid: Grid, cone: Cone, C, step0, nsteps, src_cell=(), src_emit=(), src_
                     _ptr(cell), _ptr(emit), cell.shape[0], _ptr(smap), n,
                     _ptr(pos), _ptr(dirs), _ptr(act))
     return C, pos, dirs, act
+
+
+def endpoint_loss(grid: Grid, cone: Cone, C0, src_cell, src_emit, src_map, pos, dir, targets, nsteps):
+    """Forward loss (1/n) sum_a |p_a^T - t_a|^2 of a clamp-mode run."""
+    C0 = _f64(C0)
+    cell, emit = _src(src_cell, src_emit)
+    smap = None if src_map is None else _f64(src_map)
+    pos, dirs, tg = _f64(pos), _f64(dir), _f64(targets)
+    g, c = grid._c(), cone._c()
+    return float(_load().orc_endpoint_loss(ct.byref(g), ct.byref(c), _ptr(C0), _ptr(cell), _ptr(emit),
+                                           cell.shape[0], _ptr(smap), pos.shape[1], _ptr(pos), _ptr(dirs),
+                                           _ptr(tg), int(nsteps)))
+
+
+def adjoint(grid: Grid, cone: Cone, C0, src_cell, src_emit, src_map, pos, dir, targets, nsteps):
+    """FP64 adjoint of endpoint_loss: returns (loss, dL/dD, dL/dlambda, dL/de (n_src,),
+    dL/dM (field-shaped)).  Stores every state: small problems only."""
+    C0 = _f64(C0)
+    cell, emit = _src(src_cell, src_emit)
+    smap = _f64(np.zeros(C0.shape) if src_map is None else src_map)
+    pos, dirs, tg = _f64(pos), _f64(dir), _f64(targets)
+    n = pos.shape[1]
+    nn = C0.size
+    T = int(nsteps)
+    Cs = np.empty((T + 1) * nn)
+    Ps = np.empty((T + 1) * pos.size)
+    Ds = np.empty((T + 1) * pos.size)
+    work = np.zeros(((n + 15) // 16) * 16 + 3 * nn * 8, dtype=np.uint8)
+    gD, gl = ct.c_double(), ct.c_double()
+    gsrc = np.zeros(cell.shape[0])
+    gmap = np.zeros(C0.shape)
+    g, c = grid._c(), cone._c()
+    loss = _load().orc_adjoint(ct.byref(g), ct.byref(c), _ptr(C0), _ptr(cell), _ptr(emit), cell.shape[0],
+                               _ptr(smap), n, _ptr(pos), _ptr(dirs), _ptr(tg), T, ct.byref(gD), ct.byref(gl),
+                               _ptr(gsrc), _ptr(gmap), _ptr(Cs), _ptr(Ps), _ptr(Ds), _ptr(work))
+    return float(loss), gD.value, gl.value, gsrc, gmap
