@@ -385,6 +385,10 @@ def main():
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": tot / reps}
 
+    # adjoint workload: gradients of the endpoint loss against the forward run's own time
+    if w.targets is not None and w.wall_mode == 1 and rank == 0:
+        line["adjoint"] = adjoint_timing(cue, torch, sim, w, reset, stream, flush, total_ms / args.steps)
+
     # HBM probe: plain field kernel on 2D 8192^2 (256 MiB per buffer), never L2-resident
     if not args.no_probe and rank == 0:
         line["hbm_probe"] = hbm_probe(cue, torch, dev, hbm)
@@ -401,6 +405,28 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def adjoint_timing(cue, torch, sim, w, reset, stream, flush, forward_ms):
+    """Time sim_adjoint (forward with checkpoints every 64 steps, recompute, adjoint) on the
+    same workload; the ratio divides by the timed forward run."""
+    k = 64
+    reset()
+    sim.adjoint(w.targets, w.nsteps, k)          # warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+    reset()
+    e0.record(stream)
+    g = sim.adjoint(w.targets, w.nsteps, k)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"ms_per_run": ms, "forward_ms_per_run": forward_ms, "ratio_to_forward": ms / forward_ms,
+            "ckpt_every": k, "loss": float(g["loss"]), "dL_dD": float(g["dD"]),
+            "dL_dlambda": float(g["dlambda"]), "dL_de_max": float(g["dsrc"].abs().max()),
+            "dL_dM_max": float(g["dmap"].abs().max())}
 
 
 def launches_per_run(sim, w):

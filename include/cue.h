@@ -151,6 +151,42 @@ int cone_step(cue_sim *sim, int32_t nsteps);
  * field counters to be equal (else CUE_ERR_STATE); advances both. */
 int sim_run(cue_sim *sim, int32_t nsteps);
 
+/*
+ * sim_adjoint: gradients of the endpoint loss
+ *     L = (1/n_axons) sum_a |p_a(T) - t_a|^2,   T = current step + nsteps,
+ * with respect to D, lambda, the per-step source emissions e_k and the rate
+ * map M (dL/dM_i; pass d_gmap = NULL to skip).  Needs a run without stopping:
+ * cone_params.wall_mode = 1 (clamp) and stop_radius <= 0 (else CUE_ERR_ARG),
+ * because stopping is a discrete event without a derivative.
+ *
+ * The call runs the coupled model nsteps forward from the handle's state,
+ * keeping (C, p, d) every ckpt_every steps, computes L, then walks back: each
+ * segment is recomputed storing every step, and the adjoint field
+ * mu = dL/dC^n is advanced backwards with the (symmetric) field operator while
+ * the cone adjoint -- back through the clamp, the step length, the
+ * normalisation Jacobians and the multilinear gradient sample -- scatters into
+ * it.  Parameter gradients: dL/dD = dt/h^2 sum_n <mu^{n+1}, lap C^n>,
+ * dL/dlambda = -dt sum_n <mu^{n+1}, C^n>, dL/de_k = sum_n mu^{n+1}[cell_k],
+ * dL/dM = dt sum_n mu^{n+1}.
+ *
+ *   d_targets : dim*n_axons floats (SoA, like pos)
+ *   d_adj_ws  : >= cue_adjoint_workspace_bytes(...) bytes, 256-byte aligned,
+ *               caller-owned (checkpoints, one recomputed segment, adjoint
+ *               state)
+ *   outputs   : d_gD, d_glambda, d_loss one float each; d_gsrc n_src floats;
+ *               d_gmap nx*ny(*nz) floats or NULL
+ * On return (asynchronously) the handle is at step + nsteps, as after
+ * sim_run(nsteps).  Errors: CUE_ERR_ARG, CUE_ERR_STATE, CUE_ERR_WORKSPACE,
+ * CUE_ERR_CUDA.  Derivation: the model of the calls above (Sec. 3.5, 5.2);
+ * the paper itself computes no gradients.
+ */
+int sim_adjoint(cue_sim *sim, const float *d_targets, int32_t nsteps, int32_t ckpt_every, void *d_adj_ws,
+                size_t adj_ws_bytes, float *d_gD, float *d_glambda, float *d_gsrc, float *d_gmap, float *d_loss);
+
+/* Bytes of adjoint workspace sim_adjoint needs (0 for invalid arguments). */
+size_t cue_adjoint_workspace_bytes(const cue_params *params, int32_t n_src, int32_t n_axons, int32_t nsteps,
+                                   int32_t ckpt_every);
+
 /* Step counters and the index (0 = d_field_a, 1 = d_field_b) of the buffer
  * that holds the current field. */
 int cue_get_state(const cue_sim *sim, int64_t *field_step, int64_t *cone_step_out,

@@ -511,12 +511,15 @@ static void cone_step_adjoint(const orc_grid *g, const orc_cone *cp, const doubl
 
 /* Forward T clamp-mode steps from (C0, pos0, dir0), then the adjoint.
  * Returns the loss; writes dL/dD, dL/dlambda, dL/de_k (n_src), dL/dM (cells).
- * pos0/dir0/targets are SoA [dim][n].  Memory: (T+1) fields and cone states. */
+ * pos0/dir0/targets are SoA [dim][n].  Memory: (T+1) fields and cone states.
+ * state_binary32 != 0 stores every forward state (field, positions, directions) rounded to
+ * binary32: a perturbation of exactly the size single-precision storage makes, used by the
+ * tests to measure how strongly a case's gradients depend on it.  0 is the oracle proper. */
 double orc_adjoint(const orc_grid *g, const orc_cone *cp, const double *C0,
                    const int32_t *src_cell, const double *src_emit, int n_src, const double *src_map,
                    int n, const double *pos0, const double *dir0, const double *targets, int T,
                    double *gD, double *glam, double *gsrc, double *gmap, double *Cs, double *Ps, double *Ds,
-                   double *work)
+                   double *work, int state_binary32)
 {
     const int dim = g->dim;
     const int64_t nn = nodes_of(g);
@@ -535,6 +538,14 @@ double orc_adjoint(const orc_grid *g, const orc_cone *cp, const double *C0,
         orc_cone_step(g, cp, Cs + (size_t)s * nn, (uint32_t)s, n, Ps + (size_t)(s + 1) * cs,
                       Ds + (size_t)(s + 1) * cs, act, src_cell, n_src);
         orc_field_step(g, Cs + (size_t)s * nn, Cs + (size_t)(s + 1) * nn, src_cell, src_emit, n_src, src_map);
+        if (state_binary32) {
+            double *Cn = Cs + (size_t)(s + 1) * nn, *Pn = Ps + (size_t)(s + 1) * cs, *Dn = Ds + (size_t)(s + 1) * cs;
+            for (int64_t i = 0; i < nn; ++i) Cn[i] = (double)(float)Cn[i];
+            for (size_t i = 0; i < cs; ++i) {
+                Pn[i] = (double)(float)Pn[i];
+                Dn[i] = (double)(float)Dn[i];
+            }
+        }
     }
     /* loss and its adjoint at T */
     double loss = 0.0;

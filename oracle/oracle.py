@@ -106,7 +106,7 @@ def _load():
             lib.orc_run.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, ct.c_uint32,
                                     ct.c_int, P, P, ct.c_int, P, ct.c_int, P, P, P]
             lib.orc_adjoint.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, P, ct.c_int, P, ct.c_int,
-                                        P, P, P, ct.c_int, P, P, P, P, P, P, P, P]
+                                        P, P, P, ct.c_int, P, P, P, P, P, P, P, P, ct.c_int]
             lib.orc_adjoint.restype = ct.c_double
             lib.orc_endpoint_loss.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, P, ct.c_int, P,
                                               ct.c_int, P, P, P, ct.c_int]
@@ -235,9 +235,13 @@ def endpoint_loss(grid: Grid, cone: Cone, C0, src_cell, src_emit, src_map, pos, 
                                            _ptr(tg), int(nsteps)))
 
 
-def adjoint(grid: Grid, cone: Cone, C0, src_cell, src_emit, src_map, pos, dir, targets, nsteps):
+def adjoint(grid: Grid, cone: Cone, C0, src_cell, src_emit, src_map, pos, dir, targets, nsteps,
+            state_binary32=False):
     """FP64 adjoint of endpoint_loss: returns (loss, dL/dD, dL/dlambda, dL/de (n_src,),
-    dL/dM (field-shaped)).  Stores every state: small problems only."""
+    dL/dM (field-shaped)).  Stores every state: small problems only.
+
+    ``state_binary32`` rounds each stored forward state to binary32 (a measuring knob for
+    the tests: how far single-precision storage alone moves the gradients)."""
     C0 = _f64(C0)
     cell, emit = _src(src_cell, src_emit)
     smap = _f64(np.zeros(C0.shape) if src_map is None else src_map)
@@ -255,5 +259,6 @@ def adjoint(grid: Grid, cone: Cone, C0, src_cell, src_emit, src_map, pos, dir, t
     g, c = grid._c(), cone._c()
     loss = _load().orc_adjoint(ct.byref(g), ct.byref(c), _ptr(C0), _ptr(cell), _ptr(emit), cell.shape[0],
                                _ptr(smap), n, _ptr(pos), _ptr(dirs), _ptr(tg), T, ct.byref(gD), ct.byref(gl),
-                               _ptr(gsrc), _ptr(gmap), _ptr(Cs), _ptr(Ps), _ptr(Ds), _ptr(work))
+                               _ptr(gsrc), _ptr(gmap), _ptr(Cs), _ptr(Ps), _ptr(Ds), _ptr(work),
+                               1 if state_binary32 else 0)
     return float(loss), gD.value, gl.value, gsrc, gmap

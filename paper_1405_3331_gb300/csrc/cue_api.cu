@@ -94,6 +94,24 @@ static void timing_free(Sim &s)
     s.ev_stop.clear();
 }
 
+int run_coupled(Sim &s, int nsteps)
+{
+    int rc = run_fused_if_supported(s, nsteps);
+    if (rc != 1) return rc;       // handled (0 = ok, < 0 = error)
+    s.fused_used = false;
+    for (int k = 0; k < nsteps; ++k) {
+        float *in = s.field[s.cur], *out = s.field[s.cur ^ 1];
+        cudaError_t e = launch_cone_step(s, in, (uint32_t)s.cone_step);
+        if (e == cudaSuccess) e = launch_field_step(s, in, out);
+        if (e == cudaSuccess) e = launch_sources(s, out);
+        if (e != cudaSuccess) return CUE_ERR_CUDA;
+        s.cur ^= 1;
+        s.field_step++;
+        s.cone_step++;
+    }
+    return CUE_OK;
+}
+
 }  // namespace cue
 
 using namespace cue;
@@ -255,20 +273,29 @@ int sim_run(cue_sim *s, int32_t nsteps)
     if (!s || nsteps < 0) return CUE_ERR_ARG;
     if (s->cone_step != s->field_step) return CUE_ERR_STATE;
     if (s->field_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
-    int rc = run_fused_if_supported(*s, nsteps);
-    if (rc != 1) return rc;       // handled (0 = ok, < 0 = error)
-    s->fused_used = false;
-    for (int k = 0; k < nsteps; ++k) {
-        float *in = s->field[s->cur], *out = s->field[s->cur ^ 1];
-        cudaError_t e = launch_cone_step(*s, in, (uint32_t)s->cone_step);
-        if (e == cudaSuccess) e = launch_field_step(*s, in, out);
-        if (e == cudaSuccess) e = launch_sources(*s, out);
-        if (e != cudaSuccess) return CUE_ERR_CUDA;
-        s->cur ^= 1;
-        s->field_step++;
-        s->cone_step++;
-    }
-    return CUE_OK;
+    return run_coupled(*s, nsteps);
+}
+
+size_t cue_adjoint_workspace_bytes(const cue_params *params, int32_t n_src, int32_t n_axons, int32_t nsteps,
+                                   int32_t ckpt_every)
+{
+    if (!params_ok(params) || n_src < 0 || n_axons < 0) return 0;
+    cue_params p = *params;
+    if (p.dim == 2) p.nz = 1;
+    return adjoint_workspace_bytes(p, n_src, n_axons, nsteps, ckpt_every);
+}
+
+int sim_adjoint(cue_sim *s, const float *d_targets, int32_t nsteps, int32_t ckpt_every, void *d_adj_ws,
+                size_t adj_ws_bytes, float *d_gD, float *d_glambda, float *d_gsrc, float *d_gmap, float *d_loss)
+{
+    if (!s || nsteps <= 0 || ckpt_every <= 0) return CUE_ERR_ARG;
+    if (!d_gD || !d_glambda || !d_loss || (s->n_src > 0 && !d_gsrc) || (s->n_axons > 0 && !d_targets))
+        return CUE_ERR_ARG;
+    if (s->cone.wall_mode != 1 || s->cd.stop_r2 >= 0.0f) return CUE_ERR_ARG;   // needs a run without stopping
+    if (s->cone_step != s->field_step) return CUE_ERR_STATE;
+    if (s->field_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
+    return run_adjoint(*s, d_targets, nsteps, ckpt_every, d_adj_ws, adj_ws_bytes, d_gD, d_glambda, d_gsrc, d_gmap,
+                       d_loss);
 }
 
 int cue_get_state(const cue_sim *s, int64_t *field_step, int64_t *cone_step_out, int32_t *cur_buffer)

@@ -115,11 +115,20 @@ int field_fused_if_supported(Sim &s, int nsteps);
 void timing_begin(Sim &s);
 void timing_end(Sim &s);
 
+// ---- coupled steps without the public entry point's checks (cue_api.cu)
+int run_coupled(Sim &s, int nsteps);
+// ---- adjoint (k_adjoint.cu)
+size_t adjoint_workspace_bytes(const cue_params &p, int n_src, int n_axons, int nsteps, int ckpt_every);
+int run_adjoint(Sim &s, const float *targets, int nsteps, int ckpt_every, void *ws, size_t ws_bytes, float *gD,
+                float *gl, float *gsrc, float *gmap, float *loss);
+
 // ---- launchers (each returns cudaGetLastError() after its launches) ----
 cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout);
 cudaError_t launch_sources(Sim &s, float *Cout);
 cudaError_t launch_src_xyz(Sim &s);
 cudaError_t launch_cone_step(Sim &s, const float *C, uint32_t step);
+cudaError_t launch_cone_step_io(Sim &s, const float *C, uint32_t step, const float *pin, const float *din,
+                                float *pout, float *dout);
 // 3D field step through the TMA plane pipeline (k_field3d.cu)
 bool field3d_tma_prepare(Sim &s);
 cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout);

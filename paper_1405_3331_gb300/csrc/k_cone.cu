@@ -14,10 +14,13 @@ namespace {
 
 constexpr int kMaxSmemSources = 2048;   // [3][2048] floats = 24 KiB
 
+// State is read from (pin, din) and written to (pout, dout); the coupled run
+// passes the same arrays for both, the adjoint's recompute passes the next
+// stored step.
 template <int DIM>
 __global__ void __launch_bounds__(256) cone_plain(FieldDesc f, ConeDesc c, const float *__restrict__ C,
-                                                  uint32_t step, int n, float *__restrict__ pos,
-                                                  float *__restrict__ dir, uint8_t *__restrict__ active,
+                                                  uint32_t step, int n, const float *pin, const float *din,
+                                                  float *pout, float *dout, uint8_t *__restrict__ active,
                                                   const float *__restrict__ src_xyz, int n_src,
                                                   unsigned *status, unsigned long long *counter)
 {
@@ -38,8 +41,8 @@ __global__ void __launch_bounds__(256) cone_plain(FieldDesc f, ConeDesc c, const
     float p[DIM], d[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-        p[i] = pos[(size_t)i * n + a];
-        d[i] = dir[(size_t)i * n + a];
+        p[i] = pin[(size_t)i * n + a];
+        d[i] = din[(size_t)i * n + a];
     }
     const size_t sy = f.nx, sz = (size_t)f.nx * f.ny;
     auto ld = [&](int i, int j, int k) { return __ldg(C + (size_t)i + sy * j + sz * k); };
@@ -49,8 +52,8 @@ __global__ void __launch_bounds__(256) cone_plain(FieldDesc f, ConeDesc c, const
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-        pos[(size_t)i * n + a] = p[i];
-        dir[(size_t)i * n + a] = d[i];
+        pout[(size_t)i * n + a] = p[i];
+        dout[(size_t)i * n + a] = d[i];
         bad |= !(fabsf(p[i]) <= 3.402823466e38f) || !(fabsf(d[i]) <= 3.402823466e38f);
     }
     if (!alive) active[a] = 0;
@@ -59,18 +62,24 @@ __global__ void __launch_bounds__(256) cone_plain(FieldDesc f, ConeDesc c, const
 
 }  // namespace
 
-cudaError_t launch_cone_step(Sim &s, const float *C, uint32_t step)
+cudaError_t launch_cone_step_io(Sim &s, const float *C, uint32_t step, const float *pin, const float *din,
+                                float *pout, float *dout)
 {
     if (s.n_axons == 0) return cudaSuccess;
     const int blocks = (s.n_axons + 255) / 256;
     if (s.fd.dim == 2)
-        cone_plain<2><<<blocks, 256, 0, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, s.pos, s.dir, s.active,
+        cone_plain<2><<<blocks, 256, 0, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, pin, din, pout, dout, s.active,
                                                     s.src_xyz(), s.n_src, s.status(), s.cone_counter());
     else
-        cone_plain<3><<<blocks, 256, 0, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, s.pos, s.dir, s.active,
+        cone_plain<3><<<blocks, 256, 0, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, pin, din, pout, dout, s.active,
                                                     s.src_xyz(), s.n_src, s.status(), s.cone_counter());
     s.launches++;
     return cudaGetLastError();
+}
+
+cudaError_t launch_cone_step(Sim &s, const float *C, uint32_t step)
+{
+    return launch_cone_step_io(s, C, step, s.pos, s.dir, s.pos, s.dir);
 }
 
 }  // namespace cue

@@ -42,7 +42,7 @@ CUE_PATH_FUSED = 2
 EXPORTED = ("cue_workspace_bytes", "cue_init", "cue_step", "cone_step", "sim_run", "cue_get_state",
             "cue_set_state", "cue_set_stream", "cue_set_option", "cue_launch_count", "cue_status",
             "cue_destroy", "cue_strerror", "cue_kernel_time", "cue_cone_updates", "cue_get_option", "sim_run_static",
-            "cue_static_scratch_bytes")
+            "cue_static_scratch_bytes", "sim_adjoint", "cue_adjoint_workspace_bytes")
 
 
 class cue_params(ct.Structure):
@@ -96,6 +96,10 @@ def lib():
             L.sim_run_static.argtypes = [ct.POINTER(cue_params), ct.POINTER(cone_params), P, P, P, P, I32, P,
                                          P, P, P, I32, I64, I32, P, ct.POINTER(I32)]
             L.sim_run_static.restype = ct.c_int
+            L.sim_adjoint.argtypes = [P, P, I32, I32, P, SZ, P, P, P, P, P]
+            L.sim_adjoint.restype = ct.c_int
+            L.cue_adjoint_workspace_bytes.argtypes = [ct.POINTER(cue_params), I32, I32, I32, I32]
+            L.cue_adjoint_workspace_bytes.restype = SZ
             L.cue_static_scratch_bytes.argtypes = []
             L.cue_static_scratch_bytes.restype = SZ
             L.cue_launch_count.argtypes = [P]
@@ -205,6 +209,17 @@ def sim_run_static(params: cue_params, cone: cone_params, field_a: int, field_b:
                               src_map or None, pos, dir, active, n_axons, step0, nsteps, stream or None,
                               ct.byref(cur))
     return rc, cur.value
+
+
+def cue_adjoint_workspace_bytes(params: cue_params, n_src: int, n_axons: int, nsteps: int,
+                                ckpt_every: int) -> int:
+    return int(lib().cue_adjoint_workspace_bytes(ct.byref(params), n_src, n_axons, nsteps, ckpt_every))
+
+
+def sim_adjoint(h, targets: int, nsteps: int, ckpt_every: int, ws: int, ws_bytes: int, gD: int, glam: int,
+                gsrc: int, gmap: int, loss: int) -> int:
+    return lib().sim_adjoint(h, targets, nsteps, ckpt_every, ws, ws_bytes, gD, glam, gsrc or None,
+                             gmap or None, loss)
 
 
 def cue_static_scratch_bytes() -> int:
@@ -353,6 +368,29 @@ class Simulation:
         fs, cs, cur = self.state()
         return (self.fields[cur].cpu().numpy(), self.pos.cpu().numpy(), self.dir.cpu().numpy(),
                 self.active.cpu().numpy(), fs, cs)
+
+    def adjoint(self, targets, nsteps: int, ckpt_every: int = 64, want_map: bool = True):
+        """Gradients of L = mean_a |p_a(T) - t_a|^2 after ``nsteps`` more steps (no-stopping
+        runs only).  Returns a dict of device tensors: loss, dD, dlambda, dsrc, dmap (or None).
+        The handle advances by ``nsteps``, as with sim_run."""
+        torch = self.torch
+        dev = self.device
+        tg = torch.as_tensor(targets, dtype=torch.float32, device=dev).contiguous()
+        nbytes = cue_adjoint_workspace_bytes(self.params, self.n_src, self.n_axons, nsteps, ckpt_every)
+        if nbytes == 0:
+            raise CueError(CUE_ERR_ARG, "cue_adjoint_workspace_bytes")
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        ws_ptr = (ws.data_ptr() + 255) & ~255
+        out = {k: torch.zeros((), dtype=torch.float32, device=dev) for k in ("loss", "dD", "dlambda")}
+        out["dsrc"] = torch.zeros(max(self.n_src, 1), dtype=torch.float32, device=dev)
+        out["dmap"] = torch.zeros(self.fields[0].shape, dtype=torch.float32, device=dev) if want_map else None
+        rc = sim_adjoint(self.h, tg.data_ptr(), nsteps, ckpt_every, ws_ptr, nbytes, out["dD"].data_ptr(),
+                         out["dlambda"].data_ptr(), out["dsrc"].data_ptr() if self.n_src else 0,
+                         out["dmap"].data_ptr() if want_map else 0, out["loss"].data_ptr())
+        _check(rc, "sim_adjoint")
+        self._adj_keep = (ws, tg)            # keep the buffers alive until the stream has used them
+        out["dsrc"] = out["dsrc"][: self.n_src]
+        return out
 
     def run_host(self, C, pos, dir, active, nsteps: int, out=None):
         """End-to-end call from host memory: copy the state in (pinned host tensors copy

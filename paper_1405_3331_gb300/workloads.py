@@ -128,7 +128,8 @@ def make(name, dim, nx, ny, nz=1, *, h=1.0, D=1.0, lam=0.01, dt=0.2, n_src=4, em
          n_axons=64, stop_radius=0.0, wall_mode=0, nsteps=1, seed=0, philox_seed=None,
          src_map=False, targets=False, C0=None, w=(0.5, 0.4, 0.1), step_len=0.5,
          grad_eps=1e-15) -> Workload:
-    """Draw one workload.  ``C0`` may be None (zeros), 'random' (U[0,1]) or 'smooth'."""
+    """Draw one workload.  ``C0`` may be None (zeros), 'random' (U[0,1]), 'smooth' or 'ramp';
+    ``src_map`` may be False (none), True / 'random' (U[0,1] per node) or 'zeros'."""
     rng = np.random.default_rng(seed)
     nz = nz if dim == 3 else 1
     extents = (nx, ny, nz)[:dim]
@@ -142,13 +143,20 @@ def make(name, dim, nx, ny, nz=1, *, h=1.0, D=1.0, lam=0.01, dt=0.2, n_src=4, em
     pos = _positions(rng, extents, h, n_axons, avoid=src_xy, radius=stop_radius)
     dirs = _directions(rng, dim, n_axons)
     shape = (nz, ny, nx) if dim == 3 else (ny, nx)
-    smap = rng.uniform(0.0, 1.0, shape).astype(np.float32) if src_map else None
+    if src_map == "zeros":
+        smap = np.zeros(shape, np.float32)
+    elif src_map:                                   # True or "random": U[0, 1] per node
+        smap = rng.uniform(0.0, 1.0, shape).astype(np.float32)
+    else:
+        smap = None
     tg = _positions(rng, extents, h, n_axons).astype(np.float32) if targets else None
     if isinstance(C0, str):
         if C0 == "random":
             C0 = rng.uniform(0.0, 1.0, shape).astype(np.float32)
         elif C0 == "smooth":
             C0 = _smooth_field(rng, shape)
+        elif C0 == "ramp":
+            C0 = _ramp_field(rng, shape)
         else:
             raise ValueError(C0)
     return Workload(
@@ -176,6 +184,22 @@ def _smooth_field(rng, shape):
     return out.astype(np.float32)
 
 
+def _ramp_field(rng, shape):
+    """A tilted plane of slope 0.05 per node along a random direction, plus bumps too shallow
+    (slope below 0.005) to create a local maximum: a cue field with no interior critical point."""
+    grids = np.meshgrid(*[np.arange(s, dtype=np.float64) for s in shape], indexing="ij")
+    axis = rng.standard_normal(len(shape))
+    axis /= np.linalg.norm(axis)
+    out = 1.0 + 0.05 * sum(a * (g - 0.5 * (s - 1)) for a, g, s in zip(axis, grids, shape))
+    out -= out.min() - 0.5
+    for _ in range(4):
+        centre = [rng.uniform(0, s) for s in shape]
+        width = 0.25 * max(shape)
+        r2 = sum((g - c) ** 2 for g, c in zip(grids, centre))
+        out += 0.005 * width * np.sqrt(np.e) * rng.uniform(0.2, 1.0) * np.exp(-r2 / (2.0 * width * width))
+    return out.astype(np.float32)
+
+
 # ---------------------------------------------------------------- configs
 def config_c1(seed=0) -> Workload:
     return make("c1-2d-128", 2, 128, 128, h=1.0, D=1.0, lam=0.01, dt=0.2, n_src=4,
@@ -194,9 +218,12 @@ def config_c3(seed=2) -> Workload:
 
 
 def config_c5(seed=4, n=1024, n_src=32, n_axons=4096, nsteps=2000) -> Workload:
+    """Adjoint workload.  The dense rate map is the learnable per-node source term and its
+    gradient is taken at M = 0 (a white-noise map makes the field rough and the cone paths
+    chaotic, so the endpoint loss has no useful derivative)."""
     return make(f"c5-adjoint-2d-{n}", 2, n, n, h=1.0, D=1.0, lam=0.01, dt=0.2, n_src=n_src,
                 emit=(0.5, 2.0), n_axons=n_axons, wall_mode=1, nsteps=nsteps, seed=seed,
-                philox_seed=5, src_map=True, targets=True)
+                philox_seed=5, src_map="zeros", targets=True)
 
 
 def config_c4(seed=3, n_instances=512, nsteps=1000) -> List[Workload]:

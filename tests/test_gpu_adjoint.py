@@ -1,0 +1,214 @@
+"""sim_adjoint (FP32 forward, FP64 adjoint field, through the C ABI) vs the FP64 oracle
+adjoint and vs FP64 central finite differences of the oracle's forward loss.
+
+How close an FP32 forward pass can bring the gradient to the FP64 one depends on the
+problem, not only on the code: a cone that climbs to a cue maximum or reaches a point
+source circles it, and there the gradient direction turns within a cell, so a rounding
+difference of 1e-7 in a position grows by 10^3-10^4 over the circling and moves the
+derivative of the endpoint loss by 1e-3 to 1e-1.  Each test therefore first measures, with
+the oracle alone, how far its own gradients move when the inputs are perturbed at the size
+of the rounding an FP32 run accumulates (``_spread``):
+
+* well-conditioned cases (spread well under the bar) must match the oracle and central
+  differences to ADJ_RTOL = 1e-4;
+* the adjoint workload's own setting (cue front growing from C = 0, 200 steps) is compared
+  within max(ADJ_RTOL, BAND x spread): the GPU must land inside the oracle's own band.  The
+  kernels round each value a handful of times per step where the binary32-storage run of the
+  oracle rounds it once; k independent roundings add up to about sqrt(k) times one, and
+  k <= 25, hence BAND = 5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1405_3331_gb300 import workloads as W
+from parity import cone_of, grid_of
+
+pytestmark = pytest.mark.gpu
+
+ADJ_RTOL = 1e-4
+U32 = 2.0 ** -24          # FP32 unit roundoff
+BAND = 5.0
+
+
+@pytest.fixture(scope="module")
+def cue():
+    from paper_1405_3331_gb300 import build
+    build.build()
+    from paper_1405_3331_gb300 import cue as binding
+    return binding
+
+
+def _copy64(seed=50, nsteps=200):
+    """The adjoint workload's 64x64 copy: 2 sources, 64 cones, wall clamp, targets, C0 = 0."""
+    return W.config_c5(seed=seed, n=64, n_src=2, n_axons=64, nsteps=nsteps)
+
+
+def _ramp2d(seed=59):
+    """2D cue field on a tilted plane (no interior maximum) with weak sources: no cone
+    circles a critical point within 80 steps, so the derivative is well conditioned."""
+    return W.make("adj2d-ramp", 2, 64, 48, n_src=3, emit=(0.02, 0.05), n_axons=64, C0="ramp",
+                  seed=seed, wall_mode=1, src_map="zeros", targets=True)
+
+
+def _gpu(cue, w, nsteps, k):
+    sim = cue.Simulation(w)
+    g = sim.adjoint(w.targets, nsteps, k)
+    sim.check()
+    out = {key: (None if v is None else v.cpu().numpy()) for key, v in g.items()}
+    sim.close()
+    return out
+
+
+def _oracle(w, nsteps, pos=None, C0=None, D=None, lam=None, binary32=False):
+    grid = oracle.Grid(w.dim, w.nx, w.ny, w.nz if w.dim == 3 else 1, h=w.h,
+                       D=w.D if D is None else D, lam=w.lam if lam is None else lam, dt=w.dt)
+    return oracle.adjoint(grid, cone_of(w), w.field0().astype(np.float64) if C0 is None else C0,
+                          w.src_cell, w.src_emit, w.src_map, w.pos if pos is None else pos, w.dir,
+                          w.targets, nsteps, state_binary32=binary32)
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-30)
+
+
+def _relmax(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+KEYS = ("dD", "dlambda", "dsrc", "dmap")
+
+
+def _spread(w, T, ref):
+    """Largest relative change of each oracle gradient under perturbations of the size FP32
+    makes: every forward state stored in binary32 (the oracle's ``state_binary32`` run), and
+    the initial positions, the initial field, D and lambda perturbed by delta = sqrt(T) * u32
+    relative (the rounding a T-step run accumulates if per-step errors add like a random walk)."""
+    delta = np.sqrt(T) * U32
+    pos0 = w.pos.astype(np.float64)
+    C0 = w.field0().astype(np.float64)
+    runs = [_oracle(w, T, binary32=True)]
+    for s in range(2):
+        rng = np.random.default_rng(1000 + s)
+        runs.append(_oracle(w, T, pos=pos0 * (1 + delta * rng.standard_normal(pos0.shape)),
+                            C0=C0 * (1 + delta * rng.standard_normal(C0.shape))))
+    runs.append(_oracle(w, T, D=w.D * (1 + delta)))
+    runs.append(_oracle(w, T, lam=w.lam * (1 + delta)))
+    return {k: max(_relmax(r[i + 1], ref[i + 1]) for r in runs) for i, k in enumerate(KEYS)}
+
+
+def _check_strict(g, ref):
+    loss, gD, gl, gsrc, gmap = ref
+    assert _rel(float(g["loss"]), loss) < 1e-5
+    assert _rel(float(g["dD"]), gD) < ADJ_RTOL
+    assert _rel(float(g["dlambda"]), gl) < ADJ_RTOL
+    assert _relmax(g["dsrc"], gsrc) < ADJ_RTOL
+    assert _relmax(g["dmap"], gmap) < ADJ_RTOL
+
+
+def test_adjoint_2d_well_conditioned_matches_oracle(cue):
+    w, T = _ramp2d(), 80
+    ref = _oracle(w, T)
+    spread = _spread(w, T, ref)
+    assert max(spread.values()) < ADJ_RTOL / 3, spread       # precondition on the case
+    _check_strict(_gpu(cue, w, T, 16), ref)
+
+
+def test_adjoint_2d_matches_finite_differences(cue):
+    """GPU gradients against central differences of the FP64 oracle's loss (relative steps
+    inside the linear regime), on the well-conditioned 2D case: D, lambda, every emission,
+    and the rate map at its largest-gradient node, at a source node and at a random node."""
+    w, T = _ramp2d(), 80
+    g = _gpu(cue, w, T, 16)
+    c = cone_of(w)
+    C0 = w.field0().astype(np.float64)
+
+    def loss(D=w.D, lam=w.lam, emit=w.src_emit, smap=w.src_map):
+        grid = oracle.Grid(2, w.nx, w.ny, h=w.h, D=D, lam=lam, dt=w.dt)
+        return oracle.endpoint_loss(grid, c, C0, w.src_cell, emit, smap, w.pos, w.dir, w.targets, T)
+
+    hD, hl = 1e-6 * w.D, 1e-5 * w.lam
+    assert _rel(float(g["dD"]), (loss(D=w.D + hD) - loss(D=w.D - hD)) / (2 * hD)) < ADJ_RTOL
+    assert _rel(float(g["dlambda"]), (loss(lam=w.lam + hl) - loss(lam=w.lam - hl)) / (2 * hl)) < ADJ_RTOL
+    for k in range(w.n_src):
+        e1, e2 = w.src_emit.astype(np.float64).copy(), w.src_emit.astype(np.float64).copy()
+        h = 1e-5 * e1[k]
+        e1[k] += h
+        e2[k] -= h
+        assert _rel(float(g["dsrc"][k]), (loss(emit=e1) - loss(emit=e2)) / (2 * h)) < ADJ_RTOL
+    rng = np.random.default_rng(7)
+    nodes = {int(np.argmax(np.abs(g["dmap"]))), int(w.src_cell[0]), int(rng.integers(w.n_cells))}
+    for node in nodes:
+        m1, m2 = w.src_map.astype(np.float64).copy(), w.src_map.astype(np.float64).copy()
+        m1.flat[node] += 1e-4
+        m2.flat[node] -= 1e-4
+        fd = (loss(smap=m1) - loss(smap=m2)) / 2e-4
+        assert abs(float(g["dmap"].flat[node]) - fd) <= ADJ_RTOL * np.abs(g["dmap"]).max(), node
+
+
+@pytest.mark.parametrize("seed", [50, 51])
+def test_adjoint_front_workload_within_the_oracle_band(cue, seed):
+    """The adjoint workload's 64x64 copy over 200 steps: the loss to 1e-5; each gradient
+    within max(ADJ_RTOL, BAND x the oracle's own spread).  With C0 = 0 and M = 0 the loss does
+    not change when every emission is scaled alike, so sum_k e_k dL/de_k = 0 and dL/de is the
+    small remainder of terms that cancel: its band is wider than that of dD.  In seed 51
+    cones circle a source and every band is wide."""
+    w, T = _copy64(seed=seed), 200
+    ref = _oracle(w, T)
+    spread = _spread(w, T, ref)
+    g = _gpu(cue, w, T, 64)
+    assert _rel(float(g["loss"]), ref[0]) < 1e-5
+    for i, k in enumerate(KEYS):
+        tol = max(ADJ_RTOL, BAND * spread[k])
+        assert _relmax(g[k], ref[i + 1]) <= tol, (k, _relmax(g[k], ref[i + 1]), tol)
+    for cell in w.src_cell:                          # source-node map entries, one by one
+        tol = max(ADJ_RTOL, BAND * spread["dmap"] * np.abs(ref[4]).max() / abs(ref[4].flat[cell]))
+        assert _rel(float(g["dmap"].flat[cell]), ref[4].flat[cell]) < tol
+
+
+def test_adjoint_3d_matches_oracle(cue):
+    w = W.make("adj3d", 3, 20, 16, 12, dt=0.15, n_src=3, n_axons=40, C0="smooth", seed=52, wall_mode=1,
+               src_map=True, targets=True)
+    T = 60
+    ref = _oracle(w, T)
+    spread = _spread(w, T, ref)
+    assert max(spread.values()) < ADJ_RTOL / 3, spread
+    _check_strict(_gpu(cue, w, T, 16), ref)
+
+
+@pytest.mark.parametrize("k", [1, 7, 200])
+def test_checkpoint_interval_does_not_change_the_gradients(cue, k):
+    w = _copy64(seed=53, nsteps=100)
+    ref = _gpu(cue, w, 100, 64)
+    g = _gpu(cue, w, 100, k)
+    for key in ("loss", "dD", "dlambda"):
+        assert _rel(float(g[key]), float(ref[key])) < 1e-6
+    assert np.abs(g["dmap"] - ref["dmap"]).max() <= 1e-6 * np.abs(ref["dmap"]).max()
+
+
+def test_autograd_function_gives_the_adjoint_gradients(cue):
+    import torch
+    from paper_1405_3331_gb300.autograd import endpoint_loss
+    w = _copy64(seed=54, nsteps=80)
+    dev = torch.device("cuda:0")
+    D = torch.tensor(w.D, dtype=torch.float32, device=dev, requires_grad=True)
+    lam = torch.tensor(w.lam, dtype=torch.float32, device=dev, requires_grad=True)
+    emit = torch.as_tensor(w.src_emit, device=dev).clone().requires_grad_(True)
+    smap = torch.as_tensor(w.src_map, device=dev).clone().requires_grad_(True)
+    L = endpoint_loss(D, lam, emit, smap, w, w.targets, 80, 16)
+    (3.0 * L).backward()
+    ref = _gpu(cue, w, 80, 16)
+    assert _rel(float(L.detach()), float(ref["loss"])) < 1e-6
+    assert _rel(float(D.grad), 3 * float(ref["dD"])) < 1e-5
+    assert _rel(float(lam.grad), 3 * float(ref["dlambda"])) < 1e-5
+    np.testing.assert_allclose(emit.grad.cpu().numpy(), 3 * ref["dsrc"], rtol=1e-5)
+    np.testing.assert_allclose(smap.grad.cpu().numpy(), 3 * ref["dmap"], rtol=1e-5, atol=1e-12)
+
+
+def test_adjoint_refuses_runs_that_stop(cue):
+    w = W.make("stop", 2, 32, 32, n_src=2, n_axons=8, C0="smooth", seed=55, targets=True)   # wall stop
+    sim = cue.Simulation(w)
+    with pytest.raises(cue.CueError) as e:
+        sim.adjoint(w.targets, 10, 4)
+    assert e.value.code == cue.CUE_ERR_ARG

@@ -42,7 +42,7 @@ def _case(name):
         return W.make(name, 3, 33, 17, 9, dt=0.15, n_src=3, n_axons=200, C0="smooth", seed=16)
     if name == "c5-map-1024-clamp":
         return W.make(name, 2, 1024, 1024, n_src=32, n_axons=4096, C0="smooth", seed=17,
-                      src_map=True, wall_mode=1)
+                      src_map="random", wall_mode=1)
     if name == "c2-2048":
         w = W.config_c2()
         w.C0 = W._smooth_field(np.random.default_rng(18), w.shape)

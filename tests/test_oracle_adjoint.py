@@ -85,3 +85,26 @@ def test_no_gradient_weight_means_no_parameter_gradient():
     loss, gD, gl, gsrc, gmap = oracle.adjoint(g, c0, C0, cells, emit, smap, pos, d, tg, T)
     assert gD == 0.0 and gl == 0.0
     assert np.all(gsrc == 0.0) and np.all(gmap == 0.0)
+
+
+def test_binary32_storage_knob_only_rounds_the_stored_states():
+    """``state_binary32`` (a measuring knob) leaves the oracle proper untouched, and moves
+    a well-conditioned gradient by no more than binary32 rounding of the states can."""
+    g, c, C0, cells, emit, smap, pos, d, tg, T = _problem(2, seed=5)
+    a = oracle.adjoint(g, c, C0, cells, emit, smap, pos, d, tg, T)
+    b = oracle.adjoint(g, c, C0, cells, emit, smap, pos, d, tg, T, state_binary32=False)
+    r = oracle.adjoint(g, c, C0, cells, emit, smap, pos, d, tg, T, state_binary32=True)
+    assert a[0] == b[0] and a[1] == b[1] and np.array_equal(a[4], b[4])
+    assert r[0] != a[0]
+    assert r[0] == pytest.approx(a[0], rel=1e-5)
+    assert r[1] == pytest.approx(a[1], rel=1e-3)
+    # with states already in binary32 and exactly representable steps the knob changes nothing
+    c_still = Cone(w_prev=1.0, w_grad=0.0, w_noise=0.0, step_len=0.5, wall_mode=1, seed=77)
+    d_axis = np.zeros_like(d)
+    d_axis[0] = 1.0
+    pos32 = np.round(pos * 4) / 4
+    C0z = np.zeros_like(C0)
+    x = oracle.adjoint(g, c_still, C0z, cells[:0], emit[:0], np.zeros_like(smap), pos32, d_axis, tg, T)
+    y = oracle.adjoint(g, c_still, C0z, cells[:0], emit[:0], np.zeros_like(smap), pos32, d_axis, tg, T,
+                       state_binary32=True)
+    assert x[0] == y[0]
