@@ -102,8 +102,7 @@ int run_coupled(Sim &s, int nsteps)
     for (int k = 0; k < nsteps; ++k) {
         float *in = s.field[s.cur], *out = s.field[s.cur ^ 1];
         cudaError_t e = launch_cone_step(s, in, (uint32_t)s.cone_step);
-        if (e == cudaSuccess) e = launch_field_step(s, in, out);
-        if (e == cudaSuccess) e = launch_sources(s, out);
+        if (e == cudaSuccess) e = launch_field_and_sources(s, in, out);
         if (e != cudaSuccess) return CUE_ERR_CUDA;
         s.cur ^= 1;
         s.field_step++;
@@ -247,8 +246,7 @@ int cue_step(cue_sim *s, int32_t nsteps)
     s->fused_used = false;
     for (int k = 0; k < nsteps; ++k) {
         float *in = s->field[s->cur], *out = s->field[s->cur ^ 1];
-        cudaError_t e = launch_field_step(*s, in, out);
-        if (e == cudaSuccess) e = launch_sources(*s, out);
+        cudaError_t e = launch_field_and_sources(*s, in, out);
         if (e != cudaSuccess) return CUE_ERR_CUDA;
         s->cur ^= 1;
         s->field_step++;

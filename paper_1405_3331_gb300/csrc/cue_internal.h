@@ -123,7 +123,11 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int ckpt_every, void *
                 float *gl, float *gsrc, float *gmap, float *loss);
 
 // ---- launchers (each returns cudaGetLastError() after its launches) ----
-cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout);
+// One field step Cin -> Cout.  With `sources_done` non-null the kernel may also
+// add the point sources; *sources_done tells whether it did.
+cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout, bool *sources_done = nullptr);
+// Field step followed by the point sources (in the same kernel where it can).
+cudaError_t launch_field_and_sources(Sim &s, const float *Cin, float *Cout);
 cudaError_t launch_sources(Sim &s, float *Cout);
 cudaError_t launch_src_xyz(Sim &s);
 cudaError_t launch_cone_step(Sim &s, const float *C, uint32_t step);

@@ -16,6 +16,12 @@
 // Memory: the forward keeps (C, p, d) every ckpt_every steps; each segment is
 // recomputed with the plain kernels, storing every step, then walked
 // backwards (two kernels per step).
+//
+// Precision: the adjoint field is double-float (two FP32 planes carried with
+// error-free transformations, so GB300 runs it at FP32 rate); the cone adjoint
+// and the per-thread partial sums are FP32; block totals of the dD and dlambda
+// sums, the per-source sums and the segment totals of the rate-map sum are
+// FP64.
 #include <algorithm>
 
 #include "cue_internal.h"
@@ -25,6 +31,13 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+__device__ __forceinline__ float warp_sumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -32,66 +45,238 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Block sum of two doubles, added once per block to acc[0], acc[1].
-__device__ __forceinline__ void block_add2(double a, double b, double *acc)
+// Block sum of two per-thread FP32 partials: warps sum in FP32, the block
+// total is formed and added to acc[0], acc[1] in FP64 (GB300's FP64 rate is a
+// small fraction of its FP32 rate, so FP64 is kept to a few operations per
+// block).  Every thread of the block must call it.
+__device__ __forceinline__ void block_add2(float a, float b, double *acc)
 {
-    __shared__ double sa[32], sb[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    a = warp_sum(a);
-    b = warp_sum(b);
+    __shared__ float sa[32], sb[32];
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = t & 31, warp = t >> 5;
+    a = warp_sumf(a);
+    b = warp_sumf(b);
     if (lane == 0) {
         sa[warp] = a;
         sb[warp] = b;
     }
     __syncthreads();
     if (warp == 0) {
-        const int nw = (blockDim.x + 31) / 32;
-        a = lane < nw ? sa[lane] : 0.0;
-        b = lane < nw ? sb[lane] : 0.0;
-        a = warp_sum(a);
-        b = warp_sum(b);
+        const int nw = (blockDim.x * blockDim.y + 31) / 32;
+        double da = lane < nw ? (double)sa[lane] : 0.0;
+        double db = lane < nw ? (double)sb[lane] : 0.0;
+        da = warp_sum(da);
+        db = warp_sum(db);
         if (lane == 0) {
-            atomicAdd(&acc[0], a);
-            atomicAdd(&acc[1], b);
+            atomicAdd(&acc[0], da);
+            atomicAdd(&acc[1], db);
         }
     }
 }
 
-// mu_out = A mu_in;  acc[0] += <lap(mu_in), C>;  acc[1] += <mu_in, C>;  S += mu_in.
-// The adjoint field is carried in FP64: cones near the diffusion front, where
-// |grad C| is tiny, inject contributions of order 1/|grad C| that cancel in
-// these sums, and FP32 would lose them.
-__global__ void __launch_bounds__(256) adj_field_kernel(FieldDesc f, const double *__restrict__ mu_in,
-                                                        double *__restrict__ mu_out, const float *__restrict__ C,
-                                                        double *S, double *acc)
+// ---- double-float arithmetic (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2):
+// a value is an unevaluated sum hi + lo of two floats, and sums and products
+// carry their rounding error forward with error-free transformations, all in
+// FP32.  The explicit _rn intrinsics keep the compiler from contracting them.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+    return {s, e};
+}
+
+__device__ __forceinline__ DF quick_two_sum(float a, float b)      // |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// (a + b) with an absolute error of a few u^2 (|a| + |b|), u = 2^-24.
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    DF s = two_sum(a.hi, b.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+// a * c for a float c.
+__device__ __forceinline__ DF df_mul(DF a, float c)
+{
+    const float p = __fmul_rn(a.hi, c);
+    const float e = fmaf(a.lo, c, fmaf(a.hi, c, -p));
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_of(float hi, float lo) { return two_sum(hi, lo); }   // renormalise
+
+// atomically mu += c as a double-float: the float atomic returns the old high
+// part, from which this thread recovers the exact rounding error of the
+// addition (round-to-nearest, as the atomic rounds) and adds it to the low
+// plane.  Whatever the order of the atomics, hi + sum(lo) stays the exact sum
+// up to the low plane's own rounding.
+__device__ __forceinline__ void atomic_add_df(float *hi, float *lo, float c)
+{
+    const float old = atomicAdd(hi, c);
+    const float e = two_sum(old, c).lo;
+    if (e != 0.0f) atomicAdd(lo, e);
+}
+
+// One backward field step on an nx % 4 == 0 2D grid, laid out like the
+// forward's float4 kernel (32 lanes x 4 nodes in x, 8 warps of `rows` rows):
+//   mu_out = A mu_in (A is the forward stencil: the no-flux operator is
+//   symmetric),  acc[0] += <lap(mu_in), C>,  acc[1] += <mu_in, C>,
+//   Sseg += mu_in (the rate-map sum of this segment).
+// mu is double-float: a buffer holds the high plane, then the low plane.
+// Cones near the diffusion front, where |grad C| is tiny, scatter large
+// contributions of opposite sign into neighbouring nodes that the stencil
+// then cancels; a single float would keep only their rounding errors.
+__device__ __forceinline__ DF df_update(DF m, DF l, DF r, DF u, DF d, float alpha, float beta, float *lap)
+{
+    const DF sum = df_add(df_add(l, r), df_add(u, d));
+    const DF lp = df_add(sum, df_mul(m, -4.0f));
+    *lap = lp.hi + lp.lo;
+    return df_add(df_mul(m, beta), df_mul(sum, alpha));
+}
+
+__global__ void __launch_bounds__(256) adj_field2d_vec4(FieldDesc f, const float *__restrict__ mu_in,
+                                                        float *__restrict__ mu_out, const float *__restrict__ C,
+                                                        float *Sseg, double *acc, int rows)
+{
+    const int lane = threadIdx.x;
+    const int nx4 = f.nx >> 2;
+    const size_t cells = (size_t)f.nx * f.ny;
+    const int x4 = blockIdx.x * 32 + lane;
+    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * rows;
+    const bool act = x4 < nx4 && y0 < f.ny;
+    const int y1 = min(y0 + rows, f.ny);
+    const int x = x4 * 4;
+    const bool has_l = x > 0, has_r = x + 4 < f.nx;
+    const float4 *hi4 = reinterpret_cast<const float4 *>(mu_in);
+    const float4 *lo4 = reinterpret_cast<const float4 *>(mu_in + cells);
+    const float4 *c4 = reinterpret_cast<const float4 *>(C);
+    float4 *ohi4 = reinterpret_cast<float4 *>(mu_out);
+    float4 *olo4 = reinterpret_cast<float4 *>(mu_out + cells);
+    float4 *s4 = reinterpret_cast<float4 *>(Sseg);
+    float tD = 0.f, tL = 0.f;
+    if (y0 < f.ny) {                               // warp-uniform
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto row = [&](int y, float4 &h, float4 &l) {
+            h = __ldg(hi4 + (size_t)y * nx4 + x4);
+            l = __ldg(lo4 + (size_t)y * nx4 + x4);
+        };
+        float4 ch = z4, cl = z4, uh, ul;
+        if (act) row(y0, ch, cl);
+        uh = ch;
+        ul = cl;
+        if (act && y0 > 0) row(y0 - 1, uh, ul);
+        for (int y = y0; y < y1; ++y) {
+            float4 dh = ch, dl = cl;
+            if (act && y + 1 < f.ny) row(y + 1, dh, dl);
+            float lh = __shfl_up_sync(kFull, ch.w, 1), ll = __shfl_up_sync(kFull, cl.w, 1);
+            float rh = __shfl_down_sync(kFull, ch.x, 1), rl = __shfl_down_sync(kFull, cl.x, 1);
+            if (lane == 0) {
+                const bool e = act && has_l;
+                lh = e ? __ldg(mu_in + (size_t)y * f.nx + x - 1) : ch.x;
+                ll = e ? __ldg(mu_in + cells + (size_t)y * f.nx + x - 1) : cl.x;
+            }
+            if (lane == 31) {
+                const bool e = act && has_r;
+                rh = e ? __ldg(mu_in + (size_t)y * f.nx + x + 4) : ch.w;
+                rl = e ? __ldg(mu_in + cells + (size_t)y * f.nx + x + 4) : cl.w;
+            }
+            if (!has_l) {
+                lh = ch.x;
+                ll = cl.x;
+            }
+            if (!has_r) {
+                rh = ch.w;
+                rl = cl.w;
+            }
+            if (act) {
+                const size_t at = (size_t)y * nx4 + x4;
+                const float4 c = __ldg(c4 + at);
+                const DF m0 = df_of(ch.x, cl.x), m1 = df_of(ch.y, cl.y), m2 = df_of(ch.z, cl.z),
+                         m3 = df_of(ch.w, cl.w);
+                float L0, L1, L2, L3;
+                const DF o0 = df_update(m0, df_of(lh, ll), m1, df_of(uh.x, ul.x), df_of(dh.x, dl.x), f.alpha,
+                                        f.beta, &L0);
+                const DF o1 = df_update(m1, m0, m2, df_of(uh.y, ul.y), df_of(dh.y, dl.y), f.alpha, f.beta, &L1);
+                const DF o2 = df_update(m2, m1, m3, df_of(uh.z, ul.z), df_of(dh.z, dl.z), f.alpha, f.beta, &L2);
+                const DF o3 = df_update(m3, m2, df_of(rh, rl), df_of(uh.w, ul.w), df_of(dh.w, dl.w), f.alpha,
+                                        f.beta, &L3);
+                const float v0 = m0.hi + m0.lo, v1 = m1.hi + m1.lo, v2 = m2.hi + m2.lo, v3 = m3.hi + m3.lo;
+                tD = fmaf(L0, c.x, fmaf(L1, c.y, fmaf(L2, c.z, fmaf(L3, c.w, tD))));
+                tL = fmaf(v0, c.x, fmaf(v1, c.y, fmaf(v2, c.z, fmaf(v3, c.w, tL))));
+                if (Sseg) {
+                    float4 sv = s4[at];
+                    sv.x += v0;
+                    sv.y += v1;
+                    sv.z += v2;
+                    sv.w += v3;
+                    s4[at] = sv;
+                }
+                ohi4[at] = make_float4(o0.hi, o1.hi, o2.hi, o3.hi);
+                olo4[at] = make_float4(o0.lo, o1.lo, o2.lo, o3.lo);
+            }
+            uh = ch;
+            ul = cl;
+            ch = dh;
+            cl = dl;
+        }
+    }
+    block_add2(tD, tL, acc);
+}
+
+// The same for any grid (2D or 3D, any nx), one node per thread iteration.
+__global__ void __launch_bounds__(256) adj_field_scalar(FieldDesc f, const float *__restrict__ mu_in,
+                                                        float *__restrict__ mu_out, const float *__restrict__ C,
+                                                        float *Sseg, double *acc)
 {
     const size_t n = (size_t)f.nx * f.ny * f.nz;
     const size_t sy = f.nx, sz = (size_t)f.nx * f.ny;
-    const double alpha = f.alpha, beta = f.beta;
-    double tD = 0.0, tL = 0.0;
+    float tD = 0.f, tL = 0.f;
+    auto ld = [&](size_t c) { return df_of(mu_in[c], mu_in[n + c]); };
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(c % f.nx);
         const int j = (int)((c / f.nx) % f.ny);
         const int k = (int)(c / sz);
-        const double m = mu_in[c];
-        const double xm = i > 0 ? mu_in[c - 1] : m;
-        const double xp = i < f.nx - 1 ? mu_in[c + 1] : m;
-        const double ym = j > 0 ? mu_in[c - sy] : m;
-        const double yp = j < f.ny - 1 ? mu_in[c + sy] : m;
-        double sum = (xm + xp) + (ym + yp), nn = 4.0;
+        const DF m = ld(c);
+        const DF xm = i > 0 ? ld(c - 1) : m;
+        const DF xp = i < f.nx - 1 ? ld(c + 1) : m;
+        const DF ym = j > 0 ? ld(c - sy) : m;
+        const DF yp = j < f.ny - 1 ? ld(c + sy) : m;
+        DF sum = df_add(df_add(xm, xp), df_add(ym, yp));
+        float nn = -4.0f;
         if (f.dim == 3) {
-            const double zm = k > 0 ? mu_in[c - sz] : m;
-            const double zp = k < f.nz - 1 ? mu_in[c + sz] : m;
-            sum += zm + zp;
-            nn = 6.0;
+            const DF zm = k > 0 ? ld(c - sz) : m;
+            const DF zp = k < f.nz - 1 ? ld(c + sz) : m;
+            sum = df_add(sum, df_add(zm, zp));
+            nn = -6.0f;
         }
-        const double cc = C[c];
-        tD = fma(sum - nn * m, cc, tD);
-        tL = fma(m, cc, tL);
-        if (S) S[c] += m;
-        mu_out[c] = fma(alpha, sum, beta * m);
+        const DF lp = df_add(sum, df_mul(m, nn));
+        const DF o = df_add(df_mul(m, f.beta), df_mul(sum, f.alpha));
+        const float v = m.hi + m.lo;
+        const float cc = C[c];
+        tD = fmaf(lp.hi + lp.lo, cc, tD);
+        tL = fmaf(v, cc, tL);
+        if (Sseg) Sseg[c] += v;
+        mu_out[c] = o.hi;
+        mu_out[n + c] = o.lo;
     }
     block_add2(tD, tL, acc);
+}
+
+// End of a segment: S += Sseg in FP64, Sseg = 0.
+__global__ void __launch_bounds__(256) adj_fold_kernel(size_t n, float *Sseg, double *S)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        S[c] += (double)Sseg[c];
+        Sseg[c] = 0.0f;
+    }
 }
 
 // Node (i,j,k) as a linear index.
@@ -106,9 +291,10 @@ __device__ __forceinline__ size_t node_index(const FieldDesc &f, int i, int j, i
 template <int DIM>
 __device__ __forceinline__ void cone_adjoint(const FieldDesc &f, const ConeDesc &c, const float *__restrict__ C,
                                              uint32_t axon, uint32_t step, const float *p, const float *d,
-                                             float *pbar, float *dbar, double *mu)
+                                             float *pbar, float *dbar, float *mu)
 {
     const size_t sy = f.nx, sz = (size_t)f.nx * f.ny;
+    float *mu_lo = mu + sz * f.nz;                    // low plane of the double-float field
     auto ld = [&](int i, int j, int k) { return __ldg(C + (size_t)i + sy * j + sz * k); };
     // forward recomputation with the forward's own functions (same decisions)
     float g[DIM];
@@ -193,9 +379,10 @@ __device__ __forceinline__ void cone_adjoint(const FieldDesc &f, const ConeDesc 
                     ip[k] = min(ip[k] + 1, ext[k] - 1);
                     im[k] = max(im[k] - 1, 0);
                     gnode[k] = (ld(ip[0], ip[1], ip[2]) - ld(im[0], im[1], im[2])) * c.inv2h;
-                    const double coef = (double)gbar[k] * (double)w * (double)c.inv2h;
-                    atomicAdd(mu + node_index(f, ip[0], ip[1], ip[2]), coef);
-                    atomicAdd(mu + node_index(f, im[0], im[1], im[2]), -coef);
+                    const float coef = gbar[k] * w * c.inv2h;
+                    const size_t jp = node_index(f, ip[0], ip[1], ip[2]), jm = node_index(f, im[0], im[1], im[2]);
+                    atomic_add_df(mu + jp, mu_lo + jp, coef);
+                    atomic_add_df(mu + jm, mu_lo + jm, -coef);
                 }
 #pragma unroll
                 for (int m = 0; m < DIM; ++m) {
@@ -219,14 +406,15 @@ __global__ void __launch_bounds__(256) adj_cone_kernel(FieldDesc f, ConeDesc c, 
                                                        uint32_t step, int n, const float *__restrict__ P,
                                                        const float *__restrict__ Dd,
                                                        const uint8_t *__restrict__ active, float *pbar,
-                                                       float *dbar, double *mu_out, const double *__restrict__ mu_in,
+                                                       float *dbar, float *mu_out, const float *__restrict__ mu_in,
                                                        const int32_t *__restrict__ src_cell, int n_src,
                                                        double *de_acc)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < n_src) {
         const long long cell = src_cell[a];
-        if (cell >= 0 && cell < (long long)f.nx * f.ny * f.nz) de_acc[a] += mu_in[cell];
+        const long long n_cells = (long long)f.nx * f.ny * f.nz;
+        if (cell >= 0 && cell < n_cells) de_acc[a] += (double)mu_in[cell] + (double)mu_in[n_cells + cell];
     }
     if (a >= n || !active[a]) return;
     float p[DIM], d[DIM], pb[DIM], db[DIM];
@@ -251,16 +439,16 @@ __global__ void __launch_bounds__(256) adj_loss_kernel(int n, int dim, const flo
                                                        double *loss_acc)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    double s = 0.0;
+    float s = 0.0f;
     if (a < n) {
         for (int i = 0; i < dim; ++i) {
             const float e = P[(size_t)i * n + a] - T[(size_t)i * n + a];
-            s += (double)e * (double)e;
+            s = fmaf(e, e, s);
             pbar[(size_t)i * n + a] = 2.0f * e / (float)n;
             dbar[(size_t)i * n + a] = 0.0f;
         }
     }
-    block_add2(s, 0.0, loss_acc);
+    block_add2(s, 0.0f, loss_acc);
 }
 
 // Scale the accumulators into the caller's outputs.
@@ -279,7 +467,7 @@ __global__ void adj_finalize_kernel(FieldDesc f, int n_axons, const double *acc,
 }
 
 struct AdjLayout {
-    size_t ckpt_c, ckpt_p, seg_c, seg_p, mu, S, pbar, acc, total;
+    size_t ckpt_c, ckpt_p, seg_c, seg_p, mu, Sseg, S, pbar, acc, total;
     int nseg;
 };
 
@@ -300,9 +488,11 @@ AdjLayout adj_layout(const cue_params &p, int n_src, int n_axons, int nsteps, in
     off += align256(sizeof(float) * cells * (k + 1));
     L.seg_p = off;
     off += align256(sizeof(float) * cone * (k + 1));
-    L.mu = off;                                   // FP64 adjoint field, two buffers
-    off += align256(sizeof(double) * cells * 2);
-    L.S = off;                                    // FP64 running sum of mu (rate-map gradient)
+    L.mu = off;                                   // adjoint field, two double-float buffers (hi, lo planes)
+    off += align256(sizeof(float) * cells * 4);
+    L.Sseg = off;                                 // this segment's sum of mu
+    off += align256(sizeof(float) * cells);
+    L.S = off;                                    // FP64 sum over the segments (rate-map gradient)
     off += align256(sizeof(double) * cells);
     L.pbar = off;
     off += align256(sizeof(float) * cone);
@@ -313,6 +503,38 @@ AdjLayout adj_layout(const cue_params &p, int n_src, int n_axons, int nsteps, in
 }
 
 int blocks_for(size_t n, int per) { return (int)((n + per - 1) / per); }
+
+int sm_count_adj()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+void launch_adj_field(Sim &s, const float *mu_in, float *mu_out, const float *C, float *Sseg, double *acc)
+{
+    const FieldDesc &f = s.fd;
+    const size_t cells = (size_t)f.nx * f.ny * f.nz;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(mu_in) | reinterpret_cast<uintptr_t>(mu_out) |
+                           reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(Sseg)) & 15u) == 0;
+    if (f.dim == 2 && f.nx % 4 == 0 && aligned) {
+        const int nx4 = f.nx / 4, BY = 8;
+        const int xb = (nx4 + 31) / 32;
+        int rows = 8;      // the most rows per thread that still leaves >= 4 blocks per SM
+        while (rows > 1 && (long long)xb * ((f.ny + BY * rows - 1) / (BY * rows)) < 4LL * sm_count_adj()) rows /= 2;
+        dim3 grid(xb, (f.ny + BY * rows - 1) / (BY * rows));
+        adj_field2d_vec4<<<grid, dim3(32, BY), 0, s.stream>>>(f, mu_in, mu_out, C, Sseg, acc, rows);
+    } else {
+        const int fb = std::min(blocks_for(cells, 256), sm_count_adj() * 16);
+        adj_field_scalar<<<fb, 256, 0, s.stream>>>(f, mu_in, mu_out, C, Sseg, acc);
+    }
+    s.launches++;
+}
 
 }  // namespace
 
@@ -336,15 +558,17 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
     float *ckP = reinterpret_cast<float *>(W + L.ckpt_p);
     float *sgC = reinterpret_cast<float *>(W + L.seg_c);
     float *sgP = reinterpret_cast<float *>(W + L.seg_p);
-    double *mu[2] = {reinterpret_cast<double *>(W + L.mu), reinterpret_cast<double *>(W + L.mu) + cells};
+    float *mu[2] = {reinterpret_cast<float *>(W + L.mu), reinterpret_cast<float *>(W + L.mu) + 2 * cells};
+    float *Sseg = gmap ? reinterpret_cast<float *>(W + L.Sseg) : nullptr;
     double *S = gmap ? reinterpret_cast<double *>(W + L.S) : nullptr;
     float *pbar = reinterpret_cast<float *>(W + L.pbar), *dbar = pbar + cone_n;
     double *acc = reinterpret_cast<double *>(W + L.acc);     // sD, sL, de[n_src], loss
     cudaStream_t st = s.stream;
     auto ok = [](cudaError_t e) { return e == cudaSuccess; };
-    if (!ok(cudaMemsetAsync(mu[0], 0, sizeof(double) * cells * 2, st)) ||
+    if (!ok(cudaMemsetAsync(mu[0], 0, sizeof(float) * cells * 4, st)) ||
         !ok(cudaMemsetAsync(acc, 0, sizeof(double) * (4 + s.n_src), st)) ||
-        (S && !ok(cudaMemsetAsync(S, 0, sizeof(double) * cells, st))))
+        (S && !ok(cudaMemsetAsync(S, 0, sizeof(double) * cells, st))) ||
+        (Sseg && !ok(cudaMemsetAsync(Sseg, 0, sizeof(float) * cells, st))))
         return CUE_ERR_CUDA;
     const int64_t n0 = s.field_step;
     // ---- forward with checkpoints (any path: fused and plain agree bit for bit)
@@ -376,29 +600,30 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
             float *Pm = sgP + 2 * cone_n * m, *Pn = sgP + 2 * cone_n * (m + 1);
             if (!ok(launch_cone_step_io(s, sgC + cells * m, (uint32_t)(nstart + m), Pm, Pm + cone_n, Pn,
                                         Pn + cone_n)) ||
-                !ok(launch_field_step(s, sgC + cells * m, sgC + cells * (m + 1))) ||
-                !ok(launch_sources(s, sgC + cells * (m + 1))))
+                !ok(launch_field_and_sources(s, sgC + cells * m, sgC + cells * (m + 1))))
                 return CUE_ERR_CUDA;
         }
         for (int m = len - 1; m >= 0; --m) {
             const float *Cm = sgC + cells * m, *Pm = sgP + 2 * cone_n * m;
-            const int fb = std::min(blocks_for(cells, 256), 152 * 16);
-            adj_field_kernel<<<fb, 256, 0, st>>>(f, mu[in], mu[in ^ 1], Cm, S, acc);
-            s.launches++;
-            const int cb = blocks_for((size_t)std::max(n, s.n_src), 256);
+            launch_adj_field(s, mu[in], mu[in ^ 1], Cm, Sseg, acc);
+            const int cb = blocks_for((size_t)std::max(n, s.n_src), 64);
             if (cb > 0) {
                 if (dim == 2)
-                    adj_cone_kernel<2><<<cb, 256, 0, st>>>(f, s.cd, Cm, (uint32_t)(nstart + m), n, Pm, Pm + cone_n,
+                    adj_cone_kernel<2><<<cb, 64, 0, st>>>(f, s.cd, Cm, (uint32_t)(nstart + m), n, Pm, Pm + cone_n,
                                                            s.active, pbar, dbar, mu[in ^ 1], mu[in], s.src_cell,
                                                            s.n_src, acc + 2);
                 else
-                    adj_cone_kernel<3><<<cb, 256, 0, st>>>(f, s.cd, Cm, (uint32_t)(nstart + m), n, Pm, Pm + cone_n,
+                    adj_cone_kernel<3><<<cb, 64, 0, st>>>(f, s.cd, Cm, (uint32_t)(nstart + m), n, Pm, Pm + cone_n,
                                                            s.active, pbar, dbar, mu[in ^ 1], mu[in], s.src_cell,
                                                            s.n_src, acc + 2);
                 s.launches++;
             }
             if (!ok(cudaGetLastError())) return CUE_ERR_CUDA;
             in ^= 1;
+        }
+        if (S) {
+            adj_fold_kernel<<<std::min(blocks_for(cells, 256), 152 * 8), 256, 0, st>>>(cells, Sseg, S);
+            s.launches++;
         }
     }
     adj_finalize_kernel<<<std::max(blocks_for((size_t)s.n_src, 256), std::min(blocks_for(cells, 256), 152 * 8)),

@@ -12,28 +12,25 @@
 namespace cue {
 namespace {
 
-constexpr int kMaxSmemSources = 2048;   // [3][2048] floats = 24 KiB
+constexpr int kMaxSmemSources = 2048;   // at most [3][2048] floats = 24 KiB of dynamic shared memory
 
 // State is read from (pin, din) and written to (pout, dout); the coupled run
 // passes the same arrays for both, the adjoint's recompute passes the next
 // stored step.
 template <int DIM>
-__global__ void __launch_bounds__(256) cone_plain(FieldDesc f, ConeDesc c, const float *__restrict__ C,
+__global__ void __launch_bounds__(128) cone_plain(FieldDesc f, ConeDesc c, const float *__restrict__ C,
                                                   uint32_t step, int n, const float *pin, const float *din,
                                                   float *pout, float *dout, uint8_t *__restrict__ active,
                                                   const float *__restrict__ src_xyz, int n_src,
                                                   unsigned *status, unsigned long long *counter)
 {
-    __shared__ float s_src[3 * kMaxSmemSources];
+    extern __shared__ float s_src[];         // [DIM][n_src] when the stop test is on and fits
     const bool use_stop = c.stop_r2 >= 0.0f && n_src > 0;
     const bool in_smem = n_src <= kMaxSmemSources;
     if (use_stop && in_smem) {
-        for (int i = threadIdx.x; i < DIM * n_src; i += blockDim.x) {
-            int ax = i / n_src, s = i - ax * n_src;
-            s_src[ax * kMaxSmemSources + s] = src_xyz[ax * n_src + s];
-        }
+        for (int i = threadIdx.x; i < DIM * n_src; i += blockDim.x) s_src[i] = src_xyz[i];
+        __syncthreads();
     }
-    __syncthreads();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = a < n && active[a];
     count_active(counter, live);
@@ -47,7 +44,7 @@ __global__ void __launch_bounds__(256) cone_plain(FieldDesc f, ConeDesc c, const
     const size_t sy = f.nx, sz = (size_t)f.nx * f.ny;
     auto ld = [&](int i, int j, int k) { return __ldg(C + (size_t)i + sy * j + sz * k); };
     const float *src = in_smem ? s_src : src_xyz;
-    const int stride = in_smem ? kMaxSmemSources : n_src;
+    const int stride = n_src;
     bool alive = cone_update<DIM>(f, c, ld, (uint32_t)a, step, p, d, src, stride, use_stop ? n_src : 0);
     bool bad = false;
 #pragma unroll
@@ -66,12 +63,17 @@ cudaError_t launch_cone_step_io(Sim &s, const float *C, uint32_t step, const flo
                                 float *pout, float *dout)
 {
     if (s.n_axons == 0) return cudaSuccess;
-    const int blocks = (s.n_axons + 255) / 256;
+    // One cone per thread; small blocks spread a few thousand cones over many SMs
+    // (each cone is a short chain of dependent loads, so the more SMs the better).
+    const int threads = s.n_axons >= 65536 ? 128 : 64;
+    const int blocks = (s.n_axons + threads - 1) / threads;
+    const bool stage = s.cd.stop_r2 >= 0.0f && s.n_src > 0 && s.n_src <= kMaxSmemSources;
+    const size_t smem = stage ? sizeof(float) * s.fd.dim * s.n_src : 0;
     if (s.fd.dim == 2)
-        cone_plain<2><<<blocks, 256, 0, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, pin, din, pout, dout, s.active,
+        cone_plain<2><<<blocks, threads, smem, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, pin, din, pout, dout, s.active,
                                                     s.src_xyz(), s.n_src, s.status(), s.cone_counter());
     else
-        cone_plain<3><<<blocks, 256, 0, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, pin, din, pout, dout, s.active,
+        cone_plain<3><<<blocks, threads, smem, s.stream>>>(s.fd, s.cd, C, step, s.n_axons, pin, din, pout, dout, s.active,
                                                     s.src_xyz(), s.n_src, s.status(), s.cone_counter());
     s.launches++;
     return cudaGetLastError();

@@ -26,16 +26,66 @@ __device__ __forceinline__ bool finite4(const float4 &v)
 // Each thread streams its 4-wide column strip down its rows, keeping the
 // rows above/at/below in registers; x neighbours come from the adjacent lane
 // by shuffle, and from global memory at the warp edges.
+//
+// Point sources are added by the block that owns their node, after the
+// update of that node and in source order (the same rounding as a separate
+// pass): the block first lists the sources inside its rectangle in shared
+// memory, so a block without sources pays one pass over the source table.
+constexpr int kBlockSources = 64;
+
 template <bool MAP>
 __global__ void __launch_bounds__(256) field2d_vec4(FieldDesc f, const float *__restrict__ Cin,
                                                     float *__restrict__ Cout,
                                                     const float *__restrict__ M, int rows,
+                                                    const int32_t *__restrict__ src_cell,
+                                                    const float *__restrict__ src_emit, int n_src,
                                                     unsigned *status)
 {
+    __shared__ int s_n;
+    __shared__ int s_cell[kBlockSources];
+    __shared__ float s_emit[kBlockSources];
     const int lane = threadIdx.x;
     const int nx4 = f.nx >> 2;
     const int x4 = blockIdx.x * 32 + lane;
     const bool xin = x4 < nx4;
+    const int bx0 = blockIdx.x * 128, bx1 = min(bx0 + 128, f.nx);
+    const int by0 = blockIdx.y * blockDim.y * rows, by1 = min(by0 + (int)blockDim.y * rows, f.ny);
+    const int tid = threadIdx.y * 32 + lane;
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    for (int k = tid; k < n_src; k += blockDim.x * blockDim.y) {
+        const int c = src_cell[k];
+        if (c < 0 || (long long)c >= (long long)f.nx * f.ny) {
+            if (blockIdx.x == 0 && blockIdx.y == 0) flag_status(status, kStatusBounds);
+            continue;
+        }
+        const int cx = c % f.nx, cy = c / f.nx;
+        if (cx >= bx0 && cx < bx1 && cy >= by0 && cy < by1) {
+            const int slot = atomicAdd(&s_n, 1);
+            if (slot < kBlockSources) {
+                s_cell[slot] = k;          // source index first: sorted below
+            } else {
+                flag_status(status, kStatusBounds);
+            }
+        }
+    }
+    __syncthreads();
+    const int nb = min(s_n, kBlockSources);
+    if (tid == 0 && nb > 1) {          // keep the table's order (ties add as a separate pass would)
+        for (int i = 1; i < nb; ++i)
+            for (int j = i; j > 0 && s_cell[j - 1] > s_cell[j]; --j) {
+                const int t = s_cell[j];
+                s_cell[j] = s_cell[j - 1];
+                s_cell[j - 1] = t;
+            }
+    }
+    __syncthreads();
+    if (tid < nb) {
+        const int k = s_cell[tid];
+        s_emit[tid] = src_emit[k];
+        s_cell[tid] = src_cell[k];
+    }
+    __syncthreads();
     const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * rows;
     if (y0 >= f.ny) return;                       // warp-uniform
     const int y1 = min(y0 + rows, f.ny);
@@ -69,6 +119,13 @@ __global__ void __launch_bounds__(256) field2d_vec4(FieldDesc f, const float *__
                 o.y = fmaf(f.dt, m.y, o.y);
                 o.z = fmaf(f.dt, m.z, o.z);
                 o.w = fmaf(f.dt, m.w, o.w);
+            }
+            for (int i = 0; i < nb; ++i) {
+                const int c = s_cell[i] - y * f.nx - x;
+                if (c == 0) o.x += s_emit[i];
+                else if (c == 1) o.y += s_emit[i];
+                else if (c == 2) o.z += s_emit[i];
+                else if (c == 3) o.w += s_emit[i];
             }
             bad |= !finite4(o);
             out4[(size_t)y * nx4 + x4] = o;
@@ -230,10 +287,11 @@ int sm_count()
 
 }  // namespace
 
-cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout)
+cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout, bool *sources_done)
 {
     const FieldDesc &f = s.fd;
     const bool map = s.src_map != nullptr;
+    if (sources_done) *sources_done = false;
     timing_begin(s);
     if (s.vec4 && f.dim == 2) {
         const int nx4 = f.nx / 4;
@@ -248,8 +306,14 @@ cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout)
         }
         dim3 grid(xb, (f.ny + BY * rows - 1) / (BY * rows));
         dim3 block(32, BY);
-        if (map) field2d_vec4<true><<<grid, block, 0, s.stream>>>(f, Cin, Cout, s.src_map, rows, s.status());
-        else field2d_vec4<false><<<grid, block, 0, s.stream>>>(f, Cin, Cout, nullptr, rows, s.status());
+        const int ns = (sources_done && s.n_src <= kBlockSources) ? s.n_src : 0;
+        if (map)
+            field2d_vec4<true><<<grid, block, 0, s.stream>>>(f, Cin, Cout, s.src_map, rows, s.src_cell, s.src_emit,
+                                                             ns, s.status());
+        else
+            field2d_vec4<false><<<grid, block, 0, s.stream>>>(f, Cin, Cout, nullptr, rows, s.src_cell, s.src_emit,
+                                                              ns, s.status());
+        if (sources_done) *sources_done = ns == s.n_src;
     } else if (s.vec4 && f.dim == 3 && (Cin == s.field[0] || Cin == s.field[1]) && field3d_tma_prepare(s)) {
         cudaError_t e = launch_field3d_tma(s, Cin == s.field[0] ? 0 : 1, Cout);
         timing_end(s);
@@ -276,6 +340,14 @@ cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout)
     timing_end(s);
     s.launches++;
     return cudaGetLastError();
+}
+
+cudaError_t launch_field_and_sources(Sim &s, const float *Cin, float *Cout)
+{
+    bool done = false;
+    cudaError_t e = launch_field_step(s, Cin, Cout, &done);
+    if (e == cudaSuccess && !done) e = launch_sources(s, Cout);
+    return e;
 }
 
 cudaError_t launch_sources(Sim &s, float *Cout)
