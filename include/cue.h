@@ -103,13 +103,28 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
 #define CUE_OPT_TIME_KERNEL     4  /* value v >= 1: bracket every v-th launch of the dominant
                                       field kernel with CUDA events on the handle's stream,
                                       read back by cue_kernel_time; 0: off (default)        */
+#define CUE_OPT_PERSIST_ROWS    5  /* value: rows per thread of a persistent-path field tile
+                                      (1, 2 or 4), 0 = library choice                        */
+#define CUE_OPT_PERSIST_BLOCKS  6  /* value: blocks per SM of the persistent launch (1..8,
+                                      capped by occupancy), 0 = library choice (2)           */
+#define CUE_OPT_WAIT_LIMIT      7  /* value: polls (about 32 ns apart) before a bounded
+                                      device-side wait of the persistent path gives up and
+                                      raises CUE_ERR_TIMEOUT; 0 = default (2^24)            */
+#define CUE_OPT_BARRIER_PHANTOM 8  /* diagnostic: the persistent grid barrier also waits for
+                                      this many arrivals that never come, so its bounded
+                                      wait runs out (tests the timeout path); 0 = off       */
 /* read-only values for cue_get_option */
-#define CUE_INFO_LAST_PATH     16  /* CUE_PATH_PLAIN or CUE_PATH_FUSED: path of the last step */
+#define CUE_INFO_LAST_PATH     16  /* CUE_PATH_*: path the last sim_run took                  */
 #define CUE_INFO_TILE          17  /* fused tile interior: TX | TY << 16 (0 if not prepared) */
 #define CUE_INFO_DEPTH         18  /* temporal depth the fused path runs with                 */
-#define CUE_PATH_AUTO   0          /* library picks (fused when supported)                 */
+#define CUE_INFO_GRID          19  /* blocks of the last persistent launch                    */
+#define CUE_PATH_AUTO   0          /* library picks: fused for grids of at least one tile per
+                                      SM, else persistent, else plain                       */
 #define CUE_PATH_PLAIN  1          /* one launch per half-step: cone kernel, field kernel  */
 #define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel       */
+#define CUE_PATH_PERSIST 3         /* 2D, nx % 4 == 0: one cooperative launch for the whole
+                                      run; per step one pass over field tiles and cone
+                                      chunks, then a bounded grid barrier                   */
 
 /* Bytes of device workspace the simulation needs (256-byte aligned). */
 size_t cue_workspace_bytes(const cue_params *params, int32_t n_src, int32_t n_axons);

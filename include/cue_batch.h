@@ -1,0 +1,109 @@
+/*
+ * cue_batch.h -- many independent 2D cue-field / growth-cone simulations of
+ * uneven sizes and parameters stepped together by one persistent launch.
+ *
+ * Each instance is the model of cue.h (Sec. 5.2 field update with no-flux
+ * walls, decay and point sources; Sec. 3.5 growth-cone steering with Philox
+ * noise; Sec. 3.3-3.4 stop tests), with its own grid, physics, sources and
+ * cones.  The paper steps one environment; running many small ones in one
+ * launch is this library's own addition.  One cue_batch_run call is one
+ * cooperative launch (or one replay of a captured CUDA graph holding it): per
+ * step every block takes field tiles and cone chunks from a work list that
+ * interleaves all instances, then the blocks meet at a bounded grid barrier.
+ * Per node and per cone the arithmetic is cue.h's plain path, so an instance
+ * here evolves bit for bit as it would alone (source cells distinct).
+ *
+ * Layout: instance i's field buffers hold ny rows of `pitch[i]` floats
+ * (pitch >= nx, a multiple of 4, 16-byte aligned buffers); columns
+ * nx..pitch-1 are padding the library never changes.  Source cells are
+ * linear node indices x + nx*y (as in cue.h), cone state is SoA [2][n].
+ *
+ * Ownership: every device buffer, the workspace and the stream belong to the
+ * caller and must outlive the batch.  Calls are asynchronous on the stream;
+ * two calls on one batch must not overlap.
+ *
+ * Errors: negative CUE_ERR_* codes of cue.h; device-side conditions (non-
+ * finite values, out-of-range source cells, a barrier wait that ran out) are
+ * latched on the device and reported by cue_batch_status.
+ */
+#ifndef CUE_BATCH_H
+#define CUE_BATCH_H
+
+#include "cue.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cue_batch cue_batch;   /* opaque, host-side */
+
+/* One instance: host struct of device pointers and sizes. */
+typedef struct {
+    cue_params params;        /* dim must be 2; boundary 0                          */
+    cone_params cone;
+    int32_t pitch;            /* row pitch of both field buffers, floats           */
+    float *field_a;           /* C^n on entry (buffer 0), ny * pitch floats         */
+    float *field_b;           /* second buffer, same size                           */
+    const int32_t *src_cell;  /* n_src node indices x + nx*y                        */
+    const float *src_emit;    /* n_src emissions per step                           */
+    int32_t n_src;
+    const float *src_map;     /* nullable: rate map, ny * pitch floats (adds dt*M)  */
+    float *pos, *dir;         /* [2][n_axons] each                                  */
+    uint8_t *active;          /* n_axons                                            */
+    int32_t n_axons;
+} cue_instance;
+
+/* Device workspace bytes for a batch of n instances (256-byte aligned).
+ * with_backup != 0 adds room for one copy of every instance's state, which
+ * cue_batch_autotune needs (it measures candidates and restores the state). */
+size_t cue_batch_workspace_bytes(int32_t n, const cue_instance *inst, int32_t with_backup);
+
+/* Create a batch.  inst[0..n) is copied (the device buffers are not).  Stages
+ * the instance table and the work list in the workspace on `stream` (a
+ * cudaStream_t, NULL = default stream).  Returns NULL and sets *err on error:
+ * CUE_ERR_ARG (bad instance, dim != 2, pitch, alignment), CUE_ERR_UNSTABLE
+ * (1 - 4 alpha - lambda dt < 0 for an instance), CUE_ERR_WORKSPACE,
+ * CUE_ERR_CUDA. */
+cue_batch *cue_batch_create(int32_t n, const cue_instance *inst, void *d_ws, size_t ws_bytes, void *stream,
+                            int32_t *err);
+
+/* Advance every instance by nsteps coupled steps (cones on C^n, then
+ * C^n -> C^{n+1}).  One cooperative launch, or one graph replay when
+ * CUE_BOPT_GRAPH is on (the graph is captured at the first call with a given
+ * nsteps and replayed afterwards; the step counter and buffer parity live on
+ * the device, so a replay needs no new arguments). */
+int cue_batch_run(cue_batch *b, int32_t nsteps);
+
+/* Time each candidate launch shape (rows per thread 1, 2, 4 x blocks per SM
+ * 1..3) on probe_steps steps from the current state, restoring the state after
+ * every candidate, and keep the fastest.  Needs the backup area (see
+ * cue_batch_workspace_bytes).  Synchronises the stream.  Writes the chosen
+ * rows and blocks per SM and the best time per step (ms) when non-null. */
+int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows, int32_t *blocks_per_sm,
+                       double *ms_per_step);
+
+#define CUE_BOPT_ROWS    1    /* rows per thread of a field tile (1, 2, 4)          */
+#define CUE_BOPT_BLOCKS  2    /* blocks per SM (1..8, capped by occupancy)          */
+#define CUE_BOPT_GRAPH   3    /* 1: run through a captured CUDA graph; 0: direct    */
+#define CUE_BINFO_ITEMS  16   /* work-list length (field tiles + cone chunks)       */
+#define CUE_BINFO_STEP   17   /* steps taken so far (host mirror)                   */
+#define CUE_BINFO_CUR    18   /* current buffer of every instance: 0 = field_a      */
+#define CUE_BINFO_GRID   19   /* blocks of the last launch                          */
+
+int cue_batch_set_option(cue_batch *b, int32_t option, int64_t value);
+int cue_batch_get_option(const cue_batch *b, int32_t option, int64_t *value);
+
+/* Synchronise the stream; return and clear the latched device status. */
+int cue_batch_status(cue_batch *b);
+
+/* Number of active-cone updates since the last call (synchronises). */
+int cue_batch_cone_updates(cue_batch *b, uint64_t *count);
+
+/* Release the handle (not the caller's buffers); destroys a captured graph. */
+void cue_batch_destroy(cue_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUE_BATCH_H */

@@ -31,6 +31,11 @@ WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons)
     off += align256(sizeof(int32_t) * na);
     w.cone_slot_off = off;
     off += align256(sizeof(int32_t) * na);
+    w.persist_off = off;
+    if (p.dim == 2 && p.nx >= 4) {
+        w.persist_items_cap = (size_t)persist_tiles(p.nx, p.ny, 1) + (na + kPersistConeChunk - 1) / kPersistConeChunk;
+        off += 256 + align256(2 * sizeof(PInst)) + align256(sizeof(PItem) * w.persist_items_cap);
+    }
     w.total = off;
     return w;
 }
@@ -94,11 +99,30 @@ static void timing_free(Sim &s)
     s.ev_stop.clear();
 }
 
+static int sm_count_api()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
 int run_coupled(Sim &s, int nsteps)
 {
-    int rc = run_fused_if_supported(s, nsteps);
-    if (rc != 1) return rc;       // handled (0 = ok, < 0 = error)
     s.fused_used = false;
+    s.persist_used = false;
+    // AUTO: the temporally blocked kernel when the grid gives every SM a tile,
+    // else the persistent launch (small grids, or a rate map), else plain.
+    const bool small = !fused_supported(s) || fused_tile_count(s.params) < sm_count_api();
+    int rc = 1;
+    if (s.path == CUE_PATH_PERSIST || (s.path == CUE_PATH_AUTO && small)) rc = run_persist_if_supported(s, nsteps);
+    if (rc != 1) return rc;
+    rc = run_fused_if_supported(s, nsteps);
+    if (rc != 1) return rc;       // handled (0 = ok, < 0 = error)
     for (int k = 0; k < nsteps; ++k) {
         float *in = s.field[s.cur], *out = s.field[s.cur ^ 1];
         cudaError_t e = launch_cone_step(s, in, (uint32_t)s.cone_step);
@@ -117,7 +141,39 @@ using namespace cue;
 
 struct cue_sim : public cue::Sim {};
 
-namespace {
+namespace cue {
+
+int make_descs(const cue_params &params, const cone_params &cone, FieldDesc &f, ConeDesc &c)
+{
+    const int dim = params.dim;
+    const float alpha = params.D * params.dt / (params.h * params.h);
+    const float decay = params.lambda * params.dt;
+    if (alpha > 1.0f / (2.0f * dim) * (1.0f + 1e-6f) || decay > 1.0f) return CUE_ERR_UNSTABLE;
+    f.dim = dim;
+    f.nx = params.nx;
+    f.ny = params.ny;
+    f.nz = dim == 3 ? params.nz : 1;
+    f.h = params.h;
+    f.alpha = alpha;
+    f.decay = decay;
+    f.dt = params.dt;
+    f.beta = (float)(1.0 - 2.0 * dim * (double)alpha - (double)decay);
+    f.inv_h = 1.0f / params.h;
+    c.w_prev = cone.w_prev;
+    c.w_grad = cone.w_grad;
+    c.w_noise = cone.w_noise;
+    c.step_len = cone.step_len;
+    c.stop_r2 = cone.stop_radius > 0.f ? cone.stop_radius * cone.stop_radius : -1.0f;
+    c.eps2 = cone.grad_eps * cone.grad_eps;
+    c.inv2h = 1.0f / (2.0f * params.h);
+    c.hi0 = (float)(f.nx - 1) * f.h;
+    c.hi1 = (float)(f.ny - 1) * f.h;
+    c.hi2 = (float)(f.nz - 1) * f.h;
+    c.wall_mode = cone.wall_mode;
+    c.key0 = (uint32_t)(cone.seed & 0xFFFFFFFFull);
+    c.key1 = (uint32_t)(cone.seed >> 32);
+    return CUE_OK;
+}
 
 bool params_ok(const cue_params *p)
 {
@@ -149,7 +205,7 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? CUE_OK : CUE_ERR_CUDA; }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-}  // namespace
+}  // namespace cue
 
 extern "C" {
 
@@ -172,9 +228,9 @@ int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone, f
     if (n_src > 0 && (!d_src_cell || !d_src_emit)) return CUE_ERR_ARG;
     if (n_axons > 0 && (!d_pos || !d_dir || !d_active)) return CUE_ERR_ARG;
     const int dim = params->dim;
-    const float alpha = params->D * params->dt / (params->h * params->h);
-    const float decay = params->lambda * params->dt;
-    if (alpha > 1.0f / (2.0f * dim) * (1.0f + 1e-6f) || decay > 1.0f) return CUE_ERR_UNSTABLE;
+    FieldDesc fdesc;
+    ConeDesc cdesc;
+    if (make_descs(*params, *cone, fdesc, cdesc) != CUE_OK) return CUE_ERR_UNSTABLE;
     WorkspaceLayout wl = workspace_layout(*params, n_src, n_axons);
     if (!d_workspace || ws_bytes < wl.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
         return CUE_ERR_WORKSPACE;
@@ -184,31 +240,9 @@ int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone, f
     s->params = *params;
     if (dim == 2) s->params.nz = 1;
     s->cone = *cone;
-    FieldDesc &f = s->fd;
-    f.dim = dim;
-    f.nx = params->nx;
-    f.ny = params->ny;
-    f.nz = dim == 3 ? params->nz : 1;
-    f.h = params->h;
-    f.alpha = alpha;
-    f.decay = decay;
-    f.dt = params->dt;
-    f.beta = (float)(1.0 - 2.0 * dim * (double)alpha - (double)decay);
-    f.inv_h = 1.0f / params->h;
-    ConeDesc &c = s->cd;
-    c.w_prev = cone->w_prev;
-    c.w_grad = cone->w_grad;
-    c.w_noise = cone->w_noise;
-    c.step_len = cone->step_len;
-    c.stop_r2 = cone->stop_radius > 0.f ? cone->stop_radius * cone->stop_radius : -1.0f;
-    c.eps2 = cone->grad_eps * cone->grad_eps;
-    c.inv2h = 1.0f / (2.0f * params->h);
-    c.hi0 = (float)(f.nx - 1) * f.h;
-    c.hi1 = (float)(f.ny - 1) * f.h;
-    c.hi2 = (float)(f.nz - 1) * f.h;
-    c.wall_mode = cone->wall_mode;
-    c.key0 = (uint32_t)(cone->seed & 0xFFFFFFFFull);
-    c.key1 = (uint32_t)(cone->seed >> 32);
+    s->fd = fdesc;
+    s->cd = cdesc;
+    const FieldDesc &f = s->fd;
     s->field[0] = d_field_a;
     s->field[1] = d_field_b;
     s->src_cell = d_src_cell;
@@ -328,9 +362,28 @@ int cue_set_option(cue_sim *s, int32_t option, int64_t value)
     if (!s) return CUE_ERR_ARG;
     switch (option) {
     case CUE_OPT_PATH:
-        if (value != CUE_PATH_AUTO && value != CUE_PATH_PLAIN && value != CUE_PATH_FUSED) return CUE_ERR_ARG;
+        if (value != CUE_PATH_AUTO && value != CUE_PATH_PLAIN && value != CUE_PATH_FUSED &&
+            value != CUE_PATH_PERSIST)
+            return CUE_ERR_ARG;
         if (value == CUE_PATH_FUSED && !fused_supported(*s)) return CUE_ERR_ARG;
+        if (value == CUE_PATH_PERSIST && !persist_supported(*s)) return CUE_ERR_ARG;
         s->path = (int)value;
+        return CUE_OK;
+    case CUE_OPT_PERSIST_ROWS:
+        if (value != 0 && value != 1 && value != 2 && value != 4) return CUE_ERR_ARG;
+        s->persist_rows = (int)value;
+        return CUE_OK;
+    case CUE_OPT_PERSIST_BLOCKS:
+        if (value < 0 || value > 8) return CUE_ERR_ARG;
+        s->persist_bpsm = (int)value;
+        return CUE_OK;
+    case CUE_OPT_WAIT_LIMIT:
+        if (value < 0 || value > (1LL << 40)) return CUE_ERR_ARG;
+        s->persist_limit = value;
+        return CUE_OK;
+    case CUE_OPT_BARRIER_PHANTOM:
+        if (value < 0 || value > 1024) return CUE_ERR_ARG;
+        s->persist_phantom = (int)value;
         return CUE_OK;
     case CUE_OPT_TEMPORAL_DEPTH:
         if (value < 0 || value > kMaxTemporalDepth) return CUE_ERR_ARG;
@@ -373,7 +426,14 @@ int cue_get_option(const cue_sim *s, int32_t option, int64_t *value)
     case CUE_OPT_TEMPORAL_DEPTH: *value = s->temporal_depth; return CUE_OK;
     case CUE_OPT_ROWS_PER_THREAD: *value = s->rows_per_thread; return CUE_OK;
     case CUE_OPT_TIME_KERNEL: *value = s->time_kernel ? s->time_period : 0; return CUE_OK;
-    case CUE_INFO_LAST_PATH: *value = s->fused_used ? CUE_PATH_FUSED : CUE_PATH_PLAIN; return CUE_OK;
+    case CUE_INFO_LAST_PATH:
+        *value = s->fused_used ? CUE_PATH_FUSED : (s->persist_used ? CUE_PATH_PERSIST : CUE_PATH_PLAIN);
+        return CUE_OK;
+    case CUE_OPT_PERSIST_ROWS: *value = s->persist_rows; return CUE_OK;
+    case CUE_OPT_PERSIST_BLOCKS: *value = s->persist_bpsm; return CUE_OK;
+    case CUE_OPT_WAIT_LIMIT: *value = s->persist_limit; return CUE_OK;
+    case CUE_OPT_BARRIER_PHANTOM: *value = s->persist_phantom; return CUE_OK;
+    case CUE_INFO_GRID: *value = s->persist_grid; return CUE_OK;
     case CUE_INFO_TILE: *value = s->geom_ready ? (int64_t)s->geom.TX | ((int64_t)s->geom.TY << 16) : 0; return CUE_OK;
     case CUE_INFO_DEPTH: *value = s->geom_ready ? s->geom.K : 0; return CUE_OK;
     default: return CUE_ERR_ARG;

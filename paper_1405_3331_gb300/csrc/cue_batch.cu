@@ -1,0 +1,509 @@
+// cue_batch.cu -- C ABI of batched runs (include/cue_batch.h): many
+// independent 2D instances stepped by the persistent engine of k_persist.cu,
+// optionally through a captured CUDA graph, with a measuring autotuner for
+// the launch shape.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cue_batch.h"
+#include "cue_internal.h"
+
+namespace cue {
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace: [status 0, counter 8 | ctrl 256 | barrier 512 | instance table |
+// work list | source coordinates | backup (optional)].
+struct BatchLayout {
+    size_t ctrl, bar, inst, items, src_xyz, backup, total;
+    size_t items_cap;
+    std::vector<size_t> xyz_off, bk_field, bk_cone;   // per instance
+};
+
+size_t inst_cells(const cue_instance &I) { return (size_t)I.pitch * I.params.ny; }
+
+BatchLayout batch_layout(int n, const cue_instance *in, bool backup)
+{
+    BatchLayout L;
+    size_t off = 256;
+    L.ctrl = off;
+    off += 256;
+    L.bar = off;
+    off += 256;
+    L.inst = off;
+    off += align256(sizeof(PInst) * (size_t)n);
+    L.items_cap = 0;
+    for (int i = 0; i < n; ++i)
+        L.items_cap += (size_t)persist_tiles(in[i].params.nx, in[i].params.ny, 1) +
+                       (size_t)(std::max(in[i].n_axons, 0) + kPersistConeChunk - 1) / kPersistConeChunk;
+    L.items = off;
+    off += align256(sizeof(PItem) * std::max<size_t>(L.items_cap, 1));
+    L.src_xyz = off;
+    L.xyz_off.resize(n);
+    for (int i = 0; i < n; ++i) {
+        L.xyz_off[i] = off;
+        off += align256(sizeof(float) * 3 * (size_t)std::max(in[i].n_src, 0));
+    }
+    L.backup = off;
+    L.bk_field.resize(n);
+    L.bk_cone.resize(n);
+    if (backup) {
+        for (int i = 0; i < n; ++i) {
+            L.bk_field[i] = off;
+            off += align256(sizeof(float) * inst_cells(in[i]));
+            L.bk_cone[i] = off;                          // pos, dir ([2][n] each), active (n bytes)
+            off += align256(sizeof(float) * 4 * (size_t)in[i].n_axons + (size_t)in[i].n_axons);
+        }
+    }
+    L.total = off;
+    return L;
+}
+
+bool instance_ok(const cue_instance &I)
+{
+    if (!params_ok(&I.params) || !cone_ok(&I.cone)) return false;
+    if (I.params.dim != 2) return false;
+    if (I.pitch < I.params.nx || I.pitch % 4 != 0) return false;
+    if (!I.field_a || !I.field_b || I.field_a == I.field_b) return false;
+    if (!aligned16(I.field_a) || !aligned16(I.field_b) || (I.src_map && !aligned16(I.src_map))) return false;
+    if (I.n_src < 0 || I.n_axons < 0) return false;
+    if (I.n_src > 0 && (!I.src_cell || !I.src_emit)) return false;
+    if (I.n_axons > 0 && (!I.pos || !I.dir || !I.active)) return false;
+    if ((long long)I.pitch * I.params.ny > (1LL << 31) - 1) return false;
+    return true;
+}
+
+// Source node coordinates of one instance for the cones' stop test.
+__global__ void batch_source_coords(int nx, int ny, float h, const int32_t *__restrict__ cell, int n_src, float *xyz,
+                                    unsigned *status)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_src) return;
+    const long long c = cell[s];
+    if (c < 0 || c >= (long long)nx * ny) {
+        flag_status(status, kStatusBounds);
+        xyz[s] = xyz[n_src + s] = xyz[2 * n_src + s] = 3.0e38f;
+        return;
+    }
+    xyz[s] = (float)(c % nx) * h;
+    xyz[n_src + s] = (float)(c / nx) * h;
+    xyz[2 * n_src + s] = 0.0f;
+}
+
+}  // namespace
+}  // namespace cue
+
+using namespace cue;
+
+struct cue_batch {
+    int n = 0;
+    std::vector<cue_instance> in;
+    std::vector<PInst> insts;
+    BatchLayout L;
+    bool has_backup = false;
+    unsigned char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    int rows = 0, bpsm = 0;          // options (0 = library choice)
+    int rows_used = 0;
+    int n_items = 0;
+    bool list_ready = false;
+    bool use_graph = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = -1;
+    int graph_grid = 0;
+    long long step = 0;
+    int cur = 0;
+    int grid = 0;
+
+    unsigned *status() const { return reinterpret_cast<unsigned *>(ws); }
+    unsigned long long *counter() const { return reinterpret_cast<unsigned long long *>(ws + 8); }
+    PCtrl *ctrl() const { return reinterpret_cast<PCtrl *>(ws + L.ctrl); }
+    PBar *bar() const { return reinterpret_cast<PBar *>(ws + L.bar); }
+    PInst *d_inst() const { return reinterpret_cast<PInst *>(ws + L.inst); }
+    PItem *d_items() const { return reinterpret_cast<PItem *>(ws + L.items); }
+};
+
+namespace {
+
+int sm_count_b()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+void drop_graph(cue_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_steps = -1;
+}
+
+int pick_rows_b(const cue_batch *b)
+{
+    if (b->rows > 0) return b->rows;
+    long long tiles4 = 0;
+    for (int i = 0; i < b->n; ++i) tiles4 += persist_tiles(b->in[i].params.nx, b->in[i].params.ny, 4);
+    const long long target = 2LL * sm_count_b();
+    int rows = 4;
+    while (rows > 1 && tiles4 * (4 / rows) < target) rows /= 2;
+    return rows;
+}
+
+// (Re)build the instance table and the work list for the current rows.
+int stage_list(cue_batch *b)
+{
+    const int rows = pick_rows_b(b);
+    if (b->list_ready && rows == b->rows_used) return CUE_OK;
+    for (int i = 0; i < b->n; ++i) persist_fill(b->insts[i], b->insts[i].f, rows, b->in[i].pitch);
+    std::vector<PItem> items;
+    persist_items(b->insts, items);
+    if (items.size() > b->L.items_cap) return CUE_ERR_WORKSPACE;
+    if (cudaMemcpyAsync(b->d_inst(), b->insts.data(), sizeof(PInst) * b->insts.size(), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess ||
+        (!items.empty() && cudaMemcpyAsync(b->d_items(), items.data(), sizeof(PItem) * items.size(),
+                                           cudaMemcpyHostToDevice, b->stream) != cudaSuccess) ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)       // the host vectors are released below
+        return CUE_ERR_CUDA;
+    b->n_items = (int)items.size();
+    b->rows_used = rows;
+    b->list_ready = true;
+    drop_graph(b);
+    return CUE_OK;
+}
+
+cudaError_t launch_direct(cue_batch *b, int nsteps)
+{
+    return persist_launch(b->d_inst(), b->d_items(), b->n_items, nsteps, 0, 0, b->bar(), b->bpsm, 0, 0, b->status(),
+                          b->stream, &b->grid, b->ctrl());
+}
+
+int run_graph(cue_batch *b, int nsteps)
+{
+    if (!b->graph || b->graph_steps != nsteps) {
+        drop_graph(b);
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CUE_ERR_CUDA;
+        cudaError_t e = launch_direct(b, nsteps);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return CUE_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return CUE_ERR_CUDA;
+        }
+        b->graph_steps = nsteps;
+        b->graph_grid = b->grid;
+    }
+    b->grid = b->graph_grid;
+    return cudaGraphLaunch(b->graph, b->stream) == cudaSuccess ? CUE_OK : CUE_ERR_CUDA;
+}
+
+int run_batch(cue_batch *b, int nsteps)
+{
+    int rc = stage_list(b);
+    if (rc != CUE_OK) return rc;
+    if (b->use_graph) {
+        rc = run_graph(b, nsteps);
+    } else {
+        rc = launch_direct(b, nsteps) == cudaSuccess ? CUE_OK : CUE_ERR_CUDA;
+    }
+    if (rc != CUE_OK) return rc;
+    b->step += nsteps;
+    b->cur ^= (nsteps & 1);
+    return CUE_OK;
+}
+
+// Save / restore every instance's current state (field, pos, dir, active),
+// the step control block and the cone counter.
+int save_state(cue_batch *b, unsigned long long *counter)
+{
+    for (int i = 0; i < b->n; ++i) {
+        const cue_instance &I = b->in[i];
+        const float *f = b->cur ? I.field_b : I.field_a;
+        unsigned char *bf = b->ws + b->L.bk_field[i], *bc = b->ws + b->L.bk_cone[i];
+        const size_t na = (size_t)I.n_axons;
+        if (cudaMemcpyAsync(bf, f, sizeof(float) * inst_cells(I), cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+            return CUE_ERR_CUDA;
+        if (na && (cudaMemcpyAsync(bc, I.pos, sizeof(float) * 2 * na, cudaMemcpyDeviceToDevice, b->stream) !=
+                       cudaSuccess ||
+                   cudaMemcpyAsync(bc + sizeof(float) * 2 * na, I.dir, sizeof(float) * 2 * na,
+                                   cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+                   cudaMemcpyAsync(bc + sizeof(float) * 4 * na, I.active, na, cudaMemcpyDeviceToDevice, b->stream) !=
+                       cudaSuccess))
+            return CUE_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(counter, b->counter(), sizeof(*counter), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return CUE_ERR_CUDA;
+    return CUE_OK;
+}
+
+int restore_state(cue_batch *b, int cur, long long step, unsigned long long counter)
+{
+    for (int i = 0; i < b->n; ++i) {
+        const cue_instance &I = b->in[i];
+        float *f = cur ? I.field_b : I.field_a;
+        const unsigned char *bf = b->ws + b->L.bk_field[i], *bc = b->ws + b->L.bk_cone[i];
+        const size_t na = (size_t)I.n_axons;
+        if (cudaMemcpyAsync(f, bf, sizeof(float) * inst_cells(I), cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+            return CUE_ERR_CUDA;
+        if (na && (cudaMemcpyAsync(I.pos, bc, sizeof(float) * 2 * na, cudaMemcpyDeviceToDevice, b->stream) !=
+                       cudaSuccess ||
+                   cudaMemcpyAsync(I.dir, bc + sizeof(float) * 2 * na, sizeof(float) * 2 * na,
+                                   cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+                   cudaMemcpyAsync(I.active, bc + sizeof(float) * 4 * na, na, cudaMemcpyDeviceToDevice, b->stream) !=
+                       cudaSuccess))
+            return CUE_ERR_CUDA;
+    }
+    PCtrl c{};
+    c.cur = cur;
+    c.step0 = (uint32_t)step;
+    if (cudaMemcpyAsync(b->ctrl(), &c, sizeof(c), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->counter(), &counter, sizeof(counter), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return CUE_ERR_CUDA;
+    b->cur = cur;
+    b->step = step;
+    return CUE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cue_batch_workspace_bytes(int32_t n, const cue_instance *inst, int32_t with_backup)
+{
+    if (n <= 0 || !inst) return 0;
+    for (int i = 0; i < n; ++i)
+        if (inst[i].params.dim != 2 || inst[i].pitch < inst[i].params.nx || inst[i].n_src < 0 ||
+            inst[i].n_axons < 0)
+            return 0;
+    return batch_layout(n, inst, with_backup != 0).total;
+}
+
+cue_batch *cue_batch_create(int32_t n, const cue_instance *inst, void *d_ws, size_t ws_bytes, void *stream,
+                            int32_t *err)
+{
+    int32_t dummy;
+    if (!err) err = &dummy;
+    *err = CUE_ERR_ARG;
+    if (n <= 0 || !inst) return nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!instance_ok(inst[i])) return nullptr;
+    std::vector<FieldDesc> fd(n);
+    std::vector<ConeDesc> cd(n);
+    for (int i = 0; i < n; ++i) {
+        cue_params p = inst[i].params;
+        p.nz = 1;
+        if (make_descs(p, inst[i].cone, fd[i], cd[i]) != CUE_OK) {
+            *err = CUE_ERR_UNSTABLE;
+            return nullptr;
+        }
+    }
+    const BatchLayout with = batch_layout(n, inst, true), without = batch_layout(n, inst, false);
+    const bool backup = ws_bytes >= with.total;
+    if (!d_ws || ws_bytes < without.total || (reinterpret_cast<uintptr_t>(d_ws) & 255u)) {
+        *err = CUE_ERR_WORKSPACE;
+        return nullptr;
+    }
+    cue_batch *b = new (std::nothrow) cue_batch();
+    if (!b) return nullptr;
+    b->n = n;
+    b->in.assign(inst, inst + n);
+    b->L = backup ? with : without;
+    b->has_backup = backup;
+    b->ws = static_cast<unsigned char *>(d_ws);
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->insts.resize(n);
+    for (int i = 0; i < n; ++i) {
+        const cue_instance &I = inst[i];
+        PInst &P = b->insts[i];
+        P = PInst{};
+        P.f = fd[i];
+        P.c = cd[i];
+        P.field0 = I.field_a;
+        P.field1 = I.field_b;
+        P.map = I.src_map;
+        P.src_cell = I.src_cell;
+        P.src_emit = I.src_emit;
+        P.src_xyz = reinterpret_cast<const float *>(b->ws + b->L.xyz_off[i]);
+        P.n_src = I.n_src;
+        P.n_axons = I.n_axons;
+        P.pos = I.pos;
+        P.dir = I.dir;
+        P.active = I.active;
+        P.status = b->status();
+        P.counter = b->counter();
+    }
+    cudaError_t e = cudaMemsetAsync(b->ws, 0, b->L.inst, b->stream);     // status, counter, ctrl, barrier
+    for (int i = 0; e == cudaSuccess && i < n; ++i) {
+        const cue_instance &I = inst[i];
+        if (I.n_src > 0 && cd[i].stop_r2 >= 0.0f) {
+            batch_source_coords<<<(I.n_src + 127) / 128, 128, 0, b->stream>>>(
+                I.params.nx, I.params.ny, I.params.h, I.src_cell, I.n_src,
+                reinterpret_cast<float *>(b->ws + b->L.xyz_off[i]), b->status());
+            e = cudaGetLastError();
+        }
+    }
+    int rc = e == cudaSuccess ? stage_list(b) : CUE_ERR_CUDA;
+    if (rc != CUE_OK) {
+        *err = rc;
+        delete b;
+        return nullptr;
+    }
+    *err = CUE_OK;
+    return b;
+}
+
+int cue_batch_run(cue_batch *b, int32_t nsteps)
+{
+    if (!b || nsteps < 0) return CUE_ERR_ARG;
+    if (b->step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
+    if (nsteps == 0) return CUE_OK;
+    return run_batch(b, nsteps);
+}
+
+int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows_out, int32_t *bpsm_out, double *ms_out)
+{
+    if (!b || probe_steps <= 0) return CUE_ERR_ARG;
+    if (!b->has_backup) return CUE_ERR_WORKSPACE;
+    unsigned long long counter = 0;
+    const int cur0 = b->cur;
+    const long long step0 = b->step;
+    int rc = save_state(b, &counter);
+    if (rc != CUE_OK) return rc;
+    const int keep_rows = b->rows, keep_bpsm = b->bpsm;
+    const bool keep_graph = b->use_graph;
+    b->use_graph = false;
+    const int maxb = std::max(1, std::min(3, persist_max_blocks_per_sm()));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CUE_ERR_CUDA;
+    double best = 1e30;
+    int best_rows = 0, best_b = 0;
+    const int rows_c[3] = {1, 2, 4};
+    for (int ri = 0; ri < 3 && rc == CUE_OK; ++ri)
+        for (int bb = 1; bb <= maxb && rc == CUE_OK; ++bb) {
+            b->rows = rows_c[ri];
+            b->bpsm = bb;
+            rc = run_batch(b, 1);                              // warm: stages the list, first touch
+            if (rc == CUE_OK) rc = restore_state(b, cur0, step0, counter);
+            if (rc != CUE_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e0, b->stream) != cudaSuccess) rc = CUE_ERR_CUDA;
+            if (rc == CUE_OK) rc = run_batch(b, probe_steps);
+            if (rc == CUE_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess ||
+                                 cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = CUE_ERR_CUDA;
+            if (rc == CUE_OK && ms / probe_steps < best) {
+                best = ms / probe_steps;
+                best_rows = rows_c[ri];
+                best_b = bb;
+            }
+            if (rc == CUE_OK) rc = restore_state(b, cur0, step0, counter);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->use_graph = keep_graph;
+    if (rc != CUE_OK) {
+        b->rows = keep_rows;
+        b->bpsm = keep_bpsm;
+        return rc;
+    }
+    b->rows = best_rows;
+    b->bpsm = best_b;
+    b->list_ready = false;
+    drop_graph(b);
+    if (rows_out) *rows_out = best_rows;
+    if (bpsm_out) *bpsm_out = best_b;
+    if (ms_out) *ms_out = best;
+    return stage_list(b);
+}
+
+int cue_batch_set_option(cue_batch *b, int32_t option, int64_t value)
+{
+    if (!b) return CUE_ERR_ARG;
+    switch (option) {
+    case CUE_BOPT_ROWS:
+        if (value != 0 && value != 1 && value != 2 && value != 4) return CUE_ERR_ARG;
+        b->rows = (int)value;
+        b->list_ready = b->list_ready && pick_rows_b(b) == b->rows_used;
+        drop_graph(b);
+        return CUE_OK;
+    case CUE_BOPT_BLOCKS:
+        if (value < 0 || value > 8) return CUE_ERR_ARG;
+        b->bpsm = (int)value;
+        drop_graph(b);
+        return CUE_OK;
+    case CUE_BOPT_GRAPH:
+        if (value != 0 && value != 1) return CUE_ERR_ARG;
+        b->use_graph = value != 0;
+        if (!b->use_graph) drop_graph(b);
+        return CUE_OK;
+    default:
+        return CUE_ERR_ARG;
+    }
+}
+
+int cue_batch_get_option(const cue_batch *b, int32_t option, int64_t *value)
+{
+    if (!b || !value) return CUE_ERR_ARG;
+    switch (option) {
+    case CUE_BOPT_ROWS: *value = b->rows_used; return CUE_OK;
+    case CUE_BOPT_BLOCKS: *value = b->bpsm; return CUE_OK;
+    case CUE_BOPT_GRAPH: *value = b->use_graph ? 1 : 0; return CUE_OK;
+    case CUE_BINFO_ITEMS: *value = b->n_items; return CUE_OK;
+    case CUE_BINFO_STEP: *value = b->step; return CUE_OK;
+    case CUE_BINFO_CUR: *value = b->cur; return CUE_OK;
+    case CUE_BINFO_GRID: *value = b->grid; return CUE_OK;
+    default: return CUE_ERR_ARG;
+    }
+}
+
+int cue_batch_status(cue_batch *b)
+{
+    if (!b) return CUE_ERR_ARG;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return CUE_ERR_CUDA;
+    unsigned word = 0;
+    if (cudaMemcpy(&word, b->status(), sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess) return CUE_ERR_CUDA;
+    if (word && cudaMemset(b->status(), 0, sizeof(unsigned)) != cudaSuccess) return CUE_ERR_CUDA;
+    if (word & kStatusNonFinite) return CUE_ERR_NONFINITE;
+    if (word & kStatusTimeout) return CUE_ERR_TIMEOUT;
+    if (word & kStatusBounds) return CUE_ERR_BOUNDS;
+    return cuda_err(cudaGetLastError());
+}
+
+int cue_batch_cone_updates(cue_batch *b, uint64_t *count)
+{
+    if (!b || !count) return CUE_ERR_ARG;
+    unsigned long long v = 0;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return CUE_ERR_CUDA;
+    if (cudaMemcpy(&v, b->counter(), sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return CUE_ERR_CUDA;
+    if (cudaMemset(b->counter(), 0, sizeof(v)) != cudaSuccess) return CUE_ERR_CUDA;
+    *count = v;
+    return CUE_OK;
+}
+
+void cue_batch_destroy(cue_batch *b)
+{
+    if (!b) return;
+    drop_graph(b);
+    delete b;
+}
+
+}  // extern "C"

@@ -26,6 +26,8 @@ struct WorkspaceLayout {
     size_t bin_list_off = 0;     // n_axons int32 (cone ids grouped by tile)
     size_t cone_tile_off = 0;    // n_axons int32 (tile of each cone, -1 = inactive)
     size_t cone_slot_off = 0;    // n_axons int32 (slot within its tile)
+    size_t persist_off = 0;      // persistent path: barrier, two instance records, work list
+    size_t persist_items_cap = 0;
     size_t total = 0;
     int n_tiles = 0;
 };
@@ -42,6 +44,56 @@ struct FusedGeom {
 };
 
 WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons);
+// Device descriptors of one simulation (CUE_ERR_UNSTABLE when the explicit step is unstable).
+int make_descs(const cue_params &params, const cone_params &cone, FieldDesc &f, ConeDesc &c);
+bool params_ok(const cue_params *p);
+bool cone_ok(const cone_params *c);
+bool aligned16(const void *p);
+int cuda_err(cudaError_t e);
+
+// ---- persistent path (k_persist.cu) ----
+constexpr int kPersistThreads = 256;          // 32 lanes x 8 warps
+constexpr int kPersistWarps = 8;
+constexpr int kPersistConeChunk = 256;        // cones per work item (one per thread)
+constexpr long long kPersistSpinLimit = 1LL << 24;   // polls (~32 ns apart) before a barrier gives up
+
+// One instance of the persistent engine (device-side table entry).
+struct PInst {
+    FieldDesc f;
+    ConeDesc c;
+    float *field0, *field1;
+    const float *map;                 // dense rate map or null
+    const int32_t *src_cell;
+    const float *src_emit;
+    const float *src_xyz;
+    int n_src;
+    int n_axons;
+    float *pos, *dir;
+    uint8_t *active;
+    unsigned *status;
+    unsigned long long *counter;
+    float *traj_field;                // trajectory mode: [nsteps + 1][cells] (else null)
+    float *traj_cone;                 // trajectory mode: [nsteps + 1][pos, dir][2][n] (else null)
+    size_t cells;                     // pitch * ny: elements of one field buffer
+    int ntx, rows;                    // field tiles per tile row, rows per thread
+    int pitch;                        // row pitch in floats (multiple of 4, >= nx)
+};
+struct PItem {
+    int inst;
+    int idx;                          // >= 0: field tile; < 0: cone chunk ~idx
+};
+struct PBar {
+    unsigned count, gen;
+    int abort;
+    unsigned pad;
+};
+// Step counter and buffer parity kept on the device (batched runs), so that a
+// captured launch can be replayed without new arguments.
+struct PCtrl {
+    int cur;
+    uint32_t step0;
+    uint32_t pad[2];
+};
 
 struct Sim {
     cue_params params;
@@ -79,6 +131,16 @@ struct Sim {
     double timed_ms = 0.0;
     uint64_t timed_launches = 0;
 
+    // persistent path
+    bool persist_ready = false, persist_used = false;
+    int persist_rows = 0;         // option (0 = heuristic)
+    int persist_rows_used = 0;
+    int persist_bpsm = 0;         // option: blocks per SM (0 = default)
+    int persist_phantom = 0;      // diagnostic option: barrier arrivals that never come
+    long long persist_limit = 0;  // option: polls before a bounded wait gives up (0 = default)
+    int persist_n_items = 0;
+    int persist_grid = 0;
+
     // fused path
     FusedGeom geom{};
     bool geom_ready = false;
@@ -99,7 +161,29 @@ struct Sim {
         return reinterpret_cast<unsigned long long *>(ws + wl.status_off + 8);
     }
     float *src_xyz() const { return reinterpret_cast<float *>(ws + wl.src_xyz_off); }
+    PBar *persist_bar() const { return reinterpret_cast<PBar *>(ws + wl.persist_off); }
+    PInst *persist_inst() const { return reinterpret_cast<PInst *>(ws + wl.persist_off + 256); }
+    PItem *persist_items() const
+    {
+        return reinterpret_cast<PItem *>(ws + wl.persist_off + 256 + ((2 * sizeof(PInst) + 255) & ~(size_t)255));
+    }
 };
+
+bool persist_supported(const Sim &s);
+int persist_max_blocks_per_sm();
+int persist_tiles(int nx, int ny, int rows);
+void persist_fill(PInst &I, const FieldDesc &f, int rows, int pitch);
+void persist_items(const std::vector<PInst> &insts, std::vector<PItem> &items);
+// ctrl null: cur0 / step0 are used; else they are read from *ctrl at the start,
+// and *ctrl is advanced by nsteps after the launch (a second, one-thread kernel).
+cudaError_t persist_launch(const PInst *d_insts, const PItem *d_items, int n_items, int nsteps, int cur0,
+                           uint32_t step0, PBar *d_bar, int blocks_per_sm, int phantom, long long limit,
+                           unsigned *status, cudaStream_t stream, int *grid_out, PCtrl *ctrl = nullptr);
+// Runs nsteps on the persistent path when selected (or AUTO) and supported:
+// CUE_OK / negative error when it ran, 1 when the caller should fall back.
+int run_persist_if_supported(Sim &s, int nsteps);
+// Coupled steps storing every state (trajectory slot 0 holds the start).
+int run_persist_trajectory(Sim &s, float *traj_field, float *traj_cone, uint32_t step0, int nsteps);
 
 // ---- fused, temporally blocked path (k_fused.cu) ----
 constexpr int kMaxTemporalDepth = 16;

@@ -46,9 +46,13 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // Block sum of two per-thread FP32 partials: warps sum in FP32, the block
-// total is formed and added to acc[0], acc[1] in FP64 (GB300's FP64 rate is a
-// small fraction of its FP32 rate, so FP64 is kept to a few operations per
-// block).  Every thread of the block must call it.
+// total is formed in FP64 (GB300's FP64 rate is a small fraction of its FP32
+// rate, so FP64 is kept to a few operations per block) and added to acc[0],
+// acc[1].  PART: acc is this block's own pair of slots (a plain
+// read-modify-write, no two blocks on one address, and the same sum order on
+// every run); otherwise acc is shared and updated atomically.  Every thread of
+// the block must call it.
+template <bool PART>
 __device__ __forceinline__ void block_add2(float a, float b, double *acc)
 {
     __shared__ float sa[32], sb[32];
@@ -68,8 +72,14 @@ __device__ __forceinline__ void block_add2(float a, float b, double *acc)
         da = warp_sum(da);
         db = warp_sum(db);
         if (lane == 0) {
-            atomicAdd(&acc[0], da);
-            atomicAdd(&acc[1], db);
+            if (PART) {
+                const size_t bid = blockIdx.x + (size_t)gridDim.x * blockIdx.y;
+                acc[2 * bid] += da;
+                acc[2 * bid + 1] += db;
+            } else {
+                atomicAdd(&acc[0], da);
+                atomicAdd(&acc[1], db);
+            }
         }
     }
 }
@@ -228,7 +238,7 @@ __global__ void __launch_bounds__(256) adj_field2d_vec4(FieldDesc f, const float
             cl = dl;
         }
     }
-    block_add2(tD, tL, acc);
+    block_add2<true>(tD, tL, acc);
 }
 
 // The same for any grid (2D or 3D, any nx), one node per thread iteration.
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(256) adj_field_scalar(FieldDesc f, const float
         mu_out[c] = o.hi;
         mu_out[n + c] = o.lo;
     }
-    block_add2(tD, tL, acc);
+    block_add2<true>(tD, tL, acc);
 }
 
 // End of a segment: S += Sseg in FP64, Sseg = 0.
@@ -400,6 +410,104 @@ __device__ __forceinline__ void cone_adjoint(const FieldDesc &f, const ConeDesc 
     for (int i = 0; i < DIM; ++i) pbar[i] = pb[i];
 }
 
+// 2D specialisation: the 12-node patch gathered for the forward recomputation
+// also gives the corner node gradients (position derivative), and the field
+// adjoint is summed per patch node in registers, then scattered with 12
+// independent double-float atomics (instead of reloading the nodes and
+// scattering 16 pairs corner by corner).  Patch slots are gather2's:
+//   0..3 (xm, x0, x1, xp) at y0;  4..7 the same at y1;  8, 9 (x0, x1) at ym;
+//   10, 11 (x0, x1) at yp.
+__device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc &c, const float *__restrict__ C,
+                                              uint32_t axon, uint32_t step, const float *p, const float *d,
+                                              float *pbar, float *dbar, float *mu)
+{
+    const size_t sy = f.nx;
+    auto ld = [&](int i, int j, int) { return __ldg(C + (size_t)i + sy * j); };
+    float xi[2];
+    cone_noise<2>(c.key0, c.key1, axon, step, xi);
+    int lo[3] = {0, 0, 0};
+    float fr[3] = {0.f, 0.f, 0.f};
+    cell_of<2>(f, p, lo, fr);
+    float v[kPatch2];
+    gather2(f, lo, ld, v);
+    float g[2];
+    grad2(c, v, fr, g);                                   // the forward's gradient, bit for bit
+    const float gn2 = fmaf(g[1], g[1], g[0] * g[0]);
+    const bool has_g = gn2 > c.eps2;
+    const float ginv = has_g ? rsqrtf(gn2) : 0.0f;
+    float vv[2], ghat[2], vn2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        ghat[i] = g[i] * ginv;
+        vv[i] = c.w_prev * d[i] + c.w_grad * ghat[i] + c.w_noise * xi[i];
+        vn2 = fmaf(vv[i], vv[i], vn2);
+    }
+    const bool has_v = vn2 > 1e-30f;
+    const float vinv = has_v ? rsqrtf(vn2) : 0.0f;
+    float dn[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) dn[i] = has_v ? vv[i] * vinv : d[i];
+    const float hi[2] = {c.hi0, c.hi1};
+    float qbar[2], dnbar[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float q = fmaf(c.step_len, dn[i], p[i]);
+        qbar[i] = (q < 0.0f || q > hi[i]) ? 0.0f : pbar[i];
+        dnbar[i] = fmaf(c.step_len, qbar[i], dbar[i]);
+    }
+    float vbar[2];
+    if (has_v) {
+        const float dot = fmaf(dn[1], dnbar[1], dn[0] * dnbar[0]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            vbar[i] = (dnbar[i] - dn[i] * dot) * vinv;
+            dbar[i] = c.w_prev * vbar[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            vbar[i] = 0.f;
+            dbar[i] = dnbar[i];
+        }
+    }
+    float gbar[2];
+    {
+        const float dot = fmaf(ghat[1], c.w_grad * vbar[1], ghat[0] * (c.w_grad * vbar[0]));
+#pragma unroll
+        for (int i = 0; i < 2; ++i) gbar[i] = has_g ? (c.w_grad * vbar[i] - ghat[i] * dot) * ginv : 0.0f;
+    }
+    // corner weights and node gradients (corner (a, b) = node (x_a, y_b))
+    const float wx0 = 1.0f - fr[0], wx1 = fr[0], wy0 = 1.0f - fr[1], wy1 = fr[1];
+    const float w00 = wx0 * wy0, w10 = wx1 * wy0, w01 = wx0 * wy1, w11 = wx1 * wy1;
+    const float gx00 = (v[2] - v[0]) * c.inv2h, gx10 = (v[3] - v[1]) * c.inv2h;
+    const float gx01 = (v[6] - v[4]) * c.inv2h, gx11 = (v[7] - v[5]) * c.inv2h;
+    const float gy00 = (v[5] - v[8]) * c.inv2h, gy10 = (v[6] - v[9]) * c.inv2h;
+    const float gy01 = (v[10] - v[1]) * c.inv2h, gy11 = (v[11] - v[2]) * c.inv2h;
+    // position: g(p) = sum_c w_c(p) G_c, dw/dp from the bilinear weights
+    const float s00 = fmaf(gbar[1], gy00, gbar[0] * gx00), s10 = fmaf(gbar[1], gy10, gbar[0] * gx10);
+    const float s01 = fmaf(gbar[1], gy01, gbar[0] * gx01), s11 = fmaf(gbar[1], gy11, gbar[0] * gx11);
+    pbar[0] = fmaf(f.inv_h, wy0 * (s10 - s00) + wy1 * (s11 - s01), qbar[0]);
+    pbar[1] = fmaf(f.inv_h, wx0 * (s01 - s00) + wx1 * (s11 - s10), qbar[1]);
+    if (!has_g) return;
+    // field: coefficient of each patch node in gbar . g
+    const float ax = gbar[0] * c.inv2h, ay = gbar[1] * c.inv2h;
+    const float cx00 = ax * w00, cx10 = ax * w10, cx01 = ax * w01, cx11 = ax * w11;
+    const float cy00 = ay * w00, cy10 = ay * w10, cy01 = ay * w01, cy11 = ay * w11;
+    const float sc[kPatch2] = {-cx00,        -cx10 - cy01, cx00 - cy11, cx10,
+                               -cx01,        cy00 - cx11,  cy10 + cx01, cx11,
+                               -cy00,        -cy10,        cy01,        cy11};
+    const int xm = max(lo[0] - 1, 0), x0 = lo[0], x1 = lo[0] + 1, xp = min(lo[0] + 2, f.nx - 1);
+    const int ym = max(lo[1] - 1, 0), y0 = lo[1], y1 = lo[1] + 1, yp = min(lo[1] + 2, f.ny - 1);
+    const int xs[kPatch2] = {xm, x0, x1, xp, xm, x0, x1, xp, x0, x1, x0, x1};
+    const int ys[kPatch2] = {y0, y0, y0, y0, y1, y1, y1, y1, ym, ym, yp, yp};
+    float *mu_lo = mu + sy * f.ny;
+#pragma unroll
+    for (int k = 0; k < kPatch2; ++k) {
+        const size_t j = (size_t)xs[k] + sy * ys[k];
+        atomic_add_df(mu + j, mu_lo + j, sc[k]);
+    }
+}
+
 // One backward step of the cones (+ de_k += mu_in[cell_k] by the first threads).
 template <int DIM>
 __global__ void __launch_bounds__(256) adj_cone_kernel(FieldDesc f, ConeDesc c, const float *__restrict__ C,
@@ -425,7 +533,10 @@ __global__ void __launch_bounds__(256) adj_cone_kernel(FieldDesc f, ConeDesc c, 
         pb[i] = pbar[(size_t)i * n + a];
         db[i] = dbar[(size_t)i * n + a];
     }
-    cone_adjoint<DIM>(f, c, C, (uint32_t)a, step, p, d, pb, db, mu_out);
+    if constexpr (DIM == 2)
+        cone_adjoint2(f, c, C, (uint32_t)a, step, p, d, pb, db, mu_out);
+    else
+        cone_adjoint<DIM>(f, c, C, (uint32_t)a, step, p, d, pb, db, mu_out);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
         pbar[(size_t)i * n + a] = pb[i];
@@ -448,18 +559,39 @@ __global__ void __launch_bounds__(256) adj_loss_kernel(int n, int dim, const flo
             dbar[(size_t)i * n + a] = 0.0f;
         }
     }
-    block_add2(s, 0.0f, loss_acc);
+    block_add2<false>(s, 0.0f, loss_acc);
 }
 
-// Scale the accumulators into the caller's outputs.
-__global__ void adj_finalize_kernel(FieldDesc f, int n_axons, const double *acc, int n_src, float *gD, float *gl,
-                                    float *gsrc, float *loss, const double *S, float *gmap, size_t n_cells)
+// Scale the accumulators into the caller's outputs (block 0 sums the field
+// kernel's per-block dD / dlambda slots).
+__global__ void __launch_bounds__(256) adj_finalize_kernel(FieldDesc f, int n_axons, const double *acc, int n_src,
+                                                           const double *part, int n_part, float *gD, float *gl,
+                                                           float *gsrc, float *loss, const double *S, float *gmap,
+                                                           size_t n_cells)
 {
     const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (t == 0) {
-        *gD = (float)((double)f.dt / ((double)f.h * f.h) * acc[0]);
-        *gl = (float)(-(double)f.dt * acc[1]);
-        *loss = (float)(acc[2 + n_src] / (n_axons > 0 ? n_axons : 1));
+    if (blockIdx.x == 0) {
+        __shared__ double sd[256], sl[256];
+        double d = 0.0, l = 0.0;
+        for (int i = threadIdx.x; i < n_part; i += blockDim.x) {
+            d += part[2 * i];
+            l += part[2 * i + 1];
+        }
+        sd[threadIdx.x] = d;
+        sl[threadIdx.x] = l;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+                sd[threadIdx.x] += sd[threadIdx.x + w];
+                sl[threadIdx.x] += sl[threadIdx.x + w];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            *gD = (float)((double)f.dt / ((double)f.h * f.h) * sd[0]);
+            *gl = (float)(-(double)f.dt * sl[0]);
+            *loss = (float)(acc[2 + n_src] / (n_axons > 0 ? n_axons : 1));
+        }
     }
     if (t < (size_t)n_src) gsrc[t] = (float)acc[2 + t];
     if (gmap)
@@ -467,11 +599,55 @@ __global__ void adj_finalize_kernel(FieldDesc f, int n_axons, const double *acc,
 }
 
 struct AdjLayout {
-    size_t ckpt_c, ckpt_p, seg_c, seg_p, mu, Sseg, S, pbar, acc, total;
+    size_t ckpt_c, ckpt_p, seg_c, seg_p, mu, Sseg, S, pbar, acc, part, total;
+    int n_part;
     int nseg;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int blocks_for(size_t n, int per) { return (int)((n + per - 1) / per); }
+
+int sm_count_adj()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+// Launch shape of the backward field kernel: the float4 kernel's (x blocks,
+// y blocks, rows) for 2D grids with nx % 4 == 0, else a 1D grid.  The layout
+// reserves one (dD, dlambda) slot pair per block.
+struct AdjFieldShape {
+    bool vec4;
+    int xb, yb, rows, blocks;
+};
+
+AdjFieldShape adj_field_shape(const cue_params &p)
+{
+    AdjFieldShape g{};
+    const size_t cells = (size_t)p.nx * p.ny * (p.dim == 3 ? p.nz : 1);
+    g.vec4 = p.dim == 2 && p.nx % 4 == 0;
+    if (g.vec4) {
+        const int BY = 8;
+        g.xb = (p.nx / 4 + 31) / 32;
+        g.rows = 8;      // the most rows per thread that still leaves >= 4 blocks per SM
+        while (g.rows > 1 && (long long)g.xb * ((p.ny + BY * g.rows - 1) / (BY * g.rows)) < 4LL * sm_count_adj())
+            g.rows /= 2;
+        g.yb = (p.ny + BY * g.rows - 1) / (BY * g.rows);
+        g.blocks = g.xb * g.yb;
+    } else {
+        g.blocks = std::min(blocks_for(cells, 256), sm_count_adj() * 16);
+    }
+    return g;
+}
+
+int adj_field_blocks(const cue_params &p) { return adj_field_shape(p).blocks; }
 
 AdjLayout adj_layout(const cue_params &p, int n_src, int n_axons, int nsteps, int k)
 {
@@ -496,24 +672,13 @@ AdjLayout adj_layout(const cue_params &p, int n_src, int n_axons, int nsteps, in
     off += align256(sizeof(double) * cells);
     L.pbar = off;
     off += align256(sizeof(float) * cone);
-    L.acc = off;                                  // sD, sL, de[n_src], loss, spare
+    L.acc = off;                                  // spare, spare, de[n_src], loss, spare
     off += align256(sizeof(double) * (4 + n_src));
+    L.n_part = adj_field_blocks(p);
+    L.part = off;                                 // per-block (dD, dlambda) sums of the field kernel
+    off += align256(sizeof(double) * 2 * (size_t)L.n_part);
     L.total = off;
     return L;
-}
-
-int blocks_for(size_t n, int per) { return (int)((n + per - 1) / per); }
-
-int sm_count_adj()
-{
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 152;
-    }
-    return n;
 }
 
 void launch_adj_field(Sim &s, const float *mu_in, float *mu_out, const float *C, float *Sseg, double *acc)
@@ -522,16 +687,12 @@ void launch_adj_field(Sim &s, const float *mu_in, float *mu_out, const float *C,
     const size_t cells = (size_t)f.nx * f.ny * f.nz;
     const bool aligned = ((reinterpret_cast<uintptr_t>(mu_in) | reinterpret_cast<uintptr_t>(mu_out) |
                            reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(Sseg)) & 15u) == 0;
-    if (f.dim == 2 && f.nx % 4 == 0 && aligned) {
-        const int nx4 = f.nx / 4, BY = 8;
-        const int xb = (nx4 + 31) / 32;
-        int rows = 8;      // the most rows per thread that still leaves >= 4 blocks per SM
-        while (rows > 1 && (long long)xb * ((f.ny + BY * rows - 1) / (BY * rows)) < 4LL * sm_count_adj()) rows /= 2;
-        dim3 grid(xb, (f.ny + BY * rows - 1) / (BY * rows));
-        adj_field2d_vec4<<<grid, dim3(32, BY), 0, s.stream>>>(f, mu_in, mu_out, C, Sseg, acc, rows);
+    const AdjFieldShape g = adj_field_shape(s.params);
+    if (g.vec4 && aligned) {
+        adj_field2d_vec4<<<dim3(g.xb, g.yb), dim3(32, 8), 0, s.stream>>>(f, mu_in, mu_out, C, Sseg, acc, g.rows);
     } else {
-        const int fb = std::min(blocks_for(cells, 256), sm_count_adj() * 16);
-        adj_field_scalar<<<fb, 256, 0, s.stream>>>(f, mu_in, mu_out, C, Sseg, acc);
+        adj_field_scalar<<<std::min(g.blocks, blocks_for(cells, 256)), 256, 0, s.stream>>>(f, mu_in, mu_out, C,
+                                                                                           Sseg, acc);
     }
     s.launches++;
 }
@@ -562,11 +723,13 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
     float *Sseg = gmap ? reinterpret_cast<float *>(W + L.Sseg) : nullptr;
     double *S = gmap ? reinterpret_cast<double *>(W + L.S) : nullptr;
     float *pbar = reinterpret_cast<float *>(W + L.pbar), *dbar = pbar + cone_n;
-    double *acc = reinterpret_cast<double *>(W + L.acc);     // sD, sL, de[n_src], loss
+    double *acc = reinterpret_cast<double *>(W + L.acc);     // spare, spare, de[n_src], loss
+    double *part = reinterpret_cast<double *>(W + L.part);   // per-block (dD, dlambda) sums
     cudaStream_t st = s.stream;
     auto ok = [](cudaError_t e) { return e == cudaSuccess; };
     if (!ok(cudaMemsetAsync(mu[0], 0, sizeof(float) * cells * 4, st)) ||
         !ok(cudaMemsetAsync(acc, 0, sizeof(double) * (4 + s.n_src), st)) ||
+        !ok(cudaMemsetAsync(part, 0, sizeof(double) * 2 * (size_t)L.n_part, st)) ||
         (S && !ok(cudaMemsetAsync(S, 0, sizeof(double) * cells, st))) ||
         (Sseg && !ok(cudaMemsetAsync(Sseg, 0, sizeof(float) * cells, st))))
         return CUE_ERR_CUDA;
@@ -596,7 +759,13 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
         if (!ok(cudaMemcpyAsync(sgC, ckC + cells * j, sizeof(float) * cells, cudaMemcpyDeviceToDevice, st)) ||
             !ok(cudaMemcpyAsync(sgP, ckP + 2 * cone_n * j, sizeof(float) * 2 * cone_n, cudaMemcpyDeviceToDevice, st)))
             return CUE_ERR_CUDA;
-        for (int m = 0; m < len; ++m) {      // recompute, storing every step
+        // recompute the segment, storing every step: one persistent launch where
+        // the path runs, else a cone and a field launch per step
+        int rc = (s.path != CUE_PATH_PLAIN && persist_supported(s))
+                     ? run_persist_trajectory(s, sgC, sgP, (uint32_t)nstart, len)
+                     : 1;
+        if (rc < 0) return rc;
+        for (int m = 0; rc == 1 && m < len; ++m) {
             float *Pm = sgP + 2 * cone_n * m, *Pn = sgP + 2 * cone_n * (m + 1);
             if (!ok(launch_cone_step_io(s, sgC + cells * m, (uint32_t)(nstart + m), Pm, Pm + cone_n, Pn,
                                         Pn + cone_n)) ||
@@ -605,7 +774,7 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
         }
         for (int m = len - 1; m >= 0; --m) {
             const float *Cm = sgC + cells * m, *Pm = sgP + 2 * cone_n * m;
-            launch_adj_field(s, mu[in], mu[in ^ 1], Cm, Sseg, acc);
+            launch_adj_field(s, mu[in], mu[in ^ 1], Cm, Sseg, part);
             const int cb = blocks_for((size_t)std::max(n, s.n_src), 64);
             if (cb > 0) {
                 if (dim == 2)
@@ -628,7 +797,7 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
     }
     adj_finalize_kernel<<<std::max(blocks_for((size_t)s.n_src, 256), std::min(blocks_for(cells, 256), 152 * 8)),
                           256, 0, st>>>(
-        f, n, acc, s.n_src, gD, gl, gsrc, loss, S, gmap, cells);
+        f, n, acc, s.n_src, part, L.n_part, gD, gl, gsrc, loss, S, gmap, cells);
     s.launches++;
     return ok(cudaGetLastError()) ? CUE_OK : CUE_ERR_CUDA;
 }

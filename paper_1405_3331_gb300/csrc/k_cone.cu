@@ -31,21 +31,28 @@ __global__ void __launch_bounds__(128) cone_plain(FieldDesc f, ConeDesc c, const
         for (int i = threadIdx.x; i < DIM * n_src; i += blockDim.x) s_src[i] = src_xyz[i];
         __syncthreads();
     }
+    // the state loads go out together and the noise is drawn while they are in flight
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = a < n && active[a];
-    count_active(counter, live);
-    if (!live) return;
+    const bool inr = a < n;
+    const uint8_t act = inr ? active[a] : 0;
     float p[DIM], d[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-        p[i] = pin[(size_t)i * n + a];
-        d[i] = din[(size_t)i * n + a];
+        p[i] = inr ? pin[(size_t)i * n + a] : 0.0f;
+        d[i] = inr ? din[(size_t)i * n + a] : 0.0f;
     }
+    float xi[DIM];
+    cone_noise<DIM>(c.key0, c.key1, (uint32_t)a, step, xi);
+    const bool live = inr && act;
+    count_active(counter, live);
+    if (!live) return;
     const size_t sy = f.nx, sz = (size_t)f.nx * f.ny;
     auto ld = [&](int i, int j, int k) { return __ldg(C + (size_t)i + sy * j + sz * k); };
     const float *src = in_smem ? s_src : src_xyz;
     const int stride = n_src;
-    bool alive = cone_update<DIM>(f, c, ld, (uint32_t)a, step, p, d, src, stride, use_stop ? n_src : 0);
+    float g[DIM];
+    sample_gradient<DIM>(f, c, p, ld, g);
+    bool alive = cone_finish_xi<DIM>(c, g, xi, p, d, src, stride, use_stop ? n_src : 0);
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {

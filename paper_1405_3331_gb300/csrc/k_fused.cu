@@ -804,7 +804,7 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
 
 int run_fused_if_supported(Sim &s, int nsteps)
 {
-    if (s.path == CUE_PATH_PLAIN) return 1;
+    if (s.path == CUE_PATH_PLAIN || s.path == CUE_PATH_PERSIST) return 1;
     if (!fused_supported(s)) {
         if (s.path == CUE_PATH_FUSED) return CUE_ERR_ARG;
         return 1;
@@ -826,7 +826,7 @@ int run_fused_if_supported(Sim &s, int nsteps)
 
 int field_fused_if_supported(Sim &s, int nsteps)
 {
-    if (s.path == CUE_PATH_PLAIN) return 1;
+    if (s.path == CUE_PATH_PLAIN || s.path == CUE_PATH_PERSIST) return 1;
     if (!fused_supported(s)) return s.path == CUE_PATH_FUSED ? CUE_ERR_ARG : 1;
     int rc = prepare(s);
     if (rc != CUE_OK) return s.path == CUE_PATH_FUSED ? rc : 1;

@@ -1,0 +1,485 @@
+// k_persist.cu -- persistent coupled-step engine for 2D grids: one cooperative
+// launch runs many steps of one or many simulation instances.
+//
+// A step of an instance is one phase: its field tiles (C^n -> C^{n+1} with the
+// rate map and the point sources) and its cone chunks (cones read C^n) touch
+// disjoint outputs, so every block walks one shared work list of (instance,
+// item) pairs, then all blocks meet at a grid barrier and the buffers swap.
+// The step costs a pass over the list plus one barrier instead of two or three
+// kernel launches, which is what a grid that fits in L2 (a few MB) is bound
+// by.  The same kernel steps a batch of independent instances of uneven sizes
+// and parameters: the per-instance table holds each one's physics, buffers
+// and tiling, and the work list interleaves their items.
+//
+// Arithmetic per node and per cone is the plain path's (node_update2, the map
+// as fma(dt, M, C'), sources added after the update; cone_update), so this
+// path matches the plain kernels bit for bit for distinct source cells.
+//
+// Coherence: data written during the launch (field buffers, cone state) is
+// read with ld.global.cg (L2), never through the non-coherent read-only path;
+// the barrier orders the steps with device-scope fences.  Every wait in the
+// barrier is bounded: past the limit the block raises the timeout status and
+// sets an abort flag that makes every other block leave at its next barrier.
+#include <algorithm>
+#include <vector>
+
+#include "cue_internal.h"
+
+namespace cue {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ bool finite4(const float4 &v)
+{
+    const float big = 3.402823466e38f;
+    return fabsf(v.x) <= big && fabsf(v.y) <= big && fabsf(v.z) <= big && fabsf(v.w) <= big;
+}
+
+// ---------------------------------------------------------------- one field tile
+// 32 lanes x 4 nodes in x (128 columns), 8 warps x R rows in y: the plain
+// float4 field kernel's block, here one work item.  Every load of the strip
+// (R + 2 rows, the R rows of the map, the warp-edge columns) is issued before
+// the first update, so a tile costs one L2 round trip.  Sources inside the
+// tile are added after its update (atomic, so duplicate cells accumulate).
+template <int R>
+__device__ __forceinline__ void field_tile_r(const PInst &I, const float *Cin, float *Cout, int tile)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const FieldDesc &f = I.f;
+    const int tx = tile % I.ntx, ty = tile / I.ntx;
+    const int p4 = I.pitch >> 2;                       // row pitch in float4
+    const int nxq = (f.nx + 3) >> 2;                   // float4 groups holding real columns
+    const int x4 = tx * 32 + lane;
+    const bool xin = x4 < nxq;
+    const int y0 = (ty * kPersistWarps + warp) * R;
+    const int x = x4 * 4;
+    const bool has_l = x > 0, has_r = x + 4 < f.nx;
+    const float4 *in4 = reinterpret_cast<const float4 *>(Cin);
+    float4 *out4 = reinterpret_cast<float4 *>(Cout);
+    const float4 *m4 = reinterpret_cast<const float4 *>(I.map);
+    bool bad = false;
+    if (y0 < f.ny) {                                   // warp-uniform
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 v[R + 2], m[R];
+        float el[R], er[R];
+#pragma unroll
+        for (int k = 0; k < R + 2; ++k) {              // rows y0 - 1 .. y0 + R (clamped; walls fixed below)
+            const int y = min(max(y0 - 1 + k, 0), f.ny - 1);
+            v[k] = xin ? __ldcg(in4 + (size_t)y * p4 + x4) : z4;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int y = min(y0 + k, f.ny - 1);
+            m[k] = (m4 && xin) ? __ldg(m4 + (size_t)y * p4 + x4) : z4;
+            el[k] = (lane == 0 && xin && has_l) ? __ldcg(Cin + (size_t)y * I.pitch + x - 1) : 0.f;
+            er[k] = (lane == 31 && xin && has_r) ? __ldcg(Cin + (size_t)y * I.pitch + x + 4) : 0.f;
+        }
+        // columns x .. x+3: which are real, and which have a real right neighbour
+        const bool v1 = x + 1 < f.nx, v2 = x + 2 < f.nx, v3 = x + 3 < f.nx;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int y = y0 + k;
+            if (y >= f.ny) break;                      // warp-uniform
+            const float4 cur = v[k + 1];
+            const float4 up = y > 0 ? v[k] : cur;
+            const float4 dn = y + 1 < f.ny ? v[k + 2] : cur;
+            float l = __shfl_up_sync(kFull, cur.w, 1);
+            float r = __shfl_down_sync(kFull, cur.x, 1);
+            if (lane == 0) l = el[k];
+            if (lane == 31) r = er[k];
+            if (!has_l) l = cur.x;
+            if (!has_r) r = cur.w;
+            if (xin) {
+                // a missing right neighbour (the wall, possibly inside this float4) is the node itself
+                const float rx = v1 ? cur.y : cur.x, ry = v2 ? cur.z : cur.y, rz = v3 ? cur.w : cur.z;
+                float4 o;
+                o.x = node_update2(cur.x, l, rx, up.x, dn.x, f.alpha, f.beta);
+                o.y = node_update2(cur.y, cur.x, ry, up.y, dn.y, f.alpha, f.beta);
+                o.z = node_update2(cur.z, cur.y, rz, up.z, dn.z, f.alpha, f.beta);
+                o.w = node_update2(cur.w, cur.z, r, up.w, dn.w, f.alpha, f.beta);
+                if (m4) {
+                    o.x = fmaf(f.dt, m[k].x, o.x);
+                    o.y = fmaf(f.dt, m[k].y, o.y);
+                    o.z = fmaf(f.dt, m[k].z, o.z);
+                    o.w = fmaf(f.dt, m[k].w, o.w);
+                }
+                if (!v1) o.y = cur.y;                  // padding columns keep their contents
+                if (!v2) o.z = cur.z;
+                if (!v3) o.w = cur.w;
+                bad |= !finite4(o);
+                out4[(size_t)y * p4 + x4] = o;
+            }
+        }
+    }
+    if (__any_sync(kFull, bad) && lane == 0) flag_status(I.status, kStatusNonFinite);
+    if (I.n_src > 0) {
+        __syncthreads();                               // the tile's stores, visible to the block
+        const int bx0 = tx * 128, bx1 = min(bx0 + 128, f.nx);
+        const int by0 = ty * kPersistWarps * R, by1 = min(by0 + kPersistWarps * R, f.ny);
+        const long long n_cells = (long long)f.nx * f.ny;
+        for (int k = threadIdx.x; k < I.n_src; k += blockDim.x) {
+            const int c = __ldg(I.src_cell + k);
+            if (c < 0 || (long long)c >= n_cells) {
+                if (tile == 0) flag_status(I.status, kStatusBounds);
+                continue;
+            }
+            const int cx = c % f.nx, cy = c / f.nx;
+            if (cx >= bx0 && cx < bx1 && cy >= by0 && cy < by1)
+                atomicAdd(Cout + (size_t)cy * I.pitch + cx, __ldg(I.src_emit + k));
+        }
+    }
+}
+
+__device__ __forceinline__ void field_tile(const PInst &I, const float *Cin, float *Cout, int tile)
+{
+    switch (I.rows) {
+    case 1: field_tile_r<1>(I, Cin, Cout, tile); break;
+    case 2: field_tile_r<2>(I, Cin, Cout, tile); break;
+    default: field_tile_r<4>(I, Cin, Cout, tile); break;
+    }
+}
+
+// ---------------------------------------------------------------- one cone chunk
+// The cone's state loads are issued together and its noise is drawn while they
+// are in flight; the active count goes to a per-thread counter (added to the
+// handle's counter once, at the end of the launch).
+__device__ __forceinline__ void cone_chunk(const PInst &I, const float *C, int chunk, uint32_t step,
+                                           const float *pin, const float *din, float *pout, float *dout,
+                                           unsigned &n_live)
+{
+    const int a = chunk * kPersistConeChunk + threadIdx.x;
+    const int n = I.n_axons;
+    if (a >= n) return;
+    const uint8_t act = __ldcg(I.active + a);
+    float p[2], d[2];
+    p[0] = __ldcg(pin + a);
+    p[1] = __ldcg(pin + n + a);
+    d[0] = __ldcg(din + a);
+    d[1] = __ldcg(din + n + a);
+    float xi[2];
+    cone_noise<2>(I.c.key0, I.c.key1, (uint32_t)a, step, xi);
+    if (!act) return;
+    n_live++;
+    const size_t sy = I.pitch;
+    auto ld = [&](int i, int j, int) { return __ldcg(C + (size_t)i + sy * j); };
+    float g[2];
+    sample_gradient<2>(I.f, I.c, p, ld, g);
+    const bool stop = I.c.stop_r2 >= 0.0f && I.n_src > 0;
+    const bool alive = cone_finish_xi<2>(I.c, g, xi, p, d, I.src_xyz, I.n_src, stop ? I.n_src : 0);
+    pout[a] = p[0];
+    pout[n + a] = p[1];
+    dout[a] = d[0];
+    dout[n + a] = d[1];
+    if (!alive) I.active[a] = 0;
+    const float big = 3.402823466e38f;
+    if (!(fabsf(p[0]) <= big && fabsf(p[1]) <= big && fabsf(d[0]) <= big && fabsf(d[1]) <= big))
+        flag_status(I.status, kStatusNonFinite);
+}
+
+// ---------------------------------------------------------------- grid barrier
+// Sense by generation: a block reads the generation, publishes its writes
+// (device fence), arrives; the last arrival resets the count and bumps the
+// generation; the others poll it with a bounded wait.  Returns false when the
+// launch is aborting.
+__device__ __forceinline__ bool grid_barrier(PBar *bar, unsigned expected, long long limit, unsigned *status)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &bar->gen;
+        volatile int *vabort = &bar->abort;
+        int ok = *vabort ? 0 : 1;
+        if (ok) {
+            const unsigned g = *vgen;
+            __threadfence();
+            const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
+            if (arrived == expected) {
+                atomicExch(&bar->count, 0u);
+                __threadfence();
+                atomicAdd(&bar->gen, 1u);
+            } else {
+                long long it = 0;
+                while (*vgen == g) {
+                    if (*vabort) {
+                        ok = 0;
+                        break;
+                    }
+                    if (++it > limit) {
+                        flag_status(status, kStatusTimeout);
+                        atomicExch(&bar->abort, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Add a thread's cone-update count to its instance's counter when the thread
+// moves to another instance's cones (and at the end of the launch).
+__device__ __forceinline__ void flush_live(const PInst *insts, int &live_inst, int next, unsigned &n_live)
+{
+    if (live_inst == next) return;
+    if (live_inst >= 0 && n_live) atomicAdd(insts[live_inst].counter, (unsigned long long)n_live);
+    n_live = 0;
+    live_inst = next;
+}
+
+__global__ void __launch_bounds__(kPersistThreads) persist_kernel(const PInst *__restrict__ insts,
+                                                                  const PItem *__restrict__ items, int n_items,
+                                                                  int nsteps, int cur0, uint32_t step0, PBar *bar,
+                                                                  unsigned expected, long long limit,
+                                                                  unsigned *status, const PCtrl *ctrl)
+{
+    if (ctrl) {
+        cur0 = ctrl->cur;
+        step0 = ctrl->step0;
+    }
+    unsigned n_live = 0;                               // cone updates by this thread (one instance per item)
+    int live_inst = -1;
+    for (int s = 0; s < nsteps; ++s) {
+        const int cur = (cur0 + s) & 1;
+        for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+            const PItem w = items[it];
+            const PInst &I = insts[w.inst];
+            const float *Cin;
+            float *Cout;
+            if (I.traj_field) {                         // trajectory mode: step s reads slot s, writes s + 1
+                Cin = I.traj_field + (size_t)s * I.cells;
+                Cout = I.traj_field + (size_t)(s + 1) * I.cells;
+            } else {
+                Cin = cur ? I.field1 : I.field0;
+                Cout = cur ? I.field0 : I.field1;
+            }
+            if (w.idx >= 0) {
+                field_tile(I, Cin, Cout, w.idx);
+            } else if (I.traj_cone) {
+                const size_t cn = (size_t)2 * I.n_axons;
+                const float *pin = I.traj_cone + (size_t)s * 2 * cn;
+                float *pout = I.traj_cone + (size_t)(s + 1) * 2 * cn;
+                flush_live(insts, live_inst, w.inst, n_live);
+                cone_chunk(I, Cin, ~w.idx, step0 + (uint32_t)s, pin, pin + cn, pout, pout + cn, n_live);
+            } else {
+                flush_live(insts, live_inst, w.inst, n_live);
+                cone_chunk(I, Cin, ~w.idx, step0 + (uint32_t)s, I.pos, I.dir, I.pos, I.dir, n_live);
+            }
+        }
+        if (s + 1 < nsteps && !grid_barrier(bar, expected, limit, status)) break;
+    }
+    flush_live(insts, live_inst, -1, n_live);
+}
+
+__global__ void persist_advance(PCtrl *ctrl, int nsteps)
+{
+    ctrl->cur ^= (nsteps & 1);
+    ctrl->step0 += (uint32_t)nsteps;
+}
+
+int sm_count_p()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+}  // namespace
+
+int persist_max_blocks_per_sm()
+{
+    static int nb = -1;
+    if (nb < 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, persist_kernel, kPersistThreads, 0) != cudaSuccess)
+            v = 0;
+        nb = v;
+    }
+    return nb;
+}
+
+int persist_tiles(int nx, int ny, int rows)
+{
+    const int ntx = ((nx + 3) / 4 + 31) / 32;
+    const int nty = (ny + kPersistWarps * rows - 1) / (kPersistWarps * rows);
+    return ntx * nty;
+}
+
+void persist_fill(PInst &I, const FieldDesc &f, int rows, int pitch)
+{
+    I.rows = rows;
+    I.ntx = ((f.nx + 3) / 4 + 31) / 32;
+    I.pitch = pitch;
+    I.cells = (size_t)pitch * f.ny;
+}
+
+// Work list: every instance's cone chunks first (their dependent loads take
+// longest), then the field tiles, instances interleaved round-robin so that a
+// block's consecutive items come from different instances.
+void persist_items(const std::vector<PInst> &insts, std::vector<PItem> &items)
+{
+    items.clear();
+    const int ni = (int)insts.size();
+    std::vector<int> ntile(ni), nchunk(ni);
+    int maxc = 0, maxt = 0;
+    for (int i = 0; i < ni; ++i) {
+        const PInst &I = insts[i];
+        ntile[i] = persist_tiles(I.f.nx, I.f.ny, I.rows);
+        nchunk[i] = (I.n_axons + kPersistConeChunk - 1) / kPersistConeChunk;
+        maxc = std::max(maxc, nchunk[i]);
+        maxt = std::max(maxt, ntile[i]);
+    }
+    for (int k = 0; k < maxc; ++k)
+        for (int i = 0; i < ni; ++i)
+            if (k < nchunk[i]) items.push_back(PItem{i, ~k});
+    for (int k = 0; k < maxt; ++k)
+        for (int i = 0; i < ni; ++i)
+            if (k < ntile[i]) items.push_back(PItem{i, k});
+}
+
+cudaError_t persist_launch(const PInst *d_insts, const PItem *d_items, int n_items, int nsteps, int cur0,
+                           uint32_t step0, PBar *d_bar, int blocks_per_sm, int phantom, long long limit,
+                           unsigned *status, cudaStream_t stream, int *grid_out, PCtrl *ctrl)
+{
+    const int maxb = persist_max_blocks_per_sm();
+    if (maxb <= 0) return cudaErrorInvalidConfiguration;
+    int bpsm = blocks_per_sm > 0 ? std::min(blocks_per_sm, maxb) : std::min(2, maxb);
+    int grid = std::min(n_items, bpsm * sm_count_p());
+    if (grid < 1) grid = 1;
+    if (grid_out) *grid_out = grid;
+    cudaError_t e = cudaMemsetAsync(d_bar, 0, sizeof(PBar), stream);
+    if (e != cudaSuccess) return e;
+    const unsigned expected = (unsigned)grid + (unsigned)(phantom > 0 ? phantom : 0);
+    const long long lim = limit > 0 ? limit : kPersistSpinLimit;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kPersistThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;     // all blocks co-resident: the barrier cannot starve
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, persist_kernel, d_insts, d_items, n_items, nsteps, cur0, step0, d_bar, expected,
+                           lim, status, static_cast<const PCtrl *>(ctrl));
+    if (e != cudaSuccess || !ctrl) return e;
+    persist_advance<<<1, 1, 0, stream>>>(ctrl, nsteps);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- single simulation
+bool persist_supported(const Sim &s)
+{
+    return s.fd.dim == 2 && s.vec4 && persist_max_blocks_per_sm() > 0;
+}
+
+static int pick_rows(const Sim &s)
+{
+    if (s.persist_rows > 0) return std::min(s.persist_rows, 4);
+    // enough tiles for every block of the launch to get one, with the longest strips
+    const int target = std::min(2, std::max(1, persist_max_blocks_per_sm())) * sm_count_p();
+    int rows = 4;
+    while (rows > 1 && persist_tiles(s.fd.nx, s.fd.ny, rows) < target) rows /= 2;
+    return rows;
+}
+
+static PInst sim_instance(const Sim &s, int rows)
+{
+    PInst I{};
+    I.f = s.fd;
+    I.c = s.cd;
+    I.field0 = s.field[0];
+    I.field1 = s.field[1];
+    I.map = s.src_map;
+    I.src_cell = s.src_cell;
+    I.src_emit = s.src_emit;
+    I.src_xyz = s.src_xyz();
+    I.n_src = s.n_src;
+    I.pos = s.pos;
+    I.dir = s.dir;
+    I.active = s.active;
+    I.n_axons = s.n_axons;
+    I.status = s.status();
+    I.counter = s.cone_counter();
+    persist_fill(I, s.fd, rows, s.fd.nx);
+    return I;
+}
+
+// Upload the instance record and the work list into the workspace (once per
+// configuration; the trajectory variant is built per call).
+static int persist_prepare(Sim &s, const PInst &I, int slot)
+{
+    std::vector<PInst> v{I};
+    std::vector<PItem> items;
+    persist_items(v, items);
+    if ((size_t)items.size() > s.wl.persist_items_cap) return CUE_ERR_WORKSPACE;
+    PInst *d_inst = s.persist_inst() + slot;
+    if (cudaMemcpyAsync(d_inst, &v[0], sizeof(PInst), cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
+        cudaMemcpyAsync(s.persist_items(), items.data(), sizeof(PItem) * items.size(), cudaMemcpyHostToDevice,
+                        s.stream) != cudaSuccess)
+        return CUE_ERR_CUDA;
+    s.persist_n_items = (int)items.size();
+    return CUE_OK;
+}
+
+int run_persist_if_supported(Sim &s, int nsteps)
+{
+    if (s.path != CUE_PATH_AUTO && s.path != CUE_PATH_PERSIST) return 1;
+    if (!persist_supported(s)) return s.path == CUE_PATH_PERSIST ? CUE_ERR_ARG : 1;
+    if (nsteps <= 0) return CUE_OK;
+    if (s.cd.stop_r2 >= 0.0f && s.n_src > 0 && !s.src_xyz_ready) {
+        if (launch_src_xyz(s) != cudaSuccess) return CUE_ERR_CUDA;
+        s.src_xyz_ready = true;
+    }
+    const int rows = pick_rows(s);
+    if (!s.persist_ready || s.persist_rows_used != rows) {
+        int rc = persist_prepare(s, sim_instance(s, rows), 0);
+        if (rc != CUE_OK) return rc;
+        s.persist_ready = true;
+        s.persist_rows_used = rows;
+    }
+    timing_begin(s);
+    cudaError_t e = persist_launch(s.persist_inst(), s.persist_items(), s.persist_n_items, nsteps, s.cur,
+                                   (uint32_t)s.cone_step, s.persist_bar(), s.persist_bpsm, s.persist_phantom,
+                                   s.persist_limit, s.status(), s.stream, &s.persist_grid);
+    timing_end(s);
+    s.launches++;
+    if (e != cudaSuccess) return CUE_ERR_CUDA;
+    s.cur ^= (nsteps & 1);
+    s.field_step += nsteps;
+    s.cone_step += nsteps;
+    s.persist_used = true;
+    return CUE_OK;
+}
+
+// nsteps coupled steps from (C, p, d) at traj slot 0, storing every step's
+// field and cone state in the trajectory buffers (the adjoint's recompute).
+int run_persist_trajectory(Sim &s, float *traj_field, float *traj_cone, uint32_t step0, int nsteps)
+{
+    if (!persist_supported(s)) return 1;
+    const int rows = pick_rows(s);
+    PInst I = sim_instance(s, rows);
+    I.traj_field = traj_field;
+    I.traj_cone = traj_cone;
+    int rc = persist_prepare(s, I, 1);
+    if (rc != CUE_OK) return rc;
+    s.persist_ready = false;                            // the work list was overwritten
+    cudaError_t e = persist_launch(s.persist_inst() + 1, s.persist_items(), s.persist_n_items, nsteps, 0, step0,
+                                   s.persist_bar(), s.persist_bpsm, 0, s.persist_limit, s.status(), s.stream,
+                                   nullptr);
+    s.launches++;
+    return e == cudaSuccess ? CUE_OK : CUE_ERR_CUDA;
+}
+
+}  // namespace cue

@@ -32,12 +32,18 @@ CUE_OPT_PATH = 1
 CUE_OPT_TEMPORAL_DEPTH = 2
 CUE_OPT_ROWS_PER_THREAD = 3
 CUE_OPT_TIME_KERNEL = 4
+CUE_OPT_PERSIST_ROWS = 5
+CUE_OPT_PERSIST_BLOCKS = 6
+CUE_OPT_WAIT_LIMIT = 7
+CUE_OPT_BARRIER_PHANTOM = 8
 CUE_INFO_LAST_PATH = 16
 CUE_INFO_TILE = 17
 CUE_INFO_DEPTH = 18
+CUE_INFO_GRID = 19
 CUE_PATH_AUTO = 0
 CUE_PATH_PLAIN = 1
 CUE_PATH_FUSED = 2
+CUE_PATH_PERSIST = 3
 
 EXPORTED = ("cue_workspace_bytes", "cue_init", "cue_step", "cone_step", "sim_run", "cue_get_state",
             "cue_set_state", "cue_set_stream", "cue_set_option", "cue_launch_count", "cue_status",
@@ -319,6 +325,10 @@ class Simulation:
     def fused_active(self) -> bool:
         """True when the last stepping call ran on the fused, temporally blocked path."""
         return self.get_option(CUE_INFO_LAST_PATH) == CUE_PATH_FUSED
+
+    def last_path(self) -> int:
+        """CUE_PATH_PLAIN, CUE_PATH_FUSED or CUE_PATH_PERSIST: the path of the last sim_run."""
+        return self.get_option(CUE_INFO_LAST_PATH)
 
     def launches(self) -> int:
         return cue_launch_count(self.h)

@@ -139,3 +139,35 @@ def test_calls_on_null_handle(cue):
     assert L.cue_set_option(None, 1, 0) == cue.CUE_ERR_ARG
     assert L.cue_launch_count(None) == 0
     L.cue_destroy(None)
+
+
+def test_batch_host_checks_answer_without_a_gpu(cue):
+    from paper_1405_3331_gb300 import batch
+    L = batch._lib()
+    inst = (batch.cue_instance * 2)()
+    for I in inst:
+        I.params = _params(cue, nx=66, ny=40)
+        I.cone = _cone(cue)
+        I.pitch = 68
+        I.field_a, I.field_b = 0x100000, 0x200000         # never dereferenced by the host checks
+        I.pos, I.dir, I.active = 0x300000, 0x400000, 0x500000
+        I.n_axons = 10
+    ws = L.cue_batch_workspace_bytes(2, inst, 0)
+    ws_bk = L.cue_batch_workspace_bytes(2, inst, 1)
+    assert ws > 0 and ws % 256 == 0 and ws_bk > ws
+    inst[1].pitch = 64                                     # pitch < nx
+    assert L.cue_batch_workspace_bytes(2, inst, 0) == 0
+    err = ct.c_int32(0)
+    assert not L.cue_batch_create(2, inst, None, 0, None, ct.byref(err))
+    assert err.value == cue.CUE_ERR_ARG
+    inst[1].pitch = 66                                     # not a multiple of 4
+    assert not L.cue_batch_create(2, inst, None, 0, None, ct.byref(err))
+    assert err.value == cue.CUE_ERR_ARG
+    inst[1].pitch = 68
+    inst[1].params = _params(cue, nx=66, ny=40, D=5.0)    # alpha = 1 > 1/4
+    assert not L.cue_batch_create(2, inst, None, 0, None, ct.byref(err))
+    assert err.value == cue.CUE_ERR_UNSTABLE
+    inst[1].params = _params(cue, nx=66, ny=40)
+    assert not L.cue_batch_create(2, inst, None, 0, None, ct.byref(err))   # no workspace
+    assert err.value == cue.CUE_ERR_WORKSPACE
+    assert L.cue_batch_run(None, 1) == cue.CUE_ERR_ARG

@@ -1,0 +1,136 @@
+"""Batched runs (include/cue_batch.h): independent 2D instances of uneven sizes and
+parameters stepped by one persistent launch.
+
+Each instance must evolve bit for bit as it does alone on the plain path (same
+arithmetic per node and per cone, source cells distinct), whatever its nx (the
+batch stores rows with a pitch rounded up to 4 and walls can fall inside a
+float4), whether the launch is direct or a replayed CUDA graph, and after the
+autotuner has measured its candidates (it must restore the state it found).
+"""
+import numpy as np
+import pytest
+
+from paper_1405_3331_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cue():
+    from paper_1405_3331_gb300 import build
+    build.build()
+    from paper_1405_3331_gb300 import cue as binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def batch_mod(cue):
+    from paper_1405_3331_gb300 import batch
+    return batch
+
+
+def _mixed():
+    """Uneven sizes (nx % 4 in {0, 1, 2, 3}), physics, sources, cones, stop and clamp modes."""
+    out = [
+        W.make("b0", 2, 66, 70, D=0.8, lam=0.02, dt=0.2, n_src=3, n_axons=40, C0="smooth", seed=70),
+        W.make("b1", 2, 97, 64, D=1.5, lam=0.001, dt=0.12, n_src=5, n_axons=300, C0="smooth", seed=71,
+               stop_radius=2.0),
+        W.make("b2", 2, 128, 129, D=1.0, lam=0.05, dt=0.2, n_src=4, n_axons=257, C0="random", seed=72,
+               wall_mode=1),
+        W.make("b3", 2, 203, 51, D=0.6, lam=0.01, dt=0.3, n_src=8, n_axons=600, C0="smooth", seed=73,
+               src_map="random"),
+        W.make("b4", 2, 255, 255, D=2.0, lam=0.003, dt=0.1, n_src=16, n_axons=1000, C0="smooth", seed=74,
+               stop_radius=3.0),
+        W.make("b5", 2, 8, 9, n_src=1, n_axons=3, C0="random", seed=75),
+        W.make("b6", 2, 64, 64, n_src=0, n_axons=0, C0="smooth", seed=76),
+    ]
+    return out
+
+
+def _alone(cue, w, nsteps):
+    sim = cue.Simulation(w, path=cue.CUE_PATH_PLAIN)
+    sim.sim_run(nsteps)
+    sim.check()
+    C, pos, dirs, act, _, _ = sim.snapshot()
+    sim.close()
+    return C, pos, dirs, act
+
+
+def _assert_same(a, b, tag):
+    for x, y, what in zip(a, b, ("field", "pos", "dir", "active")):
+        assert np.array_equal(x, y), f"{tag}: {what} differs, max {np.abs(x.astype(float) - y.astype(float)).max()}"
+
+
+@pytest.mark.parametrize("nsteps", [1, 5, 33])
+def test_batch_equals_each_instance_alone(cue, batch_mod, nsteps):
+    ws = _mixed()
+    b = batch_mod.Batch(ws)
+    b.run(nsteps)
+    b.check()
+    for i, w in enumerate(ws):
+        _assert_same(b.snapshot(i), _alone(cue, w, nsteps), w.name)
+    assert b.get_option(batch_mod.CUE_BINFO_STEP) == nsteps
+    b.close()
+
+
+@pytest.mark.parametrize("rows,blocks", [(1, 1), (2, 3), (4, 2)])
+def test_launch_shape_does_not_change_results(cue, batch_mod, rows, blocks):
+    ws = _mixed()
+    b = batch_mod.Batch(ws)
+    b.set_option(batch_mod.CUE_BOPT_ROWS, rows)
+    b.set_option(batch_mod.CUE_BOPT_BLOCKS, blocks)
+    b.run(12)
+    b.check()
+    assert b.get_option(batch_mod.CUE_BOPT_ROWS) == rows
+    for i, w in enumerate(ws):
+        _assert_same(b.snapshot(i), _alone(cue, w, 12), w.name)
+    b.close()
+
+
+def test_graph_replays_equal_direct_launches(cue, batch_mod):
+    ws = _mixed()
+    a = batch_mod.Batch(ws)
+    a.run(30)
+    g = batch_mod.Batch(ws)
+    g.set_option(batch_mod.CUE_BOPT_GRAPH, 1)
+    for _ in range(3):
+        g.run(10)                                  # captured once, replayed twice
+    a.check()
+    g.check()
+    assert g.get_option(batch_mod.CUE_BOPT_GRAPH) == 1
+    for i, w in enumerate(ws):
+        _assert_same(a.snapshot(i), g.snapshot(i), w.name)
+    a.close()
+    g.close()
+
+
+def test_autotune_restores_the_state_and_keeps_a_valid_shape(cue, batch_mod):
+    ws = _mixed()
+    b = batch_mod.Batch(ws)
+    b.run(3)
+    before = [b.snapshot(i) for i in range(len(ws))]
+    updates_before = b.cone_updates()
+    rows, blocks, ms = b.autotune(4)
+    assert rows in (1, 2, 4) and 1 <= blocks <= 8 and ms > 0
+    assert b.get_option(batch_mod.CUE_BINFO_STEP) == 3
+    for i in range(len(ws)):
+        _assert_same(b.snapshot(i), before[i], ws[i].name)
+    assert b.cone_updates() == 0                    # the probes' updates were taken back
+    b.run(9)
+    b.check()
+    for i, w in enumerate(ws):
+        _assert_same(b.snapshot(i), _alone(cue, w, 12), w.name)
+    assert updates_before > 0
+    b.close()
+
+
+def test_batched_workload_sample_equals_instances_alone(cue, batch_mod):
+    """Sixteen instances of the 512-instance batched workload (sides U{64..1024}, D ~ U[0.5, 2],
+    lambda log-uniform, dt = 0.2 / D, 4-64 sources, 256-4096 cones)."""
+    ws = W.config_c4(n_instances=16, nsteps=8)
+    b = batch_mod.Batch(ws)
+    b.run(8)
+    b.check()
+    for i, w in enumerate(ws):
+        _assert_same(b.snapshot(i), _alone(cue, w, 8), w.name)
+    b.close()
