@@ -35,6 +35,9 @@ WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons)
     if (p.dim == 2 && p.nx >= 4) {
         w.persist_items_cap = (size_t)persist_tiles(p.nx, p.ny, 1) + (na + kPersistConeChunk - 1) / kPersistConeChunk;
         off += 256 + align256(2 * sizeof(PInst)) + align256(sizeof(PItem) * w.persist_items_cap);
+        const size_t ns = (size_t)(n_src > 0 ? n_src : 0);
+        w.persist_src_off = off;
+        off += align256(sizeof(PSrc) * ns) + align256(sizeof(int) * ns);
     }
     w.total = off;
     return w;

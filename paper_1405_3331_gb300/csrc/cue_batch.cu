@@ -16,12 +16,13 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Workspace: [status 0, counter 8 | ctrl 256 | barrier 512 | instance table |
-// work list | source coordinates | backup (optional)].
+// Workspace: [status | ctrl 256 | barrier 512 | per-instance cone counters |
+// instance table | work list | source coordinates and binned sources | backup
+// (optional)].
 struct BatchLayout {
-    size_t ctrl, bar, inst, items, src_xyz, backup, total;
+    size_t ctrl, bar, counters, inst, items, src_xyz, backup, total;
     size_t items_cap;
-    std::vector<size_t> xyz_off, bk_field, bk_cone;   // per instance
+    std::vector<size_t> xyz_off, ent_off, key_off, bk_field, bk_cone;   // per instance
 };
 
 size_t inst_cells(const cue_instance &I) { return (size_t)I.pitch * I.params.ny; }
@@ -34,6 +35,8 @@ BatchLayout batch_layout(int n, const cue_instance *in, bool backup)
     off += 256;
     L.bar = off;
     off += 256;
+    L.counters = off;                                    // one cone-update counter per instance
+    off += align256(sizeof(unsigned long long) * (size_t)n);
     L.inst = off;
     off += align256(sizeof(PInst) * (size_t)n);
     L.items_cap = 0;
@@ -44,9 +47,16 @@ BatchLayout batch_layout(int n, const cue_instance *in, bool backup)
     off += align256(sizeof(PItem) * std::max<size_t>(L.items_cap, 1));
     L.src_xyz = off;
     L.xyz_off.resize(n);
+    L.ent_off.resize(n);
+    L.key_off.resize(n);
     for (int i = 0; i < n; ++i) {
+        const size_t ns = (size_t)std::max(in[i].n_src, 0);
         L.xyz_off[i] = off;
-        off += align256(sizeof(float) * 3 * (size_t)std::max(in[i].n_src, 0));
+        off += align256(sizeof(float) * 3 * ns);
+        L.ent_off[i] = off;                              // sources binned to field tiles
+        off += align256(sizeof(PSrc) * ns);
+        L.key_off[i] = off;
+        off += align256(sizeof(int) * ns);
     }
     L.backup = off;
     L.bk_field.resize(n);
@@ -120,7 +130,7 @@ struct cue_batch {
     int grid = 0;
 
     unsigned *status() const { return reinterpret_cast<unsigned *>(ws); }
-    unsigned long long *counter() const { return reinterpret_cast<unsigned long long *>(ws + 8); }
+    unsigned long long *counters() const { return reinterpret_cast<unsigned long long *>(ws + L.counters); }
     PCtrl *ctrl() const { return reinterpret_cast<PCtrl *>(ws + L.ctrl); }
     PBar *bar() const { return reinterpret_cast<PBar *>(ws + L.bar); }
     PInst *d_inst() const { return reinterpret_cast<PInst *>(ws + L.inst); }
@@ -172,6 +182,8 @@ int stage_list(cue_batch *b)
                         b->stream) != cudaSuccess ||
         (!items.empty() && cudaMemcpyAsync(b->d_items(), items.data(), sizeof(PItem) * items.size(),
                                            cudaMemcpyHostToDevice, b->stream) != cudaSuccess) ||
+        persist_bin_sources(b->d_inst(), b->n, b->d_items(), (int)items.size(), b->status(), b->stream) !=
+            cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)       // the host vectors are released below
         return CUE_ERR_CUDA;
     b->n_items = (int)items.size();
@@ -230,8 +242,9 @@ int run_batch(cue_batch *b, int nsteps)
 
 // Save / restore every instance's current state (field, pos, dir, active),
 // the step control block and the cone counter.
-int save_state(cue_batch *b, unsigned long long *counter)
+int save_state(cue_batch *b, std::vector<unsigned long long> &counter)
 {
+    counter.assign(b->n, 0ull);
     for (int i = 0; i < b->n; ++i) {
         const cue_instance &I = b->in[i];
         const float *f = b->cur ? I.field_b : I.field_a;
@@ -247,13 +260,14 @@ int save_state(cue_batch *b, unsigned long long *counter)
                        cudaSuccess))
             return CUE_ERR_CUDA;
     }
-    if (cudaMemcpyAsync(counter, b->counter(), sizeof(*counter), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(counter.data(), b->counters(), sizeof(unsigned long long) * b->n, cudaMemcpyDeviceToHost,
+                        b->stream) != cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return CUE_ERR_CUDA;
     return CUE_OK;
 }
 
-int restore_state(cue_batch *b, int cur, long long step, unsigned long long counter)
+int restore_state(cue_batch *b, int cur, long long step, const std::vector<unsigned long long> &counter)
 {
     for (int i = 0; i < b->n; ++i) {
         const cue_instance &I = b->in[i];
@@ -274,7 +288,8 @@ int restore_state(cue_batch *b, int cur, long long step, unsigned long long coun
     c.cur = cur;
     c.step0 = (uint32_t)step;
     if (cudaMemcpyAsync(b->ctrl(), &c, sizeof(c), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(b->counter(), &counter, sizeof(counter), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->counters(), counter.data(), sizeof(unsigned long long) * b->n, cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return CUE_ERR_CUDA;
     b->cur = cur;
@@ -348,9 +363,11 @@ cue_batch *cue_batch_create(int32_t n, const cue_instance *inst, void *d_ws, siz
         P.dir = I.dir;
         P.active = I.active;
         P.status = b->status();
-        P.counter = b->counter();
+        P.counter = b->counters() + i;
+        P.src_ent = I.n_src > 0 ? reinterpret_cast<PSrc *>(b->ws + b->L.ent_off[i]) : nullptr;
+        P.src_key = I.n_src > 0 ? reinterpret_cast<int *>(b->ws + b->L.key_off[i]) : nullptr;
     }
-    cudaError_t e = cudaMemsetAsync(b->ws, 0, b->L.inst, b->stream);     // status, counter, ctrl, barrier
+    cudaError_t e = cudaMemsetAsync(b->ws, 0, b->L.inst, b->stream);     // status, ctrl, barrier, counters
     for (int i = 0; e == cudaSuccess && i < n; ++i) {
         const cue_instance &I = inst[i];
         if (I.n_src > 0 && cd[i].stop_r2 >= 0.0f) {
@@ -374,18 +391,23 @@ int cue_batch_run(cue_batch *b, int32_t nsteps)
 {
     if (!b || nsteps < 0) return CUE_ERR_ARG;
     if (b->step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
-    if (nsteps == 0) return CUE_OK;
-    return run_batch(b, nsteps);
+    for (int done = 0; done < nsteps;) {
+        const int k = std::min(nsteps - done, kPersistMaxSteps);
+        const int rc = run_batch(b, k);
+        if (rc != CUE_OK) return rc;
+        done += k;
+    }
+    return CUE_OK;
 }
 
 int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows_out, int32_t *bpsm_out, double *ms_out)
 {
     if (!b || probe_steps <= 0) return CUE_ERR_ARG;
     if (!b->has_backup) return CUE_ERR_WORKSPACE;
-    unsigned long long counter = 0;
+    std::vector<unsigned long long> counter;
     const int cur0 = b->cur;
     const long long step0 = b->step;
-    int rc = save_state(b, &counter);
+    int rc = save_state(b, counter);
     if (rc != CUE_OK) return rc;
     const int keep_rows = b->rows, keep_bpsm = b->bpsm;
     const bool keep_graph = b->use_graph;
@@ -491,11 +513,14 @@ int cue_batch_status(cue_batch *b)
 int cue_batch_cone_updates(cue_batch *b, uint64_t *count)
 {
     if (!b || !count) return CUE_ERR_ARG;
-    unsigned long long v = 0;
+    std::vector<unsigned long long> v(b->n, 0ull);
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return CUE_ERR_CUDA;
-    if (cudaMemcpy(&v, b->counter(), sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return CUE_ERR_CUDA;
-    if (cudaMemset(b->counter(), 0, sizeof(v)) != cudaSuccess) return CUE_ERR_CUDA;
-    *count = v;
+    if (cudaMemcpy(v.data(), b->counters(), sizeof(unsigned long long) * b->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CUE_ERR_CUDA;
+    if (cudaMemset(b->counters(), 0, sizeof(unsigned long long) * b->n) != cudaSuccess) return CUE_ERR_CUDA;
+    unsigned long long tot = 0;
+    for (unsigned long long x : v) tot += x;
+    *count = tot;
     return CUE_OK;
 }
 

@@ -28,6 +28,7 @@ struct WorkspaceLayout {
     size_t cone_slot_off = 0;    // n_axons int32 (slot within its tile)
     size_t persist_off = 0;      // persistent path: barrier, two instance records, work list
     size_t persist_items_cap = 0;
+    size_t persist_src_off = 0;  // persistent path: binned sources (PSrc) and their tile keys
     size_t total = 0;
     int n_tiles = 0;
 };
@@ -56,7 +57,14 @@ constexpr int kPersistThreads = 256;          // 32 lanes x 8 warps
 constexpr int kPersistWarps = 8;
 constexpr int kPersistConeChunk = 256;        // cones per work item (one per thread)
 constexpr long long kPersistSpinLimit = 1LL << 24;   // polls (~32 ns apart) before a barrier gives up
+constexpr int kPersistMaxSteps = 1 << 19;            // steps per launch (the barrier's ticket counter stays < 2^31)
 
+// A point source binned to its field tile: node offset y * pitch + x (-1 when
+// the cell is outside the grid) and the source's index.
+struct PSrc {
+    int off;
+    int k;
+};
 // One instance of the persistent engine (device-side table entry).
 struct PInst {
     FieldDesc f;
@@ -74,6 +82,8 @@ struct PInst {
     unsigned long long *counter;
     float *traj_field;                // trajectory mode: [nsteps + 1][cells] (else null)
     float *traj_cone;                 // trajectory mode: [nsteps + 1][pos, dir][2][n] (else null)
+    PSrc *src_ent;                    // n_src binned sources, sorted by (tile, index), or null
+    int *src_key;                     // their tiles (same order)
     size_t cells;                     // pitch * ny: elements of one field buffer
     int ntx, rows;                    // field tiles per tile row, rows per thread
     int pitch;                        // row pitch in floats (multiple of 4, >= nx)
@@ -81,7 +91,10 @@ struct PInst {
 struct PItem {
     int inst;
     int idx;                          // >= 0: field tile; < 0: cone chunk ~idx
+    int src_begin, src_n;             // field tile: its range of the instance's binned sources
+                                      // (src_n < 0: sources not binned, the tile scans them)
 };
+constexpr int kPersistBinCap = 4096;  // instances with more sources scan them per tile
 struct PBar {
     unsigned count, gen;
     int abort;
@@ -167,6 +180,11 @@ struct Sim {
     {
         return reinterpret_cast<PItem *>(ws + wl.persist_off + 256 + ((2 * sizeof(PInst) + 255) & ~(size_t)255));
     }
+    PSrc *persist_src_ent() const { return reinterpret_cast<PSrc *>(ws + wl.persist_src_off); }
+    int *persist_src_key() const
+    {
+        return reinterpret_cast<int *>(ws + wl.persist_src_off + ((sizeof(PSrc) * (size_t)n_src + 255) & ~(size_t)255));
+    }
 };
 
 bool persist_supported(const Sim &s);
@@ -176,6 +194,10 @@ void persist_fill(PInst &I, const FieldDesc &f, int rows, int pitch);
 void persist_items(const std::vector<PInst> &insts, std::vector<PItem> &items);
 // ctrl null: cur0 / step0 are used; else they are read from *ctrl at the start,
 // and *ctrl is advanced by nsteps after the launch (a second, one-thread kernel).
+// Bin every instance's sources to its field tiles and give each field-tile item
+// its range (after the table and the list are in device memory).
+cudaError_t persist_bin_sources(PInst *d_insts, int n_inst, PItem *d_items, int n_items, unsigned *status,
+                                cudaStream_t stream);
 cudaError_t persist_launch(const PInst *d_insts, const PItem *d_items, int n_items, int nsteps, int cur0,
                            uint32_t step0, PBar *d_bar, int blocks_per_sm, int phantom, long long limit,
                            unsigned *status, cudaStream_t stream, int *grid_out, PCtrl *ctrl = nullptr);

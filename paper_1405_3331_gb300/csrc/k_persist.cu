@@ -42,8 +42,9 @@ __device__ __forceinline__ bool finite4(const float4 &v)
 // (R + 2 rows, the R rows of the map, the warp-edge columns) is issued before
 // the first update, so a tile costs one L2 round trip.  Sources inside the
 // tile are added after its update (atomic, so duplicate cells accumulate).
-template <int R>
-__device__ __forceinline__ void field_tile_r(const PInst &I, const float *Cin, float *Cout, int tile)
+template <int R, bool MAP>
+__device__ __forceinline__ void field_tile_r(const PInst &I, const float *Cin, float *Cout, int tile, int src_begin,
+                                             int src_n, bool check)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const FieldDesc &f = I.f;
@@ -55,30 +56,44 @@ __device__ __forceinline__ void field_tile_r(const PInst &I, const float *Cin, f
     const int y0 = (ty * kPersistWarps + warp) * R;
     const int x = x4 * 4;
     const bool has_l = x > 0, has_r = x + 4 < f.nx;
+    const bool ragged = (tx + 1) * 128 > f.nx;          // this tile holds the right wall (tile-uniform)
     const float4 *in4 = reinterpret_cast<const float4 *>(Cin);
     float4 *out4 = reinterpret_cast<float4 *>(Cout);
     const float4 *m4 = reinterpret_cast<const float4 *>(I.map);
     bool bad = false;
     if (y0 < f.ny) {                                   // warp-uniform
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 v[R + 2], m[R];
+        float4 v[R + 2], m[MAP ? R : 1];
         float el[R], er[R];
+        const float4 *col = in4 + x4;
 #pragma unroll
         for (int k = 0; k < R + 2; ++k) {              // rows y0 - 1 .. y0 + R (clamped; walls fixed below)
             const int y = min(max(y0 - 1 + k, 0), f.ny - 1);
-            v[k] = xin ? __ldcg(in4 + (size_t)y * p4 + x4) : z4;
+            v[k] = xin ? __ldcg(col + y * p4) : z4;
+        }
+        if constexpr (MAP) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) m[k] = xin ? __ldg(m4 + min(y0 + k, f.ny - 1) * p4 + x4) : z4;
         }
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            const int y = min(y0 + k, f.ny - 1);
-            m[k] = (m4 && xin) ? __ldg(m4 + (size_t)y * p4 + x4) : z4;
-            el[k] = (lane == 0 && xin && has_l) ? __ldcg(Cin + (size_t)y * I.pitch + x - 1) : 0.f;
-            er[k] = (lane == 31 && xin && has_r) ? __ldcg(Cin + (size_t)y * I.pitch + x + 4) : 0.f;
+            el[k] = 0.f;
+            er[k] = 0.f;
+        }
+        if (lane == 0 && xin && has_l) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) el[k] = __ldcg(Cin + (size_t)min(y0 + k, f.ny - 1) * I.pitch + x - 1);
+        }
+        if (lane == 31 && xin && has_r) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) er[k] = __ldcg(Cin + (size_t)min(y0 + k, f.ny - 1) * I.pitch + x + 4);
         }
         // columns x .. x+3: which are real, and which have a real right neighbour
-        const bool v1 = x + 1 < f.nx, v2 = x + 2 < f.nx, v3 = x + 3 < f.nx;
+        const bool v1 = !ragged || x + 1 < f.nx, v2 = !ragged || x + 2 < f.nx, v3 = !ragged || x + 3 < f.nx;
+        float4 *orow = out4 + x4 + y0 * p4;
+        int base = y0 * I.pitch + x;
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
+        for (int k = 0; k < R; ++k, orow += p4, base += I.pitch) {
             const int y = y0 + k;
             if (y >= f.ny) break;                      // warp-uniform
             const float4 cur = v[k + 1];
@@ -86,34 +101,54 @@ __device__ __forceinline__ void field_tile_r(const PInst &I, const float *Cin, f
             const float4 dn = y + 1 < f.ny ? v[k + 2] : cur;
             float l = __shfl_up_sync(kFull, cur.w, 1);
             float r = __shfl_down_sync(kFull, cur.x, 1);
-            if (lane == 0) l = el[k];
-            if (lane == 31) r = er[k];
+            if (lane == 0) l = has_l ? el[k] : cur.x;
+            if (lane == 31) r = has_r ? er[k] : cur.w;
             if (!has_l) l = cur.x;
             if (!has_r) r = cur.w;
             if (xin) {
-                // a missing right neighbour (the wall, possibly inside this float4) is the node itself
-                const float rx = v1 ? cur.y : cur.x, ry = v2 ? cur.z : cur.y, rz = v3 ? cur.w : cur.z;
                 float4 o;
-                o.x = node_update2(cur.x, l, rx, up.x, dn.x, f.alpha, f.beta);
-                o.y = node_update2(cur.y, cur.x, ry, up.y, dn.y, f.alpha, f.beta);
-                o.z = node_update2(cur.z, cur.y, rz, up.z, dn.z, f.alpha, f.beta);
+                if (ragged) {
+                    // a missing right neighbour (the wall, possibly inside this float4) is the node itself
+                    const float rx = v1 ? cur.y : cur.x, ry = v2 ? cur.z : cur.y, rz = v3 ? cur.w : cur.z;
+                    o.x = node_update2(cur.x, l, rx, up.x, dn.x, f.alpha, f.beta);
+                    o.y = node_update2(cur.y, cur.x, ry, up.y, dn.y, f.alpha, f.beta);
+                    o.z = node_update2(cur.z, cur.y, rz, up.z, dn.z, f.alpha, f.beta);
+                } else {
+                    o.x = node_update2(cur.x, l, cur.y, up.x, dn.x, f.alpha, f.beta);
+                    o.y = node_update2(cur.y, cur.x, cur.z, up.y, dn.y, f.alpha, f.beta);
+                    o.z = node_update2(cur.z, cur.y, cur.w, up.z, dn.z, f.alpha, f.beta);
+                }
                 o.w = node_update2(cur.w, cur.z, r, up.w, dn.w, f.alpha, f.beta);
-                if (m4) {
+                if constexpr (MAP) {
                     o.x = fmaf(f.dt, m[k].x, o.x);
                     o.y = fmaf(f.dt, m[k].y, o.y);
                     o.z = fmaf(f.dt, m[k].z, o.z);
                     o.w = fmaf(f.dt, m[k].w, o.w);
                 }
-                if (!v1) o.y = cur.y;                  // padding columns keep their contents
-                if (!v2) o.z = cur.z;
-                if (!v3) o.w = cur.w;
-                bad |= !finite4(o);
-                out4[(size_t)y * p4 + x4] = o;
+                // this tile's binned sources at these four nodes, in source order
+                for (int e = 0; e < src_n; ++e) {
+                    const int2 ent = __ldg(reinterpret_cast<const int2 *>(I.src_ent) + src_begin + e);
+                    const int rel = ent.x - base;
+                    if (rel >= 0 && rel < 4) {
+                        const float em = __ldg(I.src_emit + ent.y);
+                        if (rel == 0) o.x += em;
+                        else if (rel == 1) o.y += em;
+                        else if (rel == 2) o.z += em;
+                        else o.w += em;
+                    }
+                }
+                if (ragged) {
+                    if (!v1) o.y = cur.y;              // padding columns keep their contents
+                    if (!v2) o.z = cur.z;
+                    if (!v3) o.w = cur.w;
+                }
+                if (check) bad |= !finite4(o);
+                *orow = o;
             }
         }
     }
-    if (__any_sync(kFull, bad) && lane == 0) flag_status(I.status, kStatusNonFinite);
-    if (I.n_src > 0) {
+    if (check && __any_sync(kFull, bad) && lane == 0) flag_status(I.status, kStatusNonFinite);
+    if (src_n < 0) {                                   // sources not binned: scan them, add atomically
         __syncthreads();                               // the tile's stores, visible to the block
         const int bx0 = tx * 128, bx1 = min(bx0 + 128, f.nx);
         const int by0 = ty * kPersistWarps * R, by1 = min(by0 + kPersistWarps * R, f.ny);
@@ -131,12 +166,22 @@ __device__ __forceinline__ void field_tile_r(const PInst &I, const float *Cin, f
     }
 }
 
-__device__ __forceinline__ void field_tile(const PInst &I, const float *Cin, float *Cout, int tile)
+// Non-finite values persist once they appear, so the check runs on the last
+// step of a launch only (`check`).
+__device__ __forceinline__ void field_tile(const PInst &I, const float *Cin, float *Cout, const PItem &w, bool check)
 {
-    switch (I.rows) {
-    case 1: field_tile_r<1>(I, Cin, Cout, tile); break;
-    case 2: field_tile_r<2>(I, Cin, Cout, tile); break;
-    default: field_tile_r<4>(I, Cin, Cout, tile); break;
+    if (I.map) {
+        switch (I.rows) {
+        case 1: field_tile_r<1, true>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check); break;
+        case 2: field_tile_r<2, true>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check); break;
+        default: field_tile_r<4, true>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check); break;
+        }
+    } else {
+        switch (I.rows) {
+        case 1: field_tile_r<1, false>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check); break;
+        case 2: field_tile_r<2, false>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check); break;
+        default: field_tile_r<4, false>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check); break;
+        }
     }
 }
 
@@ -178,43 +223,51 @@ __device__ __forceinline__ void cone_chunk(const PInst &I, const float *C, int c
 }
 
 // ---------------------------------------------------------------- grid barrier
-// Sense by generation: a block reads the generation, publishes its writes
-// (device fence), arrives; the last arrival resets the count and bumps the
-// generation; the others poll it with a bounded wait.  Returns false when the
-// launch is aborting.
+// Ticket barrier: the arrival counter only grows (it is zeroed per launch).
+// A block's thread 0 takes a ticket with one acquire-release atomic (the
+// release publishes the block's writes, which the preceding __syncthreads
+// orders before it), and the barrier is passed once the counter reaches the
+// next multiple of `expected`: the last arrival needs no second write, and
+// the others poll with acquire loads, a bounded number of times.  Returns
+// false when the launch is aborting.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ bool grid_barrier(PBar *bar, unsigned expected, long long limit, unsigned *status)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = &bar->gen;
         volatile int *vabort = &bar->abort;
         int ok = *vabort ? 0 : 1;
         if (ok) {
-            const unsigned g = *vgen;
-            __threadfence();
-            const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
-            if (arrived == expected) {
-                atomicExch(&bar->count, 0u);
-                __threadfence();
-                atomicAdd(&bar->gen, 1u);
-            } else {
-                long long it = 0;
-                while (*vgen == g) {
-                    if (*vabort) {
-                        ok = 0;
-                        break;
-                    }
-                    if (++it > limit) {
-                        flag_status(status, kStatusTimeout);
-                        atomicExch(&bar->abort, 1);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(32);
+            const unsigned ticket = atom_add_acq_rel(&bar->count, 1u);
+            const unsigned target = (ticket / expected + 1u) * expected;
+            long long it = 0;
+            while ((int)(ld_acquire(&bar->count) - target) < 0) {
+                if (*vabort) {
+                    ok = 0;
+                    break;
                 }
+                if (++it > limit) {
+                    flag_status(status, kStatusTimeout);
+                    atomicExch(&bar->abort, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
             }
-            __threadfence();
         }
         s_ok = ok;
     }
@@ -224,15 +277,18 @@ __device__ __forceinline__ bool grid_barrier(PBar *bar, unsigned expected, long 
 
 // Add a thread's cone-update count to its instance's counter when the thread
 // moves to another instance's cones (and at the end of the launch).
+// Called by every thread of the block (block-uniform): one atomic per warp.
 __device__ __forceinline__ void flush_live(const PInst *insts, int &live_inst, int next, unsigned &n_live)
 {
     if (live_inst == next) return;
-    if (live_inst >= 0 && n_live) atomicAdd(insts[live_inst].counter, (unsigned long long)n_live);
+    const unsigned tot = __reduce_add_sync(kFull, n_live);
+    if (live_inst >= 0 && tot && (threadIdx.x & 31) == 0)
+        atomicAdd(insts[live_inst].counter, (unsigned long long)tot);
     n_live = 0;
     live_inst = next;
 }
 
-__global__ void __launch_bounds__(kPersistThreads) persist_kernel(const PInst *__restrict__ insts,
+__global__ void __launch_bounds__(kPersistThreads, 3) persist_kernel(const PInst *__restrict__ insts,
                                                                   const PItem *__restrict__ items, int n_items,
                                                                   int nsteps, int cur0, uint32_t step0, PBar *bar,
                                                                   unsigned expected, long long limit,
@@ -246,8 +302,10 @@ __global__ void __launch_bounds__(kPersistThreads) persist_kernel(const PInst *_
     int live_inst = -1;
     for (int s = 0; s < nsteps; ++s) {
         const int cur = (cur0 + s) & 1;
+        PItem nxt = (int)blockIdx.x < n_items ? items[blockIdx.x] : PItem{};
         for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-            const PItem w = items[it];
+            const PItem w = nxt;
+            if (it + (int)gridDim.x < n_items) nxt = items[it + gridDim.x];   // in flight while w runs
             const PInst &I = insts[w.inst];
             const float *Cin;
             float *Cout;
@@ -259,7 +317,7 @@ __global__ void __launch_bounds__(kPersistThreads) persist_kernel(const PInst *_
                 Cout = cur ? I.field0 : I.field1;
             }
             if (w.idx >= 0) {
-                field_tile(I, Cin, Cout, w.idx);
+                field_tile(I, Cin, Cout, w, s + 1 == nsteps);
             } else if (I.traj_cone) {
                 const size_t cn = (size_t)2 * I.n_axons;
                 const float *pin = I.traj_cone + (size_t)s * 2 * cn;
@@ -274,6 +332,69 @@ __global__ void __launch_bounds__(kPersistThreads) persist_kernel(const PInst *_
         if (s + 1 < nsteps && !grid_barrier(bar, expected, limit, status)) break;
     }
     flush_live(insts, live_inst, -1, n_live);
+}
+
+// One block per instance: each source's field tile (by the instance's rows),
+// then its rank among the (tile, index) keys by counting, which places it in
+// the sorted entry list.  Out-of-range cells raise the bounds status and sort
+// last with offset -1, never matched.
+__global__ void __launch_bounds__(256) bin_sources_kernel(const PInst *__restrict__ insts, unsigned *status)
+{
+    __shared__ int key[kPersistBinCap];
+    const PInst &I = insts[blockIdx.x];
+    const int n = I.n_src;
+    if (n <= 0 || n > kPersistBinCap || !I.src_ent) return;
+    const long long n_cells = (long long)I.f.nx * I.f.ny;
+    const int rows_px = kPersistWarps * I.rows;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int c = I.src_cell[k];
+        if (c < 0 || (long long)c >= n_cells) {
+            key[k] = 0x7fffffff;
+            flag_status(I.status, kStatusBounds);
+        } else {
+            key[k] = (c % I.f.nx) / 128 + I.ntx * ((c / I.f.nx) / rows_px);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int kk = key[k];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) rank += (key[j] < kk) || (key[j] == kk && j < k);
+        const int c = I.src_cell[k];
+        PSrc e;
+        e.off = kk == 0x7fffffff ? -1 : (c / I.f.nx) * I.pitch + c % I.f.nx;
+        e.k = k;
+        I.src_ent[rank] = e;
+        I.src_key[rank] = kk;
+    }
+}
+
+// Each field-tile item's range of its instance's binned sources.
+__global__ void item_sources_kernel(const PInst *__restrict__ insts, PItem *items, int n_items)
+{
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= n_items) return;
+    PItem w = items[it];
+    w.src_begin = 0;
+    w.src_n = 0;
+    if (w.idx >= 0) {
+        const PInst &I = insts[w.inst];
+        if (I.n_src > kPersistBinCap || (I.n_src > 0 && !I.src_ent)) {
+            w.src_n = -1;
+        } else if (I.n_src > 0) {
+            int lo = 0, hi = I.n_src;                  // first key >= tile
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (I.src_key[mid] < w.idx) lo = mid + 1;
+                else hi = mid;
+            }
+            int end = lo;
+            while (end < I.n_src && I.src_key[end] == w.idx) ++end;
+            w.src_begin = lo;
+            w.src_n = end - lo;
+        }
+    }
+    items[it] = w;
 }
 
 __global__ void persist_advance(PCtrl *ctrl, int nsteps)
@@ -306,6 +427,15 @@ int persist_max_blocks_per_sm()
         nb = v;
     }
     return nb;
+}
+
+cudaError_t persist_bin_sources(PInst *d_insts, int n_inst, PItem *d_items, int n_items, unsigned *status,
+                                cudaStream_t stream)
+{
+    if (n_inst <= 0 || n_items <= 0) return cudaSuccess;
+    bin_sources_kernel<<<n_inst, 256, 0, stream>>>(d_insts, status);
+    item_sources_kernel<<<(n_items + 255) / 256, 256, 0, stream>>>(d_insts, d_items, n_items);
+    return cudaGetLastError();
 }
 
 int persist_tiles(int nx, int ny, int rows)
@@ -341,10 +471,10 @@ void persist_items(const std::vector<PInst> &insts, std::vector<PItem> &items)
     }
     for (int k = 0; k < maxc; ++k)
         for (int i = 0; i < ni; ++i)
-            if (k < nchunk[i]) items.push_back(PItem{i, ~k});
+            if (k < nchunk[i]) items.push_back(PItem{i, ~k, 0, 0});
     for (int k = 0; k < maxt; ++k)
         for (int i = 0; i < ni; ++i)
-            if (k < ntile[i]) items.push_back(PItem{i, k});
+            if (k < ntile[i]) items.push_back(PItem{i, k, 0, 0});
 }
 
 cudaError_t persist_launch(const PInst *d_insts, const PItem *d_items, int n_items, int nsteps, int cur0,
@@ -360,6 +490,7 @@ cudaError_t persist_launch(const PInst *d_insts, const PItem *d_items, int n_ite
     cudaError_t e = cudaMemsetAsync(d_bar, 0, sizeof(PBar), stream);
     if (e != cudaSuccess) return e;
     const unsigned expected = (unsigned)grid + (unsigned)(phantom > 0 ? phantom : 0);
+    if ((long long)nsteps * expected >= (1LL << 31)) return cudaErrorInvalidValue;   // caller splits the run
     const long long lim = limit > 0 ? limit : kPersistSpinLimit;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -387,8 +518,8 @@ bool persist_supported(const Sim &s)
 static int pick_rows(const Sim &s)
 {
     if (s.persist_rows > 0) return std::min(s.persist_rows, 4);
-    // enough tiles for every block of the launch to get one, with the longest strips
-    const int target = std::min(2, std::max(1, persist_max_blocks_per_sm())) * sm_count_p();
+    // the longest strips that still give every SM a tile
+    const int target = sm_count_p();
     int rows = 4;
     while (rows > 1 && persist_tiles(s.fd.nx, s.fd.ny, rows) < target) rows /= 2;
     return rows;
@@ -412,6 +543,8 @@ static PInst sim_instance(const Sim &s, int rows)
     I.n_axons = s.n_axons;
     I.status = s.status();
     I.counter = s.cone_counter();
+    I.src_ent = s.n_src > 0 ? s.persist_src_ent() : nullptr;
+    I.src_key = s.n_src > 0 ? s.persist_src_key() : nullptr;
     persist_fill(I, s.fd, rows, s.fd.nx);
     return I;
 }
@@ -427,7 +560,8 @@ static int persist_prepare(Sim &s, const PInst &I, int slot)
     PInst *d_inst = s.persist_inst() + slot;
     if (cudaMemcpyAsync(d_inst, &v[0], sizeof(PInst), cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
         cudaMemcpyAsync(s.persist_items(), items.data(), sizeof(PItem) * items.size(), cudaMemcpyHostToDevice,
-                        s.stream) != cudaSuccess)
+                        s.stream) != cudaSuccess ||
+        persist_bin_sources(d_inst, 1, s.persist_items(), (int)items.size(), s.status(), s.stream) != cudaSuccess)
         return CUE_ERR_CUDA;
     s.persist_n_items = (int)items.size();
     return CUE_OK;
@@ -449,16 +583,20 @@ int run_persist_if_supported(Sim &s, int nsteps)
         s.persist_ready = true;
         s.persist_rows_used = rows;
     }
-    timing_begin(s);
-    cudaError_t e = persist_launch(s.persist_inst(), s.persist_items(), s.persist_n_items, nsteps, s.cur,
-                                   (uint32_t)s.cone_step, s.persist_bar(), s.persist_bpsm, s.persist_phantom,
-                                   s.persist_limit, s.status(), s.stream, &s.persist_grid);
-    timing_end(s);
-    s.launches++;
-    if (e != cudaSuccess) return CUE_ERR_CUDA;
-    s.cur ^= (nsteps & 1);
-    s.field_step += nsteps;
-    s.cone_step += nsteps;
+    for (int done = 0; done < nsteps;) {                // launches of at most kPersistMaxSteps steps
+        const int k = std::min(nsteps - done, kPersistMaxSteps);
+        timing_begin(s);
+        cudaError_t e = persist_launch(s.persist_inst(), s.persist_items(), s.persist_n_items, k, s.cur,
+                                       (uint32_t)s.cone_step, s.persist_bar(), s.persist_bpsm, s.persist_phantom,
+                                       s.persist_limit, s.status(), s.stream, &s.persist_grid);
+        timing_end(s);
+        s.launches++;
+        if (e != cudaSuccess) return CUE_ERR_CUDA;
+        s.cur ^= (k & 1);
+        s.field_step += k;
+        s.cone_step += k;
+        done += k;
+    }
     s.persist_used = true;
     return CUE_OK;
 }
