@@ -39,8 +39,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cue", "reference"], default="cue")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"])
-    ap.add_argument("--path", default="auto", choices=["auto", "plain", "fused"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "fused", "persist"])
     ap.add_argument("--depth", type=int, default=0, help="temporal depth on the fused path (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -275,10 +275,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    if args.workload == "c4":
+        return main_batch(args, torch, cue, dev, rank, world, dist, barrier)
     w = workload(args.workload, rank)
     if args.run_steps:
         w.nsteps = args.run_steps
-    path = {"auto": cue.CUE_PATH_AUTO, "plain": cue.CUE_PATH_PLAIN, "fused": cue.CUE_PATH_FUSED}[args.path]
+    path = {"auto": cue.CUE_PATH_AUTO, "plain": cue.CUE_PATH_PLAIN, "fused": cue.CUE_PATH_FUSED,
+            "persist": cue.CUE_PATH_PERSIST}[args.path]
     sim = cue.Simulation(w, device=dev, path=path)
     if args.depth:
         sim.set_option(cue.CUE_OPT_TEMPORAL_DEPTH, args.depth)
@@ -308,7 +311,9 @@ def main():
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     sampler = ClockSampler(gpu_id_for(local))
-    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 16)     # events around every 16th launch
+    # events around every 16th launch of the dominant kernel (every launch on the persistent
+    # path, where one launch is a whole run)
+    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 1 if sim_path_used(sim) == "persist" else 16)
     sim.kernel_time()
     barrier()
     sampler.start()
@@ -337,12 +342,16 @@ def main():
     bytes_per_cell = 12 if w.src_map is not None else 8
     if kern_n:
         steps_per_launch = (w.nsteps / (launches_per_run(sim, w)))
-        alg_bytes = bytes_per_cell * w.n_cells          # compulsory field traffic of one launch
+        # compulsory field traffic of one launch: the fused kernel reads and writes the field once
+        # for its K steps; the plain kernel once per step; the persistent kernel once per step of
+        # the whole run it covers
+        per_launch_passes = steps_per_launch if sim_path_used(sim) == "persist" else 1
+        alg_bytes = bytes_per_cell * w.n_cells * per_launch_passes
         avg_s = kern_ms / kern_n / 1e3
         achieved = alg_bytes / avg_s / 1e9
     else:
         steps_per_launch, alg_bytes, avg_s, achieved = 0, 0, 0, 0.0
-    kname = "fused" if fused else "field"
+    kname = {"fused": "fused", "persist": "persist"}.get(sim_path_used(sim), "field")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm if hbm else None,
                 "traffic": recorded_traffic(kname, args.workload),
@@ -407,6 +416,133 @@ def main():
     return 0
 
 
+def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
+    """512 independent 2D instances of uneven sizes and physics, 1,000 coupled steps, in one
+    persistent launch replayed from a captured CUDA graph, launch shape chosen by the autotuner.
+    One benchmark step = the whole batch from its initial state."""
+    from paper_1405_3331_gb300 import batch as B
+    from paper_1405_3331_gb300 import workloads as W
+    ws = W.config_c4(seed=3 + 100 * rank)
+    T = args.run_steps or ws[0].nsteps
+    cells = sum(w.n_cells for w in ws)
+    b = B.Batch(ws, device=dev)
+    stream = b.stream
+    init = [(b.fields[i][0].clone(), b.pos[i].clone(), b.dir[i].clone(), b.active[i].clone())
+            for i in range(len(ws))]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def reset():
+        with torch.cuda.stream(stream):
+            for i, (C, p, d, a) in enumerate(init):
+                b.fields[i][0].copy_(C)
+                b.pos[i].copy_(p)
+                b.dir[i].copy_(d)
+                b.active[i].copy_(a)
+        b.reset_state(0, 0)
+
+    rows, bpsm, tuned_ms = b.autotune(10)
+    b.set_option(B.CUE_BOPT_GRAPH, 1)
+    for _ in range(max(args.warmup, 3)):
+        reset()
+        b.run(T)
+    b.check()
+    b.cone_updates()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_id_for(dev.index or 0))
+    barrier()
+    sampler.start()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        reset()
+        evs[k][0].record(stream)
+        b.run(T)
+        evs[k][1].record(stream)
+    barrier()
+    clocks = sampler.stop()
+    b.check()
+    cone_updates = b.cone_updates() / args.steps
+    local_ms = sum(x.elapsed_time(y) for x, y in evs)
+    total_ms, value = aggregate(local_ms, cells * T, args.steps, world, dist, dev)
+    hbm, peak_kind = peaks()
+    per_launch_s = total_ms / args.steps / 1e3
+    achieved = 8.0 * cells * T / per_launch_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: {len(ws)} independent 2D instances (sides U{{64..1024}}, "
+                               f"{cells / 1e6:.1f} M cells, {sum(w.n_axons for w in ws)} cones), {T} steps",
+                   "instances": len(ws), "cells": cells, "steps_per_run": T,
+                   "launch": "one persistent launch per run, replayed from a CUDA graph",
+                   "autotuned": {"rows": rows, "blocks_per_sm": bpsm, "probe_ms_per_step": tuned_ms},
+                   "l2": "flushed between timed steps (512 MiB write); 1.2 GB working set",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "axon_steps_per_s": world * cone_updates * args.steps / (total_ms / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": recorded_traffic("persist", "c4"), "kernel": "persist", "peak_kind": peak_kind,
+                     "launches": args.steps, "avg_launch_us": per_launch_s * 1e6, "steps_per_launch": T,
+                     "algorithmic_bytes_per_launch": 8.0 * cells * T},
+        "clocks": clocks, "gpu_launches": 2 * args.steps,      # the persistent kernel + the step advance
+    }
+    # the one-instance-per-launch plain solver on the first 32 instances (100 steps each)
+    sub = ws[:32]
+    sims = [cue.Simulation(w, device=dev, path=cue.CUE_PATH_PLAIN) for w in sub]
+    for sm in sims:
+        sm.sim_run(2)
+    torch.cuda.synchronize()
+    Tb = 100
+    t0 = time.perf_counter()
+    for sm in sims:
+        sm.sim_run(Tb)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sub_cells = sum(w.n_cells for w in sub)
+    plain_rate = sub_cells * Tb / dt
+    for sm in sims:
+        sm.close()
+    line["baseline_plain_per_instance"] = {
+        "value": plain_rate, "unit": UNIT, "speedup": value / plain_rate,
+        "sample": f"first 32 instances x {Tb} steps, each instance its own cone and field launches per step"}
+    if not args.no_e2e:
+        # end to end: every instance's state from pinned host memory, the run, the fields back
+        host = [tuple(t.cpu().pin_memory() for t in st) for st in init]
+        outs = [torch.empty_like(h[0]).pin_memory() for h in host]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for i, (C, p, d, a) in enumerate(host):
+                b.fields[i][0].copy_(C, non_blocking=True)
+                b.pos[i].copy_(p, non_blocking=True)
+                b.dir[i].copy_(d, non_blocking=True)
+                b.active[i].copy_(a, non_blocking=True)
+        b.reset_state()
+        b.run(T)
+        cur = b.get_option(B.CUE_BINFO_CUR)
+        with torch.cuda.stream(stream):
+            for i in range(len(ws)):
+                outs[i].copy_(b.fields[i][cur], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        line["e2e"] = {"value": cells * T / (ms / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": sum(sum(t.numel() * t.element_size() for t in h) for h in host),
+                       "d2h_bytes_per_step": sum(o.numel() * o.element_size() for o in outs), "ms_per_step": ms}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nsteps, secs = oracle_sample(ws[0], args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": ws[0].n_cells * nsteps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"instance 0 ({ws[0].nx}x{ws[0].ny}), first {nsteps} of {T} steps (FP64, one thread)",
+            "seconds": secs}
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def adjoint_timing(cue, torch, sim, w, reset, stream, flush, forward_ms):
     """Time sim_adjoint (forward with checkpoints every 64 steps, recompute, adjoint) on the
     same workload; the ratio divides by the timed forward run."""
@@ -423,23 +559,41 @@ def adjoint_timing(cue, torch, sim, w, reset, stream, flush, forward_ms):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
+    # the plain forward solver (one cone and one field launch per step) on the same workload
+    plain = cue.Simulation(w, device=sim.device, path=cue.CUE_PATH_PLAIN)
+    plain.sim_run(w.nsteps)
+    torch.cuda.synchronize()
+    plain.load(C=w.field0(), pos=w.pos, dir=w.dir, active=w.active, step=0)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(plain.stream)
+    plain.sim_run(w.nsteps)
+    p1.record(plain.stream)
+    p1.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    plain.check()
+    plain.close()
     return {"ms_per_run": ms, "forward_ms_per_run": forward_ms, "ratio_to_forward": ms / forward_ms,
+            "plain_forward_ms_per_run": plain_ms, "ratio_to_plain_forward": ms / plain_ms,
             "ckpt_every": k, "loss": float(g["loss"]), "dL_dD": float(g["dD"]),
             "dL_dlambda": float(g["dlambda"]), "dL_de_max": float(g["dsrc"].abs().max()),
             "dL_dM_max": float(g["dmap"].abs().max())}
 
 
 def launches_per_run(sim, w):
-    """Launches of the dominant kernel in one run (K steps per launch on the fused path)."""
+    """Launches of the dominant kernel in one run (K steps per launch on the fused path, the
+    whole run per launch on the persistent path)."""
     from paper_1405_3331_gb300 import cue
     if sim.fused_active():
         K = sim.get_option(cue.CUE_INFO_DEPTH)
         return (w.nsteps + K - 1) // K
+    if sim_path_used(sim) == "persist":
+        return 1
     return w.nsteps
 
 
 def sim_path_used(sim):
-    return "fused" if sim.fused_active() else "plain"
+    from paper_1405_3331_gb300 import cue
+    return {cue.CUE_PATH_FUSED: "fused", cue.CUE_PATH_PERSIST: "persist"}.get(sim.last_path(), "plain")
 
 
 def hbm_probe(cue, torch, dev, hbm):

@@ -82,6 +82,11 @@ int cue_batch_run(cue_batch *b, int32_t nsteps);
 int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows, int32_t *blocks_per_sm,
                        double *ms_per_step);
 
+/* Set every instance's step counter and current buffer (0 = field_a), e.g. after
+ * the caller has written new states into the buffers.  Asynchronous on the
+ * stream.  CUE_ERR_ARG for cur not 0/1 or step outside [0, 2^32). */
+int cue_batch_set_state(cue_batch *b, int64_t step, int32_t cur);
+
 #define CUE_BOPT_ROWS    1    /* rows per thread of a field tile (1, 2, 4)          */
 #define CUE_BOPT_BLOCKS  2    /* blocks per SM (1..8, capped by occupancy)          */
 #define CUE_BOPT_GRAPH   3    /* 1: run through a captured CUDA graph; 0: direct    */

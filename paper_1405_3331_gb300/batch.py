@@ -20,8 +20,8 @@ CUE_BINFO_CUR = 18
 CUE_BINFO_GRID = 19
 
 EXPORTED = ("cue_batch_workspace_bytes", "cue_batch_create", "cue_batch_run", "cue_batch_autotune",
-            "cue_batch_set_option", "cue_batch_get_option", "cue_batch_status", "cue_batch_cone_updates",
-            "cue_batch_destroy")
+            "cue_batch_set_state", "cue_batch_set_option", "cue_batch_get_option", "cue_batch_status",
+            "cue_batch_cone_updates", "cue_batch_destroy")
 
 
 class cue_instance(ct.Structure):
@@ -46,12 +46,14 @@ def _lib():
         L.cue_batch_run.argtypes = [P, I32]
         L.cue_batch_autotune.argtypes = [P, I32, ct.POINTER(I32), ct.POINTER(I32), ct.POINTER(ct.c_double)]
         L.cue_batch_set_option.argtypes = [P, I32, I64]
+        L.cue_batch_set_state.argtypes = [P, I64, I32]
         L.cue_batch_get_option.argtypes = [P, I32, ct.POINTER(I64)]
         L.cue_batch_status.argtypes = [P]
         L.cue_batch_cone_updates.argtypes = [P, ct.POINTER(ct.c_uint64)]
         L.cue_batch_destroy.argtypes = [P]
         L.cue_batch_destroy.restype = None
-        for f in ("cue_batch_run", "cue_batch_autotune", "cue_batch_set_option", "cue_batch_get_option",
+        for f in ("cue_batch_run", "cue_batch_autotune", "cue_batch_set_state", "cue_batch_set_option",
+                  "cue_batch_get_option",
                   "cue_batch_status", "cue_batch_cone_updates"):
             getattr(L, f).restype = ct.c_int
         _declared = True
@@ -137,6 +139,10 @@ class Batch:
 
     def set_option(self, option: int, value: int):
         _check(_lib().cue_batch_set_option(self.h, option, value), "cue_batch_set_option")
+
+    def reset_state(self, step: int = 0, cur: int = 0):
+        """Every instance back to step ``step`` with buffer ``cur`` (0 = the first) current."""
+        _check(_lib().cue_batch_set_state(self.h, step, cur), "cue_batch_set_state")
 
     def get_option(self, option: int) -> int:
         v = ct.c_int64()

@@ -457,6 +457,19 @@ int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows_out, int
     return stage_list(b);
 }
 
+int cue_batch_set_state(cue_batch *b, int64_t step, int32_t cur)
+{
+    if (!b || (cur != 0 && cur != 1) || step < 0 || step > 0xFFFFFFFFLL) return CUE_ERR_ARG;
+    PCtrl c{};
+    c.cur = cur;
+    c.step0 = (uint32_t)step;
+    if (cudaMemcpyAsync(b->ctrl(), &c, sizeof(c), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        return CUE_ERR_CUDA;
+    b->cur = cur;
+    b->step = step;
+    return CUE_OK;
+}
+
 int cue_batch_set_option(cue_batch *b, int32_t option, int64_t value)
 {
     if (!b) return CUE_ERR_ARG;
