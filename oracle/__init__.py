@@ -11,6 +11,8 @@ from .oracle import (  # noqa: F401
     noise,
     node_gradient,
     gradient_at,
+    value_at,
+    snr,
     field_step,
     cone_step,
     run,

@@ -82,6 +82,18 @@ typedef struct {
     double grad_eps;
     int wall_mode;      /* 0 = stop at the wall, 1 = clamp to the wall */
     uint64_t seed;
+    /* steering rule: 0 = vector addition of the current direction and the
+     * sensed cue direction (Sec. 3.5, Eq. 6-7); 1 = the SNR turn rule of
+     * Sec. 3.5, Eq. 5 (2D): the cone turns by snr_turn to the right when a draw
+     * from N(SNR, 1) is positive, else to the left, while the cue value at the
+     * cone lies in [snr_cmin, snr_cmax]; outside that window it keeps its
+     * direction. */
+    int steer;
+    double snr_gain;    /* the gain of Eq. 5 */
+    double snr_width;   /* growth-cone width w: gradient steepness mu = w |grad C| / C */
+    double snr_kd;      /* concentration scale: gamma = C / kd */
+    double snr_cmin, snr_cmax;
+    double snr_turn;    /* turn angle per step (the paper: pi/30) */
 } orc_cone;
 
 static int64_t nodes_of(const orc_grid *g)
@@ -256,6 +268,45 @@ void orc_gradient_at(const orc_grid *g, const double *C, const double p[3], doub
             }
 }
 
+/* Cue value at p (2D): bilinear interpolation of the four nodes of the cell
+ * holding p, the cell chosen as for the gradient. */
+double orc_value_at(const orc_grid *g, const double *C, const double p[3])
+{
+    int lo[2];
+    double f[2];
+    for (int ax = 0; ax < 2; ++ax) {
+        double s = p[ax] / g->h;
+        int i0 = (int)floor(s);
+        i0 = clampi(i0, 0, extent(g, ax) - 2);
+        lo[ax] = i0;
+        f[ax] = s - (double)i0;
+    }
+    double v = 0.0;
+    for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+            double w = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]);
+            v += w * C[(int64_t)(lo[0] + di) + (int64_t)g->nx * (lo[1] + dj)];
+        }
+    return v;
+}
+
+/* SNR of the cone's gradient measurement (Sec. 3.5, Eq. 5, 2D):
+ *   SNR = gain * mu * sqrt(gamma / (1 + gamma)^3) * sin(theta - theta_NGF),
+ * gamma = C/kd (background concentration), mu = w |grad C| / C (gradient
+ * steepness across the cone), theta the heading and theta_NGF the gradient's
+ * direction, sin(theta - theta_NGF) from the cross product of the unit vectors
+ * (d_y g_x - d_x g_y) / |g| as in the Eq. 6-7 discussion. */
+double orc_snr(const orc_cone *cp, double Cp, const double *gr, const double *d)
+{
+    double gn = sqrt(gr[0] * gr[0] + gr[1] * gr[1]);
+    if (!(gn > 0.0) || !(Cp > 0.0)) return 0.0;
+    double gamma = Cp / cp->snr_kd;
+    double mu = cp->snr_width * gn / Cp;
+    double sin_rel = (d[1] * gr[0] - d[0] * gr[1]) / gn;
+    double onep = 1.0 + gamma;
+    return cp->snr_gain * mu * sqrt(gamma / (onep * onep * onep)) * sin_rel;
+}
+
 void orc_gradient_many(const orc_grid *g, const double *C, int n, const double *p /* [n][3] */,
                        double *out /* [n][3] */)
 {
@@ -284,26 +335,42 @@ void orc_cone_step(const orc_grid *g, const orc_cone *cp, const double *C, uint3
         /* sensed cue direction */
         double gr[3];
         orc_gradient_at(g, C, p, gr);
-        double gn2 = 0.0;
-        for (int c = 0; c < dim; ++c) gn2 += gr[c] * gr[c];
-        double ghat[3] = {0, 0, 0};
-        if (gn2 > eps2) {
-            double inv = 1.0 / sqrt(gn2);
-            for (int c = 0; c < dim; ++c) ghat[c] = gr[c] * inv;
-        }
         /* noise */
         double xi[3];
         orc_noise(cp->seed, (uint32_t)a, step, dim, xi);
-        /* vector addition of previous direction, cue direction and noise */
-        double v[3] = {0, 0, 0}, vn2 = 0.0;
-        for (int c = 0; c < dim; ++c) {
-            v[c] = cp->w_prev * d[c] + cp->w_grad * ghat[c] + cp->w_noise * xi[c];
-            vn2 += v[c] * v[c];
-        }
         double dn[3] = {d[0], d[1], d[2]};
-        if (vn2 > 1e-30) {
-            double inv = 1.0 / sqrt(vn2);
-            for (int c = 0; c < dim; ++c) dn[c] = v[c] * inv;
+        if (cp->steer == 1 && dim == 2) {
+            /* SNR rule (Eq. 5): inside the detectable window, turn right by the
+             * turn angle when SNR + z > 0 (z = the cone's first normal draw: a
+             * draw from N(SNR, 1) is SNR + z), else left */
+            double Cp = orc_value_at(g, C, p);
+            if (Cp >= cp->snr_cmin && Cp <= cp->snr_cmax) {
+                double snr = orc_snr(cp, Cp, gr, d);
+                double ang = (snr + xi[0] > 0.0) ? -cp->snr_turn : cp->snr_turn;
+                double cs = cos(ang), sn = sin(ang);
+                double r0 = d[0] * cs - d[1] * sn, r1 = d[0] * sn + d[1] * cs;
+                double inv = 1.0 / sqrt(r0 * r0 + r1 * r1);
+                dn[0] = r0 * inv;
+                dn[1] = r1 * inv;
+            }
+        } else {
+            double gn2 = 0.0;
+            for (int c = 0; c < dim; ++c) gn2 += gr[c] * gr[c];
+            double ghat[3] = {0, 0, 0};
+            if (gn2 > eps2) {
+                double inv = 1.0 / sqrt(gn2);
+                for (int c = 0; c < dim; ++c) ghat[c] = gr[c] * inv;
+            }
+            /* vector addition of previous direction, cue direction and noise */
+            double v[3] = {0, 0, 0}, vn2 = 0.0;
+            for (int c = 0; c < dim; ++c) {
+                v[c] = cp->w_prev * d[c] + cp->w_grad * ghat[c] + cp->w_noise * xi[c];
+                vn2 += v[c] * v[c];
+            }
+            if (vn2 > 1e-30) {
+                double inv = 1.0 / sqrt(vn2);
+                for (int c = 0; c < dim; ++c) dn[c] = v[c] * inv;
+            }
         }
         double pn[3] = {0, 0, 0};
         for (int c = 0; c < dim; ++c) pn[c] = p[c] + cp->step_len * dn[c];

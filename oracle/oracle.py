@@ -8,6 +8,7 @@ and returns numpy arrays; fields are shaped (ny, nx) in 2D and (nz, ny, nx) in
 from __future__ import annotations
 
 import ctypes as ct
+import math
 import dataclasses
 import os
 import subprocess
@@ -31,7 +32,9 @@ class _Grid(ct.Structure):
 class _Cone(ct.Structure):
     _fields_ = [("w_prev", ct.c_double), ("w_grad", ct.c_double), ("w_noise", ct.c_double),
                 ("step_len", ct.c_double), ("stop_radius", ct.c_double), ("grad_eps", ct.c_double),
-                ("wall_mode", ct.c_int), ("seed", ct.c_uint64)]
+                ("wall_mode", ct.c_int), ("seed", ct.c_uint64), ("steer", ct.c_int),
+                ("snr_gain", ct.c_double), ("snr_width", ct.c_double), ("snr_kd", ct.c_double),
+                ("snr_cmin", ct.c_double), ("snr_cmax", ct.c_double), ("snr_turn", ct.c_double)]
 
 
 @dataclasses.dataclass
@@ -70,10 +73,21 @@ class Cone:
     grad_eps: float = 1e-15
     wall_mode: int = 0
     seed: int = 0
+    # SNR turn rule (Sec. 3.5, Eq. 5; 2D): steer = 1 turns by snr_turn right / left by the
+    # sign of a draw from N(SNR, 1) while C(p) lies in [snr_cmin, snr_cmax]
+    steer: int = 0
+    snr_gain: float = 1.0
+    snr_width: float = 1.0
+    snr_kd: float = 1.0
+    snr_cmin: float = 0.0
+    snr_cmax: float = float("inf")
+    snr_turn: float = math.pi / 30
 
     def _c(self) -> _Cone:
         return _Cone(self.w_prev, self.w_grad, self.w_noise, self.step_len, self.stop_radius,
-                     self.grad_eps, self.wall_mode, self.seed & 0xFFFFFFFFFFFFFFFF)
+                     self.grad_eps, self.wall_mode, self.seed & 0xFFFFFFFFFFFFFFFF, self.steer,
+                     self.snr_gain, self.snr_width, self.snr_kd, self.snr_cmin,
+                     min(self.snr_cmax, 1.7976931348623157e308), self.snr_turn)
 
 
 def build(force: bool = False) -> str:
@@ -108,6 +122,10 @@ def _load():
             lib.orc_adjoint.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, P, ct.c_int, P, ct.c_int,
                                         P, P, P, ct.c_int, P, P, P, P, P, P, P, P, ct.c_int]
             lib.orc_adjoint.restype = ct.c_double
+            lib.orc_value_at.argtypes = [ct.POINTER(_Grid), P, P]
+            lib.orc_value_at.restype = ct.c_double
+            lib.orc_snr.argtypes = [ct.POINTER(_Cone), ct.c_double, P, P]
+            lib.orc_snr.restype = ct.c_double
             lib.orc_endpoint_loss.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, P, ct.c_int, P,
                                               ct.c_int, P, P, P, ct.c_int]
             lib.orc_endpoint_loss.restype = ct.c_double
@@ -158,6 +176,27 @@ def node_gradient(grid: Grid, C, i, j, k=0):
     g = grid._c()
     _load().orc_node_gradient(ct.byref(g), _ptr(C), i, j, k, _ptr(out))
     return out
+
+
+def value_at(grid: Grid, C, p):
+    """Bilinear cue value at 2D points ``p`` (n, 2) -> (n,)."""
+    C = _f64(C)
+    p = np.atleast_2d(np.asarray(p, dtype=np.float64))
+    out = np.empty(p.shape[0])
+    g = grid._c()
+    L = _load()
+    for i in range(p.shape[0]):
+        q = (ct.c_double * 3)(p[i, 0], p[i, 1], 0.0)
+        out[i] = L.orc_value_at(ct.byref(g), _ptr(C), q)
+    return out
+
+
+def snr(cone: Cone, Cp, g, d):
+    """Eq. 5 for one cone: cue value Cp, gradient g (2,), direction d (2,)."""
+    gg = (ct.c_double * 2)(float(g[0]), float(g[1]))
+    dd = (ct.c_double * 2)(float(d[0]), float(d[1]))
+    c = cone._c()
+    return float(_load().orc_snr(ct.byref(c), float(Cp), gg, dd))
 
 
 def gradient_at(grid: Grid, C, p):
