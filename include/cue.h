@@ -126,6 +126,22 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
                                       run; per step one pass over field tiles and cone
                                       chunks, then a bounded grid barrier                   */
 
+/* Parameters of the SNR turn rule (Sec. 3.5, Eq. 5; 2D).  Inside the
+ * detectable window c_min <= C(p) <= c_max the cone turns by `turn` radians to
+ * the right (clockwise) when a draw from N(SNR, 1) is positive, else to the
+ * left, with SNR = gain * mu * sqrt(gamma / (1 + gamma)^3) * sin(theta -
+ * theta_NGF), gamma = C(p) / kd, mu = width * |grad C(p)| / C(p); outside the
+ * window it keeps its direction.  C(p) is the bilinear cue value, grad C(p)
+ * the sampled gradient of the vector-addition rule, the draw SNR plus the
+ * cone's first Philox/Box-Muller normal of (cone, step). */
+typedef struct {
+    float gain;         /* Eq. 5's gain                                     */
+    float width;        /* growth-cone width w                              */
+    float kd;           /* concentration scale (> 0)                        */
+    float c_min, c_max; /* detectable concentration window                  */
+    float turn;         /* turn angle per step; the paper: pi/30            */
+} cue_snr_params;
+
 /* Bytes of device workspace the simulation needs (256-byte aligned). */
 size_t cue_workspace_bytes(const cue_params *params, int32_t n_src, int32_t n_axons);
 
@@ -212,6 +228,14 @@ int cue_set_state(cue_sim *sim, int64_t field_step, int64_t cone_step_in, int32_
 
 /* Re-target the stream used by later calls. */
 int cue_set_stream(cue_sim *sim, void *stream);
+
+/* Steering rule of the handle's cones: NULL = vector addition of the current
+ * direction, the normalised cue gradient and noise (Sec. 3.5, Eq. 6-7; the
+ * default); non-NULL = the SNR turn rule above (2D only).  Takes effect at the
+ * next cone step.  The fused path and sim_adjoint support vector addition
+ * only (the fused path is then skipped; sim_adjoint returns CUE_ERR_ARG).
+ * Errors: CUE_ERR_ARG (3D handle, kd <= 0, non-finite values, c_min > c_max). */
+int cue_set_steering(cue_sim *s, const cue_snr_params *snr);
 
 /* Set an option (CUE_OPT_*). */
 int cue_set_option(cue_sim *sim, int32_t option, int64_t value);

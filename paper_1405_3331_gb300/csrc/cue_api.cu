@@ -175,6 +175,10 @@ int make_descs(const cue_params &params, const cone_params &cone, FieldDesc &f, 
     c.wall_mode = cone.wall_mode;
     c.key0 = (uint32_t)(cone.seed & 0xFFFFFFFFull);
     c.key1 = (uint32_t)(cone.seed >> 32);
+    c.steer = 0;                     // vector addition until cue_set_steering says otherwise
+    c.snr_gain = c.snr_width = c.snr_inv_kd = c.snr_cmin = c.snr_cmax = 0.0f;
+    c.turn_c = 1.0f;
+    c.turn_s = 0.0f;
     return CUE_OK;
 }
 
@@ -327,6 +331,7 @@ int sim_adjoint(cue_sim *s, const float *d_targets, int32_t nsteps, int32_t ckpt
     if (!d_gD || !d_glambda || !d_loss || (s->n_src > 0 && !d_gsrc) || (s->n_axons > 0 && !d_targets))
         return CUE_ERR_ARG;
     if (s->cone.wall_mode != 1 || s->cd.stop_r2 >= 0.0f) return CUE_ERR_ARG;   // needs a run without stopping
+    if (s->cd.steer != 0) return CUE_ERR_ARG;                                    // vector addition only
     if (s->cone_step != s->field_step) return CUE_ERR_STATE;
     if (s->field_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
     return run_adjoint(*s, d_targets, nsteps, ckpt_every, d_adj_ws, adj_ws_bytes, d_gD, d_glambda, d_gsrc, d_gmap,
@@ -357,6 +362,32 @@ int cue_set_stream(cue_sim *s, void *stream)
 {
     if (!s) return CUE_ERR_ARG;
     s->stream = static_cast<cudaStream_t>(stream);
+    return CUE_OK;
+}
+
+int cue_set_steering(cue_sim *s, const cue_snr_params *snr)
+{
+    if (!s) return CUE_ERR_ARG;
+    if (!snr) {
+        s->cd.steer = 0;
+        s->persist_ready = false;
+        return CUE_OK;
+    }
+    if (s->fd.dim != 2) return CUE_ERR_ARG;
+    const float v[] = {snr->gain, snr->width, snr->kd, snr->c_min, snr->turn};
+    for (float x : v)
+        if (!std::isfinite(x)) return CUE_ERR_ARG;
+    if (!(snr->kd > 0.0f) || std::isnan(snr->c_max) || snr->c_min > snr->c_max) return CUE_ERR_ARG;
+    s->cd.steer = 1;
+    s->cd.snr_gain = snr->gain;
+    s->cd.snr_width = snr->width;
+    s->cd.snr_inv_kd = (float)(1.0 / (double)snr->kd);
+    s->cd.snr_cmin = snr->c_min;
+    s->cd.snr_cmax = snr->c_max;
+    s->cd.turn_c = (float)std::cos((double)snr->turn);
+    s->cd.turn_s = (float)std::sin((double)snr->turn);
+    s->persist_ready = false;          // the persistent path's instance record holds the cone parameters
+    if (s->path == CUE_PATH_FUSED) s->path = CUE_PATH_AUTO;
     return CUE_OK;
 }
 

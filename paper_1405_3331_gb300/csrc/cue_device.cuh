@@ -54,6 +54,10 @@ struct ConeDesc {
     float hi0, hi1, hi2; // domain upper bound per axis: (N - 1) h
     int wall_mode;      // 0 stop, 1 clamp
     uint32_t key0, key1;
+    // steering rule: 0 vector addition (Sec. 3.5, Eq. 6-7); 1 the SNR turn rule (Eq. 5, 2D)
+    int steer;
+    float snr_gain, snr_width, snr_inv_kd, snr_cmin, snr_cmax;
+    float turn_c, turn_s;   // cos and sin of the turn angle
 };
 
 // Bits of the device status word.
@@ -302,6 +306,101 @@ __device__ __forceinline__ bool cone_finish_xi(const ConeDesc &c, const float *g
         }
     }
     return true;
+}
+
+// --------------------------------------------------------------------------
+// The SNR turn rule (Sec. 3.5, Eq. 5; 2D).  From the cell's 12-node patch: the
+// cue value C at p (bilinear in the cell's four nodes, summed in the order
+// (x0,y0), (x1,y0), (x0,y1), (x1,y1)) and the gradient g.  Inside the window
+// [cmin, cmax]: SNR = gain * mu * sqrt(gamma / (1 + gamma)^3) * sin(theta -
+// theta_NGF) with gamma = C / kd, mu = w |g| / C, sin(theta - theta_NGF) =
+// (d_y g_x - d_x g_y) / |g|; the cone turns right (clockwise) by the turn
+// angle when SNR + xi0 > 0 (a draw from N(SNR, 1)), else left, and the
+// rotated direction is renormalised.  Outside the window the direction is
+// kept.  Then the same advance and stop tests as the vector-addition rule.
+// --------------------------------------------------------------------------
+template <class Load>
+__device__ __forceinline__ bool cone_update_snr(const FieldDesc &f, const ConeDesc &c, const Load &ld,
+                                                const float *xi, float *p, float *d, const float *src_xyz,
+                                                int src_stride, int n_src)
+{
+    int lo[3] = {0, 0, 0};
+    float fr[3] = {0.f, 0.f, 0.f};
+    cell_of<2>(f, p, lo, fr);
+    float v[kPatch2];
+    gather2(f, lo, ld, v);
+    float g[2];
+    grad2(c, v, fr, g);
+    // every rounding written out (explicit fma / _rn operations), so the rule
+    // gives the same bits in every kernel it is inlined into
+    const float wx0 = __fsub_rn(1.0f, fr[0]), wx1 = fr[0], wy0 = __fsub_rn(1.0f, fr[1]), wy1 = fr[1];
+    float Cp = __fmul_rn(__fmul_rn(wx0, wy0), v[1]);
+    Cp = fmaf(__fmul_rn(wx1, wy0), v[2], Cp);
+    Cp = fmaf(__fmul_rn(wx0, wy1), v[5], Cp);
+    Cp = fmaf(__fmul_rn(wx1, wy1), v[6], Cp);
+    float dn[2] = {d[0], d[1]};
+    if (Cp >= c.snr_cmin && Cp <= c.snr_cmax) {
+        const float gn = __fsqrt_rn(fmaf(g[0], g[0], __fmul_rn(g[1], g[1])));
+        float snr = 0.0f;
+        if (gn > 0.0f && Cp > 0.0f) {
+            const float gamma = __fmul_rn(Cp, c.snr_inv_kd);
+            const float mu = __fdiv_rn(__fmul_rn(c.snr_width, gn), Cp);
+            const float sin_rel = __fdiv_rn(fmaf(d[1], g[0], -__fmul_rn(d[0], g[1])), gn);
+            const float onep = __fadd_rn(1.0f, gamma);
+            const float den = __fmul_rn(__fmul_rn(onep, onep), onep);
+            snr = __fmul_rn(__fmul_rn(__fmul_rn(c.snr_gain, mu), __fsqrt_rn(__fdiv_rn(gamma, den))), sin_rel);
+        }
+        const float sn = (__fadd_rn(snr, xi[0]) > 0.0f) ? -c.turn_s : c.turn_s;   // right: clockwise
+        const float r0 = fmaf(d[0], c.turn_c, -__fmul_rn(d[1], sn));
+        const float r1 = fmaf(d[0], sn, __fmul_rn(d[1], c.turn_c));
+        const float inv = __fdiv_rn(1.0f, __fsqrt_rn(fmaf(r0, r0, __fmul_rn(r1, r1))));
+        dn[0] = __fmul_rn(r0, inv);
+        dn[1] = __fmul_rn(r1, inv);
+    }
+    const float hi[2] = {c.hi0, c.hi1};
+    float pn[2];
+    bool outside = false;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        pn[i] = fmaf(c.step_len, dn[i], p[i]);
+        if (pn[i] < 0.0f || pn[i] > hi[i]) {
+            outside = true;
+            pn[i] = pn[i] < 0.0f ? 0.0f : hi[i];
+        }
+    }
+    if (outside && c.wall_mode == 0) return false;   // keeps p, d of this step
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        p[i] = pn[i];
+        d[i] = dn[i];
+    }
+    if (c.stop_r2 >= 0.0f) {
+        for (int s = 0; s < n_src; ++s) {
+            float d2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float e = pn[i] - src_xyz[i * src_stride + s];
+                d2 = fmaf(e, e, d2);
+            }
+            if (d2 <= c.stop_r2) return false;
+        }
+    }
+    return true;
+}
+
+// One cone step by the handle's steering rule, with the noise already drawn:
+// the vector-addition rule is exactly sample_gradient + cone_finish_xi.
+template <int DIM, class Load>
+__device__ __forceinline__ bool cone_step_rule(const FieldDesc &f, const ConeDesc &c, const Load &ld,
+                                               const float *xi, float *p, float *d, const float *src_xyz,
+                                               int src_stride, int n_src)
+{
+    if constexpr (DIM == 2) {
+        if (c.steer == 1) return cone_update_snr(f, c, ld, xi, p, d, src_xyz, src_stride, n_src);
+    }
+    float g[DIM];
+    sample_gradient<DIM>(f, c, p, ld, g);
+    return cone_finish_xi<DIM>(c, g, xi, p, d, src_xyz, src_stride, n_src);
 }
 
 // cone_finish_xi with the noise of (axon, step) drawn here.

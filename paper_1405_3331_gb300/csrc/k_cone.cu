@@ -50,9 +50,7 @@ __global__ void __launch_bounds__(128) cone_plain(FieldDesc f, ConeDesc c, const
     auto ld = [&](int i, int j, int k) { return __ldg(C + (size_t)i + sy * j + sz * k); };
     const float *src = in_smem ? s_src : src_xyz;
     const int stride = n_src;
-    float g[DIM];
-    sample_gradient<DIM>(f, c, p, ld, g);
-    bool alive = cone_finish_xi<DIM>(c, g, xi, p, d, src, stride, use_stop ? n_src : 0);
+    bool alive = cone_step_rule<DIM>(f, c, ld, xi, p, d, src, stride, use_stop ? n_src : 0);
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {

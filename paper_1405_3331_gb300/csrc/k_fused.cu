@@ -690,7 +690,7 @@ static int default_depth(const Sim &s) { return s.temporal_depth > 0 ? s.tempora
 
 bool fused_supported(const Sim &s)
 {
-    if (s.fd.dim != 2 || !s.vec4 || s.src_map || s.n_src > kMaxTileSrc) return false;
+    if (s.fd.dim != 2 || !s.vec4 || s.src_map || s.n_src > kMaxTileSrc || s.cd.steer != 0) return false;
     if (!encode_fn()) return false;
     FusedGeom g;
     if (!choose_geometry(s.fd, s.cd.step_len, s.cd.stop_r2, s.n_axons > 0, default_depth(s), device_sm_count(), g))

@@ -208,10 +208,8 @@ __device__ __forceinline__ void cone_chunk(const PInst &I, const float *C, int c
     n_live++;
     const size_t sy = I.pitch;
     auto ld = [&](int i, int j, int) { return __ldcg(C + (size_t)i + sy * j); };
-    float g[2];
-    sample_gradient<2>(I.f, I.c, p, ld, g);
     const bool stop = I.c.stop_r2 >= 0.0f && I.n_src > 0;
-    const bool alive = cone_finish_xi<2>(I.c, g, xi, p, d, I.src_xyz, I.n_src, stop ? I.n_src : 0);
+    const bool alive = cone_step_rule<2>(I.f, I.c, ld, xi, p, d, I.src_xyz, I.n_src, stop ? I.n_src : 0);
     pout[a] = p[0];
     pout[n + a] = p[1];
     dout[a] = d[0];

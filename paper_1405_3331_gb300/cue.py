@@ -45,7 +45,12 @@ CUE_PATH_PLAIN = 1
 CUE_PATH_FUSED = 2
 CUE_PATH_PERSIST = 3
 
-EXPORTED = ("cue_workspace_bytes", "cue_init", "cue_step", "cone_step", "sim_run", "cue_get_state",
+class cue_snr_params(ct.Structure):
+    _fields_ = [("gain", ct.c_float), ("width", ct.c_float), ("kd", ct.c_float), ("c_min", ct.c_float),
+                ("c_max", ct.c_float), ("turn", ct.c_float)]
+
+
+EXPORTED = ("cue_set_steering", "cue_workspace_bytes", "cue_init", "cue_step", "cone_step", "sim_run", "cue_get_state",
             "cue_set_state", "cue_set_stream", "cue_set_option", "cue_launch_count", "cue_status",
             "cue_destroy", "cue_strerror", "cue_kernel_time", "cue_cone_updates", "cue_get_option", "sim_run_static",
             "cue_static_scratch_bytes", "sim_adjoint", "cue_adjoint_workspace_bytes")
@@ -98,6 +103,8 @@ def lib():
             L.cue_set_state.argtypes = [P, I64, I64, I32]
             L.cue_set_stream.argtypes = [P, P]
             L.cue_set_option.argtypes = [P, I32, I64]
+            L.cue_set_steering.argtypes = [P, ct.POINTER(cue_snr_params)]
+            L.cue_set_steering.restype = ct.c_int
             L.cue_get_option.argtypes = [P, I32, ct.POINTER(I64)]
             L.sim_run_static.argtypes = [ct.POINTER(cue_params), ct.POINTER(cone_params), P, P, P, P, I32, P,
                                          P, P, P, I32, I64, I32, P, ct.POINTER(I32)]
@@ -316,6 +323,16 @@ class Simulation:
 
     def set_option(self, option: int, value: int):
         _check(cue_set_option(self.h, option, value), "cue_set_option")
+
+    def set_steering(self, snr=None):
+        """None: vector-addition steering; else a dict / object with gain, width, kd, c_min,
+        c_max, turn for the SNR turn rule (2D)."""
+        if snr is None:
+            _check(lib().cue_set_steering(self.h, None), "cue_set_steering")
+            return
+        get = (lambda k: snr[k]) if isinstance(snr, dict) else (lambda k: getattr(snr, k))
+        p = cue_snr_params(get("gain"), get("width"), get("kd"), get("c_min"), get("c_max"), get("turn"))
+        _check(lib().cue_set_steering(self.h, ct.byref(p)), "cue_set_steering")
 
     def get_option(self, option: int) -> int:
         rc, v = cue_get_option(self.h, option)
