@@ -18,4 +18,8 @@ from .oracle import (  # noqa: F401
     run,
     endpoint_loss,
     adjoint,
+    bin_points,
+    connect,
+    csr,
+    bfs,
 )

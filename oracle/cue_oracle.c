@@ -696,3 +696,148 @@ double orc_endpoint_loss(const orc_grid *g, const orc_cone *cp, const double *C0
     free(C); free(W); free(P); free(D); free(act);
     return loss / n;
 }
+
+/* ==========================================================================
+ * Connectivity (the paper's collision-detection and graph stages).
+ *
+ * Uniform grid (Sec. 3.5, "Diffusion of guidance molecules"): each point's
+ * cell is its linear grid index (the hash), the (cell, id) pairs are sorted,
+ * and a change of cell id between consecutive sorted entries marks a cell's
+ * start and end (Table 1).  Connection test (Sec. 3.3): a growth cone at x and
+ * a neuron at y connect when |x - y|^2 < r^2, r the sum of the two radii (the
+ * squared form avoids the square root).  Adjacency list (Sec. 3.4, Fig. 4):
+ * vertex heads V_a into one edge array E_a, the edges of vertex i+1 after
+ * those of i.  Traversal (Sec. 3.4, Fig. 5): breadth-first, level by level,
+ * the level (cost) of each vertex from a source.
+ * ========================================================================== */
+
+/* Grid cell of one point: floor(x / cell) per axis, clamped into the grid. */
+static int64_t grid_cell_of(int dim, const double *pos, int n, int i, double cell, const int32_t *grid)
+{
+    int64_t c = 0, stride = 1;
+    for (int ax = 0; ax < dim; ++ax) {
+        int64_t k = (int64_t)floor(pos[(size_t)ax * n + i] / cell);
+        if (k < 0) k = 0;
+        if (k > grid[ax] - 1) k = grid[ax] - 1;
+        c += k * stride;
+        stride *= grid[ax];
+    }
+    return c;
+}
+
+typedef struct {
+    int64_t cell;
+    int32_t id;
+} cell_pair;
+
+static int cmp_cell_pair(const void *a, const void *b)
+{
+    const cell_pair *x = (const cell_pair *)a, *y = (const cell_pair *)b;
+    if (x->cell != y->cell) return x->cell < y->cell ? -1 : 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* Hash, sort by (cell, id), cell start / one-past-end (-1 for empty cells). */
+void orc_bin_points(int dim, int n, const double *pos, double cell, const int32_t *grid, int32_t *cell_of,
+                    int32_t *sorted_id, int32_t *cell_start, int32_t *cell_end)
+{
+    int64_t ncell = 1;
+    for (int ax = 0; ax < dim; ++ax) ncell *= grid[ax];
+    for (int64_t c = 0; c < ncell; ++c) cell_start[c] = cell_end[c] = -1;
+    cell_pair *pr = (cell_pair *)malloc(sizeof(cell_pair) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        pr[i].cell = grid_cell_of(dim, pos, n, i, cell, grid);
+        pr[i].id = i;
+        cell_of[i] = (int32_t)pr[i].cell;
+    }
+    qsort(pr, (size_t)n, sizeof(cell_pair), cmp_cell_pair);
+    for (int j = 0; j < n; ++j) {
+        sorted_id[j] = pr[j].id;
+        if (j == 0 || pr[j].cell != pr[j - 1].cell) cell_start[pr[j].cell] = j;
+        if (j == n - 1 || pr[j].cell != pr[j + 1].cell) cell_end[pr[j].cell] = j + 1;
+    }
+    free(pr);
+}
+
+/* Every (active cone, neuron) pair with |x - y|^2 < radius^2, except a cone and
+ * its own neuron, as (owner[cone], neuron), cones in order then neurons in
+ * order; at most cap pairs are written, the full count is returned. */
+int orc_connect(int dim, int n_cones, const double *pos, const int32_t *owner, const uint8_t *active,
+                int n_neurons, const double *npos, double radius, int cap, int32_t *src, int32_t *dst)
+{
+    const double r2 = radius * radius;
+    int count = 0;
+    for (int a = 0; a < n_cones; ++a) {
+        if (active && !active[a]) continue;
+        for (int j = 0; j < n_neurons; ++j) {
+            if (owner[a] == j) continue;
+            double d2 = 0.0;
+            for (int ax = 0; ax < dim; ++ax) {
+                double e = pos[(size_t)ax * n_cones + a] - npos[(size_t)ax * n_neurons + j];
+                d2 += e * e;
+            }
+            if (d2 < r2) {
+                if (count < cap) {
+                    src[count] = owner[a];
+                    dst[count] = j;
+                }
+                ++count;
+            }
+        }
+    }
+    return count;
+}
+
+typedef struct {
+    int32_t s, d;
+} edge_pair;
+
+static int cmp_edge(const void *a, const void *b)
+{
+    const edge_pair *x = (const edge_pair *)a, *y = (const edge_pair *)b;
+    if (x->s != y->s) return (x->s > y->s) - (x->s < y->s);
+    return (x->d > y->d) - (x->d < y->d);
+}
+
+/* Adjacency list of the distinct edges: row[v] .. row[v+1] index col, sorted. */
+int orc_csr(int nv, int ne, const int32_t *src, const int32_t *dst, int32_t *row, int32_t *col)
+{
+    edge_pair *e = (edge_pair *)malloc(sizeof(edge_pair) * (size_t)(ne > 0 ? ne : 1));
+    for (int k = 0; k < ne; ++k) {
+        e[k].s = src[k];
+        e[k].d = dst[k];
+    }
+    qsort(e, (size_t)ne, sizeof(edge_pair), cmp_edge);
+    int m = 0;
+    for (int k = 0; k < ne; ++k)
+        if (k == 0 || e[k].s != e[k - 1].s || e[k].d != e[k - 1].d) e[m++] = e[k];
+    for (int v = 0; v <= nv; ++v) row[v] = 0;
+    for (int k = 0; k < m; ++k) row[e[k].s + 1]++;
+    for (int v = 0; v < nv; ++v) row[v + 1] += row[v];
+    for (int k = 0; k < m; ++k) col[k] = e[k].d;
+    free(e);
+    return m;
+}
+
+/* Breadth-first levels from `source` (-1: unreachable), a FIFO queue. */
+void orc_bfs(int nv, const int32_t *row, const int32_t *col, int source, int32_t *level)
+{
+    int32_t *q = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    for (int v = 0; v < nv; ++v) level[v] = -1;
+    int head = 0, tail = 0;
+    if (source >= 0 && source < nv) {
+        level[source] = 0;
+        q[tail++] = source;
+    }
+    while (head < tail) {
+        int v = q[head++];
+        for (int k = row[v]; k < row[v + 1]; ++k) {
+            int u = col[k];
+            if (level[u] < 0) {
+                level[u] = level[v] + 1;
+                q[tail++] = u;
+            }
+        }
+    }
+    free(q);
+}

@@ -122,6 +122,12 @@ def _load():
             lib.orc_adjoint.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, P, ct.c_int, P, ct.c_int,
                                         P, P, P, ct.c_int, P, P, P, P, P, P, P, P, ct.c_int]
             lib.orc_adjoint.restype = ct.c_double
+            lib.orc_bin_points.argtypes = [ct.c_int, ct.c_int, P, ct.c_double, P, P, P, P, P]
+            lib.orc_connect.argtypes = [ct.c_int, ct.c_int, P, P, P, ct.c_int, P, ct.c_double, ct.c_int, P, P]
+            lib.orc_connect.restype = ct.c_int
+            lib.orc_csr.argtypes = [ct.c_int, ct.c_int, P, P, P, P]
+            lib.orc_csr.restype = ct.c_int
+            lib.orc_bfs.argtypes = [ct.c_int, P, P, ct.c_int, P]
             lib.orc_value_at.argtypes = [ct.POINTER(_Grid), P, P]
             lib.orc_value_at.restype = ct.c_double
             lib.orc_snr.argtypes = [ct.POINTER(_Cone), ct.c_double, P, P]
@@ -301,3 +307,57 @@ def adjoint(grid: Grid, cone: Cone, C0, src_cell, src_emit, src_map, pos, dir, t
                                _ptr(gsrc), _ptr(gmap), _ptr(Cs), _ptr(Ps), _ptr(Ds), _ptr(work),
                                1 if state_binary32 else 0)
     return float(loss), gD.value, gl.value, gsrc, gmap
+
+
+# ------------------------------------------------------------------ connectivity
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def bin_points(pos, cell, grid):
+    """Uniform-grid binning of points ``pos`` [dim][n]: (cell of each point, ids sorted by
+    (cell, id), cell start, cell one-past-end), empty cells -1."""
+    pos = _f64(pos)
+    dim, n = pos.shape
+    g = _i32(list(grid) + [1] * (3 - len(grid)))
+    ncell = int(np.prod(g[:dim]))
+    cell_of = np.empty(n, np.int32)
+    sid = np.empty(n, np.int32)
+    start = np.empty(ncell, np.int32)
+    end = np.empty(ncell, np.int32)
+    _load().orc_bin_points(dim, n, _ptr(pos), float(cell), _ptr(g), _ptr(cell_of), _ptr(sid), _ptr(start),
+                           _ptr(end))
+    return cell_of, sid, start, end
+
+
+def connect(pos, owner, active, npos, radius):
+    """(owner, neuron) pairs of active cones within ``radius`` of a neuron other than their own."""
+    pos, npos = _f64(pos), _f64(npos)
+    dim, n = pos.shape
+    m = npos.shape[1]
+    owner = _i32(owner)
+    act = np.ascontiguousarray(np.ones(n) if active is None else active, dtype=np.uint8)
+    cap = n * max(m, 1)
+    src = np.empty(max(cap, 1), np.int32)
+    dst = np.empty(max(cap, 1), np.int32)
+    k = _load().orc_connect(dim, n, _ptr(pos), _ptr(owner), _ptr(act), m, _ptr(npos), float(radius), cap,
+                            _ptr(src), _ptr(dst))
+    return src[:k].copy(), dst[:k].copy()
+
+
+def csr(nv, src, dst):
+    """Adjacency list of the distinct edges: (row [nv+1], col [m])."""
+    src, dst = _i32(src), _i32(dst)
+    row = np.empty(nv + 1, np.int32)
+    col = np.empty(max(src.shape[0], 1), np.int32)
+    m = _load().orc_csr(nv, src.shape[0], _ptr(src), _ptr(dst), _ptr(row), _ptr(col))
+    return row, col[:m].copy()
+
+
+def bfs(row, col, source):
+    """Breadth-first levels from ``source`` (-1 unreachable)."""
+    row, col = _i32(row), _i32(col)
+    nv = row.shape[0] - 1
+    level = np.empty(nv, np.int32)
+    _load().orc_bfs(nv, _ptr(row), _ptr(col if col.size else np.zeros(1, np.int32)), int(source), _ptr(level))
+    return level
