@@ -57,7 +57,7 @@ constexpr int kPersistThreads = 256;          // 32 lanes x 8 warps
 constexpr int kPersistWarps = 8;
 constexpr int kPersistConeChunk = 256;        // cones per work item (one per thread)
 constexpr long long kPersistSpinLimit = 1LL << 24;   // polls (~32 ns apart) before a barrier gives up
-constexpr int kPersistMaxSteps = 1 << 19;            // steps per launch (the barrier's ticket counter stays < 2^31)
+constexpr int kPersistMaxSteps = 1 << 20;            // steps per launch (longer runs take several)
 
 // A point source binned to its field tile: node offset y * pitch + x (-1 when
 // the cell is outside the grid) and the source's index.
@@ -96,7 +96,7 @@ struct PItem {
 };
 constexpr int kPersistBinCap = 4096;  // instances with more sources scan them per tile
 struct PBar {
-    unsigned count, gen;
+    unsigned long long count;   // arrivals since the launch began (only grows)
     int abort;
     unsigned pad;
 };

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "cue_barrier.cuh"
 #include "cue_internal.h"
 
 namespace cue {
@@ -218,59 +219,6 @@ __device__ __forceinline__ void cone_chunk(const PInst &I, const float *C, int c
     const float big = 3.402823466e38f;
     if (!(fabsf(p[0]) <= big && fabsf(p[1]) <= big && fabsf(d[0]) <= big && fabsf(d[1]) <= big))
         flag_status(I.status, kStatusNonFinite);
-}
-
-// ---------------------------------------------------------------- grid barrier
-// Ticket barrier: the arrival counter only grows (it is zeroed per launch).
-// A block's thread 0 takes a ticket with one acquire-release atomic (the
-// release publishes the block's writes, which the preceding __syncthreads
-// orders before it), and the barrier is passed once the counter reaches the
-// next multiple of `expected`: the last arrival needs no second write, and
-// the others poll with acquire loads, a bounded number of times.  Returns
-// false when the launch is aborting.
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
-{
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ bool grid_barrier(PBar *bar, unsigned expected, long long limit, unsigned *status)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile int *vabort = &bar->abort;
-        int ok = *vabort ? 0 : 1;
-        if (ok) {
-            const unsigned ticket = atom_add_acq_rel(&bar->count, 1u);
-            const unsigned target = (ticket / expected + 1u) * expected;
-            long long it = 0;
-            while ((int)(ld_acquire(&bar->count) - target) < 0) {
-                if (*vabort) {
-                    ok = 0;
-                    break;
-                }
-                if (++it > limit) {
-                    flag_status(status, kStatusTimeout);
-                    atomicExch(&bar->abort, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
 }
 
 // Add a thread's cone-update count to its instance's counter when the thread
@@ -488,7 +436,6 @@ cudaError_t persist_launch(const PInst *d_insts, const PItem *d_items, int n_ite
     cudaError_t e = cudaMemsetAsync(d_bar, 0, sizeof(PBar), stream);
     if (e != cudaSuccess) return e;
     const unsigned expected = (unsigned)grid + (unsigned)(phantom > 0 ? phantom : 0);
-    if ((long long)nsteps * expected >= (1LL << 31)) return cudaErrorInvalidValue;   // caller splits the run
     const long long lim = limit > 0 ? limit : kPersistSpinLimit;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
