@@ -24,6 +24,7 @@
 // FP64.
 #include <algorithm>
 
+#include "cue_barrier.cuh"
 #include "cue_internal.h"
 
 namespace cue {
@@ -414,15 +415,36 @@ __device__ __forceinline__ void cone_adjoint(const FieldDesc &f, const ConeDesc 
 // also gives the corner node gradients (position derivative), and the field
 // adjoint is summed per patch node in registers, then scattered with 12
 // independent double-float atomics (instead of reloading the nodes and
-// scattering 16 pairs corner by corner).  Patch slots are gather2's:
+// scattering 16 pairs corner by corner).  pbar and dbar are FP64.  Patch slots are gather2's:
 //   0..3 (xm, x0, x1, xp) at y0;  4..7 the same at y1;  8, 9 (x0, x1) at ym;
 //   10, 11 (x0, x1) at yp.
+// 1/sqrt(x) in FP64 for x in the normal float range: a float seed and two
+// Newton steps y <- y (3 - x y^2) / 2 (relative error about 1e-14), far fewer
+// FP64 instructions than an IEEE square root and division.
+__device__ __forceinline__ double rsqrt_d(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y * (1.5 - 0.5 * x * y * y);
+}
+
+__device__ __forceinline__ void atomic_add_dfd(float *hi, float *lo, double c)
+{
+    const float ch = (float)c;
+    const float cl = (float)(c - (double)ch);
+    const float old = atomicAdd(hi, ch);
+    const float r = two_sum(old, ch).lo + cl;
+    if (r != 0.0f) atomicAdd(lo, r);
+}
+
 __device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc &c, const float *__restrict__ C,
                                               uint32_t axon, uint32_t step, const float *p, const float *d,
-                                              float *pbar, float *dbar, float *mu)
+                                              double *pbar, double *dbar, float *mu)
 {
     const size_t sy = f.nx;
     auto ld = [&](int i, int j, int) { return __ldg(C + (size_t)i + sy * j); };
+    // the forward step in FP32, for its decisions (gradient threshold, blend
+    // threshold, clamp) and the values it stepped from
     float xi[2];
     cone_noise<2>(c.key0, c.key1, axon, step, xi);
     int lo[3] = {0, 0, 0};
@@ -435,67 +457,88 @@ __device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc
     const float gn2 = fmaf(g[1], g[1], g[0] * g[0]);
     const bool has_g = gn2 > c.eps2;
     const float ginv = has_g ? rsqrtf(gn2) : 0.0f;
-    float vv[2], ghat[2], vn2 = 0.f;
+    float vv[2], vn2 = 0.f;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        ghat[i] = g[i] * ginv;
-        vv[i] = c.w_prev * d[i] + c.w_grad * ghat[i] + c.w_noise * xi[i];
+        vv[i] = c.w_prev * d[i] + c.w_grad * (g[i] * ginv) + c.w_noise * xi[i];
         vn2 = fmaf(vv[i], vv[i], vn2);
     }
     const bool has_v = vn2 > 1e-30f;
     const float vinv = has_v ? rsqrtf(vn2) : 0.0f;
-    float dn[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) dn[i] = has_v ? vv[i] * vinv : d[i];
-    const float hi[2] = {c.hi0, c.hi1};
-    float qbar[2], dnbar[2];
+    bool clamped[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const float q = fmaf(c.step_len, dn[i], p[i]);
-        qbar[i] = (q < 0.0f || q > hi[i]) ? 0.0f : pbar[i];
-        dnbar[i] = fmaf(c.step_len, qbar[i], dbar[i]);
+        const float dnf = has_v ? vv[i] * vinv : d[i];
+        const float q = fmaf(c.step_len, dnf, p[i]);
+        clamped[i] = q < 0.0f || q > (i ? c.hi1 : c.hi0);
     }
-    float vbar[2];
+    // the reverse mode in FP64 at those values: the adjoint of the endpoint
+    // loss cancels heavily between cones and steps, and the per-cone work is
+    // small next to the field's
+    const double gd[2] = {(double)g[0], (double)g[1]};
+    double ghat[2] = {0.0, 0.0}, ginvd = 0.0;
+    if (has_g) {
+        ginvd = rsqrt_d(gd[0] * gd[0] + gd[1] * gd[1]);
+        ghat[0] = gd[0] * ginvd;
+        ghat[1] = gd[1] * ginvd;
+    }
+    double vd[2], dn[2], vinvd = 0.0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        vd[i] = (double)c.w_prev * (double)d[i] + (double)c.w_grad * ghat[i] + (double)c.w_noise * (double)xi[i];
+    if (has_v) vinvd = rsqrt_d(vd[0] * vd[0] + vd[1] * vd[1]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) dn[i] = has_v ? vd[i] * vinvd : (double)d[i];
+    double qbar[2], dnbar[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        qbar[i] = clamped[i] ? 0.0 : pbar[i];
+        dnbar[i] = (double)c.step_len * qbar[i] + dbar[i];
+    }
+    double vbar[2];
     if (has_v) {
-        const float dot = fmaf(dn[1], dnbar[1], dn[0] * dnbar[0]);
+        const double dot = dn[0] * dnbar[0] + dn[1] * dnbar[1];
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-            vbar[i] = (dnbar[i] - dn[i] * dot) * vinv;
-            dbar[i] = c.w_prev * vbar[i];
+            vbar[i] = (dnbar[i] - dn[i] * dot) * vinvd;
+            dbar[i] = (double)c.w_prev * vbar[i];
         }
     } else {
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-            vbar[i] = 0.f;
+            vbar[i] = 0.0;
             dbar[i] = dnbar[i];
         }
     }
-    float gbar[2];
-    {
-        const float dot = fmaf(ghat[1], c.w_grad * vbar[1], ghat[0] * (c.w_grad * vbar[0]));
+    double gbar[2] = {0.0, 0.0};
+    if (has_g) {
+        const double wg = (double)c.w_grad;
+        const double dot = ghat[0] * (wg * vbar[0]) + ghat[1] * (wg * vbar[1]);
 #pragma unroll
-        for (int i = 0; i < 2; ++i) gbar[i] = has_g ? (c.w_grad * vbar[i] - ghat[i] * dot) * ginv : 0.0f;
+        for (int i = 0; i < 2; ++i) gbar[i] = (wg * vbar[i] - ghat[i] * dot) * ginvd;
     }
     // corner weights and node gradients (corner (a, b) = node (x_a, y_b))
-    const float wx0 = 1.0f - fr[0], wx1 = fr[0], wy0 = 1.0f - fr[1], wy1 = fr[1];
-    const float w00 = wx0 * wy0, w10 = wx1 * wy0, w01 = wx0 * wy1, w11 = wx1 * wy1;
-    const float gx00 = (v[2] - v[0]) * c.inv2h, gx10 = (v[3] - v[1]) * c.inv2h;
-    const float gx01 = (v[6] - v[4]) * c.inv2h, gx11 = (v[7] - v[5]) * c.inv2h;
-    const float gy00 = (v[5] - v[8]) * c.inv2h, gy10 = (v[6] - v[9]) * c.inv2h;
-    const float gy01 = (v[10] - v[1]) * c.inv2h, gy11 = (v[11] - v[2]) * c.inv2h;
+    const double i2h = (double)c.inv2h;
+    const double wx0 = 1.0 - (double)fr[0], wx1 = (double)fr[0], wy0 = 1.0 - (double)fr[1], wy1 = (double)fr[1];
+    const double w00 = wx0 * wy0, w10 = wx1 * wy0, w01 = wx0 * wy1, w11 = wx1 * wy1;
+    const double gx00 = ((double)v[2] - v[0]) * i2h, gx10 = ((double)v[3] - v[1]) * i2h;
+    const double gx01 = ((double)v[6] - v[4]) * i2h, gx11 = ((double)v[7] - v[5]) * i2h;
+    const double gy00 = ((double)v[5] - v[8]) * i2h, gy10 = ((double)v[6] - v[9]) * i2h;
+    const double gy01 = ((double)v[10] - v[1]) * i2h, gy11 = ((double)v[11] - v[2]) * i2h;
     // position: g(p) = sum_c w_c(p) G_c, dw/dp from the bilinear weights
-    const float s00 = fmaf(gbar[1], gy00, gbar[0] * gx00), s10 = fmaf(gbar[1], gy10, gbar[0] * gx10);
-    const float s01 = fmaf(gbar[1], gy01, gbar[0] * gx01), s11 = fmaf(gbar[1], gy11, gbar[0] * gx11);
-    pbar[0] = fmaf(f.inv_h, wy0 * (s10 - s00) + wy1 * (s11 - s01), qbar[0]);
-    pbar[1] = fmaf(f.inv_h, wx0 * (s01 - s00) + wx1 * (s11 - s10), qbar[1]);
+    const double s00 = gbar[0] * gx00 + gbar[1] * gy00, s10 = gbar[0] * gx10 + gbar[1] * gy10;
+    const double s01 = gbar[0] * gx01 + gbar[1] * gy01, s11 = gbar[0] * gx11 + gbar[1] * gy11;
+    const double ih = (double)f.inv_h;
+    pbar[0] = ih * (wy0 * (s10 - s00) + wy1 * (s11 - s01)) + qbar[0];
+    pbar[1] = ih * (wx0 * (s01 - s00) + wx1 * (s11 - s10)) + qbar[1];
     if (!has_g) return;
     // field: coefficient of each patch node in gbar . g
-    const float ax = gbar[0] * c.inv2h, ay = gbar[1] * c.inv2h;
-    const float cx00 = ax * w00, cx10 = ax * w10, cx01 = ax * w01, cx11 = ax * w11;
-    const float cy00 = ay * w00, cy10 = ay * w10, cy01 = ay * w01, cy11 = ay * w11;
-    const float sc[kPatch2] = {-cx00,        -cx10 - cy01, cx00 - cy11, cx10,
-                               -cx01,        cy00 - cx11,  cy10 + cx01, cx11,
-                               -cy00,        -cy10,        cy01,        cy11};
+    const double ax = gbar[0] * i2h, ay = gbar[1] * i2h;
+    const double cx00 = ax * w00, cx10 = ax * w10, cx01 = ax * w01, cx11 = ax * w11;
+    const double cy00 = ay * w00, cy10 = ay * w10, cy01 = ay * w01, cy11 = ay * w11;
+    const double sc[kPatch2] = {-cx00,        -cx10 - cy01, cx00 - cy11, cx10,
+                                -cx01,        cy00 - cx11,  cy10 + cx01, cx11,
+                                -cy00,        -cy10,        cy01,        cy11};
     const int xm = max(lo[0] - 1, 0), x0 = lo[0], x1 = lo[0] + 1, xp = min(lo[0] + 2, f.nx - 1);
     const int ym = max(lo[1] - 1, 0), y0 = lo[1], y1 = lo[1] + 1, yp = min(lo[1] + 2, f.ny - 1);
     const int xs[kPatch2] = {xm, x0, x1, xp, xm, x0, x1, xp, x0, x1, x0, x1};
@@ -504,7 +547,188 @@ __device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc
 #pragma unroll
     for (int k = 0; k < kPatch2; ++k) {
         const size_t j = (size_t)xs[k] + sy * ys[k];
-        atomic_add_df(mu + j, mu_lo + j, sc[k]);
+        atomic_add_dfd(mu + j, mu_lo + j, sc[k]);
+    }
+}
+
+// ---------------------------------------------------------------- persistent backward
+// The cone adjoint never reads the adjoint field: going back through step m,
+//   mu^m = A mu^{m+1} + X^m,   X^m = the cones' scatter at step m.
+// With Y^m = A mu^{m+1}, one phase per step computes Y^m from
+// mu^{m+1} = Y^{m+1} + X^{m+1} (field tiles) while the cone chunks scatter X^m,
+// then the blocks meet at the grid barrier.  Y ping-pongs; X rotates over
+// three buffers: a phase reads X^{m+1}, writes X^m and zeroes X^{m+2}, which
+// the previous phase read and the next one writes.  All are double-float
+// (hi plane, lo plane).  A segment's backward steps are one cooperative launch.
+struct AdjP {
+    FieldDesc f;
+    ConeDesc c;
+    int n;                        // cones
+    int n_src;
+    const int32_t *src_cell;
+    const uint8_t *active;
+    double *pbar, *dbar;          // dL/d(p, d), FP64
+    const float *segC;            // [k + 1][cells]
+    const float *segP;            // [k + 1][pos, dir][2][n]
+    size_t cells, cone_n;
+    float *Y[2];
+    float *X[3];
+    float *Sseg;                  // nullable
+    double *part;                 // per-block (dD, dlambda) slots
+    double *de;                   // per-source sums
+    int ntx, n_chunks, n_items;
+};
+
+__device__ __forceinline__ DF mu_load(const float *Y, const float *X, size_t cells, size_t i)
+{
+    return df_add(df_of(__ldcg(Y + i), __ldcg(Y + cells + i)), df_of(__ldcg(X + i), __ldcg(X + cells + i)));
+}
+
+__device__ __forceinline__ void mu_row(const float *Y, const float *X, size_t cells, size_t at4, DF *m)
+{
+    const float4 yh = __ldcg(reinterpret_cast<const float4 *>(Y) + at4);
+    const float4 yl = __ldcg(reinterpret_cast<const float4 *>(Y + cells) + at4);
+    const float4 xh = __ldcg(reinterpret_cast<const float4 *>(X) + at4);
+    const float4 xl = __ldcg(reinterpret_cast<const float4 *>(X + cells) + at4);
+    m[0] = df_add(df_of(yh.x, yl.x), df_of(xh.x, xl.x));
+    m[1] = df_add(df_of(yh.y, yl.y), df_of(xh.y, xl.y));
+    m[2] = df_add(df_of(yh.z, yl.z), df_of(xh.z, xl.z));
+    m[3] = df_add(df_of(yh.w, yl.w), df_of(xh.w, xl.w));
+}
+
+// One field tile (32 lanes x 4 columns, 8 warps x 1 row) of one backward step.
+// Every load (three rows of Y and X, hi and lo; the warp-edge columns; C and
+// the map sum) is issued before the first arithmetic.
+__device__ __forceinline__ void adj_tile(const AdjP &A, const float *Yin, const float *Xin, float *Yout, float *Xz,
+                                         const float *Cm, int tile, float &tD, float &tL)
+{
+    const FieldDesc &f = A.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tx = tile % A.ntx, ty = tile / A.ntx;
+    const int nx4 = f.nx >> 2;
+    const int x4 = tx * 32 + lane;
+    const int y = ty * 8 + warp;
+    if (y >= f.ny) return;                                 // warp-uniform
+    const bool xin = x4 < nx4;
+    const int x = x4 * 4;
+    const bool has_l = x > 0, has_r = x + 4 < f.nx;
+    const size_t cells = A.cells;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 *yh4 = reinterpret_cast<const float4 *>(Yin), *yl4 = reinterpret_cast<const float4 *>(Yin + cells);
+    const float4 *xh4 = reinterpret_cast<const float4 *>(Xin), *xl4 = reinterpret_cast<const float4 *>(Xin + cells);
+    float4 YH[3], YL[3], XH[3], XL[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {                          // rows y - 1, y, y + 1 (the walls repeat y)
+        const int yy = r == 0 ? (y > 0 ? y - 1 : y) : (r == 2 ? (y + 1 < f.ny ? y + 1 : y) : y);
+        const size_t at = (size_t)yy * nx4 + x4;
+        YH[r] = xin ? __ldcg(yh4 + at) : z4;
+        YL[r] = xin ? __ldcg(yl4 + at) : z4;
+        XH[r] = xin ? __ldcg(xh4 + at) : z4;
+        XL[r] = xin ? __ldcg(xl4 + at) : z4;
+    }
+    float el[4] = {0.f, 0.f, 0.f, 0.f}, er[4] = {0.f, 0.f, 0.f, 0.f};
+    if (lane == 0 && xin && has_l) {
+        const size_t i = (size_t)y * f.nx + x - 1;
+        el[0] = __ldcg(Yin + i);
+        el[1] = __ldcg(Yin + cells + i);
+        el[2] = __ldcg(Xin + i);
+        el[3] = __ldcg(Xin + cells + i);
+    }
+    if (lane == 31 && xin && has_r) {
+        const size_t i = (size_t)y * f.nx + x + 4;
+        er[0] = __ldcg(Yin + i);
+        er[1] = __ldcg(Yin + cells + i);
+        er[2] = __ldcg(Xin + i);
+        er[3] = __ldcg(Xin + cells + i);
+    }
+    const size_t at = (size_t)y * nx4 + x4;
+    const float4 c = xin ? __ldg(reinterpret_cast<const float4 *>(Cm) + at) : z4;
+    float4 *s4 = A.Sseg ? reinterpret_cast<float4 *>(A.Sseg) + at : nullptr;
+    const float4 sv0 = (s4 && xin) ? *s4 : z4;
+    auto mu4 = [&](int r, DF *m) {
+        m[0] = df_add(df_of(YH[r].x, YL[r].x), df_of(XH[r].x, XL[r].x));
+        m[1] = df_add(df_of(YH[r].y, YL[r].y), df_of(XH[r].y, XL[r].y));
+        m[2] = df_add(df_of(YH[r].z, YL[r].z), df_of(XH[r].z, XL[r].z));
+        m[3] = df_add(df_of(YH[r].w, YL[r].w), df_of(XH[r].w, XL[r].w));
+    };
+    DF up[4], cu[4], dn[4];
+    mu4(0, up);
+    mu4(1, cu);
+    mu4(2, dn);
+    DF l, r;
+    l.hi = __shfl_up_sync(kFull, cu[3].hi, 1);
+    l.lo = __shfl_up_sync(kFull, cu[3].lo, 1);
+    r.hi = __shfl_down_sync(kFull, cu[0].hi, 1);
+    r.lo = __shfl_down_sync(kFull, cu[0].lo, 1);
+    if (lane == 0) l = has_l ? df_add(df_of(el[0], el[1]), df_of(el[2], el[3])) : cu[0];
+    if (lane == 31) r = has_r ? df_add(df_of(er[0], er[1]), df_of(er[2], er[3])) : cu[3];
+    if (!has_l) l = cu[0];
+    if (!has_r) r = cu[3];
+    if (!xin) return;
+    float L0, L1, L2, L3;
+    const DF o0 = df_update(cu[0], l, cu[1], up[0], dn[0], f.alpha, f.beta, &L0);
+    const DF o1 = df_update(cu[1], cu[0], cu[2], up[1], dn[1], f.alpha, f.beta, &L1);
+    const DF o2 = df_update(cu[2], cu[1], cu[3], up[2], dn[2], f.alpha, f.beta, &L2);
+    const DF o3 = df_update(cu[3], cu[2], r, up[3], dn[3], f.alpha, f.beta, &L3);
+    const float v0 = cu[0].hi + cu[0].lo, v1 = cu[1].hi + cu[1].lo, v2 = cu[2].hi + cu[2].lo,
+                v3 = cu[3].hi + cu[3].lo;
+    tD = fmaf(L0, c.x, fmaf(L1, c.y, fmaf(L2, c.z, fmaf(L3, c.w, tD))));
+    tL = fmaf(v0, c.x, fmaf(v1, c.y, fmaf(v2, c.z, fmaf(v3, c.w, tL))));
+    if (s4) *s4 = make_float4(sv0.x + v0, sv0.y + v1, sv0.z + v2, sv0.w + v3);
+    reinterpret_cast<float4 *>(Yout)[at] = make_float4(o0.hi, o1.hi, o2.hi, o3.hi);
+    reinterpret_cast<float4 *>(Yout + cells)[at] = make_float4(o0.lo, o1.lo, o2.lo, o3.lo);
+    reinterpret_cast<float4 *>(Xz)[at] = z4;
+    reinterpret_cast<float4 *>(Xz + cells)[at] = z4;
+}
+
+__global__ void __launch_bounds__(256, 2) adj_persist_kernel(AdjP A, int len, uint32_t g0, PBar *bar,
+                                                             unsigned expected, long long limit, unsigned *status)
+{
+    for (int m = len - 1; m >= 0; --m) {
+        const uint32_t g = g0 + (uint32_t)m;              // global step index
+        const float *Yin = A.Y[(g + 1) & 1];
+        float *Yout = A.Y[g & 1];
+        const float *Xin = A.X[(g + 1) % 3];
+        float *Xout = A.X[g % 3];
+        float *Xz = A.X[(g + 2) % 3];
+        const float *Cm = A.segC + A.cells * m;
+        const float *Pm = A.segP + 2 * A.cone_n * m;
+        if (blockIdx.x == 0)                              // de_k += mu^{m+1}[cell_k]
+            for (int k = threadIdx.x; k < A.n_src; k += blockDim.x) {
+                const long long c = A.src_cell[k];
+                if (c >= 0 && c < (long long)A.cells) {
+                    const DF v = mu_load(Yin, Xin, A.cells, (size_t)c);
+                    A.de[k] += (double)v.hi + (double)v.lo;
+                }
+            }
+        float tD = 0.f, tL = 0.f;
+        for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
+            if (it < A.n_chunks) {
+                // 32 cones per item, one warp: the FP64 work of the cones spreads over
+                // many SMs (GB300's FP64 rate per SM is low); the other warps move on
+                if ((threadIdx.x >> 5) != (it & 7)) continue;
+                const int a = it * 32 + (threadIdx.x & 31);
+                if (a < A.n && A.active[a]) {
+                    float p[2], d[2];
+                    double pb[2], db[2];
+                    for (int i = 0; i < 2; ++i) {
+                        p[i] = __ldg(Pm + (size_t)i * A.n + a);
+                        d[i] = __ldg(Pm + A.cone_n + (size_t)i * A.n + a);
+                        pb[i] = __ldcg(A.pbar + (size_t)i * A.n + a);
+                        db[i] = __ldcg(A.dbar + (size_t)i * A.n + a);
+                    }
+                    cone_adjoint2(A.f, A.c, Cm, (uint32_t)a, g, p, d, pb, db, Xout);
+                    for (int i = 0; i < 2; ++i) {
+                        A.pbar[(size_t)i * A.n + a] = pb[i];
+                        A.dbar[(size_t)i * A.n + a] = db[i];
+                    }
+                }
+            } else {
+                adj_tile(A, Yin, Xin, Yout, Xz, Cm, it - A.n_chunks, tD, tL);
+            }
+        }
+        block_add2<true>(tD, tL, A.part);
+        if (!grid_barrier(bar, expected, limit, status)) return;
     }
 }
 
@@ -513,8 +737,8 @@ template <int DIM>
 __global__ void __launch_bounds__(256) adj_cone_kernel(FieldDesc f, ConeDesc c, const float *__restrict__ C,
                                                        uint32_t step, int n, const float *__restrict__ P,
                                                        const float *__restrict__ Dd,
-                                                       const uint8_t *__restrict__ active, float *pbar,
-                                                       float *dbar, float *mu_out, const float *__restrict__ mu_in,
+                                                       const uint8_t *__restrict__ active, double *pbar,
+                                                       double *dbar, float *mu_out, const float *__restrict__ mu_in,
                                                        const int32_t *__restrict__ src_cell, int n_src,
                                                        double *de_acc)
 {
@@ -525,7 +749,8 @@ __global__ void __launch_bounds__(256) adj_cone_kernel(FieldDesc f, ConeDesc c, 
         if (cell >= 0 && cell < n_cells) de_acc[a] += (double)mu_in[cell] + (double)mu_in[n_cells + cell];
     }
     if (a >= n || !active[a]) return;
-    float p[DIM], d[DIM], pb[DIM], db[DIM];
+    float p[DIM], d[DIM];
+    double pb[DIM], db[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
         p[i] = P[(size_t)i * n + a];
@@ -533,10 +758,22 @@ __global__ void __launch_bounds__(256) adj_cone_kernel(FieldDesc f, ConeDesc c, 
         pb[i] = pbar[(size_t)i * n + a];
         db[i] = dbar[(size_t)i * n + a];
     }
-    if constexpr (DIM == 2)
+    if constexpr (DIM == 2) {
         cone_adjoint2(f, c, C, (uint32_t)a, step, p, d, pb, db, mu_out);
-    else
-        cone_adjoint<DIM>(f, c, C, (uint32_t)a, step, p, d, pb, db, mu_out);
+    } else {
+        float pf[DIM], df_[DIM];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            pf[i] = (float)pb[i];
+            df_[i] = (float)db[i];
+        }
+        cone_adjoint<DIM>(f, c, C, (uint32_t)a, step, p, d, pf, df_, mu_out);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            pb[i] = pf[i];
+            db[i] = df_[i];
+        }
+    }
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
         pbar[(size_t)i * n + a] = pb[i];
@@ -546,7 +783,7 @@ __global__ void __launch_bounds__(256) adj_cone_kernel(FieldDesc f, ConeDesc c, 
 
 // Loss and dL/dp^T = 2 (p^T - t)/n, dL/dd^T = 0.
 __global__ void __launch_bounds__(256) adj_loss_kernel(int n, int dim, const float *__restrict__ P,
-                                                       const float *__restrict__ T, float *pbar, float *dbar,
+                                                       const float *__restrict__ T, double *pbar, double *dbar,
                                                        double *loss_acc)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -555,8 +792,8 @@ __global__ void __launch_bounds__(256) adj_loss_kernel(int n, int dim, const flo
         for (int i = 0; i < dim; ++i) {
             const float e = P[(size_t)i * n + a] - T[(size_t)i * n + a];
             s = fmaf(e, e, s);
-            pbar[(size_t)i * n + a] = 2.0f * e / (float)n;
-            dbar[(size_t)i * n + a] = 0.0f;
+            pbar[(size_t)i * n + a] = 2.0 * (double)e / (double)n;
+            dbar[(size_t)i * n + a] = 0.0;
         }
     }
     block_add2<false>(s, 0.0f, loss_acc);
@@ -599,7 +836,7 @@ __global__ void __launch_bounds__(256) adj_finalize_kernel(FieldDesc f, int n_ax
 }
 
 struct AdjLayout {
-    size_t ckpt_c, ckpt_p, seg_c, seg_p, mu, Sseg, S, pbar, acc, part, total;
+    size_t ckpt_c, ckpt_p, seg_c, seg_p, mu, Sseg, S, pbar, acc, part, bar, total;
     int n_part;
     int nseg;
 };
@@ -607,6 +844,8 @@ struct AdjLayout {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int blocks_for(size_t n, int per) { return (int)((n + per - 1) / per); }
+
+constexpr int kAdjMaxBlocksPerSm = 8;
 
 int sm_count_adj()
 {
@@ -664,21 +903,39 @@ AdjLayout adj_layout(const cue_params &p, int n_src, int n_axons, int nsteps, in
     off += align256(sizeof(float) * cells * (k + 1));
     L.seg_p = off;
     off += align256(sizeof(float) * cone * (k + 1));
-    L.mu = off;                                   // adjoint field, two double-float buffers (hi, lo planes)
-    off += align256(sizeof(float) * cells * 4);
+    L.mu = off;                                   // adjoint field: five double-float buffers (hi, lo planes):
+    off += align256(sizeof(float) * cells * 10);  // Y[2] and X[3] of the persistent backward, or mu[2]
     L.Sseg = off;                                 // this segment's sum of mu
     off += align256(sizeof(float) * cells);
     L.S = off;                                    // FP64 sum over the segments (rate-map gradient)
     off += align256(sizeof(double) * cells);
     L.pbar = off;
-    off += align256(sizeof(float) * cone);
+    off += align256(sizeof(double) * cone);        // dL/dp and dL/dd, FP64
     L.acc = off;                                  // spare, spare, de[n_src], loss, spare
     off += align256(sizeof(double) * (4 + n_src));
-    L.n_part = adj_field_blocks(p);
+    L.n_part = std::max(adj_field_blocks(p), kAdjMaxBlocksPerSm * sm_count_adj());
     L.part = off;                                 // per-block (dD, dlambda) sums of the field kernel
     off += align256(sizeof(double) * 2 * (size_t)L.n_part);
+    L.bar = off;                                  // grid barrier of the persistent backward
+    off += 256;
     L.total = off;
     return L;
+}
+
+int adj_persist_blocks_per_sm()
+{
+    static int nb = -1;
+    if (nb < 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, adj_persist_kernel, 256, 0) != cudaSuccess) v = 0;
+        nb = std::min(v, kAdjMaxBlocksPerSm);
+    }
+    return nb;
+}
+
+bool adj_persist_supported(const Sim &s)
+{
+    return s.path != CUE_PATH_PLAIN && s.fd.dim == 2 && s.fd.nx % 4 == 0 && adj_persist_blocks_per_sm() > 0;
 }
 
 void launch_adj_field(Sim &s, const float *mu_in, float *mu_out, const float *C, float *Sseg, double *acc)
@@ -722,12 +979,12 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
     float *mu[2] = {reinterpret_cast<float *>(W + L.mu), reinterpret_cast<float *>(W + L.mu) + 2 * cells};
     float *Sseg = gmap ? reinterpret_cast<float *>(W + L.Sseg) : nullptr;
     double *S = gmap ? reinterpret_cast<double *>(W + L.S) : nullptr;
-    float *pbar = reinterpret_cast<float *>(W + L.pbar), *dbar = pbar + cone_n;
+    double *pbar = reinterpret_cast<double *>(W + L.pbar), *dbar = pbar + cone_n;
     double *acc = reinterpret_cast<double *>(W + L.acc);     // spare, spare, de[n_src], loss
     double *part = reinterpret_cast<double *>(W + L.part);   // per-block (dD, dlambda) sums
     cudaStream_t st = s.stream;
     auto ok = [](cudaError_t e) { return e == cudaSuccess; };
-    if (!ok(cudaMemsetAsync(mu[0], 0, sizeof(float) * cells * 4, st)) ||
+    if (!ok(cudaMemsetAsync(mu[0], 0, sizeof(float) * cells * 10, st)) ||
         !ok(cudaMemsetAsync(acc, 0, sizeof(double) * (4 + s.n_src), st)) ||
         !ok(cudaMemsetAsync(part, 0, sizeof(double) * 2 * (size_t)L.n_part, st)) ||
         (S && !ok(cudaMemsetAsync(S, 0, sizeof(double) * cells, st))) ||
@@ -751,7 +1008,34 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
         adj_loss_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, dim, s.pos, targets, pbar, dbar, acc + 2 + s.n_src);
         s.launches++;
     }
-    // ---- backwards through the segments
+    // ---- backwards through the segments: one persistent launch per segment where
+    // the path runs (2D, nx % 4 == 0), else two launches per step
+    const bool persist_bw = adj_persist_supported(s);
+    AdjP A{};
+    int bw_grid = 0;
+    if (persist_bw) {
+        A.f = f;
+        A.c = s.cd;
+        A.n = n;
+        A.n_src = s.n_src;
+        A.src_cell = s.src_cell;
+        A.active = s.active;
+        A.pbar = pbar;
+        A.dbar = dbar;
+        A.cells = cells;
+        A.cone_n = cone_n;
+        float *base = reinterpret_cast<float *>(W + L.mu);
+        A.Y[0] = base;
+        A.Y[1] = base + 2 * cells;
+        for (int i = 0; i < 3; ++i) A.X[i] = base + (4 + 2 * i) * cells;
+        A.Sseg = Sseg;
+        A.part = part;
+        A.de = acc + 2;
+        A.ntx = (f.nx / 4 + 31) / 32;
+        A.n_chunks = blocks_for((size_t)n, 32);
+        A.n_items = A.n_chunks + A.ntx * blocks_for((size_t)f.ny, 8);
+        bw_grid = std::max(1, std::min(A.n_items, std::min(2, adj_persist_blocks_per_sm()) * sm_count_adj()));
+    }
     int in = 0;
     for (int j = L.nseg - 1; j >= 0; --j) {
         const int len = std::min(k, nsteps - j * k);
@@ -772,17 +1056,36 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
                 !ok(launch_field_and_sources(s, sgC + cells * m, sgC + cells * (m + 1))))
                 return CUE_ERR_CUDA;
         }
-        for (int m = len - 1; m >= 0; --m) {
+        if (persist_bw) {
+            A.segC = sgC;
+            A.segP = sgP;
+            if (!ok(cudaMemsetAsync(W + L.bar, 0, 256, st))) return CUE_ERR_CUDA;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(bw_grid);
+            cfg.blockDim = dim3(256);
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (!ok(cudaLaunchKernelEx(&cfg, adj_persist_kernel, A, len, (uint32_t)nstart,
+                                       reinterpret_cast<PBar *>(W + L.bar), (unsigned)bw_grid, kPersistSpinLimit,
+                                       s.status())))
+                return CUE_ERR_CUDA;
+            s.launches++;
+        }
+        for (int m = len - 1; !persist_bw && m >= 0; --m) {
             const float *Cm = sgC + cells * m, *Pm = sgP + 2 * cone_n * m;
             launch_adj_field(s, mu[in], mu[in ^ 1], Cm, Sseg, part);
-            const int cb = blocks_for((size_t)std::max(n, s.n_src), 64);
+            const int cb = blocks_for((size_t)std::max(n, s.n_src), 32);   // FP64 work: many SMs
             if (cb > 0) {
                 if (dim == 2)
-                    adj_cone_kernel<2><<<cb, 64, 0, st>>>(f, s.cd, Cm, (uint32_t)(nstart + m), n, Pm, Pm + cone_n,
+                    adj_cone_kernel<2><<<cb, 32, 0, st>>>(f, s.cd, Cm, (uint32_t)(nstart + m), n, Pm, Pm + cone_n,
                                                            s.active, pbar, dbar, mu[in ^ 1], mu[in], s.src_cell,
                                                            s.n_src, acc + 2);
                 else
-                    adj_cone_kernel<3><<<cb, 64, 0, st>>>(f, s.cd, Cm, (uint32_t)(nstart + m), n, Pm, Pm + cone_n,
+                    adj_cone_kernel<3><<<cb, 32, 0, st>>>(f, s.cd, Cm, (uint32_t)(nstart + m), n, Pm, Pm + cone_n,
                                                            s.active, pbar, dbar, mu[in ^ 1], mu[in], s.src_cell,
                                                            s.n_src, acc + 2);
                 s.launches++;
