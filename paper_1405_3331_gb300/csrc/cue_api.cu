@@ -23,14 +23,12 @@ WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons)
     const size_t na = (size_t)(n_axons > 0 ? n_axons : 1);
     w.bin_count_off = off;
     off += align256(sizeof(int32_t) * 2 * nt);
-    w.bin_off_off = off;
-    off += align256(sizeof(int32_t) * (nt + 1));
+    w.bin_ctl_off = off;
+    off += 256;
     w.bin_list_off = off;
-    off += align256(sizeof(int32_t) * na);
-    w.cone_tile_off = off;
-    off += align256(sizeof(int32_t) * na);
-    w.cone_slot_off = off;
-    off += align256(sizeof(int32_t) * na);
+    off += align256(sizeof(int32_t) * 2 * nt * (w.n_tiles > 0 ? kFusedBinCap : 1));
+    w.spill_off = off;
+    off += align256(sizeof(int2) * 2 * (w.n_tiles > 0 ? na : 1));
     w.persist_off = off;
     if (p.dim == 2 && p.nx >= 4) {
         w.persist_items_cap = (size_t)persist_tiles(p.nx, p.ny, 1) + (na + kPersistConeChunk - 1) / kPersistConeChunk;
@@ -268,7 +266,7 @@ int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone, f
               (!d_src_map || aligned16(d_src_map));
     cudaError_t e = cudaMemsetAsync(s->ws, 0, 256, s->stream);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(s->ws + wl.bin_count_off, 0, wl.bin_off_off - wl.bin_count_off, s->stream);
+        e = cudaMemsetAsync(s->ws + wl.bin_count_off, 0, wl.bin_list_off - wl.bin_count_off, s->stream);
     if (e == cudaSuccess) e = launch_src_xyz(*s);
     if (e != cudaSuccess) {
         delete s;

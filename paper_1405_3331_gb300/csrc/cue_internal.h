@@ -15,17 +15,19 @@ namespace cue {
 // Workspace layout (all offsets 256-byte aligned):
 //   [0,   256)  status word (unsigned) at 0, cone-update counter (u64) at 8
 //   [256, ...)  source coordinates, FP32 [3][n_src]
-//   [...]       fused-path scratch: per-tile cone counts (two rounds), bin
-//               offsets, the cone ids grouped by tile, each cone's tile and
-//               slot.  n_tiles is an upper bound over every tile geometry.
+//   [...]       fused-path scratch (two rounds each): per-tile cone counts,
+//               fixed-capacity per-tile bins of cone ids, a spill list of
+//               (cone, tile) for overfull tiles and its count.  n_tiles is an
+//               upper bound over every tile geometry.
+constexpr int kFusedBinCap = 512;   // cone ids per tile bin (the fused kernel's register slots)
+
 struct WorkspaceLayout {
     size_t status_off = 0;
     size_t src_xyz_off = 0;
     size_t bin_count_off = 0;    // 2 x n_tiles int32 (double-buffered counts)
-    size_t bin_off_off = 0;      // n_tiles + 1 int32
-    size_t bin_list_off = 0;     // n_axons int32 (cone ids grouped by tile)
-    size_t cone_tile_off = 0;    // n_axons int32 (tile of each cone, -1 = inactive)
-    size_t cone_slot_off = 0;    // n_axons int32 (slot within its tile)
+    size_t bin_ctl_off = 0;      // spill counts (2 int32) and a finished-tile counter
+    size_t bin_list_off = 0;     // 2 x n_tiles x kFusedBinCap int32 (cone ids by tile)
+    size_t spill_off = 0;        // 2 x n_axons int2 (cone, tile) that did not fit their bin
     size_t persist_off = 0;      // persistent path: barrier, two instance records, work list
     size_t persist_items_cap = 0;
     size_t persist_src_off = 0;  // persistent path: binned sources (PSrc) and their tile keys
@@ -164,10 +166,9 @@ struct Sim {
     bool tmap3_ready = false;
 
     int *bin_count() const { return reinterpret_cast<int *>(ws + wl.bin_count_off); }
-    int *bin_off() const { return reinterpret_cast<int *>(ws + wl.bin_off_off); }
+    int *bin_ctl() const { return reinterpret_cast<int *>(ws + wl.bin_ctl_off); }
     int *bin_list() const { return reinterpret_cast<int *>(ws + wl.bin_list_off); }
-    int *cone_tile() const { return reinterpret_cast<int *>(ws + wl.cone_tile_off); }
-    int *cone_slot() const { return reinterpret_cast<int *>(ws + wl.cone_slot_off); }
+    int2 *spill() const { return reinterpret_cast<int2 *>(ws + wl.spill_off); }
     unsigned *status() const { return reinterpret_cast<unsigned *>(ws + wl.status_off); }
     unsigned long long *cone_counter() const
     {

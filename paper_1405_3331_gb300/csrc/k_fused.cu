@@ -15,8 +15,12 @@
 // After K sub-steps the interior is stored.  The valid region shrinks by one
 // node per sub-step; cones move at most step_len per step and read a 4-node
 // footprint, so the halo is H = K + 1 + ceil((K-1) step_len / h) (the x halo
-// rounded up to 4 nodes for 16-byte TMA coordinates).  Cones are re-binned to
-// tiles between launches (count, scan, scatter).
+// rounded up to 4 nodes for 16-byte TMA coordinates).  Each launch re-bins its
+// cones for the next one as they finish: fixed-capacity per-tile bins (as many
+// ids as the register slots) filled through atomic counters, cones of a full
+// bin going to a spill list that the tile scans; each tile clears its own
+// count once read, the last tile past its prologue clears the spill count.
+// No separate binning launch between fused launches.
 //
 // Model: cue field on an Eulerian grid (Sec. 5.2) with sources of their own
 // rates (Sec. 4.3); cone steering by vector addition (Sec. 3.5, Eq. 6-7) with
@@ -225,8 +229,18 @@ struct FusedArgs {
     int n_axons;
     float *pos, *dir;
     uint8_t *active;
-    const int *bin_off, *bin_list;
-    int *next_count, *cone_tile, *cone_slot;   // re-binning for the next launch
+    // this launch's bins: count (each tile clears its own after reading it),
+    // ids, and the spill list of cones whose bin was full
+    int *cnt_cur;
+    const int *bins_cur;
+    const int2 *spill_cur;
+    int *spill_cnt_cur;
+    // the next launch's bins, filled as the cones finish (null: no re-binning)
+    int *cnt_next;
+    int *bins_next;
+    int2 *spill_next;
+    int *spill_cnt_next;
+    int *done;                                 // tiles past their prologue: the last clears spill_cnt_cur
     const int32_t *src_cell;
     const float *src_emit;
     int n_src;
@@ -278,15 +292,17 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     }
 
     // this tile's cones into registers (overlaps the TMA load)
-    const int b0 = A.cones_on ? A.bin_off[t] : 0;
-    const int b1 = A.cones_on ? A.bin_off[t + 1] : 0;
+    __shared__ int s_nspill;
+    if (tid == 0) s_nspill = A.cones_on ? *A.spill_cnt_cur : 0;
+    const int n_bin = A.cones_on ? min(A.cnt_cur[t], kFusedBinCap) : 0;
+    const int *bin = A.bins_cur + (size_t)t * kFusedBinCap;
     int ca[kConeSlots];
     bool cl[kConeSlots];
     float cp[kConeSlots][2], cdir[kConeSlots][2];
 #pragma unroll
     for (int q = 0; q < kConeSlots; ++q) {
-        int i = b0 + tid + q * kThreads;
-        ca[q] = i < b1 ? A.bin_list[i] : -1;
+        int i = tid + q * kThreads;
+        ca[q] = i < n_bin ? bin[i] : -1;
         cl[q] = ca[q] >= 0;
         if (cl[q]) {
             cl[q] = A.active[ca[q]] != 0;
@@ -300,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     // hold no cone (it does not depend on the cone state), unless the tile is so
     // full that few threads are free; the first sub-step's noise is drawn here,
     // while the tile copy is in flight.
-    const int cnt0 = min(b1 - b0, kThreads);
+    const int cnt0 = min(n_bin, kThreads);
     const bool pre_noise = cnt0 > 0 && cnt0 <= kThreads - 64;
     cid[tid] = ca[0];
     if (pre_noise && ca[0] >= 0) {
@@ -322,6 +338,16 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
         }
     }
     __syncthreads();
+    const int n_spill = s_nspill;
+    if (A.cones_on && tid == 0) {
+        // every thread has read this tile's count: clear it for the launch after next;
+        // the last tile past this point clears the spill count (every tile holds it)
+        A.cnt_cur[t] = 0;
+        if (atomicAdd(A.done, 1) == (int)gridDim.x - 1) {
+            *A.spill_cnt_cur = 0;
+            *A.done = 0;
+        }
+    }
     if (warp == 0) {       // exclusive scan of the per-row counts
         int carry = 0;
         for (int base = 0; base < kRows; base += 32) {
@@ -456,9 +482,10 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
                 }
             }
         }
-        for (int base = b0 + kConeSlots * kThreads; base < b1; base += kThreads) {   // overflow
-            int i = base + tid;
-            int a = i < b1 ? A.bin_list[i] : -1;
+        for (int base = 0; base < n_spill; base += kThreads) {   // spilled cones of this tile
+            const int i = base + tid;
+            const int2 e = i < n_spill ? A.spill_cur[i] : make_int2(-1, -1);
+            const int a = e.y == t ? e.x : -1;
             bool live = a >= 0 && A.active[a];
             count_active(A.counter, live);
             if (live) {
@@ -483,6 +510,16 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     }
 
     // ---- cones back to global memory, binned for the next launch
+    auto rebin = [&](int a, float px, float py) {
+        const int tile = tile_of(f, g, px, py);
+        const int slot = atomicAdd(&A.cnt_next[tile], 1);
+        if (slot < kFusedBinCap) {
+            A.bins_next[(size_t)tile * kFusedBinCap + slot] = a;
+        } else {
+            const int k = atomicAdd(A.spill_cnt_next, 1);
+            A.spill_next[k] = make_int2(a, tile);
+        }
+    };
 #pragma unroll
     for (int q = 0; q < kConeSlots; ++q) {
         const int a = ca[q];
@@ -492,26 +529,12 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
         A.dir[a] = cdir[q][0];
         A.dir[n + a] = cdir[q][1];
         if (stopped[q]) A.active[a] = 0;
-        if (A.next_count) {
-            if (cl[q]) {
-                int tile = tile_of(f, g, cp[q][0], cp[q][1]);
-                A.cone_tile[a] = tile;
-                A.cone_slot[a] = atomicAdd(&A.next_count[tile], 1);
-            } else {
-                A.cone_tile[a] = -1;
-            }
-        }
+        if (A.cnt_next && cl[q]) rebin(a, cp[q][0], cp[q][1]);
     }
-    if (A.next_count) {
-        for (int i = b0 + kConeSlots * kThreads + tid; i < b1; i += kThreads) {
-            int a = A.bin_list[i];
-            if (A.active[a]) {
-                int tile = tile_of(f, g, A.pos[a], A.pos[n + a]);
-                A.cone_tile[a] = tile;
-                A.cone_slot[a] = atomicAdd(&A.next_count[tile], 1);
-            } else {
-                A.cone_tile[a] = -1;
-            }
+    if (A.cnt_next) {
+        for (int i = tid; i < n_spill; i += kThreads) {
+            const int2 e = A.spill_cur[i];
+            if (e.y == t && A.active[e.x]) rebin(e.x, A.pos[e.x], A.pos[n + e.x]);
         }
     }
 
@@ -538,67 +561,20 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
 }
 
 // ---------------------------------------------------------------- binning
+// Start of a run: every active cone into its tile's bin (or the spill list).
 __global__ void bin_count_kernel(FieldDesc f, FusedGeom g, int n, const float *__restrict__ pos,
-                                 const uint8_t *__restrict__ active, int *count, int *cone_tile, int *cone_slot)
+                                 const uint8_t *__restrict__ active, int *count, int *bins, int2 *spill,
+                                 int *spill_cnt)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n) return;
-    if (!active[a]) {
-        cone_tile[a] = -1;
-        return;
-    }
-    int tile = tile_of(f, g, pos[a], pos[n + a]);
-    cone_tile[a] = tile;
-    cone_slot[a] = atomicAdd(&count[tile], 1);
-}
-
-// Every block scans the per-tile counts (exclusive) in shared memory, then
-// scatters its cones into the bin list; block 0 publishes the offsets.  The
-// counts of the next round are cleared here.
-__global__ void __launch_bounds__(1024) bin_scatter_kernel(int n_tiles, int n, const int *__restrict__ count,
-                                                           int *count_next, int *bin_off, int *bin_list,
-                                                           const int *__restrict__ cone_tile,
-                                                           const int *__restrict__ cone_slot)
-{
-    extern __shared__ int s_off[];     // n_tiles + 1
-    __shared__ int s_part[1024 / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (n_tiles + blockDim.x - 1) / blockDim.x;
-    const int lo = min(tid * per, n_tiles), hi = min(lo + per, n_tiles);
-    int sum = 0;
-    for (int i = lo; i < hi; ++i) sum += count[i];
-    int x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_part[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int v = lane < (int)(blockDim.x / 32) ? s_part[lane] : 0;
-        int y = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int z = __shfl_up_sync(kFull, y, o);
-            if (lane >= o) y += z;
-        }
-        if (lane < (int)(blockDim.x / 32)) s_part[lane] = y - v;
-    }
-    __syncthreads();
-    int run = s_part[warp] + x - sum;
-    for (int i = lo; i < hi; ++i) {
-        s_off[i] = run;
-        run += count[i];
-    }
-    if (tid == blockDim.x - 1) s_off[n_tiles] = run;
-    __syncthreads();
-    if (blockIdx.x == 0)
-        for (int i = tid; i <= n_tiles; i += blockDim.x) bin_off[i] = s_off[i];
-    for (int i = blockIdx.x * blockDim.x + tid; i < n_tiles; i += gridDim.x * blockDim.x) count_next[i] = 0;
-    for (int a = blockIdx.x * blockDim.x + tid; a < n; a += gridDim.x * blockDim.x) {
-        int tile = cone_tile[a];
-        if (tile >= 0) bin_list[s_off[tile] + cone_slot[a]] = a;
+    if (a >= n || !active[a]) return;
+    const int tile = tile_of(f, g, pos[a], pos[n + a]);
+    const int slot = atomicAdd(&count[tile], 1);
+    if (slot < kFusedBinCap) {
+        bins[(size_t)tile * kFusedBinCap + slot] = a;
+    } else {
+        const int k = atomicAdd(spill_cnt, 1);
+        spill[k] = make_int2(a, tile);
     }
 }
 
@@ -730,47 +706,35 @@ static int prepare(Sim &s)
     if (cudaFuncSetAttribute(fused2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return CUE_ERR_CUDA;
-    const int scan_smem = (int)(sizeof(int) * (g.ntx * g.nty + 1));
-    if (scan_smem > 48 * 1024 &&
-        cudaFuncSetAttribute(bin_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, scan_smem) !=
-            cudaSuccess)
-        return CUE_ERR_CUDA;
     s.geom_ready = true;
     return CUE_OK;
 }
 
-// Count every active cone into its tile for the current round (start of a run).
+// Bin every active cone for the current round (start of a run); both rounds'
+// counts and spill counts start at zero.
 static cudaError_t launch_bin_count(Sim &s)
 {
-    int *cur_count = s.bin_count() + (s.bin_round & 1) * s.wl.n_tiles;
     const int n_tiles = s.geom.ntx * s.geom.nty;
-    cudaError_t e = cudaMemsetAsync(cur_count, 0, sizeof(int) * n_tiles, s.stream);
+    const int r = (int)(s.bin_round & 1);
+    cudaError_t e = cudaMemsetAsync(s.bin_count(), 0, sizeof(int) * 2 * s.wl.n_tiles, s.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.bin_ctl(), 0, 256, s.stream);
     if (e != cudaSuccess) return e;
-    bin_count_kernel<<<(s.n_axons + 255) / 256, 256, 0, s.stream>>>(s.fd, s.geom, s.n_axons, s.pos, s.active,
-                                                                     cur_count, s.cone_tile(), s.cone_slot());
+    bin_count_kernel<<<(s.n_axons + 255) / 256, 256, 0, s.stream>>>(
+        s.fd, s.geom, s.n_axons, s.pos, s.active, s.bin_count() + r * s.wl.n_tiles,
+        s.bin_list() + (size_t)r * s.wl.n_tiles * kFusedBinCap, s.spill() + (size_t)r * s.n_axons, s.bin_ctl() + r);
+    (void)n_tiles;
     s.launches++;
     return cudaGetLastError();
 }
 
 // One launch of k <= K fused steps (cones on or off) from s.cur into s.cur^1.
-// With cones: scatter the current round's counts into bins first; the fused
-// kernel counts its cones into the next round as it finishes.
+// With cones: the kernel reads the current round's bins and fills the next's.
 static cudaError_t launch_fused(Sim &s, int k, bool cones)
 {
     const FusedGeom &g = s.geom;
     const int n_tiles = g.ntx * g.nty;
-    int *count = s.bin_count();
-    int *cur_count = count + (s.bin_round & 1) * s.wl.n_tiles;
-    int *next_count = count + ((s.bin_round + 1) & 1) * s.wl.n_tiles;
     const bool with_cones = cones && s.n_axons > 0;
-    if (with_cones) {
-        int blocks = (s.n_axons + 1023) / 1024;
-        size_t sm = sizeof(int) * (n_tiles + 1);
-        bin_scatter_kernel<<<blocks, 1024, sm, s.stream>>>(n_tiles, s.n_axons, cur_count, next_count, s.bin_off(),
-                                                           s.bin_list(), s.cone_tile(), s.cone_slot());
-        s.launches++;
-        s.bin_round++;
-    }
+    const int r = (int)(s.bin_round & 1), rn = r ^ 1;
     FusedArgs A;
     A.f = s.fd;
     A.c = s.cd;
@@ -783,11 +747,15 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     A.pos = s.pos;
     A.dir = s.dir;
     A.active = s.active;
-    A.bin_off = s.bin_off();
-    A.bin_list = s.bin_list();
-    A.next_count = with_cones ? next_count : nullptr;
-    A.cone_tile = s.cone_tile();
-    A.cone_slot = s.cone_slot();
+    A.cnt_cur = s.bin_count() + r * s.wl.n_tiles;
+    A.bins_cur = s.bin_list() + (size_t)r * s.wl.n_tiles * kFusedBinCap;
+    A.spill_cur = s.spill() + (size_t)r * s.n_axons;
+    A.spill_cnt_cur = s.bin_ctl() + r;
+    A.cnt_next = with_cones ? s.bin_count() + rn * s.wl.n_tiles : nullptr;
+    A.bins_next = s.bin_list() + (size_t)rn * s.wl.n_tiles * kFusedBinCap;
+    A.spill_next = s.spill() + (size_t)rn * s.n_axons;
+    A.spill_cnt_next = s.bin_ctl() + rn;
+    A.done = s.bin_ctl() + 2;
     A.src_cell = s.src_cell;
     A.src_emit = s.src_emit;
     A.n_src = s.n_src;
@@ -799,6 +767,7 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     fused2d_kernel<<<n_tiles, kThreads, fused_smem_bytes(g.R), s.stream>>>(*map, A);
     timing_end(s);
     s.launches++;
+    if (with_cones) s.bin_round++;
     return cudaGetLastError();
 }
 
