@@ -347,6 +347,10 @@ def main():
         # the whole run it covers
         per_launch_passes = steps_per_launch if sim_path_used(sim) == "persist" else 1
         alg_bytes = bytes_per_cell * w.n_cells * per_launch_passes
+        if w.dim == 3 and sim_path_used(sim) == "plain":
+            # the 3D step launch also moves the cones: position and direction read and
+            # written, the active flag read (the sampled field nodes are counted in the field)
+            alg_bytes += w.n_axons * (4 * w.dim * 4 + 1)
         avg_s = kern_ms / kern_n / 1e3
         achieved = alg_bytes / avg_s / 1e9
     else:

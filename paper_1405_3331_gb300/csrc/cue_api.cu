@@ -124,10 +124,24 @@ int run_coupled(Sim &s, int nsteps)
     if (rc != 1) return rc;
     rc = run_fused_if_supported(s, nsteps);
     if (rc != 1) return rc;       // handled (0 = ok, < 0 = error)
+    // 3D with the TMA field kernel: cones, field and sources of a step in one launch
+    const bool merged3 = s.fd.dim == 3 && s.vec4 && field3d_tma_prepare(s);
     for (int k = 0; k < nsteps; ++k) {
         float *in = s.field[s.cur], *out = s.field[s.cur ^ 1];
-        cudaError_t e = launch_cone_step(s, in, (uint32_t)s.cone_step);
-        if (e == cudaSuccess) e = launch_field_and_sources(s, in, out);
+        cudaError_t e;
+        if (merged3) {
+            bool cones = false, sources = false;
+            timing_begin(s);
+            e = launch_field3d_tma(s, s.cur, out, &cones, &sources);
+            timing_end(s);
+            s.launches++;
+            // what the launch did not take: the cones read `in`, which no launch of this step writes
+            if (e == cudaSuccess && !cones) e = launch_cone_step(s, in, (uint32_t)s.cone_step);
+            if (e == cudaSuccess && !sources) e = launch_sources(s, out);
+        } else {
+            e = launch_cone_step(s, in, (uint32_t)s.cone_step);
+            if (e == cudaSuccess) e = launch_field_and_sources(s, in, out);
+        }
         if (e != cudaSuccess) return CUE_ERR_CUDA;
         s.cur ^= 1;
         s.field_step++;

@@ -242,6 +242,13 @@ cudaError_t launch_cone_step_io(Sim &s, const float *C, uint32_t step, const flo
                                 float *pout, float *dout);
 // 3D field step through the TMA plane pipeline (k_field3d.cu)
 bool field3d_tma_prepare(Sim &s);
-cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout);
+// cones_done (optional): the field blocks also step the cones on the input
+// buffer (cone step index s.cone_step) when one thread each covers them, and
+// *cones_done says whether they did; sources_done (optional): the field
+// blocks add the point sources when there are at most kTma3BlockSources of
+// them, and *sources_done says whether they did.
+constexpr int kTma3BlockSources = 1024;
+cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout, bool *cones_done = nullptr,
+                               bool *sources_done = nullptr);
 
 }  // namespace cue

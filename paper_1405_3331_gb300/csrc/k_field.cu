@@ -315,7 +315,7 @@ cudaError_t launch_field_step(Sim &s, const float *Cin, float *Cout, bool *sourc
                                                               ns, s.status());
         if (sources_done) *sources_done = ns == s.n_src;
     } else if (s.vec4 && f.dim == 3 && (Cin == s.field[0] || Cin == s.field[1]) && field3d_tma_prepare(s)) {
-        cudaError_t e = launch_field3d_tma(s, Cin == s.field[0] ? 0 : 1, Cout);
+        cudaError_t e = launch_field3d_tma(s, Cin == s.field[0] ? 0 : 1, Cout, nullptr, sources_done);
         timing_end(s);
         s.launches++;
         return e;

@@ -79,10 +79,61 @@ struct Field3Args {
     const float *M;      // dense rate map or null
     int ntx, nty, zchunk;
     unsigned *status;
+    // the same step's cones (they read the input buffer, which no block of this
+    // launch writes): field block b steps cones [b cone_per, (b+1) cone_per),
+    // one per thread; cone_per 0 = none
+    int cone_per;
+    ConeDesc c;
+    uint32_t step;
+    int n;
+    const float *Cin;
+    float *pos, *dir;
+    uint8_t *active;
+    const float *src_xyz;
+    int n_stop;          // sources of the stop test (0: off)
+    unsigned long long *counter;
+    // point sources, added by the field block that owns their node (n_add 0: none)
+    const int32_t *src_cell;
+    const float *src_emit;
+    int n_add;
 };
 
+// Cone a (inr: a is one of this block's cones): the plain cone kernel's step
+// (same functions, same order), with the source coordinates of the stop test
+// read from global memory.  Called by whole warps (the active count is a
+// warp vote).
+__device__ __forceinline__ void cone_one3(const Field3Args &A, int a, bool inr)
+{
+    const FieldDesc &f = A.f;
+    const int n = A.n;
+    const uint8_t act = inr ? A.active[a] : 0;
+    float p[3], d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p[i] = inr ? A.pos[(size_t)i * n + a] : 0.0f;
+        d[i] = inr ? A.dir[(size_t)i * n + a] : 0.0f;
+    }
+    float xi[3];
+    cone_noise<3>(A.c.key0, A.c.key1, (uint32_t)a, A.step, xi);
+    const bool live = inr && act;
+    count_active(A.counter, live);
+    if (!live) return;
+    const size_t sy = f.nx, sz = (size_t)f.nx * f.ny;
+    auto ld = [&](int i, int j, int k) { return __ldg(A.Cin + (size_t)i + sy * j + sz * k); };
+    const bool alive = cone_step_rule<3>(f, A.c, ld, xi, p, d, A.src_xyz, A.n_stop, A.n_stop);
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        A.pos[(size_t)i * n + a] = p[i];
+        A.dir[(size_t)i * n + a] = d[i];
+        bad |= !(fabsf(p[i]) <= 3.402823466e38f) || !(fabsf(d[i]) <= 3.402823466e38f);
+    }
+    if (!alive) A.active[a] = 0;
+    if (bad) flag_status(A.status, kStatusNonFinite);
+}
+
 template <bool MAP>
-__global__ void __launch_bounds__(kThreads3) field3d_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(kThreads3, 4) field3d_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 const Field3Args A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -91,6 +142,7 @@ __global__ void __launch_bounds__(kThreads3) field3d_tma_kernel(const __grid_con
     const FieldDesc &f = A.f;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int b = blockIdx.x;
+    const int fb = b;                            // field block index
     const int tx = b % A.ntx;
     b /= A.ntx;
     const int ty = b % A.nty;
@@ -117,6 +169,12 @@ __global__ void __launch_bounds__(kThreads3) field3d_tma_kernel(const __grid_con
     };
     if (tid == 0)
         for (int p = plo; p <= min(phi, plo + kStages - 2); ++p) issue(p);
+    // this block's cones, while the first planes are on their way
+    if (A.cone_per > 0) {
+        const int first = fb * A.cone_per;
+        const int cnt = min(A.cone_per, A.n - first);
+        if (warp * 32 < cnt) cone_one3(A, first + tid, tid < cnt);
+    }
 
     const int gx = x0 + 4 * lane;
     const bool xin = gx < f.nx;
@@ -181,6 +239,20 @@ __global__ void __launch_bounds__(kThreads3) field3d_tma_kernel(const __grid_con
         __syncthreads();       // every thread is done with plane z-1's stage before it is refilled
     }
     if (__any_sync(kFull, bad) && lane == 0) flag_status(A.status, kStatusNonFinite);
+    // point sources in this block's box, after its stores (the last barrier above)
+    if (A.n_add > 0) {
+        const long long n_cells = (long long)f.nx * f.ny * f.nz;
+        for (int k = tid; k < A.n_add; k += blockDim.x) {
+            const long long c = A.src_cell[k];
+            if (c < 0 || c >= n_cells) {
+                if (fb == 0) flag_status(A.status, kStatusBounds);
+                continue;
+            }
+            const int cx = (int)(c % f.nx), cy = (int)((c / f.nx) % f.ny), cz = (int)(c / ((long long)f.nx * f.ny));
+            if (cx >= x0 && cx < x0 + kTX && cy >= y0 && cy < y0 + kBY && cz >= zs && cz < ze)
+                atomicAdd(A.Cout + c, A.src_emit[k]);
+        }
+    }
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -240,10 +312,25 @@ bool field3d_tma_prepare(Sim &s)
     return true;
 }
 
-cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout)
+cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout, bool *cones_done, bool *sources_done)
 {
-    Field3Args A;
+    Field3Args A{};
     A.f = s.fd;
+    A.c = s.cd;
+    A.step = (uint32_t)s.cone_step;
+    A.n = s.n_axons;
+    A.Cin = s.field[in_buffer];
+    A.pos = s.pos;
+    A.dir = s.dir;
+    A.active = s.active;
+    A.src_xyz = s.src_xyz();
+    A.n_stop = (s.cd.stop_r2 >= 0.0f && s.n_src > 0) ? s.n_src : 0;
+    A.counter = s.cone_counter();
+    A.src_cell = s.src_cell;
+    A.src_emit = s.src_emit;
+    // each field block scans the whole source list, so only short lists are merged
+    A.n_add = (sources_done && s.n_src <= kTma3BlockSources) ? s.n_src : 0;
+    if (sources_done) *sources_done = A.n_add == s.n_src;
     A.Cout = Cout;
     A.M = s.src_map;
     A.ntx = (s.fd.nx + kTX - 1) / kTX;
@@ -257,6 +344,10 @@ cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout)
     A.zchunk = (int)((s.fd.nz + chunks - 1) / chunks);
     chunks = (s.fd.nz + A.zchunk - 1) / A.zchunk;
     const unsigned grid = (unsigned)(cols * chunks);
+    // the cones ride along when one pass of the blocks' threads covers them
+    const long long per = ((long long)s.n_axons + grid - 1) / grid;
+    A.cone_per = (cones_done && s.n_axons > 0 && per <= kThreads3) ? (int)per : 0;
+    if (cones_done) *cones_done = A.cone_per > 0 || s.n_axons == 0;
     const int smem = 128 + kStages * kStageStride * (int)sizeof(float);
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(s.tmap3[in_buffer]);
     if (s.src_map)

@@ -258,3 +258,25 @@ def test_vector_and_tma_field_kernels_equal_the_any_size_kernel(cue, name):
     np.testing.assert_array_equal(a.field().cpu().numpy(), b.field().cpu().numpy())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("name", ["3d-40x36x20", "c3-256"])
+def test_merged_3d_step_equals_separate_launches(cue, name):
+    """With the TMA field kernel a 3D step (cones, field, sources) is one launch (each field
+    block steps a slice of the cones while its first planes load); with a one-float offset
+    it is three.  Same arithmetic in the same order: the whole state
+    agrees bit for bit after several steps (sources sit on distinct nodes)."""
+    w = _case(name)
+    a = cue.Simulation(w, path=cue.CUE_PATH_PLAIN)
+    b = cue.Simulation(w, path=cue.CUE_PATH_PLAIN, field_offset=1)
+    l0a, l0b = a.launches(), b.launches()
+    a.sim_run(4)
+    b.sim_run(4)
+    a.check()
+    b.check()
+    assert a.launches() - l0a == 4
+    assert b.launches() - l0b == 12
+    for x, y in zip(a.snapshot()[:4], b.snapshot()[:4]):
+        np.testing.assert_array_equal(x, y)
+    a.close()
+    b.close()
