@@ -428,15 +428,6 @@ __device__ __forceinline__ double rsqrt_d(double x)
     return y * (1.5 - 0.5 * x * y * y);
 }
 
-__device__ __forceinline__ void atomic_add_dfd(float *hi, float *lo, double c)
-{
-    const float ch = (float)c;
-    const float cl = (float)(c - (double)ch);
-    const float old = atomicAdd(hi, ch);
-    const float r = two_sum(old, ch).lo + cl;
-    if (r != 0.0f) atomicAdd(lo, r);
-}
-
 __device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc &c, const float *__restrict__ C,
                                               uint32_t axon, uint32_t step, const float *p, const float *d,
                                               double *pbar, double *dbar, float *mu)
@@ -544,10 +535,22 @@ __device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc
     const int xs[kPatch2] = {xm, x0, x1, xp, xm, x0, x1, xp, x0, x1, x0, x1};
     const int ys[kPatch2] = {y0, y0, y0, y0, y1, y1, y1, y1, ym, ym, yp, yp};
     float *mu_lo = mu + sy * f.ny;
+    // double-float accumulation of an FP64 coefficient c: add ch = fl(c) to
+    // the high plane, then the rounding error of that add (from the returned
+    // old value) plus c - ch to the low plane; the twelve high-plane adds are
+    // issued before the first returned value is used, so they are in flight
+    // together
+    float ch[kPatch2], old[kPatch2];
 #pragma unroll
     for (int k = 0; k < kPatch2; ++k) {
-        const size_t j = (size_t)xs[k] + sy * ys[k];
-        atomic_add_dfd(mu + j, mu_lo + j, sc[k]);
+        ch[k] = (float)sc[k];
+        old[k] = atomicAdd(mu + (size_t)xs[k] + sy * ys[k], ch[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kPatch2; ++k) {
+        const float cl = (float)(sc[k] - (double)ch[k]);
+        const float r = two_sum(old[k], ch[k]).lo + cl;
+        if (r != 0.0f) atomicAdd(mu_lo + (size_t)xs[k] + sy * ys[k], r);
     }
 }
 
@@ -577,6 +580,7 @@ struct AdjP {
     double *part;                 // per-block (dD, dlambda) slots
     double *de;                   // per-source sums
     int ntx, n_chunks, n_items;
+    int rows;                     // rows per warp of a field tile
 };
 
 __device__ __forceinline__ DF mu_load(const float *Y, const float *X, size_t cells, size_t i)
@@ -584,21 +588,72 @@ __device__ __forceinline__ DF mu_load(const float *Y, const float *X, size_t cel
     return df_add(df_of(__ldcg(Y + i), __ldcg(Y + cells + i)), df_of(__ldcg(X + i), __ldcg(X + cells + i)));
 }
 
-__device__ __forceinline__ void mu_row(const float *Y, const float *X, size_t cells, size_t at4, DF *m)
+// One row of mu = Y + X as it is read (hi and lo planes of Y and X; lanes 0
+// and 31 also the column beyond their end of the row).
+struct AdjRow {
+    float4 yh, yl, xh, xl;
+    float e[4];                  // lane 0: column x - 1, lane 31: column x + 4 (yh, yl, xh, xl)
+};
+
+__device__ __forceinline__ void adj_row_load(const AdjP &A, const float *Yin, const float *Xin, int y, int x4,
+                                             bool xin, bool has_l, bool has_r, AdjRow &R)
 {
-    const float4 yh = __ldcg(reinterpret_cast<const float4 *>(Y) + at4);
-    const float4 yl = __ldcg(reinterpret_cast<const float4 *>(Y + cells) + at4);
-    const float4 xh = __ldcg(reinterpret_cast<const float4 *>(X) + at4);
-    const float4 xl = __ldcg(reinterpret_cast<const float4 *>(X + cells) + at4);
-    m[0] = df_add(df_of(yh.x, yl.x), df_of(xh.x, xl.x));
-    m[1] = df_add(df_of(yh.y, yl.y), df_of(xh.y, xl.y));
-    m[2] = df_add(df_of(yh.z, yl.z), df_of(xh.z, xl.z));
-    m[3] = df_add(df_of(yh.w, yl.w), df_of(xh.w, xl.w));
+    const int lane = threadIdx.x & 31;
+    const size_t cells = A.cells;
+    const int nx4 = A.f.nx >> 2;
+    const size_t at = (size_t)y * nx4 + x4;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    R.yh = xin ? __ldcg(reinterpret_cast<const float4 *>(Yin) + at) : z4;
+    R.yl = xin ? __ldcg(reinterpret_cast<const float4 *>(Yin + cells) + at) : z4;
+    R.xh = xin ? __ldcg(reinterpret_cast<const float4 *>(Xin) + at) : z4;
+    R.xl = xin ? __ldcg(reinterpret_cast<const float4 *>(Xin + cells) + at) : z4;
+    R.e[0] = R.e[1] = R.e[2] = R.e[3] = 0.f;
+    const bool edge = (lane == 0 && has_l) || (lane == 31 && has_r);
+    if (xin && edge) {
+        const size_t i = (size_t)y * A.f.nx + 4 * x4 + (lane == 0 ? -1 : 4);
+        R.e[0] = __ldcg(Yin + i);
+        R.e[1] = __ldcg(Yin + cells + i);
+        R.e[2] = __ldcg(Xin + i);
+        R.e[3] = __ldcg(Xin + cells + i);
+    }
 }
 
-// One field tile (32 lanes x 4 columns, 8 warps x 1 row) of one backward step.
-// Every load (three rows of Y and X, hi and lo; the warp-edge columns; C and
-// the map sum) is issued before the first arithmetic.
+// mu of a loaded row and the neighbours of its first and last node (Y is
+// stored normalised by the tiles, X's planes take atomics and are
+// renormalised).  Every lane of the warp calls it (shuffles).
+__device__ __forceinline__ void adj_row_mu(const AdjRow &R, bool has_l, bool has_r, DF *m, DF &l, DF &r)
+{
+    const int lane = threadIdx.x & 31;
+    m[0] = df_add(DF{R.yh.x, R.yl.x}, df_of(R.xh.x, R.xl.x));
+    m[1] = df_add(DF{R.yh.y, R.yl.y}, df_of(R.xh.y, R.xl.y));
+    m[2] = df_add(DF{R.yh.z, R.yl.z}, df_of(R.xh.z, R.xl.z));
+    m[3] = df_add(DF{R.yh.w, R.yl.w}, df_of(R.xh.w, R.xl.w));
+    l.hi = __shfl_up_sync(kFull, m[3].hi, 1);
+    l.lo = __shfl_up_sync(kFull, m[3].lo, 1);
+    r.hi = __shfl_down_sync(kFull, m[0].hi, 1);
+    r.lo = __shfl_down_sync(kFull, m[0].lo, 1);
+    const DF e = df_add(DF{R.e[0], R.e[1]}, df_of(R.e[2], R.e[3]));
+    if (lane == 0) l = e;
+    if (lane == 31) r = e;
+    if (!has_l) l = m[0];
+    if (!has_r) r = m[3];
+}
+
+// Backward update of one node: Y = beta mu + alpha (sum of the four
+// neighbours), *lap = (sum - 4 mu) rounded to one float (the high part of its
+// double-float sum plus the low part, which is what adding the two parts of a
+// renormalised sum gives).
+__device__ __forceinline__ DF df_update2(DF m, DF l, DF r, DF u, DF d, float alpha, float beta, float *lap)
+{
+    const DF sum = df_add(df_add(l, r), df_add(u, d));
+    const DF s = two_sum(sum.hi, -4.0f * m.hi);
+    *lap = __fadd_rn(s.hi, __fadd_rn(s.lo, __fadd_rn(sum.lo, -4.0f * m.lo)));
+    return df_add(df_mul(m, beta), df_mul(sum, alpha));
+}
+
+// One field tile of one backward step: 128 columns (32 lanes x 4) by 8 warps
+// x `rows` rows; each warp streams its rows down y, so every row's mu is
+// formed once per warp (rows + 2 rows read for `rows` rows written).
 __device__ __forceinline__ void adj_tile(const AdjP &A, const float *Yin, const float *Xin, float *Yout, float *Xz,
                                          const float *Cm, int tile, float &tD, float &tL)
 {
@@ -607,78 +662,56 @@ __device__ __forceinline__ void adj_tile(const AdjP &A, const float *Yin, const 
     const int tx = tile % A.ntx, ty = tile / A.ntx;
     const int nx4 = f.nx >> 2;
     const int x4 = tx * 32 + lane;
-    const int y = ty * 8 + warp;
-    if (y >= f.ny) return;                                 // warp-uniform
+    const int ybeg = (ty * 8 + warp) * A.rows;
+    if (ybeg >= f.ny) return;                              // warp-uniform
+    const int yend = min(ybeg + A.rows, f.ny);
     const bool xin = x4 < nx4;
     const int x = x4 * 4;
     const bool has_l = x > 0, has_r = x + 4 < f.nx;
     const size_t cells = A.cells;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 *yh4 = reinterpret_cast<const float4 *>(Yin), *yl4 = reinterpret_cast<const float4 *>(Yin + cells);
-    const float4 *xh4 = reinterpret_cast<const float4 *>(Xin), *xl4 = reinterpret_cast<const float4 *>(Xin + cells);
-    float4 YH[3], YL[3], XH[3], XL[3];
+    AdjRow ru, rc, rd;                                     // rows y - 1, y, y + 1 (walls repeat y)
+    adj_row_load(A, Yin, Xin, ybeg > 0 ? ybeg - 1 : ybeg, x4, xin, has_l, has_r, ru);
+    adj_row_load(A, Yin, Xin, ybeg, x4, xin, has_l, has_r, rc);
+    adj_row_load(A, Yin, Xin, ybeg + 1 < f.ny ? ybeg + 1 : ybeg, x4, xin, has_l, has_r, rd);
+    DF up[4], cu[4], dn[4], l, r, tl, tr;
+    adj_row_mu(ru, has_l, has_r, up, tl, tr);
+    adj_row_mu(rc, has_l, has_r, cu, l, r);
+    for (int y = ybeg; y < yend; ++y) {
+        // the row below the next one is on its way while this one is computed
+        const int yn = y + 2 < f.ny ? y + 2 : f.ny - 1;
+        AdjRow rn;
+        if (y + 1 < yend) adj_row_load(A, Yin, Xin, yn, x4, xin, has_l, has_r, rn);
+        adj_row_mu(rd, has_l, has_r, dn, tl, tr);
+        const size_t at = (size_t)y * nx4 + x4;
+        if (xin) {
+            const float4 c = __ldg(reinterpret_cast<const float4 *>(Cm) + at);
+            float4 *s4 = A.Sseg ? reinterpret_cast<float4 *>(A.Sseg) + at : nullptr;
+            const float4 sv0 = s4 ? *s4 : z4;
+            float L0, L1, L2, L3;
+            const DF o0 = df_update2(cu[0], l, cu[1], up[0], dn[0], f.alpha, f.beta, &L0);
+            const DF o1 = df_update2(cu[1], cu[0], cu[2], up[1], dn[1], f.alpha, f.beta, &L1);
+            const DF o2 = df_update2(cu[2], cu[1], cu[3], up[2], dn[2], f.alpha, f.beta, &L2);
+            const DF o3 = df_update2(cu[3], cu[2], r, up[3], dn[3], f.alpha, f.beta, &L3);
+            const float v0 = cu[0].hi + cu[0].lo, v1 = cu[1].hi + cu[1].lo, v2 = cu[2].hi + cu[2].lo,
+                        v3 = cu[3].hi + cu[3].lo;
+            tD = fmaf(L0, c.x, fmaf(L1, c.y, fmaf(L2, c.z, fmaf(L3, c.w, tD))));
+            tL = fmaf(v0, c.x, fmaf(v1, c.y, fmaf(v2, c.z, fmaf(v3, c.w, tL))));
+            if (s4) *s4 = make_float4(sv0.x + v0, sv0.y + v1, sv0.z + v2, sv0.w + v3);
+            reinterpret_cast<float4 *>(Yout)[at] = make_float4(o0.hi, o1.hi, o2.hi, o3.hi);
+            reinterpret_cast<float4 *>(Yout + cells)[at] = make_float4(o0.lo, o1.lo, o2.lo, o3.lo);
+            reinterpret_cast<float4 *>(Xz)[at] = z4;
+            reinterpret_cast<float4 *>(Xz + cells)[at] = z4;
+        }
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {                          // rows y - 1, y, y + 1 (the walls repeat y)
-        const int yy = r == 0 ? (y > 0 ? y - 1 : y) : (r == 2 ? (y + 1 < f.ny ? y + 1 : y) : y);
-        const size_t at = (size_t)yy * nx4 + x4;
-        YH[r] = xin ? __ldcg(yh4 + at) : z4;
-        YL[r] = xin ? __ldcg(yl4 + at) : z4;
-        XH[r] = xin ? __ldcg(xh4 + at) : z4;
-        XL[r] = xin ? __ldcg(xl4 + at) : z4;
+        for (int i = 0; i < 4; ++i) {
+            up[i] = cu[i];
+            cu[i] = dn[i];
+        }
+        l = tl;
+        r = tr;
+        if (y + 1 < yend) rd = rn;
     }
-    float el[4] = {0.f, 0.f, 0.f, 0.f}, er[4] = {0.f, 0.f, 0.f, 0.f};
-    if (lane == 0 && xin && has_l) {
-        const size_t i = (size_t)y * f.nx + x - 1;
-        el[0] = __ldcg(Yin + i);
-        el[1] = __ldcg(Yin + cells + i);
-        el[2] = __ldcg(Xin + i);
-        el[3] = __ldcg(Xin + cells + i);
-    }
-    if (lane == 31 && xin && has_r) {
-        const size_t i = (size_t)y * f.nx + x + 4;
-        er[0] = __ldcg(Yin + i);
-        er[1] = __ldcg(Yin + cells + i);
-        er[2] = __ldcg(Xin + i);
-        er[3] = __ldcg(Xin + cells + i);
-    }
-    const size_t at = (size_t)y * nx4 + x4;
-    const float4 c = xin ? __ldg(reinterpret_cast<const float4 *>(Cm) + at) : z4;
-    float4 *s4 = A.Sseg ? reinterpret_cast<float4 *>(A.Sseg) + at : nullptr;
-    const float4 sv0 = (s4 && xin) ? *s4 : z4;
-    auto mu4 = [&](int r, DF *m) {
-        m[0] = df_add(df_of(YH[r].x, YL[r].x), df_of(XH[r].x, XL[r].x));
-        m[1] = df_add(df_of(YH[r].y, YL[r].y), df_of(XH[r].y, XL[r].y));
-        m[2] = df_add(df_of(YH[r].z, YL[r].z), df_of(XH[r].z, XL[r].z));
-        m[3] = df_add(df_of(YH[r].w, YL[r].w), df_of(XH[r].w, XL[r].w));
-    };
-    DF up[4], cu[4], dn[4];
-    mu4(0, up);
-    mu4(1, cu);
-    mu4(2, dn);
-    DF l, r;
-    l.hi = __shfl_up_sync(kFull, cu[3].hi, 1);
-    l.lo = __shfl_up_sync(kFull, cu[3].lo, 1);
-    r.hi = __shfl_down_sync(kFull, cu[0].hi, 1);
-    r.lo = __shfl_down_sync(kFull, cu[0].lo, 1);
-    if (lane == 0) l = has_l ? df_add(df_of(el[0], el[1]), df_of(el[2], el[3])) : cu[0];
-    if (lane == 31) r = has_r ? df_add(df_of(er[0], er[1]), df_of(er[2], er[3])) : cu[3];
-    if (!has_l) l = cu[0];
-    if (!has_r) r = cu[3];
-    if (!xin) return;
-    float L0, L1, L2, L3;
-    const DF o0 = df_update(cu[0], l, cu[1], up[0], dn[0], f.alpha, f.beta, &L0);
-    const DF o1 = df_update(cu[1], cu[0], cu[2], up[1], dn[1], f.alpha, f.beta, &L1);
-    const DF o2 = df_update(cu[2], cu[1], cu[3], up[2], dn[2], f.alpha, f.beta, &L2);
-    const DF o3 = df_update(cu[3], cu[2], r, up[3], dn[3], f.alpha, f.beta, &L3);
-    const float v0 = cu[0].hi + cu[0].lo, v1 = cu[1].hi + cu[1].lo, v2 = cu[2].hi + cu[2].lo,
-                v3 = cu[3].hi + cu[3].lo;
-    tD = fmaf(L0, c.x, fmaf(L1, c.y, fmaf(L2, c.z, fmaf(L3, c.w, tD))));
-    tL = fmaf(v0, c.x, fmaf(v1, c.y, fmaf(v2, c.z, fmaf(v3, c.w, tL))));
-    if (s4) *s4 = make_float4(sv0.x + v0, sv0.y + v1, sv0.z + v2, sv0.w + v3);
-    reinterpret_cast<float4 *>(Yout)[at] = make_float4(o0.hi, o1.hi, o2.hi, o3.hi);
-    reinterpret_cast<float4 *>(Yout + cells)[at] = make_float4(o0.lo, o1.lo, o2.lo, o3.lo);
-    reinterpret_cast<float4 *>(Xz)[at] = z4;
-    reinterpret_cast<float4 *>(Xz + cells)[at] = z4;
 }
 
 __global__ void __launch_bounds__(256, 2) adj_persist_kernel(AdjP A, int len, uint32_t g0, PBar *bar,
@@ -702,12 +735,18 @@ __global__ void __launch_bounds__(256, 2) adj_persist_kernel(AdjP A, int len, ui
                 }
             }
         float tD = 0.f, tL = 0.f;
-        for (int it = blockIdx.x; it < A.n_items; it += gridDim.x) {
-            if (it < A.n_chunks) {
+        // items: the field tiles, then the cone chunks, dealt in rounds of gridDim.x
+        // in snake order (odd rounds backwards), so the blocks that take a cone
+        // chunk in the last rounds are the ones with fewer tiles
+        for (int k = 0;; ++k) {
+            const int it = k * gridDim.x + ((k & 1) ? gridDim.x - 1 - blockIdx.x : blockIdx.x);
+            if (it >= A.n_items) break;
+            const int chunk = it - (A.n_items - A.n_chunks);
+            if (chunk >= 0) {
                 // 32 cones per item, one warp: the FP64 work of the cones spreads over
                 // many SMs (GB300's FP64 rate per SM is low); the other warps move on
-                if ((threadIdx.x >> 5) != (it & 7)) continue;
-                const int a = it * 32 + (threadIdx.x & 31);
+                if ((threadIdx.x >> 5) != (chunk & 7)) continue;
+                const int a = chunk * 32 + (threadIdx.x & 31);
                 if (a < A.n && A.active[a]) {
                     float p[2], d[2];
                     double pb[2], db[2];
@@ -724,7 +763,7 @@ __global__ void __launch_bounds__(256, 2) adj_persist_kernel(AdjP A, int len, ui
                     }
                 }
             } else {
-                adj_tile(A, Yin, Xin, Yout, Xz, Cm, it - A.n_chunks, tD, tL);
+                adj_tile(A, Yin, Xin, Yout, Xz, Cm, it, tD, tL);
             }
         }
         block_add2<true>(tD, tL, A.part);
@@ -1033,8 +1072,12 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
         A.de = acc + 2;
         A.ntx = (f.nx / 4 + 31) / 32;
         A.n_chunks = blocks_for((size_t)n, 32);
-        A.n_items = A.n_chunks + A.ntx * blocks_for((size_t)f.ny, 8);
-        bw_grid = std::max(1, std::min(A.n_items, std::min(2, adj_persist_blocks_per_sm()) * sm_count_adj()));
+        const int blocks = std::min(2, adj_persist_blocks_per_sm()) * sm_count_adj();
+        // rows per warp: the longest streams that still give every block a tile
+        A.rows = 4;
+        while (A.rows > 1 && (long long)A.ntx * blocks_for((size_t)f.ny, 8 * A.rows) < blocks) A.rows /= 2;
+        A.n_items = A.n_chunks + A.ntx * blocks_for((size_t)f.ny, 8 * A.rows);
+        bw_grid = std::max(1, std::min(A.n_items, blocks));
     }
     int in = 0;
     for (int j = L.nseg - 1; j >= 0; --j) {
