@@ -9,7 +9,7 @@
 // kernel launches, which is what a grid that fits in L2 (a few MB) is bound
 // by.  The same kernel steps a batch of independent instances of uneven sizes
 // and parameters: the per-instance table holds each one's physics, buffers
-// and tiling, and the work list interleaves their items.
+// and tiling, and the work list holds their items instance by instance.
 //
 // Arithmetic per node and per cone is the plain path's (node_update2, the map
 // as fma(dt, M, C'), sources added after the update; cone_update), so this
@@ -415,6 +415,17 @@ void persist_items(const std::vector<PInst> &insts, std::vector<PItem> &items)
         maxc = std::max(maxc, nchunk[i]);
         maxt = std::max(maxt, ntile[i]);
     }
+    if (ni > 1) {
+        // batches: instance by instance, each instance's cone chunks right after its
+        // tiles, so that the cones' field reads and the tiles' shared halo rows find
+        // the instance's field still in L2
+        for (int i = 0; i < ni; ++i) {
+            for (int k = 0; k < ntile[i]; ++k) items.push_back(PItem{i, k, 0, 0});
+            for (int k = 0; k < nchunk[i]; ++k) items.push_back(PItem{i, ~k, 0, 0});
+        }
+        return;
+    }
+    // one grid: the cone chunks first (their dependent loads overlap the tiles)
     for (int k = 0; k < maxc; ++k)
         for (int i = 0; i < ni; ++i)
             if (k < nchunk[i]) items.push_back(PItem{i, ~k, 0, 0});
