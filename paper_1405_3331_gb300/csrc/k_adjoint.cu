@@ -579,8 +579,8 @@ struct AdjP {
     float *Sseg;                  // nullable
     double *part;                 // per-block (dD, dlambda) slots
     double *de;                   // per-source sums
-    int ntx, n_chunks, n_items;
-    int rows;                     // rows per warp of a field tile
+    int ntx, n_chunks;
+    int n_cone_warps, n_row_warps;
 };
 
 __device__ __forceinline__ DF mu_load(const float *Y, const float *X, size_t cells, size_t i)
@@ -651,20 +651,17 @@ __device__ __forceinline__ DF df_update2(DF m, DF l, DF r, DF u, DF d, float alp
     return df_add(df_mul(m, beta), df_mul(sum, alpha));
 }
 
-// One field tile of one backward step: 128 columns (32 lanes x 4) by 8 warps
-// x `rows` rows; each warp streams its rows down y, so every row's mu is
-// formed once per warp (rows + 2 rows read for `rows` rows written).
-__device__ __forceinline__ void adj_tile(const AdjP &A, const float *Yin, const float *Xin, float *Yout, float *Xz,
-                                         const float *Cm, int tile, float &tD, float &tL)
+// Rows ybeg .. yend - 1 of column strip tx (128 columns: 32 lanes x 4) of one
+// backward step, by one warp streaming down y, so every row's mu is formed
+// once (yend - ybeg + 2 rows read for yend - ybeg rows written).
+__device__ __forceinline__ void adj_rows(const AdjP &A, const float *Yin, const float *Xin, float *Yout, float *Xz,
+                                         const float *Cm, int tx, int ybeg, int yend, float &tD, float &tL)
 {
     const FieldDesc &f = A.f;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tx = tile % A.ntx, ty = tile / A.ntx;
+    const int lane = threadIdx.x & 31;
     const int nx4 = f.nx >> 2;
     const int x4 = tx * 32 + lane;
-    const int ybeg = (ty * 8 + warp) * A.rows;
-    if (ybeg >= f.ny) return;                              // warp-uniform
-    const int yend = min(ybeg + A.rows, f.ny);
+    if (ybeg >= yend) return;                              // warp-uniform
     const bool xin = x4 < nx4;
     const int x = x4 * 4;
     const bool has_l = x > 0, has_r = x + 4 < f.nx;
@@ -735,35 +732,41 @@ __global__ void __launch_bounds__(256, 2) adj_persist_kernel(AdjP A, int len, ui
                 }
             }
         float tD = 0.f, tL = 0.f;
-        // items: the field tiles, then the cone chunks, dealt in rounds of gridDim.x
-        // in snake order (odd rounds backwards), so the blocks that take a cone
-        // chunk in the last rounds are the ones with fewer tiles
-        for (int k = 0;; ++k) {
-            const int it = k * gridDim.x + ((k & 1) ? gridDim.x - 1 - blockIdx.x : blockIdx.x);
-            if (it >= A.n_items) break;
-            const int chunk = it - (A.n_items - A.n_chunks);
-            if (chunk >= 0) {
-                // 32 cones per item, one warp: the FP64 work of the cones spreads over
-                // many SMs (GB300's FP64 rate per SM is low); the other warps move on
-                if ((threadIdx.x >> 5) != (chunk & 7)) continue;
-                const int a = chunk * 32 + (threadIdx.x & 31);
-                if (a < A.n && A.active[a]) {
-                    float p[2], d[2];
-                    double pb[2], db[2];
-                    for (int i = 0; i < 2; ++i) {
-                        p[i] = __ldg(Pm + (size_t)i * A.n + a);
-                        d[i] = __ldg(Pm + A.cone_n + (size_t)i * A.n + a);
-                        pb[i] = __ldcg(A.pbar + (size_t)i * A.n + a);
-                        db[i] = __ldcg(A.dbar + (size_t)i * A.n + a);
-                    }
-                    cone_adjoint2(A.f, A.c, Cm, (uint32_t)a, g, p, d, pb, db, Xout);
-                    for (int i = 0; i < 2; ++i) {
-                        A.pbar[(size_t)i * A.n + a] = pb[i];
-                        A.dbar[(size_t)i * A.n + a] = db[i];
-                    }
+        // Work per warp.  Cone warps (warp 7 of the first n_cone_warps blocks, one
+        // per block so that the FP64 work spreads over many SMs: GB300's FP64 rate
+        // per SM is low) take the 32-cone chunks; every other warp takes an equal
+        // contiguous share of the field rows, strip by strip, so every SM gets the
+        // same amount of field work.
+        const int warp = threadIdx.x >> 5;
+        const int bid = blockIdx.x;
+        const bool cone_warp = warp == 7 && bid < A.n_cone_warps;
+        for (int chunk = bid; cone_warp && chunk < A.n_chunks; chunk += A.n_cone_warps) {
+            const int a = chunk * 32 + (threadIdx.x & 31);
+            if (a < A.n && A.active[a]) {
+                float p[2], d[2];
+                double pb[2], db[2];
+                for (int i = 0; i < 2; ++i) {
+                    p[i] = __ldg(Pm + (size_t)i * A.n + a);
+                    d[i] = __ldg(Pm + A.cone_n + (size_t)i * A.n + a);
+                    pb[i] = __ldcg(A.pbar + (size_t)i * A.n + a);
+                    db[i] = __ldcg(A.dbar + (size_t)i * A.n + a);
                 }
-            } else {
-                adj_tile(A, Yin, Xin, Yout, Xz, Cm, it, tD, tL);
+                cone_adjoint2(A.f, A.c, Cm, (uint32_t)a, g, p, d, pb, db, Xout);
+                for (int i = 0; i < 2; ++i) {
+                    A.pbar[(size_t)i * A.n + a] = pb[i];
+                    A.dbar[(size_t)i * A.n + a] = db[i];
+                }
+            }
+        }
+        if (!cone_warp) {
+            const long long total = (long long)A.ntx * A.f.ny;                  // (strip, row) pairs
+            const int rw = bid * 8 - min(bid, A.n_cone_warps) + warp;           // index among the row warps
+            const long long r0 = total * rw / A.n_row_warps, r1 = total * (rw + 1) / A.n_row_warps;
+            for (long long r = r0; r < r1;) {
+                const int tx = (int)(r / A.f.ny), y = (int)(r % A.f.ny);
+                const int n = (int)min(r1 - r, (long long)(A.f.ny - y));
+                adj_rows(A, Yin, Xin, Yout, Xz, Cm, tx, y, y + n, tD, tL);
+                r += n;
             }
         }
         block_add2<true>(tD, tL, A.part);
@@ -1072,12 +1075,9 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
         A.de = acc + 2;
         A.ntx = (f.nx / 4 + 31) / 32;
         A.n_chunks = blocks_for((size_t)n, 32);
-        const int blocks = std::min(2, adj_persist_blocks_per_sm()) * sm_count_adj();
-        // rows per warp: the longest streams that still give every block a tile
-        A.rows = 4;
-        while (A.rows > 1 && (long long)A.ntx * blocks_for((size_t)f.ny, 8 * A.rows) < blocks) A.rows /= 2;
-        A.n_items = A.n_chunks + A.ntx * blocks_for((size_t)f.ny, 8 * A.rows);
-        bw_grid = std::max(1, std::min(A.n_items, blocks));
+        bw_grid = std::max(1, std::min(2, adj_persist_blocks_per_sm()) * sm_count_adj());
+        A.n_cone_warps = std::min(A.n_chunks, bw_grid);
+        A.n_row_warps = bw_grid * 8 - A.n_cone_warps;
     }
     int in = 0;
     for (int j = L.nseg - 1; j >= 0; --j) {
