@@ -48,6 +48,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--run-steps", type=int, default=0,
                     help="time steps per benchmark step (0 = the workload's own count); for profiling")
+    # internal: time the oracle with its field rows over threads, in a process of its own
+    # (no CUDA context, no second OpenMP runtime next to PyTorch's): WORKLOAD:NSTEPS:THREADS
+    ap.add_argument("--oracle-threads-sample", default="", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -194,6 +197,43 @@ def oracle_sample(w, budget_s):
     return nsteps, dt
 
 
+def oracle_threads_child(spec):
+    """Child process: the oracle on the first NSTEPS steps of WORKLOAD with the field's node
+    loop over THREADS threads; prints {"seconds", "threads", "nsteps"}."""
+    name, nsteps, threads = spec.split(":")
+    if name.startswith("c4"):
+        from paper_1405_3331_gb300 import workloads as W
+        w = W.config_c4(seed=3)[0]
+    else:
+        w = workload(name)
+    import numpy as np
+    import oracle
+    used = oracle.set_threads(int(threads))
+    g = oracle.Grid(w.dim, w.nx, w.ny, w.nz if w.dim == 3 else 1, h=w.h, D=w.D, lam=w.lam, dt=w.dt)
+    c = oracle.Cone(w.w_prev, w.w_grad, w.w_noise, w.step_len, w.stop_radius, w.grad_eps, w.wall_mode,
+                    w.seed)
+    C = w.field0().astype(np.float64)
+    oracle.run(g, c, C, 0, 1, w.src_cell, w.src_emit, w.src_map, w.pos, w.dir, w.active)
+    t0 = time.perf_counter()
+    oracle.run(g, c, C, 0, int(nsteps), w.src_cell, w.src_emit, w.src_map, w.pos, w.dir, w.active)
+    print(json.dumps({"seconds": time.perf_counter() - t0, "threads": used, "nsteps": int(nsteps)}), flush=True)
+    return 0
+
+
+def oracle_threads_sample(name, n_cells, nsteps, sample):
+    """The same bounded sample as the single-threaded baseline, the field's node loop over
+    every host core (rows are independent; the cone loop stays serial)."""
+    threads = os.cpu_count() or 1
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-threads-sample",
+                              f"{name}:{nsteps}:{threads}"], capture_output=True, text=True, timeout=300)
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:                      # the baseline is context, not a result
+        return {"unavailable": f"{type(e).__name__}"}
+    return {"value": n_cells * d["nsteps"] / d["seconds"], "unit": UNIT, "cores": d["threads"],
+            "kind": "oracle, field rows over OpenMP threads", "sample": sample, "seconds": d["seconds"]}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -251,6 +291,8 @@ def aggregate(local_ms, units_per_step, steps, world, dist=None, device=None):
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse_args()
+    if args.oracle_threads_sample:
+        return oracle_threads_child(args.oracle_threads_sample)
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np
@@ -405,13 +447,16 @@ def main():
     # HBM probe: plain field kernel on 2D 8192^2 (256 MiB per buffer), never L2-resident
     if not args.no_probe and rank == 0:
         line["hbm_probe"] = hbm_probe(cue, torch, dev, hbm)
+        if w.dim == 3:
+            line["hbm_probe_3d"] = hbm_probe(cue, torch, dev, hbm, dim=3)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nsteps, secs = oracle_sample(w, args.cpu_seconds)
+        sample = f"first {nsteps} of {w.nsteps} time steps of the same workload (FP64)"
         line["cpu_baseline"] = {
             "value": w.n_cells * nsteps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {nsteps} of {w.nsteps} time steps of the same workload (FP64, one thread)",
-            "seconds": secs}
+            "sample": sample + ", one thread", "seconds": secs}
+        line["cpu_baseline_threads"] = oracle_threads_sample(args.workload, w.n_cells, nsteps, sample)
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -489,24 +534,35 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
                      "algorithmic_bytes_per_launch": 8.0 * cells * T},
         "clocks": clocks, "gpu_launches": 2 * args.steps,      # the persistent kernel + the step advance
     }
-    # the one-instance-per-launch plain solver on the first 32 instances (100 steps each)
+    # the one-instance-per-launch plain solver on the first 32 instances (100 steps each), and
+    # the same instances one after another through sim_run on the library's own path choice
     sub = ws[:32]
-    sims = [cue.Simulation(w, device=dev, path=cue.CUE_PATH_PLAIN) for w in sub]
-    for sm in sims:
-        sm.sim_run(2)
-    torch.cuda.synchronize()
-    Tb = 100
-    t0 = time.perf_counter()
-    for sm in sims:
-        sm.sim_run(Tb)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
     sub_cells = sum(w.n_cells for w in sub)
-    plain_rate = sub_cells * Tb / dt
-    for sm in sims:
-        sm.close()
+    Tb = 100
+
+    def sequential_rate(path):
+        sims = [cue.Simulation(w, device=dev, path=path) for w in sub]
+        for sm in sims:
+            sm.sim_run(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for sm in sims:
+            sm.sim_run(Tb)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        for sm in sims:
+            sm.check()
+            sm.close()
+        return sub_cells * Tb / dt
+
+    plain_rate = sequential_rate(cue.CUE_PATH_PLAIN)
+    auto_rate = sequential_rate(cue.CUE_PATH_AUTO)
+    line["baseline_sequential_sim_run"] = {
+        "value": auto_rate, "unit": UNIT, "speedup": value / world / auto_rate,
+        "sample": "first 32 instances x 100 steps, one sim_run per instance in turn (persistent or fused "
+                  "path as the library picks)"}
     line["baseline_plain_per_instance"] = {
-        "value": plain_rate, "unit": UNIT, "speedup": value / plain_rate,
+        "value": plain_rate, "unit": UNIT, "speedup": value / world / plain_rate,
         "sample": f"first 32 instances x {Tb} steps, each instance its own cone and field launches per step"}
     if not args.no_e2e:
         # end to end: every instance's state from pinned host memory, the run, the fields back
@@ -535,10 +591,11 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
                        "d2h_bytes_per_step": sum(o.numel() * o.element_size() for o in outs), "ms_per_step": ms}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nsteps, secs = oracle_sample(ws[0], args.cpu_seconds)
+        sample = f"instance 0 ({ws[0].nx}x{ws[0].ny}), first {nsteps} of {T} steps (FP64)"
         line["cpu_baseline"] = {
             "value": ws[0].n_cells * nsteps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"instance 0 ({ws[0].nx}x{ws[0].ny}), first {nsteps} of {T} steps (FP64, one thread)",
-            "seconds": secs}
+            "sample": sample + ", one thread", "seconds": secs}
+        line["cpu_baseline_threads"] = oracle_threads_sample("c4", ws[0].n_cells, nsteps, sample)
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -600,9 +657,11 @@ def sim_path_used(sim):
     return {cue.CUE_PATH_FUSED: "fused", cue.CUE_PATH_PERSIST: "persist"}.get(sim.last_path(), "plain")
 
 
-def hbm_probe(cue, torch, dev, hbm):
+def hbm_probe(cue, torch, dev, hbm, dim=2):
+    """The unblocked field step (field + sources, no cones) on a grid that cannot stay in L2:
+    2D 8192^2 (plain float4 kernel) or 3D 512^3 (the TMA step kernel)."""
     from paper_1405_3331_gb300 import workloads as W
-    w = W.hbm_probe_2d()
+    w = W.hbm_probe_2d() if dim == 2 else W.hbm_probe_3d()
     sim = cue.Simulation(w, device=dev, path=cue.CUE_PATH_PLAIN)
     sim.cue_step(5)
     sim.set_option(cue.CUE_OPT_TIME_KERNEL, 1)
@@ -613,7 +672,9 @@ def hbm_probe(cue, torch, dev, hbm):
     sim.check()
     sim.close()
     gbs = 8 * w.n_cells * k / (ms / 1e3) / 1e9
-    return {"workload": "2D 8192x8192 field only (256 MiB per buffer), plain field kernel",
+    what = ("2D 8192x8192 field only (256 MiB per buffer), plain field kernel" if dim == 2 else
+            "3D 512x512x512 field only (512 MiB per buffer), TMA step kernel")
+    return {"workload": what,
             "cell_updates_per_s": w.n_cells * k / (ms / 1e3), "achieved_gbs": gbs, "peak_gbs": hbm,
             "frac": gbs / hbm, "launches": k, "avg_launch_us": ms / k * 1e3}
 

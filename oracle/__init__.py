@@ -7,6 +7,7 @@ from .oracle import (  # noqa: F401
     Grid,
     Cone,
     build,
+    set_threads,
     philox4x32_10,
     noise,
     node_gradient,

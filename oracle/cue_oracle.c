@@ -181,6 +181,22 @@ void orc_philox_many(int n, const uint32_t *ctr /* [n][4] */, const uint32_t *ke
  * nothing; decay removes lambda dt C_i.  Then the point sources add their
  * per-step emission, then a dense rate map adds dt M_i.
  * ---------------------------------------------------------------------- */
+/* Threads of the node loop below (rows are independent, so any count gives
+ * the same result bit for bit); 1 unless the timed baseline asks for more,
+ * and only where the library was built with OpenMP. */
+static int orc_nthreads = 1;
+
+void orc_set_threads(int n) { orc_nthreads = n > 0 ? n : 1; }
+
+int orc_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 void orc_field_step(const orc_grid *g, const double *C, double *Cn,
                     const int32_t *src_cell, const double *src_emit, int n_src,
                     const double *src_map)
@@ -189,6 +205,9 @@ void orc_field_step(const orc_grid *g, const double *C, double *Cn,
     const double decay = g->lambda * g->dt;
     const int nx = g->nx, ny = g->ny, nz = (g->dim == 3) ? g->nz : 1;
     const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(static) num_threads(orc_nthreads) if (orc_nthreads > 1)
+#endif
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {

@@ -99,7 +99,10 @@ def build(force: bool = False) -> str:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        # OpenMP only splits the field's node loop across threads when asked to
+        # (set_threads); without it the pragma is ignored and the library is the same
+        if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -128,6 +131,8 @@ def _load():
             lib.orc_csr.argtypes = [ct.c_int, ct.c_int, P, P, P, P]
             lib.orc_csr.restype = ct.c_int
             lib.orc_bfs.argtypes = [ct.c_int, P, P, ct.c_int, P]
+            lib.orc_set_threads.argtypes = [ct.c_int]
+            lib.orc_openmp.restype = ct.c_int
             lib.orc_value_at.argtypes = [ct.POINTER(_Grid), P, P]
             lib.orc_value_at.restype = ct.c_double
             lib.orc_snr.argtypes = [ct.POINTER(_Cone), ct.c_double, P, P]
@@ -215,6 +220,15 @@ def gradient_at(grid: Grid, C, p):
     g = grid._c()
     _load().orc_gradient_many(ct.byref(g), _ptr(C), p.shape[0], _ptr(pp), _ptr(out))
     return out
+
+
+def set_threads(n: int) -> int:
+    """Threads for the field's node loop (rows are independent: results do not depend on
+    the count); returns the count in effect (1 where the library has no OpenMP)."""
+    lib = _load()
+    n = max(1, int(n)) if lib.orc_openmp() else 1
+    lib.orc_set_threads(n)
+    return n
 
 
 def field_step(grid: Grid, C, src_cell=(), src_emit=(), src_map=None):

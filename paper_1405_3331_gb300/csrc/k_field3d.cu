@@ -336,9 +336,10 @@ cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout, bool *cones_d
     A.ntx = (s.fd.nx + kTX - 1) / kTX;
     A.nty = (s.fd.ny + kBY - 1) / kBY;
     A.status = s.status();
-    // enough CTAs for about four per SM; each marches a chunk of z planes
+    // at most one wave (four CTAs per SM resident): a CTA left for a second wave would
+    // stream its whole chunk after the others; each CTA marches a chunk of z planes
     const long long cols = (long long)A.ntx * A.nty;
-    long long chunks = (4LL * sm_count3() + cols - 1) / cols;
+    long long chunks = 4LL * sm_count3() / cols;
     if (chunks < 1) chunks = 1;
     if (chunks > s.fd.nz) chunks = s.fd.nz;
     A.zchunk = (int)((s.fd.nz + chunks - 1) / chunks);

@@ -268,3 +268,25 @@ def test_laplacian_self_adjoint_and_kills_constants(shape):
     assert np.abs(_apply_L(shape, np.full(shape, 3.7))).max() < 1e-15
     # negative semi-definite: <x, L x> <= 0 (diffusion never creates variance)
     assert (x * _apply_L(shape, x)).sum() < 0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_threaded_field_step_is_the_single_threaded_one(dim):
+    """The timed CPU baseline may split the field's node loop over threads; every node's
+    update reads only the old field, so the result must not change by a single bit."""
+    rng = np.random.default_rng(11 + dim)
+    if dim == 2:
+        g = oracle.Grid(2, 97, 61, h=1.0, D=1.0, lam=0.01, dt=0.2)
+    else:
+        g = oracle.Grid(3, 23, 17, 13, h=1.0, D=1.0, lam=0.01, dt=0.15)
+    C = rng.uniform(0.0, 1.0, g.shape)
+    cells = rng.choice(C.size, 5, replace=False)
+    emit = rng.uniform(0.5, 2.0, 5)
+    smap = rng.uniform(0.0, 1.0, g.shape)
+    try:
+        oracle.set_threads(4)
+        a = oracle.field_step(g, C, cells, emit, smap)
+    finally:
+        oracle.set_threads(1)
+    b = oracle.field_step(g, C, cells, emit, smap)
+    np.testing.assert_array_equal(a, b)
