@@ -6,7 +6,11 @@
 // two planes ahead of the one being computed; every thread computes four
 // nodes per plane from shared memory (x neighbours by warp shuffle) and
 // writes them with one 16-byte store.  HBM traffic: one read and one write
-// per node (8 B per node update) plus the halo overlap.
+// per node (8 B per node update) plus the halo overlap.  A ninth warp per CTA
+// steps the CTA's share of the growth cones on the input field meanwhile (its
+// gathers are dependent global loads; the eight field warps synchronise among
+// themselves on a named barrier and never wait for it), and after the last
+// plane the field warps add the point sources of the CTA's box.
 //
 // Update (Sec. 5.2, Sec. 4.3): C' = beta C + alpha * (sum of the six axis
 // neighbours) [+ dt M], a neighbour missing at a wall replaced by the node
@@ -25,7 +29,8 @@ constexpr int kBoxX = kTX + 2 * kHX;  // 136 floats = 544 bytes per row
 constexpr int kBY = 16;               // interior rows per tile
 constexpr int kBoxY = kBY + 2;
 constexpr int kStages = 4;
-constexpr int kThreads3 = 256;        // 8 warps x 2 rows
+constexpr int kThreads3 = 256;        // field warps: 8 warps x 2 rows
+constexpr int kLaunch3 = kThreads3 + 32;  // + one warp for the block's cones
 constexpr int kStageFloats = kBoxX * kBoxY;                   // one plane tile (9,792 bytes)
 // TMA writes to shared memory must start on a 128-byte boundary: stages are
 // spaced by the plane size rounded up to 128 bytes.
@@ -80,8 +85,8 @@ struct Field3Args {
     int ntx, nty, zchunk;
     unsigned *status;
     // the same step's cones (they read the input buffer, which no block of this
-    // launch writes): field block b steps cones [b cone_per, (b+1) cone_per),
-    // one per thread; cone_per 0 = none
+    // launch writes): the cone warp of block b steps cones [b cone_per,
+    // (b+1) cone_per), 32 at a time; cone_per 0 = none
     int cone_per;
     ConeDesc c;
     uint32_t step;
@@ -132,9 +137,27 @@ __device__ __forceinline__ void cone_one3(const Field3Args &A, int a, bool inr)
     if (bad) flag_status(A.status, kStatusNonFinite);
 }
 
-template <bool MAP>
-__global__ void __launch_bounds__(kThreads3, 4) field3d_tma_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                                const Field3Args A)
+// The field warps meet at named barrier 1 (kThreads3 threads), so the cone
+// warp never holds them up.
+__device__ __forceinline__ void field_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads3) : "memory"); }
+
+__device__ __forceinline__ bool field_sync_or(bool p)
+{
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, 1, %2, pi;\n"
+        " selp.u32 %0, 1, 0, po;\n}\n"
+        : "=r"(r)
+        : "r"((unsigned)p), "n"(kThreads3)
+        : "memory");
+    return r != 0;
+}
+
+// CONES: the launch carries the cone warp (kLaunch3 threads); otherwise the
+// field warps alone, with the register budget of 256 threads.
+template <bool MAP, bool CONES>
+__global__ void __launch_bounds__(CONES ? kLaunch3 : kThreads3, 4)
+    field3d_tma_kernel(const __grid_constant__ CUtensorMap tmap, const Field3Args A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);                 // kStages barriers
@@ -167,14 +190,17 @@ __global__ void __launch_bounds__(kThreads3, 4) field3d_tma_kernel(const __grid_
         const int k = p - plo;
         return mbar_wait_bounded(&bar[k % kStages], (unsigned)((k / kStages) & 1));
     };
+    if (CONES && warp == kThreads3 / 32) {        // the cone warp: this block's cones, alongside the field
+        if (A.cone_per > 0) {
+            const int first = fb * A.cone_per;
+            const int cnt = min(A.cone_per, A.n - first);
+            for (int base = 0; base < cnt; base += 32)  // whole warp each round (the active count is a vote)
+                cone_one3(A, first + base + lane, base + lane < cnt);
+        }
+        return;
+    }
     if (tid == 0)
         for (int p = plo; p <= min(phi, plo + kStages - 2); ++p) issue(p);
-    // this block's cones, while the first planes are on their way
-    if (A.cone_per > 0) {
-        const int first = fb * A.cone_per;
-        const int cnt = min(A.cone_per, A.n - first);
-        if (warp * 32 < cnt) cone_one3(A, first + tid, tid < cnt);
-    }
 
     const int gx = x0 + 4 * lane;
     const bool xin = gx < f.nx;
@@ -187,7 +213,7 @@ __global__ void __launch_bounds__(kThreads3, 4) field3d_tma_kernel(const __grid_
         // keep two planes ahead: plane z+2 into the stage plane z-2 used
         if (tid == 0 && z + 2 <= phi && z + 2 >= plo + kStages - 1) issue(z + 2);
         if (z + 1 <= phi && !wait(z + 1)) tmo = true;
-        if (__syncthreads_or(tmo)) {
+        if (field_sync_or(tmo)) {
             if (tid == 0) {
                 flag_status(A.status, kStatusTimeout);
                 for (int p = plo; p <= phi; ++p) wait(p);    // let in-flight copies land (bounded)
@@ -236,13 +262,13 @@ __global__ void __launch_bounds__(kThreads3, 4) field3d_tma_kernel(const __grid_
                 *reinterpret_cast<float4 *>(A.Cout + idx) = o;
             }
         }
-        __syncthreads();       // every thread is done with plane z-1's stage before it is refilled
+        field_sync();          // every field thread is done with plane z-1's stage before it is refilled
     }
     if (__any_sync(kFull, bad) && lane == 0) flag_status(A.status, kStatusNonFinite);
     // point sources in this block's box, after its stores (the last barrier above)
     if (A.n_add > 0) {
         const long long n_cells = (long long)f.nx * f.ny * f.nz;
-        for (int k = tid; k < A.n_add; k += blockDim.x) {
+        for (int k = tid; k < A.n_add; k += kThreads3) {
             const long long c = A.src_cell[k];
             if (c < 0 || c >= n_cells) {
                 if (fb == 0) flag_status(A.status, kStatusBounds);
@@ -303,9 +329,13 @@ bool field3d_tma_prepare(Sim &s)
         if (r != CUDA_SUCCESS) return false;
     }
     const int smem = 128 + kStages * kStageStride * (int)sizeof(float);
-    if (cudaFuncSetAttribute(field3d_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+    if (cudaFuncSetAttribute(field3d_tma_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(field3d_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaFuncSetAttribute(field3d_tma_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(field3d_tma_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(field3d_tma_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess)
         return false;
     s.tmap3_ready = true;
@@ -345,16 +375,20 @@ cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout, bool *cones_d
     A.zchunk = (int)((s.fd.nz + chunks - 1) / chunks);
     chunks = (s.fd.nz + A.zchunk - 1) / A.zchunk;
     const unsigned grid = (unsigned)(cols * chunks);
-    // the cones ride along when one pass of the blocks' threads covers them
+    // the cones ride along (at most 8 rounds of the cone warp per block)
     const long long per = ((long long)s.n_axons + grid - 1) / grid;
     A.cone_per = (cones_done && s.n_axons > 0 && per <= kThreads3) ? (int)per : 0;
     if (cones_done) *cones_done = A.cone_per > 0 || s.n_axons == 0;
     const int smem = 128 + kStages * kStageStride * (int)sizeof(float);
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(s.tmap3[in_buffer]);
-    if (s.src_map)
-        field3d_tma_kernel<true><<<grid, kThreads3, smem, s.stream>>>(*map, A);
-    else
-        field3d_tma_kernel<false><<<grid, kThreads3, smem, s.stream>>>(*map, A);
+    const bool cones = A.cone_per > 0;
+    if (s.src_map) {
+        if (cones) field3d_tma_kernel<true, true><<<grid, kLaunch3, smem, s.stream>>>(*map, A);
+        else field3d_tma_kernel<true, false><<<grid, kThreads3, smem, s.stream>>>(*map, A);
+    } else {
+        if (cones) field3d_tma_kernel<false, true><<<grid, kLaunch3, smem, s.stream>>>(*map, A);
+        else field3d_tma_kernel<false, false><<<grid, kThreads3, smem, s.stream>>>(*map, A);
+    }
     return cudaGetLastError();
 }
 
