@@ -15,6 +15,7 @@ from .oracle import (  # noqa: F401
     value_at,
     snr,
     field_step,
+    field_window,
     cone_step,
     run,
     endpoint_loss,

@@ -234,6 +234,49 @@ void orc_field_step(const orc_grid *g, const double *C, double *Cn,
 }
 
 /* ------------------------------------------------------------------------
+ * The same field step on a window of a grid too large to hold in the oracle:
+ * `Wp` holds the input values of the window grown by one node on every side
+ * ((wx + 2) x (wy + 2) x (wz + 2) values, x fastest; entries outside the grid
+ * are never read), the window's first node is (ox, oy, oz) in global
+ * coordinates, and `out` receives C' of the wx x wy x wz window nodes.  Walls
+ * are decided by global coordinates; the point sources whose node lies in the
+ * window are added, as in orc_field_step (no rate map).
+ * ---------------------------------------------------------------------- */
+void orc_field_window(const orc_grid *g, const double *Wp, int64_t ox, int64_t oy, int64_t oz, int wx, int wy,
+                      int wz, const int64_t *src_cell, const double *src_emit, int n_src, double *out)
+{
+    const double alpha = g->D * g->dt / (g->h * g->h);
+    const double decay = g->lambda * g->dt;
+    const int64_t nx = g->nx, ny = g->ny, nz = (g->dim == 3) ? g->nz : 1;
+    const int64_t px = wx + 2, py = wy + 2;          /* padded window extents */
+    const int64_t sx = 1, sy = px, sz = px * py;
+    const int pz0 = (g->dim == 3) ? 1 : 0;           /* 2D windows have no z padding */
+    for (int k = 0; k < wz; ++k)
+        for (int j = 0; j < wy; ++j)
+            for (int i = 0; i < wx; ++i) {
+                const int64_t gi = ox + i, gj = oy + j, gk = oz + k;
+                const int64_t c = (i + 1) * sx + (j + 1) * sy + (k + pz0) * sz;
+                double ci = Wp[c];
+                double flux = 0.0;
+                if (gi > 0)      flux += Wp[c - sx] - ci;
+                if (gi < nx - 1) flux += Wp[c + sx] - ci;
+                if (gj > 0)      flux += Wp[c - sy] - ci;
+                if (gj < ny - 1) flux += Wp[c + sy] - ci;
+                if (g->dim == 3) {
+                    if (gk > 0)      flux += Wp[c - sz] - ci;
+                    if (gk < nz - 1) flux += Wp[c + sz] - ci;
+                }
+                out[i + (int64_t)wx * (j + (int64_t)wy * k)] = ci + alpha * flux - decay * ci;
+            }
+    for (int s = 0; s < n_src; ++s) {
+        const int64_t cell = src_cell[s];
+        const int64_t gi = cell % nx, gj = (cell / nx) % ny, gk = cell / (nx * ny);
+        if (gi >= ox && gi < ox + wx && gj >= oy && gj < oy + wy && gk >= oz && gk < oz + wz)
+            out[(gi - ox) + (int64_t)wx * ((gj - oy) + (int64_t)wy * (gk - oz))] += src_emit[s];
+    }
+}
+
+/* ------------------------------------------------------------------------
  * Gradient.  Node gradient: central differences, a missing neighbour
  * replaced by the node itself (ghost = edge), so on a wall node the
  * one-sided difference is halved.  Point gradient: bilinear / trilinear

@@ -132,6 +132,8 @@ def _load():
             lib.orc_csr.restype = ct.c_int
             lib.orc_bfs.argtypes = [ct.c_int, P, P, ct.c_int, P]
             lib.orc_set_threads.argtypes = [ct.c_int]
+            lib.orc_field_window.argtypes = [ct.POINTER(_Grid), P, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_int,
+                                             ct.c_int, ct.c_int, P, P, ct.c_int, P]
             lib.orc_openmp.restype = ct.c_int
             lib.orc_value_at.argtypes = [ct.POINTER(_Grid), P, P]
             lib.orc_value_at.restype = ct.c_double
@@ -240,6 +242,28 @@ def field_step(grid: Grid, C, src_cell=(), src_emit=(), src_map=None):
     g = grid._c()
     _load().orc_field_step(ct.byref(g), _ptr(C), _ptr(out), _ptr(cell), _ptr(emit),
                            cell.shape[0], _ptr(smap))
+    return out
+
+
+def field_window(grid: Grid, Wp, origin, src_cell=(), src_emit=()):
+    """C' on a window of a (possibly huge) grid from the window's input values grown by one
+    node on every side (``Wp``: shape (wy + 2, wx + 2) in 2D, (wz + 2, wy + 2, wx + 2) in 3D;
+    entries outside the grid are ignored); ``origin`` = the window's first node (x, y[, z]).
+    Point sources inside the window are added; no rate map."""
+    lib = _load()
+    Wp = _f64(Wp)
+    if grid.dim == 2:
+        wy, wx = Wp.shape[0] - 2, Wp.shape[1] - 2
+        wz, (ox, oy), oz = 1, origin, 0
+    else:
+        wz, wy, wx = Wp.shape[0] - 2, Wp.shape[1] - 2, Wp.shape[2] - 2
+        ox, oy, oz = origin
+    out = np.zeros((wz, wy, wx) if grid.dim == 3 else (wy, wx), np.float64)
+    cells = np.ascontiguousarray(np.asarray(src_cell, np.int64).reshape(-1))
+    emit = _f64(np.asarray(src_emit, np.float64).reshape(-1))
+    lib.orc_field_window(ct.byref(grid._c()), _ptr(Wp), int(ox), int(oy), int(oz), wx, wy, wz,
+                         _ptr(cells) if cells.size else None, _ptr(emit) if emit.size else None, int(cells.size),
+                         _ptr(out))
     return out
 
 

@@ -46,6 +46,8 @@ constexpr int kMaxTileSrc = 256;      // sources per tile (and in total on this 
 constexpr long long kWaitLimit = 1LL << 22;
 constexpr int kBand = 12;             // rows swept by each warp per sub-step
 constexpr int kRows = kWarps * kBand; // loaded rows per tile (96)
+constexpr int kFusedMinTX = 128;      // smallest interior tile the path accepts
+constexpr int kFusedMinTY = 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -629,12 +631,12 @@ bool choose_geometry(const FieldDesc &f, float step_len, float stop_r2, bool con
         local_stop = need <= H ? 1 : 0;
     }
     int HX = (H + 3) & ~3;
-    if (kW - 2 * HX < 32) return false;
     const int R = kRows, cps = 2;
     int TY = R - 2 * H;
-    if (TY < 8) return false;
     int TX = kW - 2 * HX;
-    if (TX < 32) return false;
+    // tiles smaller than this are mostly halo (and the workspace's bins are sized for
+    // no more tiles than these interiors give): every depth up to 16 with step_len <= h
+    if (TX < kFusedMinTX || TY < kFusedMinTY) return false;
     g.W = kW;
     g.R = R;
     g.HX = HX;
@@ -653,12 +655,13 @@ bool choose_geometry(const FieldDesc &f, float step_len, float stop_r2, bool con
 
 }  // namespace
 
-// Upper bound on the tile count of any geometry (TX >= 32, TY >= 8), used to
-// size the binning workspace independently of the temporal depth.
+// Upper bound on the tile count of any accepted geometry (interior at least
+// kFusedMinTX x kFusedMinTY), used to size the binning workspace independently
+// of the temporal depth.
 int fused_tile_count(const cue_params &p)
 {
     if (p.dim != 2) return 0;
-    long long n = (long long)((p.nx + 31) / 32) * ((p.ny + 7) / 8);
+    long long n = (long long)((p.nx + kFusedMinTX - 1) / kFusedMinTX) * ((p.ny + kFusedMinTY - 1) / kFusedMinTY);
     return n > (1 << 22) ? 0 : (int)n;
 }
 
@@ -672,7 +675,7 @@ bool fused_supported(const Sim &s)
     if (!choose_geometry(s.fd, s.cd.step_len, s.cd.stop_r2, s.n_axons > 0, default_depth(s), device_sm_count(), g))
         return false;
     long long tiles = (long long)g.ntx * g.nty;
-    if (tiles > s.wl.n_tiles || tiles + 1 > 16384) return false;
+    if (tiles > s.wl.n_tiles) return false;             // the workspace's bins are sized by fused_tile_count
     return true;
 }
 

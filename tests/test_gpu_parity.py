@@ -280,3 +280,96 @@ def test_merged_3d_step_equals_separate_launches(cue, name):
         np.testing.assert_array_equal(x, y)
     a.close()
     b.close()
+
+
+def _max_case(dim):
+    """The largest grids the library accepts (fewer than 2^31 nodes): 65536 x 32767 and
+    1288 x 1288 x 1294, nx % 4 == 0 so the aligned kernels run."""
+    if dim == 2:
+        return 65536, 32767, 1
+    return 1288, 1288, 1294
+
+
+def _padded(field_t, origin, size):
+    """Input values of a window grown by one node on every side, NaN outside the grid."""
+    import torch
+    dim = field_t.dim()
+    ext = list(reversed(field_t.shape))                           # x, y(, z)
+    lo = [max(o - 1, 0) for o in origin]
+    hi = [min(o + s + 1, e) for o, s, e in zip(origin, size, ext)]
+    sl = tuple(slice(l, h) for l, h in zip(reversed(lo), reversed(hi)))
+    block = field_t[sl].to(torch.float64).cpu().numpy()
+    Wp = np.full(tuple(s + 2 for s in reversed(size)), np.nan)
+    off = tuple(slice(l - (o - 1), l - (o - 1) + n) for l, o, n in zip(reversed(lo), reversed(origin), block.shape))
+    Wp[off] = block
+    return Wp
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_maximum_grid_one_step_on_sampled_windows(cue, dim, offset):
+    """One coupled step on the largest accepted grid, through the aligned path (fused in 2D,
+    the TMA step kernel in 3D) and through the any-size kernels (a one-float offset), against
+    the oracle's windowed step on windows at the first and last nodes, along the walls, in
+    the middle and around sources at the first node, the last node and high linear indices;
+    the cones near the far corner move by exactly one step length."""
+    import torch
+    nx, ny, nz = _max_case(dim)
+    n = nx * ny * nz
+    assert n < 2 ** 31 - 1
+    free, _ = torch.cuda.mem_get_info()
+    if free < 2.5 * 2 * 4 * n:
+        pytest.skip("not enough device memory for two fields of 2^31 nodes")
+    w = W.make(f"max-{dim}d", dim, nx, ny, nz, dt=0.15 if dim == 3 else 0.2, n_src=4, n_axons=256,
+               emit=(0.5, 2.0), seed=30 + dim)
+    ext = (nx, ny, nz)[:dim]
+    w.src_cell = np.array([0, n - 1, n - 1 - 3 * nx, n // 2 + 5], np.int32)
+    rng = np.random.default_rng(31)
+    w.pos = (np.array(ext, np.float32)[:, None] - 3.0
+             - rng.uniform(0.0, 6.0, (dim, w.n_axons)).astype(np.float32) * (np.array(ext)[:, None] > 8))
+    w.pos = np.clip(w.pos, 0.5, None).astype(np.float32)
+    shape = w.shape
+    w.field0 = lambda: torch.zeros((), dtype=torch.float32, device="cuda:0").expand(shape)
+    path = cue.CUE_PATH_PLAIN if offset else cue.CUE_PATH_AUTO
+    sim = cue.Simulation(w, path=path, field_offset=offset)
+    # a separable field: random along each axis, summed (no temporaries of the grid's size)
+    g = torch.Generator(device="cuda:0").manual_seed(32 + dim)
+    axes = [torch.rand(s, generator=g, device="cuda:0") for s in reversed(ext)]    # z?, y, x
+    f0 = sim.fields[0]
+    if dim == 2:
+        torch.add(axes[0][:, None], axes[1][None, :], out=f0)
+    else:
+        torch.add((axes[0][:, None] + axes[1][None, :])[:, :, None], axes[2][None, None, :], out=f0)
+    torch.cuda.synchronize()
+    if dim == 2:
+        windows = [((0, 0), (8, 6)), ((nx - 8, ny - 6), (8, 6)), ((nx // 2, 0), (8, 3)), ((0, ny // 2), (4, 6)),
+                   ((nx // 2 - 4, ny // 2 - 3), (12, 8)), ((nx - 12, ny - 8), (12, 8))]
+    else:
+        windows = [((0, 0, 0), (8, 4, 3)), ((nx - 8, ny - 4, nz - 3), (8, 4, 3)), ((nx // 2, 0, nz // 2), (8, 3, 3)),
+                   ((0, ny // 2, nz - 2), (4, 5, 2)), ((nx // 2 - 4, ny // 2 - 2, nz // 2 - 1), (12, 6, 4))]
+    src_xyz = [((c % nx), (c // nx) % ny, c // (nx * ny)) for c in w.src_cell.astype(np.int64)]
+    for c in src_xyz[2:]:                               # windows around the sources at high indices
+        o = [max(0, min(c[a] - 2, ext[a] - 5)) for a in range(dim)]
+        windows.append((tuple(o), (5,) * dim))
+    inputs = [_padded(f0, o, s) for o, s in windows]
+    pos0, dir0, act0 = sim.pos.cpu().numpy(), sim.dir.cpu().numpy(), sim.active.cpu().numpy()
+    sim.sim_run(1)
+    sim.check()
+    out = sim.field()
+    grid = grid_of(w)
+    emit = w.src_emit.astype(np.float64)
+    for (o, s), Wp in zip(windows, inputs):
+        want = oracle.field_window(grid, Wp, o, w.src_cell.astype(np.int64), emit)
+        sl = tuple(slice(a, a + b) for a, b in zip(reversed(o), reversed(s)))
+        got = out[sl].cpu().numpy()
+        assert field_rel_err(got, want) <= FIELD_RTOL, (o, s)
+    pos1, dir1, act1 = sim.pos.cpu().numpy(), sim.dir.cpu().numpy(), sim.active.cpu().numpy()
+    moved = act0.astype(bool) & act1.astype(bool)
+    assert moved.sum() > 0.9 * w.n_axons
+    step = np.linalg.norm(pos1.astype(np.float64) - pos0, axis=0)
+    np.testing.assert_allclose(step[moved], w.step_len, atol=0.02)      # float32 ulp at x ~ 65536 is 0.004
+    np.testing.assert_allclose(np.linalg.norm(dir1[:, moved].astype(np.float64), axis=0), 1.0, atol=1e-5)
+    assert sim.last_path() == (cue.CUE_PATH_FUSED if (dim == 2 and not offset) else cue.CUE_PATH_PLAIN)
+    sim.close()
+    del sim, f0, out
+    torch.cuda.empty_cache()

@@ -290,3 +290,42 @@ def test_threaded_field_step_is_the_single_threaded_one(dim):
         oracle.set_threads(1)
     b = oracle.field_step(g, C, cells, emit, smap)
     np.testing.assert_array_equal(a, b)
+
+
+def _padded_window(C, origin, size):
+    """The input values of a window grown by one node on every side; nodes outside the grid
+    are NaN (the windowed step must never read them)."""
+    dim = C.ndim
+    shape_pad = tuple(s + 2 for s in reversed(size))             # (z,) y, x order
+    Wp = np.full(shape_pad, np.nan)
+    lo = [o - 1 for o in origin]
+    ext = list(reversed(C.shape))                                 # x, y(, z)
+    for idx in np.ndindex(*shape_pad):
+        g = [lo[a] + idx[dim - 1 - a] for a in range(dim)]       # global x, y(, z)
+        if all(0 <= g[a] < ext[a] for a in range(dim)):
+            Wp[idx] = C[tuple(reversed(g))]
+    return Wp
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_windowed_field_step_equals_the_full_step(dim):
+    """The windowed form of the field step (used to check grids too large for the oracle)
+    gives, on corner, edge and interior windows, exactly the full step's values there, and
+    never reads outside the grid (those entries are NaN)."""
+    rng = np.random.default_rng(40 + dim)
+    if dim == 2:
+        g = oracle.Grid(2, 37, 29, h=1.0, D=1.0, lam=0.01, dt=0.2)
+        windows = [((0, 0), (5, 4)), ((32, 25), (5, 4)), ((10, 0), (7, 3)), ((0, 11), (3, 6)), ((12, 9), (8, 8))]
+    else:
+        g = oracle.Grid(3, 13, 11, 9, h=1.0, D=1.0, lam=0.01, dt=0.15)
+        windows = [((0, 0, 0), (4, 3, 2)), ((9, 8, 7), (4, 3, 2)), ((5, 0, 3), (3, 2, 4)), ((4, 4, 4), (5, 5, 3))]
+    C = rng.uniform(0.0, 1.0, g.shape)
+    cells = rng.choice(C.size, 6, replace=False)
+    cells[0] = 0
+    cells[1] = C.size - 1
+    emit = rng.uniform(0.5, 2.0, 6)
+    full = oracle.field_step(g, C, cells, emit)
+    for origin, size in windows:
+        got = oracle.field_window(g, _padded_window(C, origin, size), origin, cells, emit)
+        sl = tuple(slice(o, o + s) for o, s in zip(reversed(origin), reversed(size)))
+        np.testing.assert_array_equal(got, full[sl])
