@@ -405,6 +405,9 @@ def main():
                 "avg_launch_us": avg_s * 1e6, "steps_per_launch": steps_per_launch,
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "effective_gbs": bytes_per_cell * w.n_cells * steps_per_launch / avg_s / 1e9 if avg_s else 0}
+    # a temporally blocked launch moves its field through HBM once for K steps: the bytes an
+    # unblocked kernel would move for the same node updates, against the same peak
+    roofline["effective_frac"] = roofline["effective_gbs"] / hbm if hbm else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
