@@ -493,6 +493,7 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
         b.reset_state(0, 0)
 
     rows, bpsm, tuned_ms = b.autotune(10)
+    mode = b.get_option(B.CUE_BOPT_MODE)
     b.set_option(B.CUE_BOPT_GRAPH, 1)
     for _ in range(max(args.warmup, 3)):
         reset()
@@ -526,16 +527,24 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
         "config": {"workload": f"batched: {len(ws)} independent 2D instances (sides U{{64..1024}}, "
                                f"{cells / 1e6:.1f} M cells, {sum(w.n_axons for w in ws)} cones), {T} steps",
                    "instances": len(ws), "cells": cells, "steps_per_run": T,
-                   "launch": "one persistent launch per run, replayed from a CUDA graph",
+                   "launch": ("one persistent launch per run" if mode == 1 else
+                              ("per time step one launch over every instance's cone chunks and streamed field "
+                               "tiles" if rows > 4 else
+                               "per time step one launch over the cone chunks and one over the field tiles"))
+                             + ", replayed from a CUDA graph",
                    "autotuned": {"rows": rows, "blocks_per_sm": bpsm, "probe_ms_per_step": tuned_ms},
                    "l2": "flushed between timed steps (512 MiB write); 1.2 GB working set",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "axon_steps_per_s": world * cone_updates * args.steps / (total_ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": recorded_traffic("persist", "c4"), "kernel": "persist", "peak_kind": peak_kind,
+                     "traffic": recorded_traffic("persist", "c4") if mode == 1 else None,
+                     "kernel": "persist" if mode == 1 else "step launches (per run)", "peak_kind": peak_kind,
                      "launches": args.steps, "avg_launch_us": per_launch_s * 1e6, "steps_per_launch": T,
                      "algorithmic_bytes_per_launch": 8.0 * cells * T},
-        "clocks": clocks, "gpu_launches": 2 * args.steps,      # the persistent kernel + the step advance
+        # persistent: the kernel + the step advance; per step: one launch per time step (streamed tiles
+        # with the cone chunks) or two (cone chunks, then tiles), + the advance
+        "clocks": clocks,
+        "gpu_launches": args.steps * (2 if mode == 1 else (T if rows > 4 else 2 * T) + 1),
     }
     # the one-instance-per-launch plain solver on the first 32 instances (100 steps each), and
     # the same instances one after another through sim_run on the library's own path choice

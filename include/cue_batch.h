@@ -68,17 +68,20 @@ cue_batch *cue_batch_create(int32_t n, const cue_instance *inst, void *d_ws, siz
                             int32_t *err);
 
 /* Advance every instance by nsteps coupled steps (cones on C^n, then
- * C^n -> C^{n+1}).  One cooperative launch, or one graph replay when
- * CUE_BOPT_GRAPH is on (the graph is captured at the first call with a given
- * nsteps and replayed afterwards; the step counter and buffer parity live on
- * the device, so a replay needs no new arguments). */
+ * C^n -> C^{n+1}).  One cooperative launch (CUE_BOPT_MODE 1) or two launches
+ * per step (mode 2), or one graph replay of those when CUE_BOPT_GRAPH is on
+ * (the graph is captured at the first call with a given nsteps and replayed
+ * afterwards; the step counter and buffer parity live on the device, so a
+ * replay needs no new arguments). */
 int cue_batch_run(cue_batch *b, int32_t nsteps);
 
 /* Time each candidate launch shape (rows per thread 1, 2, 4 x blocks per SM
- * 1..3) on probe_steps steps from the current state, restoring the state after
- * every candidate, and keep the fastest.  Needs the backup area (see
+ * 1..3 of the persistent launch, and rows 2, 4, 8, 16 of one launch per step) on
+ * probe_steps steps from the current state, restoring the state after every
+ * candidate, and keep the fastest.  Needs the backup area (see
  * cue_batch_workspace_bytes).  Synchronises the stream.  Writes the chosen
- * rows and blocks per SM and the best time per step (ms) when non-null. */
+ * rows, blocks per SM (0: one launch per step) and the best time per step
+ * (ms) when non-null. */
 int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows, int32_t *blocks_per_sm,
                        double *ms_per_step);
 
@@ -87,9 +90,14 @@ int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows, int32_t
  * stream.  CUE_ERR_ARG for cur not 0/1 or step outside [0, 2^32). */
 int cue_batch_set_state(cue_batch *b, int64_t step, int32_t cur);
 
-#define CUE_BOPT_ROWS    1    /* rows per thread of a field tile (1, 2, 4)          */
+#define CUE_BOPT_ROWS    1    /* rows per thread of a field tile (1, 2, 4; 8 and 16 */
+                              /* with one launch per step: the tile is streamed)    */
 #define CUE_BOPT_BLOCKS  2    /* blocks per SM (1..8, capped by occupancy)          */
 #define CUE_BOPT_GRAPH   3    /* 1: run through a captured CUDA graph; 0: direct    */
+#define CUE_BOPT_MODE    4    /* 1: one persistent launch per run (grid barrier     */
+                              /* between steps); 2: per step one launch over every  */
+                              /* instance's cone chunks and one over every tile;    */
+                              /* 0: library choice (1 unless the autotuner picked 2) */
 #define CUE_BINFO_ITEMS  16   /* work-list length (field tiles + cone chunks)       */
 #define CUE_BINFO_STEP   17   /* steps taken so far (host mirror)                   */
 #define CUE_BINFO_CUR    18   /* current buffer of every instance: 0 = field_a      */

@@ -14,6 +14,7 @@ from .cue import CueError, cone_params, cue_params
 CUE_BOPT_ROWS = 1
 CUE_BOPT_BLOCKS = 2
 CUE_BOPT_GRAPH = 3
+CUE_BOPT_MODE = 4
 CUE_BINFO_ITEMS = 16
 CUE_BINFO_STEP = 17
 CUE_BINFO_CUR = 18

@@ -20,7 +20,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // instance table | work list | source coordinates and binned sources | backup
 // (optional)].
 struct BatchLayout {
-    size_t ctrl, bar, counters, inst, items, src_xyz, backup, total;
+    size_t ctrl, bar, counters, inst, items, step_items, src_xyz, backup, total;
     size_t items_cap;
     std::vector<size_t> xyz_off, ent_off, key_off, bk_field, bk_cone;   // per instance
 };
@@ -44,6 +44,8 @@ BatchLayout batch_layout(int n, const cue_instance *in, bool backup)
         L.items_cap += (size_t)persist_tiles(in[i].params.nx, in[i].params.ny, 1) +
                        (size_t)(std::max(in[i].n_axons, 0) + kPersistConeChunk - 1) / kPersistConeChunk;
     L.items = off;
+    off += align256(sizeof(PItem) * std::max<size_t>(L.items_cap, 1));
+    L.step_items = off;                                  // the same items, cone chunks first, for one launch per step
     off += align256(sizeof(PItem) * std::max<size_t>(L.items_cap, 1));
     L.src_xyz = off;
     L.xyz_off.resize(n);
@@ -118,8 +120,10 @@ struct cue_batch {
     unsigned char *ws = nullptr;
     cudaStream_t stream = nullptr;
     int rows = 0, bpsm = 0;          // options (0 = library choice)
+    int mode = 0;                    // option: 0 library choice (persistent unless tuned), 1 persistent, 2 per step
     int rows_used = 0;
     int n_items = 0;
+    int n_step_tiles = 0, n_step_chunks = 0;
     bool list_ready = false;
     bool use_graph = false;
     cudaGraphExec_t graph = nullptr;
@@ -135,6 +139,8 @@ struct cue_batch {
     PBar *bar() const { return reinterpret_cast<PBar *>(ws + L.bar); }
     PInst *d_inst() const { return reinterpret_cast<PInst *>(ws + L.inst); }
     PItem *d_items() const { return reinterpret_cast<PItem *>(ws + L.items); }
+    PItem *d_step_items() const { return reinterpret_cast<PItem *>(ws + L.step_items); }
+    bool per_step() const { return mode == 2; }
 };
 
 namespace {
@@ -169,24 +175,41 @@ int pick_rows_b(const cue_batch *b)
     return rows;
 }
 
-// (Re)build the instance table and the work list for the current rows.
+// (Re)build the instance table and the work list for the current rows (the
+// persistent kernel's tiles have at most 4 rows per warp; the per-step
+// launches stream 8 or 16 as well).
 int stage_list(cue_batch *b)
 {
-    const int rows = pick_rows_b(b);
+    const int rows = b->per_step() ? pick_rows_b(b) : std::min(pick_rows_b(b), 4);
     if (b->list_ready && rows == b->rows_used) return CUE_OK;
     for (int i = 0; i < b->n; ++i) persist_fill(b->insts[i], b->insts[i].f, rows, b->in[i].pitch);
     std::vector<PItem> items;
     persist_items(b->insts, items);
     if (items.size() > b->L.items_cap) return CUE_ERR_WORKSPACE;
+    // one launch per step: every cone chunk, then every tile (instance by instance)
+    std::vector<PItem> step_items;
+    step_items.reserve(items.size());
+    for (const PItem &w : items)
+        if (w.idx < 0) step_items.push_back(w);
+    const int n_chunks = (int)step_items.size();
+    for (const PItem &w : items)
+        if (w.idx >= 0) step_items.push_back(w);
     if (cudaMemcpyAsync(b->d_inst(), b->insts.data(), sizeof(PInst) * b->insts.size(), cudaMemcpyHostToDevice,
                         b->stream) != cudaSuccess ||
         (!items.empty() && cudaMemcpyAsync(b->d_items(), items.data(), sizeof(PItem) * items.size(),
                                            cudaMemcpyHostToDevice, b->stream) != cudaSuccess) ||
+        (!step_items.empty() && cudaMemcpyAsync(b->d_step_items(), step_items.data(),
+                                                sizeof(PItem) * step_items.size(), cudaMemcpyHostToDevice,
+                                                b->stream) != cudaSuccess) ||
         persist_bin_sources(b->d_inst(), b->n, b->d_items(), (int)items.size(), b->status(), b->stream) !=
             cudaSuccess ||
+        persist_bin_sources(b->d_inst(), b->n, b->d_step_items(), (int)step_items.size(), b->status(),
+                            b->stream) != cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)       // the host vectors are released below
         return CUE_ERR_CUDA;
     b->n_items = (int)items.size();
+    b->n_step_chunks = n_chunks;
+    b->n_step_tiles = (int)step_items.size() - n_chunks;
     b->rows_used = rows;
     b->list_ready = true;
     drop_graph(b);
@@ -195,6 +218,11 @@ int stage_list(cue_batch *b)
 
 cudaError_t launch_direct(cue_batch *b, int nsteps)
 {
+    if (b->per_step()) {
+        b->grid = b->n_step_tiles;
+        return step_launch(b->d_inst(), b->d_step_items(), b->n_step_chunks, b->d_step_items() + b->n_step_chunks,
+                           b->n_step_tiles, b->rows_used, nsteps, b->ctrl(), b->stream);
+    }
     return persist_launch(b->d_inst(), b->d_items(), b->n_items, nsteps, 0, 0, b->bar(), b->bpsm, 0, 0, b->status(),
                           b->stream, &b->grid, b->ctrl());
 }
@@ -409,7 +437,7 @@ int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows_out, int
     const long long step0 = b->step;
     int rc = save_state(b, counter);
     if (rc != CUE_OK) return rc;
-    const int keep_rows = b->rows, keep_bpsm = b->bpsm;
+    const int keep_rows = b->rows, keep_bpsm = b->bpsm, keep_mode = b->mode;
     const bool keep_graph = b->use_graph;
     b->use_graph = false;
     const int maxb = std::max(1, std::min(3, persist_max_blocks_per_sm()));
@@ -417,11 +445,15 @@ int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows_out, int
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CUE_ERR_CUDA;
     double best = 1e30;
     int best_rows = 0, best_b = 0;
-    const int rows_c[3] = {1, 2, 4};
-    for (int ri = 0; ri < 3 && rc == CUE_OK; ++ri)
-        for (int bb = 1; bb <= maxb && rc == CUE_OK; ++bb) {
+    const int rows_c[5] = {1, 2, 4, 8, 16};
+    // candidates: the persistent launch (rows 1, 2, 4 x blocks per SM 1..maxb) and one
+    // launch per step (rows 2..16; "blocks per SM" 0)
+    for (int ri = 0; ri < 5 && rc == CUE_OK; ++ri)
+        for (int bb = 0; bb <= maxb && rc == CUE_OK; ++bb) {
+            if ((bb == 0 && rows_c[ri] == 1) || (bb > 0 && rows_c[ri] > 4)) continue;
             b->rows = rows_c[ri];
             b->bpsm = bb;
+            b->mode = bb == 0 ? 2 : 1;
             rc = run_batch(b, 1);                              // warm: stages the list, first touch
             if (rc == CUE_OK) rc = restore_state(b, cur0, step0, counter);
             if (rc != CUE_OK) break;
@@ -445,10 +477,12 @@ int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows_out, int
     if (rc != CUE_OK) {
         b->rows = keep_rows;
         b->bpsm = keep_bpsm;
+        b->mode = keep_mode;
         return rc;
     }
     b->rows = best_rows;
     b->bpsm = best_b;
+    b->mode = best_b == 0 ? 2 : 1;
     b->list_ready = false;
     drop_graph(b);
     if (rows_out) *rows_out = best_rows;
@@ -475,7 +509,7 @@ int cue_batch_set_option(cue_batch *b, int32_t option, int64_t value)
     if (!b) return CUE_ERR_ARG;
     switch (option) {
     case CUE_BOPT_ROWS:
-        if (value != 0 && value != 1 && value != 2 && value != 4) return CUE_ERR_ARG;
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16) return CUE_ERR_ARG;
         b->rows = (int)value;
         b->list_ready = b->list_ready && pick_rows_b(b) == b->rows_used;
         drop_graph(b);
@@ -489,6 +523,11 @@ int cue_batch_set_option(cue_batch *b, int32_t option, int64_t value)
         if (value != 0 && value != 1) return CUE_ERR_ARG;
         b->use_graph = value != 0;
         if (!b->use_graph) drop_graph(b);
+        return CUE_OK;
+    case CUE_BOPT_MODE:
+        if (value < 0 || value > 2) return CUE_ERR_ARG;
+        b->mode = (int)value;
+        drop_graph(b);
         return CUE_OK;
     default:
         return CUE_ERR_ARG;
@@ -506,6 +545,7 @@ int cue_batch_get_option(const cue_batch *b, int32_t option, int64_t *value)
     case CUE_BINFO_STEP: *value = b->step; return CUE_OK;
     case CUE_BINFO_CUR: *value = b->cur; return CUE_OK;
     case CUE_BINFO_GRID: *value = b->grid; return CUE_OK;
+    case CUE_BOPT_MODE: *value = b->per_step() ? 2 : 1; return CUE_OK;
     default: return CUE_ERR_ARG;
     }
 }

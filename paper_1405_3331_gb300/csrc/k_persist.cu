@@ -167,6 +167,129 @@ __device__ __forceinline__ void field_tile_r(const PInst &I, const float *Cin, f
     }
 }
 
+// The same tile of I.rows rows per warp (any count), streamed: each warp walks
+// its rows down y keeping the rows above, at and below in registers and the
+// next row, its edge columns and its map row in flight, so a tile needs few
+// registers and many can be resident (the launch-per-step batch mode).  The
+// arithmetic, wall handling and source order are field_tile_r's.
+template <bool MAP>
+__device__ __forceinline__ void field_tile_stream(const PInst &I, const float *Cin, float *Cout, int tile,
+                                                  int src_begin, int src_n, bool check)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const FieldDesc &f = I.f;
+    const int R = I.rows;
+    const int tx = tile % I.ntx, ty = tile / I.ntx;
+    const int p4 = I.pitch >> 2;
+    const int nxq = (f.nx + 3) >> 2;
+    const int x4 = tx * 32 + lane;
+    const bool xin = x4 < nxq;
+    const int y0 = (ty * kPersistWarps + warp) * R;
+    const int x = x4 * 4;
+    const bool has_l = x > 0, has_r = x + 4 < f.nx;
+    const bool ragged = (tx + 1) * 128 > f.nx;
+    const float4 *col = reinterpret_cast<const float4 *>(Cin) + x4;
+    float4 *out4 = reinterpret_cast<float4 *>(Cout);
+    const float4 *m4 = reinterpret_cast<const float4 *>(I.map);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool bad = false;
+    if (y0 < f.ny) {                                   // warp-uniform
+        const int y1 = min(y0 + R, f.ny);
+        auto row = [&](int y) { return xin ? __ldcg(col + (size_t)min(max(y, 0), f.ny - 1) * p4) : z4; };
+        auto edge_l = [&](int y) {
+            return (lane == 0 && xin && has_l) ? __ldcg(Cin + (size_t)min(y, f.ny - 1) * I.pitch + x - 1) : 0.f;
+        };
+        auto edge_r = [&](int y) {
+            return (lane == 31 && xin && has_r) ? __ldcg(Cin + (size_t)min(y, f.ny - 1) * I.pitch + x + 4) : 0.f;
+        };
+        auto map_row = [&](int y) {
+            return (MAP && xin) ? __ldg(m4 + (size_t)min(y, f.ny - 1) * p4 + x4) : z4;
+        };
+        float4 vm = row(y0 - 1), vc = row(y0), vp = row(y0 + 1);    // rows y-1, y, y+1 (clamped)
+        float el = edge_l(y0), er = edge_r(y0);
+        float4 m = map_row(y0);
+        const bool v1 = !ragged || x + 1 < f.nx, v2 = !ragged || x + 2 < f.nx, v3 = !ragged || x + 3 < f.nx;
+        for (int y = y0; y < y1; ++y) {
+            // the next row's inputs go out before this row is computed
+            const bool more = y + 1 < y1;
+            const float4 vn = more ? row(y + 2) : z4;
+            const float eln = more ? edge_l(y + 1) : 0.f, ern = more ? edge_r(y + 1) : 0.f;
+            const float4 mn = more ? map_row(y + 1) : z4;
+            const float4 cur = vc;
+            const float4 up = y > 0 ? vm : cur;
+            const float4 dn = y + 1 < f.ny ? vp : cur;
+            float l = __shfl_up_sync(kFull, cur.w, 1);
+            float r = __shfl_down_sync(kFull, cur.x, 1);
+            if (lane == 0) l = has_l ? el : cur.x;
+            if (lane == 31) r = has_r ? er : cur.w;
+            if (!has_l) l = cur.x;
+            if (!has_r) r = cur.w;
+            if (xin) {
+                float4 o;
+                if (ragged) {
+                    const float rx = v1 ? cur.y : cur.x, ry = v2 ? cur.z : cur.y, rz = v3 ? cur.w : cur.z;
+                    o.x = node_update2(cur.x, l, rx, up.x, dn.x, f.alpha, f.beta);
+                    o.y = node_update2(cur.y, cur.x, ry, up.y, dn.y, f.alpha, f.beta);
+                    o.z = node_update2(cur.z, cur.y, rz, up.z, dn.z, f.alpha, f.beta);
+                } else {
+                    o.x = node_update2(cur.x, l, cur.y, up.x, dn.x, f.alpha, f.beta);
+                    o.y = node_update2(cur.y, cur.x, cur.z, up.y, dn.y, f.alpha, f.beta);
+                    o.z = node_update2(cur.z, cur.y, cur.w, up.z, dn.z, f.alpha, f.beta);
+                }
+                o.w = node_update2(cur.w, cur.z, r, up.w, dn.w, f.alpha, f.beta);
+                if constexpr (MAP) {
+                    o.x = fmaf(f.dt, m.x, o.x);
+                    o.y = fmaf(f.dt, m.y, o.y);
+                    o.z = fmaf(f.dt, m.z, o.z);
+                    o.w = fmaf(f.dt, m.w, o.w);
+                }
+                const int base = y * I.pitch + x;
+                for (int e = 0; e < src_n; ++e) {
+                    const int2 ent = __ldg(reinterpret_cast<const int2 *>(I.src_ent) + src_begin + e);
+                    const int rel = ent.x - base;
+                    if (rel >= 0 && rel < 4) {
+                        const float em = __ldg(I.src_emit + ent.y);
+                        if (rel == 0) o.x += em;
+                        else if (rel == 1) o.y += em;
+                        else if (rel == 2) o.z += em;
+                        else o.w += em;
+                    }
+                }
+                if (ragged) {
+                    if (!v1) o.y = cur.y;
+                    if (!v2) o.z = cur.z;
+                    if (!v3) o.w = cur.w;
+                }
+                if (check) bad |= !finite4(o);
+                out4[(size_t)y * p4 + x4] = o;
+            }
+            vm = vc;
+            vc = vp;
+            vp = vn;
+            el = eln;
+            er = ern;
+            m = mn;
+        }
+    }
+    if (check && __any_sync(kFull, bad) && lane == 0) flag_status(I.status, kStatusNonFinite);
+    if (src_n < 0) {                                   // sources not binned: scan them, add atomically
+        __syncthreads();
+        const int bx0 = tx * 128, bx1 = min(bx0 + 128, f.nx);
+        const int by0 = ty * kPersistWarps * R, by1 = min(by0 + kPersistWarps * R, f.ny);
+        const long long n_cells = (long long)f.nx * f.ny;
+        for (int k = threadIdx.x; k < I.n_src; k += blockDim.x) {
+            const int c = __ldg(I.src_cell + k);
+            if (c < 0 || (long long)c >= n_cells) {
+                if (tile == 0) flag_status(I.status, kStatusBounds);
+                continue;
+            }
+            const int cx = c % f.nx, cy = c / f.nx;
+            if (cx >= bx0 && cx < bx1 && cy >= by0 && cy < by1)
+                atomicAdd(Cout + (size_t)cy * I.pitch + cx, __ldg(I.src_emit + k));
+        }
+    }
+}
+
 // Non-finite values persist once they appear, so the check runs on the last
 // step of a launch only (`check`).
 __device__ __forceinline__ void field_tile(const PInst &I, const float *Cin, float *Cout, const PItem &w, bool check)
@@ -349,6 +472,72 @@ __global__ void persist_advance(PCtrl *ctrl, int nsteps)
     ctrl->step0 += (uint32_t)nsteps;
 }
 
+// ---------------------------------------------------------------- one step per launch
+// The same work items as ordinary launches, for batches: step s of a run is
+// one launch over every instance's cone chunks (one chunk per block), then one
+// over every instance's field tiles (one tile per block, the tile function and
+// binned sources of the persistent kernel).  No grid barrier: the stream orders
+// the steps, and the hardware keeps as many small blocks resident as registers
+// allow.  Buffers and the Philox step come from the control block plus s, so a
+// captured graph replays without new arguments.
+// R > 0: field_tile_r<R>; R == 0: the streamed tile of I.rows rows.
+template <int R>
+__global__ void __launch_bounds__(kPersistThreads, R == 0 ? 6 : 1) step_tiles_kernel(const PInst *__restrict__ insts,
+                                                                     const PItem *__restrict__ items, int s,
+                                                                     const PCtrl *ctrl, int check)
+{
+    const PItem w = items[blockIdx.x];
+    const PInst &I = insts[w.inst];
+    const int cur = (ctrl->cur + s) & 1;
+    const float *Cin = cur ? I.field1 : I.field0;
+    float *Cout = cur ? I.field0 : I.field1;
+    if constexpr (R == 0) {
+        if (I.map) field_tile_stream<true>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check != 0);
+        else field_tile_stream<false>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check != 0);
+    } else {
+        if (I.map) field_tile_r<R, true>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check != 0);
+        else field_tile_r<R, false>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check != 0);
+    }
+}
+
+__device__ __forceinline__ void step_chunk(const PInst *insts, const PItem &w, int s, const PCtrl *ctrl)
+{
+    const PInst &I = insts[w.inst];
+    const int cur = (ctrl->cur + s) & 1;
+    const float *Cin = cur ? I.field1 : I.field0;
+    unsigned n_live = 0;
+    cone_chunk(I, Cin, ~w.idx, ctrl->step0 + (uint32_t)s, I.pos, I.dir, I.pos, I.dir, n_live);
+    const unsigned tot = __reduce_add_sync(kFull, n_live);
+    if (tot && (threadIdx.x & 31) == 0) atomicAdd(I.counter, (unsigned long long)tot);
+}
+
+__global__ void __launch_bounds__(kPersistThreads) step_chunks_kernel(const PInst *__restrict__ insts,
+                                                                      const PItem *__restrict__ items, int s,
+                                                                      const PCtrl *ctrl)
+{
+    step_chunk(insts, items[blockIdx.x], s, ctrl);
+}
+
+// Cone chunks and streamed tiles of one step in one launch: items[0, n_chunks)
+// are the chunks, then the tiles; the chunks' dependent loads overlap the tiles.
+__global__ void __launch_bounds__(kPersistThreads, 6) step_merged_kernel(const PInst *__restrict__ insts,
+                                                                         const PItem *__restrict__ items,
+                                                                         int n_chunks, int s, const PCtrl *ctrl,
+                                                                         int check)
+{
+    const PItem w = items[blockIdx.x];
+    if ((int)blockIdx.x < n_chunks) {
+        step_chunk(insts, w, s, ctrl);
+        return;
+    }
+    const PInst &I = insts[w.inst];
+    const int cur = (ctrl->cur + s) & 1;
+    const float *Cin = cur ? I.field1 : I.field0;
+    float *Cout = cur ? I.field0 : I.field1;
+    if (I.map) field_tile_stream<true>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check != 0);
+    else field_tile_stream<false>(I, Cin, Cout, w.idx, w.src_begin, w.src_n, check != 0);
+}
+
 int sm_count_p()
 {
     static int n = 0;
@@ -432,6 +621,31 @@ void persist_items(const std::vector<PInst> &insts, std::vector<PItem> &items)
     for (int k = 0; k < maxt; ++k)
         for (int i = 0; i < ni; ++i)
             if (k < ntile[i]) items.push_back(PItem{i, k, 0, 0});
+}
+
+cudaError_t step_launch(const PInst *d_insts, const PItem *d_chunks, int n_chunks, const PItem *d_tiles,
+                        int n_tiles, int rows, int nsteps, PCtrl *ctrl, cudaStream_t stream)
+{
+    for (int s = 0; s < nsteps; ++s) {
+        if (rows > 4 && n_chunks > 0 && n_tiles > 0 && d_tiles == d_chunks + n_chunks) {
+            // streamed tiles: the chunks and then the tiles (adjacent in the list) in one launch
+            step_merged_kernel<<<n_chunks + n_tiles, kPersistThreads, 0, stream>>>(d_insts, d_chunks, n_chunks, s,
+                                                                                   ctrl, s + 1 == nsteps);
+            continue;
+        }
+        if (n_chunks > 0) step_chunks_kernel<<<n_chunks, kPersistThreads, 0, stream>>>(d_insts, d_chunks, s, ctrl);
+        if (n_tiles > 0) {
+            const int check = s + 1 == nsteps;
+            if (rows == 1) step_tiles_kernel<1><<<n_tiles, kPersistThreads, 0, stream>>>(d_insts, d_tiles, s, ctrl, check);
+            else if (rows == 2)
+                step_tiles_kernel<2><<<n_tiles, kPersistThreads, 0, stream>>>(d_insts, d_tiles, s, ctrl, check);
+            else if (rows == 4)
+                step_tiles_kernel<4><<<n_tiles, kPersistThreads, 0, stream>>>(d_insts, d_tiles, s, ctrl, check);
+            else step_tiles_kernel<0><<<n_tiles, kPersistThreads, 0, stream>>>(d_insts, d_tiles, s, ctrl, check);
+        }
+    }
+    persist_advance<<<1, 1, 0, stream>>>(ctrl, nsteps);
+    return cudaGetLastError();
 }
 
 cudaError_t persist_launch(const PInst *d_insts, const PItem *d_items, int n_items, int nsteps, int cur0,

@@ -73,25 +73,41 @@ def test_batch_equals_each_instance_alone(cue, batch_mod, nsteps):
     b.close()
 
 
-@pytest.mark.parametrize("rows,blocks", [(1, 1), (2, 3), (4, 2)])
-def test_launch_shape_does_not_change_results(cue, batch_mod, rows, blocks):
+@pytest.mark.parametrize("rows,blocks,mode", [(1, 1, 1), (2, 3, 1), (4, 2, 1), (1, 0, 2), (2, 0, 2), (4, 0, 2),
+                                              (8, 0, 2), (16, 0, 2)])
+def test_launch_shape_does_not_change_results(cue, batch_mod, rows, blocks, mode):
+    """Persistent launches of any shape and one launch per step give every instance exactly
+    the state it reaches alone on the plain path, and the same cone-update count."""
     ws = _mixed()
     b = batch_mod.Batch(ws)
     b.set_option(batch_mod.CUE_BOPT_ROWS, rows)
     b.set_option(batch_mod.CUE_BOPT_BLOCKS, blocks)
+    b.set_option(batch_mod.CUE_BOPT_MODE, mode)
     b.run(12)
     b.check()
     assert b.get_option(batch_mod.CUE_BOPT_ROWS) == rows
+    assert b.get_option(batch_mod.CUE_BOPT_MODE) == mode
+    updates = b.cone_updates()
+    want_updates = 0
     for i, w in enumerate(ws):
-        _assert_same(b.snapshot(i), _alone(cue, w, 12), w.name)
+        alone = _alone(cue, w, 12)
+        _assert_same(b.snapshot(i), alone, w.name)
+    ref = batch_mod.Batch(ws)
+    ref.set_option(batch_mod.CUE_BOPT_MODE, 1)
+    ref.run(12)
+    want_updates = ref.cone_updates()
+    ref.close()
+    assert updates == want_updates
     b.close()
 
 
-def test_graph_replays_equal_direct_launches(cue, batch_mod):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_graph_replays_equal_direct_launches(cue, batch_mod, mode):
     ws = _mixed()
     a = batch_mod.Batch(ws)
     a.run(30)
     g = batch_mod.Batch(ws)
+    g.set_option(batch_mod.CUE_BOPT_MODE, mode)
     g.set_option(batch_mod.CUE_BOPT_GRAPH, 1)
     for _ in range(3):
         g.run(10)                                  # captured once, replayed twice
@@ -111,7 +127,8 @@ def test_autotune_restores_the_state_and_keeps_a_valid_shape(cue, batch_mod):
     before = [b.snapshot(i) for i in range(len(ws))]
     updates_before = b.cone_updates()
     rows, blocks, ms = b.autotune(4)
-    assert rows in (1, 2, 4) and 1 <= blocks <= 8 and ms > 0
+    assert rows in (1, 2, 4, 8, 16) and 0 <= blocks <= 8 and ms > 0
+    assert b.get_option(batch_mod.CUE_BOPT_MODE) == (2 if blocks == 0 else 1)
     assert b.get_option(batch_mod.CUE_BINFO_STEP) == 3
     for i in range(len(ws)):
         _assert_same(b.snapshot(i), before[i], ws[i].name)
