@@ -537,7 +537,7 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "axon_steps_per_s": world * cone_updates * args.steps / (total_ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": recorded_traffic("persist", "c4") if mode == 1 else None,
+                     "traffic": recorded_traffic("persist" if mode == 1 else "step", "c4"),
                      "kernel": "persist" if mode == 1 else "step launches (per run)", "peak_kind": peak_kind,
                      "launches": args.steps, "avg_launch_us": per_launch_s * 1e6, "steps_per_launch": T,
                      "algorithmic_bytes_per_launch": 8.0 * cells * T},
