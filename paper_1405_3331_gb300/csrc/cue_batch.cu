@@ -221,7 +221,8 @@ cudaError_t launch_direct(cue_batch *b, int nsteps)
     if (b->per_step()) {
         b->grid = b->n_step_tiles;
         return step_launch(b->d_inst(), b->d_step_items(), b->n_step_chunks, b->d_step_items() + b->n_step_chunks,
-                           b->n_step_tiles, b->rows_used, nsteps, b->ctrl(), b->stream);
+                           b->n_step_tiles, b->n_items == b->n_step_chunks + b->n_step_tiles ? b->d_items() : nullptr,
+                           b->rows_used, nsteps, b->ctrl(), b->stream);
     }
     return persist_launch(b->d_inst(), b->d_items(), b->n_items, nsteps, 0, 0, b->bar(), b->bpsm, 0, 0, b->status(),
                           b->stream, &b->grid, b->ctrl());

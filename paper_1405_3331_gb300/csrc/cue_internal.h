@@ -204,11 +204,13 @@ cudaError_t persist_launch(const PInst *d_insts, const PItem *d_items, int n_ite
                            unsigned *status, cudaStream_t stream, int *grid_out, PCtrl *ctrl = nullptr);
 // A batch's steps as ordinary launches (no grid barrier): per step one launch
 // over the cone-chunk items d_chunks, then one over the field-tile items
-// d_tiles (tiles of `rows` rows per warp, as the instance table says);
-// buffers and the Philox step from *ctrl plus the step index, and *ctrl
-// advanced by nsteps at the end.  The non-finite check runs on the last step.
+// d_tiles (tiles of `rows` rows per warp, as the instance table says); for
+// rows > 4 (streamed tiles) instead one launch over d_mixed, the same
+// n_chunks + n_tiles items in instance order.  Buffers and the Philox step
+// from *ctrl plus the step index, and *ctrl advanced by nsteps at the end.
+// The non-finite check runs on the last step.
 cudaError_t step_launch(const PInst *d_insts, const PItem *d_chunks, int n_chunks, const PItem *d_tiles,
-                        int n_tiles, int rows, int nsteps, PCtrl *ctrl, cudaStream_t stream);
+                        int n_tiles, const PItem *d_mixed, int rows, int nsteps, PCtrl *ctrl, cudaStream_t stream);
 // Runs nsteps on the persistent path when selected (or AUTO) and supported:
 // CUE_OK / negative error when it ran, 1 when the caller should fall back.
 int run_persist_if_supported(Sim &s, int nsteps);

@@ -518,15 +518,16 @@ __global__ void __launch_bounds__(kPersistThreads) step_chunks_kernel(const PIns
     step_chunk(insts, items[blockIdx.x], s, ctrl);
 }
 
-// Cone chunks and streamed tiles of one step in one launch: items[0, n_chunks)
-// are the chunks, then the tiles; the chunks' dependent loads overlap the tiles.
+// Cone chunks and streamed tiles of one step in one launch, one item per block,
+// over the instance-ordered list (each instance's tiles, then its cone chunks):
+// blocks start roughly in index order, so an instance's cones gather from rows
+// its tiles have just brought into L2.
 __global__ void __launch_bounds__(kPersistThreads, 6) step_merged_kernel(const PInst *__restrict__ insts,
-                                                                         const PItem *__restrict__ items,
-                                                                         int n_chunks, int s, const PCtrl *ctrl,
-                                                                         int check)
+                                                                         const PItem *__restrict__ items, int s,
+                                                                         const PCtrl *ctrl, int check)
 {
     const PItem w = items[blockIdx.x];
-    if ((int)blockIdx.x < n_chunks) {
+    if (w.idx < 0) {
         step_chunk(insts, w, s, ctrl);
         return;
     }
@@ -624,13 +625,13 @@ void persist_items(const std::vector<PInst> &insts, std::vector<PItem> &items)
 }
 
 cudaError_t step_launch(const PInst *d_insts, const PItem *d_chunks, int n_chunks, const PItem *d_tiles,
-                        int n_tiles, int rows, int nsteps, PCtrl *ctrl, cudaStream_t stream)
+                        int n_tiles, const PItem *d_mixed, int rows, int nsteps, PCtrl *ctrl, cudaStream_t stream)
 {
     for (int s = 0; s < nsteps; ++s) {
-        if (rows > 4 && n_chunks > 0 && n_tiles > 0 && d_tiles == d_chunks + n_chunks) {
-            // streamed tiles: the chunks and then the tiles (adjacent in the list) in one launch
-            step_merged_kernel<<<n_chunks + n_tiles, kPersistThreads, 0, stream>>>(d_insts, d_chunks, n_chunks, s,
-                                                                                   ctrl, s + 1 == nsteps);
+        if (rows > 4 && d_mixed && n_chunks + n_tiles > 0) {
+            // streamed tiles: every item of the instance-ordered list in one launch
+            step_merged_kernel<<<n_chunks + n_tiles, kPersistThreads, 0, stream>>>(d_insts, d_mixed, s, ctrl,
+                                                                                   s + 1 == nsteps);
             continue;
         }
         if (n_chunks > 0) step_chunks_kernel<<<n_chunks, kPersistThreads, 0, stream>>>(d_insts, d_chunks, s, ctrl);
