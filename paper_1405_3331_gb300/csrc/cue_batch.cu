@@ -254,11 +254,20 @@ int run_graph(cue_batch *b, int nsteps)
     return cudaGraphLaunch(b->graph, b->stream) == cudaSuccess ? CUE_OK : CUE_ERR_CUDA;
 }
 
+// Longest graph of the per-step mode (one node per time step): longer runs
+// replay it, then launch the remainder directly.  The buffer parity and the
+// step counter live on the device, so the pieces chain without new arguments.
+constexpr int kStepGraphMax = 1024;
+
 int run_batch(cue_batch *b, int nsteps)
 {
     int rc = stage_list(b);
     if (rc != CUE_OK) return rc;
-    if (b->use_graph) {
+    if (b->use_graph && b->per_step() && nsteps > kStepGraphMax) {
+        for (int i = 0; i < nsteps / kStepGraphMax && rc == CUE_OK; ++i) rc = run_graph(b, kStepGraphMax);
+        if (rc == CUE_OK && nsteps % kStepGraphMax)
+            rc = launch_direct(b, nsteps % kStepGraphMax) == cudaSuccess ? CUE_OK : CUE_ERR_CUDA;
+    } else if (b->use_graph) {
         rc = run_graph(b, nsteps);
     } else {
         rc = launch_direct(b, nsteps) == cudaSuccess ? CUE_OK : CUE_ERR_CUDA;

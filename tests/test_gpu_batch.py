@@ -151,3 +151,26 @@ def test_batched_workload_sample_equals_instances_alone(cue, batch_mod):
     for i, w in enumerate(ws):
         _assert_same(b.snapshot(i), _alone(cue, w, 8), w.name)
     b.close()
+
+
+def test_long_per_step_runs_replay_a_bounded_graph(cue, batch_mod):
+    """A per-step run longer than one captured graph replays the graph and launches the
+    remainder; the result is that of direct launches, bit for bit."""
+    ws = _mixed()
+    a = batch_mod.Batch(ws)
+    a.set_option(batch_mod.CUE_BOPT_MODE, 2)
+    a.set_option(batch_mod.CUE_BOPT_ROWS, 8)
+    a.run(2500)
+    g = batch_mod.Batch(ws)
+    g.set_option(batch_mod.CUE_BOPT_MODE, 2)
+    g.set_option(batch_mod.CUE_BOPT_ROWS, 8)
+    g.set_option(batch_mod.CUE_BOPT_GRAPH, 1)
+    g.run(2500)
+    a.check()
+    g.check()
+    assert g.get_option(batch_mod.CUE_BINFO_STEP) == 2500
+    for i, w in enumerate(ws):
+        _assert_same(a.snapshot(i), g.snapshot(i), w.name)
+    assert a.cone_updates() == g.cone_updates()
+    a.close()
+    g.close()
