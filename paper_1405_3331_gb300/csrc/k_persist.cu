@@ -196,12 +196,9 @@ __device__ __forceinline__ void field_tile_stream(const PInst &I, const float *C
     if (y0 < f.ny) {                                   // warp-uniform
         const int y1 = min(y0 + R, f.ny);
         auto row = [&](int y) { return xin ? __ldcg(col + (size_t)min(max(y, 0), f.ny - 1) * p4) : z4; };
-        auto edge_l = [&](int y) {
-            return (lane == 0 && xin && has_l) ? __ldcg(Cin + (size_t)min(y, f.ny - 1) * I.pitch + x - 1) : 0.f;
-        };
-        auto edge_r = [&](int y) {
-            return (lane == 31 && xin && has_r) ? __ldcg(Cin + (size_t)min(y, f.ny - 1) * I.pitch + x + 4) : 0.f;
-        };
+        const bool need_l = lane == 0 && xin && has_l, need_r = lane == 31 && xin && has_r;
+        auto edge_l = [&](int y) { return need_l ? __ldcg(Cin + (size_t)min(y, f.ny - 1) * I.pitch + x - 1) : 0.f; };
+        auto edge_r = [&](int y) { return need_r ? __ldcg(Cin + (size_t)min(y, f.ny - 1) * I.pitch + x + 4) : 0.f; };
         auto map_row = [&](int y) {
             return (MAP && xin) ? __ldg(m4 + (size_t)min(y, f.ny - 1) * p4 + x4) : z4;
         };
@@ -215,14 +212,12 @@ __device__ __forceinline__ void field_tile_stream(const PInst &I, const float *C
             const float4 vn = more ? row(y + 2) : z4;
             const float eln = more ? edge_l(y + 1) : 0.f, ern = more ? edge_r(y + 1) : 0.f;
             const float4 mn = more ? map_row(y + 1) : z4;
-            const float4 cur = vc;
-            const float4 up = y > 0 ? vm : cur;
-            const float4 dn = y + 1 < f.ny ? vp : cur;
+            // rows y - 1 and y + 1 were loaded clamped: at a wall they are row y itself
+            const float4 cur = vc, up = vm, dn = vp;
             float l = __shfl_up_sync(kFull, cur.w, 1);
             float r = __shfl_down_sync(kFull, cur.x, 1);
-            if (lane == 0) l = has_l ? el : cur.x;
-            if (lane == 31) r = has_r ? er : cur.w;
-            if (!has_l) l = cur.x;
+            if (lane == 0) l = has_l ? el : cur.x;     // only lane 0 can lack a left neighbour
+            if (lane == 31) r = er;
             if (!has_r) r = cur.w;
             if (xin) {
                 float4 o;
