@@ -1,15 +1,17 @@
 /*
  * cue_batch.h -- many independent 2D cue-field / growth-cone simulations of
- * uneven sizes and parameters stepped together by one persistent launch.
+ * uneven sizes and parameters stepped together.
  *
  * Each instance is the model of cue.h (Sec. 5.2 field update with no-flux
  * walls, decay and point sources; Sec. 3.5 growth-cone steering with Philox
  * noise; Sec. 3.3-3.4 stop tests), with its own grid, physics, sources and
- * cones.  The paper steps one environment; running many small ones in one
- * launch is this library's own addition.  One cue_batch_run call is one
- * cooperative launch (or one replay of a captured CUDA graph holding it): per
- * step every block takes field tiles and cone chunks from a work list that
- * interleaves all instances, then the blocks meet at a bounded grid barrier.
+ * cones.  The paper steps one environment; running many in one launch is this
+ * library's own addition.  All instances' field tiles and cone chunks form
+ * one work list, instance by instance.  A cue_batch_run call runs it in one
+ * of two modes (CUE_BOPT_MODE; the autotuner picks): one cooperative launch
+ * in which every block takes items each step and the blocks meet at a
+ * bounded grid barrier between steps, or one ordinary launch per step with
+ * one item per block; either can be replayed from a captured CUDA graph.
  * Per node and per cone the arithmetic is cue.h's plain path, so an instance
  * here evolves bit for bit as it would alone (source cells distinct).
  *
