@@ -249,3 +249,48 @@ def test_full_size_persistent_backward_equals_two_launch_backward(cue):
         x, y = a[key].astype(np.float64), b[key].astype(np.float64)
         scale = max(np.abs(y).max(), 1e-30)
         assert np.abs(x - y).max() <= 1e-4 * scale, key
+
+
+def test_adjoint_full_horizon_on_the_small_copy_is_reported(cue, record_property):
+    """The adjoint workload's 64x64 copy over its full 2,000 steps (checkpoint every 64): the
+    GPU gradients, the FP64 oracle's adjoint and FP64 central differences of the oracle's loss
+    for D, lambda and each emission, recorded as relative differences.  Over this horizon
+    the cones orbit the sources and the derivative is ill-conditioned (the oracle's own
+    spread under FP32-sized perturbations is recorded beside it), so the numbers are a
+    report, not a pass criterion; the run must stay finite and the loss must agree."""
+    w, T = _copy64(seed=50), 2000
+    g = _gpu(cue, w, T, 64)
+    ref = _oracle(w, T)
+    loss, gD, gl, gsrc, _ = ref
+    c = cone_of(w)
+    C0 = w.field0().astype(np.float64)
+
+    def loss_at(D=w.D, lam=w.lam, emit=w.src_emit):
+        grid = oracle.Grid(2, w.nx, w.ny, h=w.h, D=D, lam=lam, dt=w.dt)
+        return oracle.endpoint_loss(grid, c, C0, w.src_cell, emit, w.src_map, w.pos, w.dir, w.targets, T)
+
+    hD, hl = 1e-6 * w.D, 1e-5 * w.lam
+    fd = {"dD": (loss_at(D=w.D + hD) - loss_at(D=w.D - hD)) / (2 * hD),
+          "dlambda": (loss_at(lam=w.lam + hl) - loss_at(lam=w.lam - hl)) / (2 * hl)}
+    fd_src = []
+    for k in range(w.n_src):
+        e1, e2 = w.src_emit.astype(np.float64).copy(), w.src_emit.astype(np.float64).copy()
+        h = 1e-5 * e1[k]
+        e1[k] += h
+        e2[k] -= h
+        fd_src.append((loss_at(emit=e1) - loss_at(emit=e2)) / (2 * h))
+    for key in ("loss", "dD", "dlambda", "dsrc", "dmap"):
+        assert np.isfinite(g[key]).all(), key
+    assert _rel(float(g["loss"]), loss) < 1e-3
+    record_property("gpu_vs_oracle_dD", _rel(float(g["dD"]), gD))
+    record_property("gpu_vs_oracle_dlambda", _rel(float(g["dlambda"]), gl))
+    record_property("gpu_vs_oracle_dsrc", _relmax(g["dsrc"], gsrc))
+    record_property("oracle_vs_fd_dD", _rel(gD, fd["dD"]))
+    record_property("oracle_vs_fd_dlambda", _rel(gl, fd["dlambda"]))
+    record_property("oracle_vs_fd_dsrc", _relmax(gsrc, fd_src))
+    record_property("gpu_vs_fd_dD", _rel(float(g["dD"]), fd["dD"]))
+    record_property("gpu_vs_fd_dlambda", _rel(float(g["dlambda"]), fd["dlambda"]))
+    record_property("gpu_vs_fd_dsrc", _relmax(g["dsrc"], fd_src))
+    print("full-horizon 64x64 adjoint, relative differences:",
+          {"gpu_vs_oracle": [_rel(float(g["dD"]), gD), _rel(float(g["dlambda"]), gl), _relmax(g["dsrc"], gsrc)],
+           "oracle_vs_fd": [_rel(gD, fd["dD"]), _rel(gl, fd["dlambda"]), _relmax(gsrc, fd_src)]})
