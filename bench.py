@@ -197,6 +197,26 @@ def oracle_sample(w, budget_s):
     return nsteps, dt
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def oracle_threads_child(spec):
     """Child process: the oracle on the first NSTEPS steps of WORKLOAD with the field's node
     loop over THREADS threads; prints {"seconds", "threads", "nsteps"}."""
@@ -266,7 +286,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": describe(w),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count(), "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -458,7 +479,8 @@ def main():
         sample = f"first {nsteps} of {w.nsteps} time steps of the same workload (FP64)"
         line["cpu_baseline"] = {
             "value": w.n_cells * nsteps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": sample + ", one thread", "seconds": secs}
+            "sample": sample + ", one thread", "seconds": secs, "host_cores": os.cpu_count(),
+            "cpu_model": cpu_model()}
         line["cpu_baseline_threads"] = oracle_threads_sample(args.workload, w.n_cells, nsteps, sample)
     sim.close()
     if rank == 0:
@@ -606,7 +628,8 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
         sample = f"instance 0 ({ws[0].nx}x{ws[0].ny}), first {nsteps} of {T} steps (FP64)"
         line["cpu_baseline"] = {
             "value": ws[0].n_cells * nsteps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": sample + ", one thread", "seconds": secs}
+            "sample": sample + ", one thread", "seconds": secs, "host_cores": os.cpu_count(),
+            "cpu_model": cpu_model()}
         line["cpu_baseline_threads"] = oracle_threads_sample("c4", ws[0].n_cells, nsteps, sample)
     b.close()
     if rank == 0:
