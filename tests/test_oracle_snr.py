@@ -164,3 +164,22 @@ def test_snr_shape_in_concentration_steepness_and_angle():
         gx, gy = math.cos(math.pi / 2 - phi), math.sin(math.pi / 2 - phi)   # gradient phi right of +y
         s = oracle.snr(c, 4.0, [0.1 * gx, 0.1 * gy], d)
         assert s == pytest.approx(ratio * oracle.snr(c, 4.0, [0.1, 0.0], d), rel=1e-12)
+
+
+def test_cue_value_reproduces_bilinear_fields():
+    """The SNR rule reads C at the tip by bilinear interpolation (Sec. 3.5): any field
+    a + b x + c y + e x y is reproduced exactly between the nodes, and a node's value is
+    returned at the node itself, the last row and column included."""
+    nx, ny, h = 40, 30, 0.5
+    g = Grid(2, nx, ny, h=h, D=0.0, lam=0.0, dt=0.2)
+    x = np.arange(nx) * h
+    y = np.arange(ny) * h
+    a, b, c, e = 1.5, -0.3, 0.7, 0.05
+    C = a + b * x[None, :] + c * y[:, None] + e * x[None, :] * y[:, None]
+    rng = np.random.default_rng(21)
+    p = np.stack([rng.uniform(0, x[-1], 400), rng.uniform(0, y[-1], 400)], axis=1)
+    want = a + b * p[:, 0] + c * p[:, 1] + e * p[:, 0] * p[:, 1]
+    np.testing.assert_allclose(oracle.value_at(g, C, p), want, rtol=1e-13, atol=1e-13)
+    corners = [(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1), (17, 9)]
+    got = oracle.value_at(g, C, [(i * h, j * h) for i, j in corners])
+    np.testing.assert_allclose(got, [C[j, i] for i, j in corners], rtol=1e-14)
