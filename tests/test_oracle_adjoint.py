@@ -8,16 +8,17 @@ import oracle
 from oracle import Cone, Grid
 
 
-def _problem(dim, seed=0, T=30):
+def _problem(dim, seed=0, T=30, h=1.0):
+    """D scales with h^2, so alpha = D dt / h^2 (and stability) does not depend on h."""
     rng = np.random.default_rng(seed)
     if dim == 2:
         nx, ny, nz = 17, 13, 1
         shape = (ny, nx)
-        g = Grid(2, nx, ny, h=1.0, D=0.9, lam=0.02, dt=0.2)
+        g = Grid(2, nx, ny, h=h, D=0.9 * h * h, lam=0.02, dt=0.2)
     else:
         nx, ny, nz = 9, 8, 7
         shape = (nz, ny, nx)
-        g = Grid(3, nx, ny, nz, h=1.0, D=0.8, lam=0.03, dt=0.15)
+        g = Grid(3, nx, ny, nz, h=h, D=0.8 * h * h, lam=0.03, dt=0.15)
     n_cells = int(np.prod(shape))
     cells = rng.choice(n_cells, 3, replace=False).astype(np.int32)
     emit = rng.uniform(0.5, 2.0, 3)
@@ -25,11 +26,11 @@ def _problem(dim, seed=0, T=30):
     C0 = rng.uniform(0.0, 1.0, shape)
     n = 6
     ext = np.array((nx, ny, nz)[:dim], float)
-    pos = 1.5 + rng.uniform(0, 1, (dim, n)) * (ext[:, None] - 3)
+    pos = (1.5 + rng.uniform(0, 1, (dim, n)) * (ext[:, None] - 3)) * h
     d = rng.standard_normal((dim, n))
     d /= np.linalg.norm(d, axis=0)
-    tg = rng.uniform(0, 1, (dim, n)) * (ext[:, None] - 1)
-    c = Cone(w_prev=0.5, w_grad=0.4, w_noise=0.1, step_len=0.5, stop_radius=0.0, wall_mode=1, seed=77)
+    tg = rng.uniform(0, 1, (dim, n)) * (ext[:, None] - 1) * h
+    c = Cone(w_prev=0.5, w_grad=0.4, w_noise=0.1, step_len=0.5 * h, stop_radius=0.0, wall_mode=1, seed=77)
     return g, c, C0, cells, emit, smap, pos, d, tg, T
 
 
@@ -37,9 +38,9 @@ def _loss(g, c, C0, cells, emit, smap, pos, d, tg, T):
     return oracle.endpoint_loss(g, c, C0, cells, emit, smap, pos, d, tg, T)
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_adjoint_matches_central_differences(dim):
-    g, c, C0, cells, emit, smap, pos, d, tg, T = _problem(dim)
+@pytest.mark.parametrize("dim,h", [(2, 1.0), (3, 1.0), (2, 0.7), (3, 1.3)])
+def test_adjoint_matches_central_differences(dim, h):
+    g, c, C0, cells, emit, smap, pos, d, tg, T = _problem(dim, h=h)
     loss, gD, gl, gsrc, gmap = oracle.adjoint(g, c, C0, cells, emit, smap, pos, d, tg, T)
     assert loss == pytest.approx(_loss(g, c, C0, cells, emit, smap, pos, d, tg, T), rel=1e-14)
 

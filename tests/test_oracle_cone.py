@@ -77,6 +77,22 @@ def test_node_gradient_on_walls_is_half_one_sided_difference():
                                [(C[1, 3] - C[1, 1]) / (2 * h), (C[2, 2] - C[0, 2]) / (2 * h)])
 
 
+def test_node_gradient_on_3d_walls():
+    """3D: every axis takes half the one-sided difference on both of its walls and the central
+    difference one node inside them (the z axis included)."""
+    rng = np.random.default_rng(12)
+    nx, ny, nz, h = 5, 4, 6, 0.6
+    C = rng.uniform(0, 1, (nz, ny, nx))
+    g = Grid(3, nx, ny, nz, h=h)
+    for (i, j, k) in [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (1, 2, nz - 2), (nx - 2, 1, 1), (2, ny - 2, nz - 1)]:
+        ip, im = min(i + 1, nx - 1), max(i - 1, 0)
+        jp, jm = min(j + 1, ny - 1), max(j - 1, 0)
+        kp, km = min(k + 1, nz - 1), max(k - 1, 0)
+        want = [(C[k, j, ip] - C[k, j, im]) / (2 * h), (C[k, jp, i] - C[k, jm, i]) / (2 * h),
+                (C[kp, j, i] - C[km, j, i]) / (2 * h)]
+        np.testing.assert_allclose(oracle.node_gradient(g, C, i, j, k), want, rtol=1e-14, err_msg=str((i, j, k)))
+
+
 def test_bilinear_corners_by_hand():
     """p = (1.25, 2.5) on a 4x5 grid: corners (1,2) (2,2) (1,3) (2,3), weights written out."""
     rng = np.random.default_rng(3)
@@ -285,6 +301,11 @@ def test_source_radius_stop_after_move():
     # at distance 2.6: after the move 2.1 > 2, still active
     pos, dirs, act = oracle.cone_step(g, cone, C, 0, *_one(2, [9.4, 10.0], [1.0, 0.0]), src)
     assert act[0] == 1
+    # landing exactly on the radius (every quantity exact in binary): the test is inclusive
+    exact = Cone(w_prev=1.0, w_grad=0.0, w_noise=0.0, step_len=0.5, stop_radius=2.0)
+    pos, dirs, act = oracle.cone_step(g, exact, C, 0, *_one(2, [9.5, 10.0], [1.0, 0.0]), src)
+    np.testing.assert_array_equal(pos[:, 0], [10.0, 10.0])
+    assert act[0] == 0
     # 3D: node index -> coordinates uses x fastest, then y, then z
     g3 = Grid(3, 6, 7, 8)
     cell = 4 + 6 * (5 + 7 * 3)          # node (4, 5, 3)

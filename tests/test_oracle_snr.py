@@ -109,6 +109,29 @@ def test_snr_is_odd_in_the_heading_relative_to_the_gradient():
     assert oracle.snr(c, Cp, grad, [1.0, 0.0]) == pytest.approx(0.0, abs=1e-15)
 
 
+def test_turn_decision_uses_the_cones_first_normal_draw():
+    """The draw from N(SNR, 1) is SNR plus the cone's first normal deviate of that step, the one
+    the vector-addition rule adds to its x component: cone a at step n turns right exactly when
+    SNR + xi_0(seed, a, n) > 0."""
+    g = Grid(2, 200, 200, h=1.0, D=0.0, lam=0.0, dt=0.2)
+    C = _ramp(slope=0.02)
+    n = 4000
+    rng = np.random.default_rng(17)
+    p = np.stack([rng.uniform(20, 180, n), rng.uniform(20, 180, n)])
+    th = rng.uniform(0, 2 * np.pi, n)
+    d = np.stack([np.cos(th), np.sin(th)])
+    c = _snr_cone(snr_gain=20.0, snr_kd=3.0, snr_width=2.0, seed=31)
+    step = 5
+    _, dn, _ = oracle.cone_step(g, c, C, step, p, d, np.ones(n, np.uint8))
+    right = d[0] * dn[1] - d[1] * dn[0] < 0
+    xi = oracle.noise(31, np.arange(n, dtype=np.uint32), np.full(n, step, np.uint32), 2)
+    Cp = oracle.value_at(g, C, p.T)
+    grad = oracle.gradient_at(g, C, p.T)[:, :2]
+    s = np.array([oracle.snr(c, Cp[a], grad[a], d[:, a]) for a in range(n)])
+    assert 0.2 < np.mean(right) < 0.8 and np.mean(np.abs(s) < 1.5) > 0.3      # decisions not all forced
+    np.testing.assert_array_equal(right, s + xi[:, 0] > 0)
+
+
 def test_outside_the_window_the_cone_keeps_its_direction():
     g = Grid(2, 200, 200, h=1.0, D=0.0, lam=0.0, dt=0.2)
     C = _ramp()                                         # values 1 .. 3
@@ -157,6 +180,8 @@ def test_snr_shape_in_concentration_steepness_and_angle():
     assert oracle.snr(_snr_cone(snr_gain=6.0, snr_width=2.0, snr_kd=4.0), 4.0, [0.1, 0.0], d) == \
         pytest.approx(2 * oracle.snr(c, 4.0, [0.1, 0.0], d), rel=1e-14)
     assert oracle.snr(c, 4.0, [0.3, 0.0], d) == pytest.approx(3 * oracle.snr(c, 4.0, [0.1, 0.0], d), rel=1e-14)
+    assert oracle.snr(_snr_cone(snr_gain=3.0, snr_width=5.0, snr_kd=4.0), 4.0, [0.1, 0.0], d) == \
+        pytest.approx(2.5 * oracle.snr(c, 4.0, [0.1, 0.0], d), rel=1e-14)
     assert at_gamma(0.5) > at_gamma(0.49) and at_gamma(0.5) > at_gamma(0.51)
     assert at_gamma(4e-8) / at_gamma(1e-8) == pytest.approx(2.0, rel=1e-6)
     assert base > 0
