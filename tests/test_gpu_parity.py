@@ -170,6 +170,92 @@ def test_noise_direction_matches_oracle(cue):
         sim.close()
 
 
+def _on_walls(rng, dim, hi, n):
+    """n uniform positions, each with one to dim coordinates moved onto a wall (0 or hi)."""
+    pos = rng.uniform(0.0, 1.0, (dim, n)) * hi[:, None]
+    for a in range(n):
+        for ax in rng.choice(dim, int(rng.integers(1, dim + 1)), replace=False):
+            pos[ax, a] = 0.0 if rng.integers(2) == 0 else hi[ax]
+    return pos
+
+
+@pytest.mark.parametrize("dim,wall_mode", [(2, 0), (2, 1), (3, 0), (3, 1)])
+def test_cones_on_every_wall(cue, dim, wall_mode):
+    """Cones exactly on the walls, edges and corners of every axis: the gradient is sampled in
+    the clamped last cell (weight 1 on the far nodes) from wall nodes with ghost values, and the
+    move takes the wall rule; the cone step alone and the coupled step against the oracle."""
+    if dim == 2:
+        w = W.make("walls2d", 2, 37, 29, n_src=3, n_axons=1, C0="smooth", seed=40, wall_mode=wall_mode)
+    else:
+        w = W.make("walls3d", 3, 21, 18, 15, dt=0.15, n_src=3, n_axons=1, C0="smooth", seed=41,
+                   wall_mode=wall_mode)
+    hi = (np.array([w.nx, w.ny, w.nz][:dim], np.float64) - 1) * w.h
+    rng = np.random.default_rng(42 + dim)
+    n = 3000
+    w.pos = _on_walls(rng, dim, hi, n).astype(np.float32)
+    d = rng.standard_normal((dim, n))
+    w.dir = (d / np.linalg.norm(d, axis=0)).astype(np.float32)
+    w.active = np.ones(n, np.uint8)
+    C0 = w.field0()
+    for run in (False, True):
+        sim = _sim(cue, w, step=321)
+        if run:
+            sim.sim_run(1)
+        else:
+            sim.cone_step(1)
+        sim.check()
+        _, pos, dirs, act, _, _ = sim.snapshot()
+        _compare_cones(w, C0, 321, w.pos, w.dir, w.active, pos, dirs, act)
+        if wall_mode == 0:
+            assert 0 < int((act == 0).sum()) < n          # some leave through a wall and stop
+        else:
+            assert act.all()
+            assert ((pos >= 0) & (pos <= hi[:, None].astype(np.float32))).all()
+        sim.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_stop_exactly_at_the_radius(cue, dim):
+    """No cue and no noise (weights 1, 0, 0), axis-aligned moves of 0.5 onto or short of the stop
+    radius 2 of a source: every quantity is exact in binary32, so the GPU must take the oracle's
+    inclusive decision, ||p' - x||^2 <= r^2."""
+    if dim == 2:
+        w = W.make("radius2d", 2, 40, 30, n_src=1, n_axons=1, seed=43, stop_radius=2.0, w=(1.0, 0.0, 0.0))
+        xs = np.array([12.0, 10.0])
+        w.src_cell = np.array([12 + 40 * 10], np.int32)
+    else:
+        w = W.make("radius3d", 3, 20, 16, 12, dt=0.15, n_src=1, n_axons=1, seed=44, stop_radius=2.0,
+                   w=(1.0, 0.0, 0.0))
+        xs = np.array([6.0, 5.0, 4.0])
+        w.src_cell = np.array([6 + 20 * (5 + 16 * 4)], np.int32)
+    starts, heads, want_act = [], [], []
+    for ax in range(dim):
+        for sgn in (1.0, -1.0):
+            e = np.zeros(dim)
+            e[ax] = sgn
+            for dist, stops in ((2.5, 0), (2.75, 1)):          # lands at 2.0 (stops) or 2.25
+                starts.append(xs - dist * e)
+                heads.append(e)
+                want_act.append(stops)
+    w.pos = np.array(starts, np.float32).T.copy()
+    w.dir = np.array(heads, np.float32).T.copy()
+    w.active = np.ones(len(starts), np.uint8)
+    for run in (False, True):
+        sim = _sim(cue, w, step=5)
+        if run:
+            sim.sim_run(1)
+        else:
+            sim.cone_step(1)
+        sim.check()
+        _, pos, dirs, act, _, _ = sim.snapshot()
+        np.testing.assert_array_equal(pos, w.pos + 0.5 * w.dir)
+        np.testing.assert_array_equal(act, want_act)
+        _, _, ract = oracle.cone_step(grid_of(w), cone_of(w), w.field0().astype(np.float64), 5, w.pos,
+                                      w.dir, w.active, w.src_cell)
+        np.testing.assert_array_equal(act, ract)
+        sim.close()
+
+
 def test_empty_inputs(cue):
     w = W.make("empty", 2, 64, 32, n_src=0, n_axons=0, C0="smooth", seed=21)
     sim = _sim(cue, w)
