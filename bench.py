@@ -40,7 +40,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cue", "reference"], default="cue")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
-    ap.add_argument("--path", default="auto", choices=["auto", "plain", "fused", "persist"])
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "fused", "persist", "resident"])
     ap.add_argument("--depth", type=int, default=0, help="temporal depth on the fused path (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -344,7 +344,7 @@ def main():
     if args.run_steps:
         w.nsteps = args.run_steps
     path = {"auto": cue.CUE_PATH_AUTO, "plain": cue.CUE_PATH_PLAIN, "fused": cue.CUE_PATH_FUSED,
-            "persist": cue.CUE_PATH_PERSIST}[args.path]
+            "persist": cue.CUE_PATH_PERSIST, "resident": cue.CUE_PATH_RESIDENT}[args.path]
     sim = cue.Simulation(w, device=dev, path=path)
     if args.depth:
         sim.set_option(cue.CUE_OPT_TEMPORAL_DEPTH, args.depth)
@@ -375,8 +375,8 @@ def main():
            for _ in range(args.steps)]
     sampler = ClockSampler(gpu_id_for(local))
     # events around every 16th launch of the dominant kernel (every launch on the persistent
-    # path, where one launch is a whole run)
-    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 1 if sim_path_used(sim) == "persist" else 16)
+    # and resident paths, where one launch is a whole run)
+    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 1 if sim_path_used(sim) in ("persist", "resident") else 16)
     sim.kernel_time()
     barrier()
     sampler.start()
@@ -406,9 +406,9 @@ def main():
     if kern_n:
         steps_per_launch = (w.nsteps / (launches_per_run(sim, w)))
         # compulsory field traffic of one launch: the fused kernel reads and writes the field once
-        # for its K steps; the plain kernel once per step; the persistent kernel once per step of
-        # the whole run it covers
-        per_launch_passes = steps_per_launch if sim_path_used(sim) == "persist" else 1
+        # for its K steps; the plain kernel once per step; the persistent and resident kernels
+        # once per step of the whole run they cover
+        per_launch_passes = steps_per_launch if sim_path_used(sim) in ("persist", "resident") else 1
         alg_bytes = bytes_per_cell * w.n_cells * per_launch_passes
         if w.dim == 3 and sim_path_used(sim) == "plain":
             # the 3D step launch also moves the cones: position and direction read and
@@ -418,7 +418,7 @@ def main():
         achieved = alg_bytes / avg_s / 1e9
     else:
         steps_per_launch, alg_bytes, avg_s, achieved = 0, 0, 0, 0.0
-    kname = {"fused": "fused", "persist": "persist"}.get(sim_path_used(sim), "field")
+    kname = {"fused": "fused", "persist": "persist", "resident": "resident"}.get(sim_path_used(sim), "field")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm if hbm else None,
                 "traffic": recorded_traffic(kname, args.workload),
@@ -429,6 +429,10 @@ def main():
     # a temporally blocked launch moves its field through HBM once for K steps: the bytes an
     # unblocked kernel would move for the same node updates, against the same peak
     roofline["effective_frac"] = roofline["effective_gbs"] / hbm if hbm else None
+    if kname == "resident":
+        roofline["note"] = ("one block holds the grid in shared memory for the whole run: HBM is read "
+                            "and written once per launch, and a step is bound by one SM's shared-memory "
+                            "and issue rate; achieved counts 8 B per node update as for the other kernels")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -677,19 +681,20 @@ def adjoint_timing(cue, torch, sim, w, reset, stream, flush, forward_ms):
 
 def launches_per_run(sim, w):
     """Launches of the dominant kernel in one run (K steps per launch on the fused path, the
-    whole run per launch on the persistent path)."""
+    whole run per launch on the persistent and resident paths)."""
     from paper_1405_3331_gb300 import cue
     if sim.fused_active():
         K = sim.get_option(cue.CUE_INFO_DEPTH)
         return (w.nsteps + K - 1) // K
-    if sim_path_used(sim) == "persist":
+    if sim_path_used(sim) in ("persist", "resident"):
         return 1
     return w.nsteps
 
 
 def sim_path_used(sim):
     from paper_1405_3331_gb300 import cue
-    return {cue.CUE_PATH_FUSED: "fused", cue.CUE_PATH_PERSIST: "persist"}.get(sim.last_path(), "plain")
+    return {cue.CUE_PATH_FUSED: "fused", cue.CUE_PATH_PERSIST: "persist",
+            cue.CUE_PATH_RESIDENT: "resident"}.get(sim.last_path(), "plain")
 
 
 def hbm_probe(cue, torch, dev, hbm, dim=2):

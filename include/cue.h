@@ -119,12 +119,16 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
 #define CUE_INFO_DEPTH         18  /* temporal depth the fused path runs with                 */
 #define CUE_INFO_GRID          19  /* blocks of the last persistent launch                    */
 #define CUE_PATH_AUTO   0          /* library picks: fused for grids of at least one tile per
-                                      SM, else persistent, else plain                       */
+                                      SM, else resident, else persistent, else plain         */
 #define CUE_PATH_PLAIN  1          /* one launch per half-step: cone kernel, field kernel  */
 #define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel       */
 #define CUE_PATH_PERSIST 3         /* 2D, nx % 4 == 0: one cooperative launch for the whole
                                       run; per step one pass over field tiles and cone
                                       chunks, then a bounded grid barrier                   */
+#define CUE_PATH_RESIDENT 4        /* 2D, nx % 4 == 0, both field buffers within one block's
+                                      shared memory (128^2: 128 KB), at most 256 cones and
+                                      1024 sources: one block holds the grid in shared
+                                      memory and the cones in registers for the whole call  */
 
 /* Parameters of the SNR turn rule (Sec. 3.5, Eq. 5; 2D).  Inside the
  * detectable window c_min <= C(p) <= c_max the cone turns by `turn` radians to

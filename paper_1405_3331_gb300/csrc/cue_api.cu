@@ -116,10 +116,14 @@ int run_coupled(Sim &s, int nsteps)
 {
     s.fused_used = false;
     s.persist_used = false;
-    // AUTO: the temporally blocked kernel when the grid gives every SM a tile,
-    // else the persistent launch (small grids, or a rate map), else plain.
+    s.resident_used = false;
+    // AUTO: the temporally blocked kernel when the grid gives every SM a tile;
+    // else one block with the grid in shared memory when it fits; else the
+    // persistent launch (small grids, or a rate map); else plain.
     const bool small = !fused_supported(s) || fused_tile_count(s.params) < sm_count_api();
     int rc = 1;
+    if (s.path == CUE_PATH_RESIDENT || (s.path == CUE_PATH_AUTO && small)) rc = run_resident_if_supported(s, nsteps);
+    if (rc != 1) return rc;
     if (s.path == CUE_PATH_PERSIST || (s.path == CUE_PATH_AUTO && small)) rc = run_persist_if_supported(s, nsteps);
     if (rc != 1) return rc;
     rc = run_fused_if_supported(s, nsteps);
@@ -409,10 +413,11 @@ int cue_set_option(cue_sim *s, int32_t option, int64_t value)
     switch (option) {
     case CUE_OPT_PATH:
         if (value != CUE_PATH_AUTO && value != CUE_PATH_PLAIN && value != CUE_PATH_FUSED &&
-            value != CUE_PATH_PERSIST)
+            value != CUE_PATH_PERSIST && value != CUE_PATH_RESIDENT)
             return CUE_ERR_ARG;
         if (value == CUE_PATH_FUSED && !fused_supported(*s)) return CUE_ERR_ARG;
         if (value == CUE_PATH_PERSIST && !persist_supported(*s)) return CUE_ERR_ARG;
+        if (value == CUE_PATH_RESIDENT && !resident_supported(*s)) return CUE_ERR_ARG;
         s->path = (int)value;
         return CUE_OK;
     case CUE_OPT_PERSIST_ROWS:
@@ -473,7 +478,10 @@ int cue_get_option(const cue_sim *s, int32_t option, int64_t *value)
     case CUE_OPT_ROWS_PER_THREAD: *value = s->rows_per_thread; return CUE_OK;
     case CUE_OPT_TIME_KERNEL: *value = s->time_kernel ? s->time_period : 0; return CUE_OK;
     case CUE_INFO_LAST_PATH:
-        *value = s->fused_used ? CUE_PATH_FUSED : (s->persist_used ? CUE_PATH_PERSIST : CUE_PATH_PLAIN);
+        *value = s->fused_used      ? CUE_PATH_FUSED
+                 : s->persist_used  ? CUE_PATH_PERSIST
+                 : s->resident_used ? CUE_PATH_RESIDENT
+                                    : CUE_PATH_PLAIN;
         return CUE_OK;
     case CUE_OPT_PERSIST_ROWS: *value = s->persist_rows; return CUE_OK;
     case CUE_OPT_PERSIST_BLOCKS: *value = s->persist_bpsm; return CUE_OK;

@@ -146,6 +146,9 @@ struct Sim {
     double timed_ms = 0.0;
     uint64_t timed_launches = 0;
 
+    // resident path
+    bool resident_used = false;
+
     // persistent path
     bool persist_ready = false, persist_used = false;
     int persist_rows = 0;         // option (0 = heuristic)
@@ -216,6 +219,15 @@ cudaError_t step_launch(const PInst *d_insts, const PItem *d_chunks, int n_chunk
 int run_persist_if_supported(Sim &s, int nsteps);
 // Coupled steps storing every state (trajectory slot 0 holds the start).
 int run_persist_trajectory(Sim &s, float *traj_field, float *traj_cone, uint32_t step0, int nsteps);
+
+// ---- shared-memory resident path for small 2D grids (k_resident.cu) ----
+constexpr int kResThreads = 1024;         // one block: field warps first, then one warp per 32 cones
+constexpr int kResMaxCones = 256;         // at most 8 cone warps (24 warps stay on the field)
+constexpr int kResMaxSources = 1024;
+bool resident_supported(const Sim &s);
+// Runs nsteps on the resident path when selected (or AUTO) and supported:
+// CUE_OK / negative error when it ran, 1 when the caller should fall back.
+int run_resident_if_supported(Sim &s, int nsteps);
 
 // ---- fused, temporally blocked path (k_fused.cu) ----
 constexpr int kMaxTemporalDepth = 16;

@@ -44,6 +44,7 @@ CUE_PATH_AUTO = 0
 CUE_PATH_PLAIN = 1
 CUE_PATH_FUSED = 2
 CUE_PATH_PERSIST = 3
+CUE_PATH_RESIDENT = 4
 
 class cue_snr_params(ct.Structure):
     _fields_ = [("gain", ct.c_float), ("width", ct.c_float), ("kd", ct.c_float), ("c_min", ct.c_float),
@@ -344,7 +345,8 @@ class Simulation:
         return self.get_option(CUE_INFO_LAST_PATH) == CUE_PATH_FUSED
 
     def last_path(self) -> int:
-        """CUE_PATH_PLAIN, CUE_PATH_FUSED or CUE_PATH_PERSIST: the path of the last sim_run."""
+        """CUE_PATH_PLAIN, CUE_PATH_FUSED, CUE_PATH_PERSIST or CUE_PATH_RESIDENT: the path of the
+        last sim_run."""
         return self.get_option(CUE_INFO_LAST_PATH)
 
     def launches(self) -> int:

@@ -52,6 +52,20 @@ def test_library_exports_every_declared_symbol(cue):
     assert set(cue.EXPORTED) <= set(declared_functions())
 
 
+def test_binding_constants_match_the_headers(cue):
+    """Every CUE_* constant of the Python binding has its header's value (paths, options,
+    error codes)."""
+    defines = {}
+    for h in HEADERS:
+        for m in re.finditer(r"^#define\s+(CUE_\w+)\s+\(?(-?\d+)\)?", open(h).read(), flags=re.M):
+            defines[m.group(1)] = int(m.group(2))
+    consts = {k: v for k, v in vars(cue).items() if k.startswith("CUE_") and isinstance(v, int)}
+    assert "CUE_PATH_RESIDENT" in consts and "CUE_PATH_RESIDENT" in defines
+    mismatched = {k: (v, defines[k]) for k, v in consts.items() if k in defines and defines[k] != v}
+    assert not mismatched, mismatched
+    assert len(set(consts) & set(defines)) >= 20
+
+
 def test_strerror_covers_every_code(cue):
     for code in range(0, -10, -1):
         s = cue.cue_strerror(code)
