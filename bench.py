@@ -39,7 +39,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cue", "reference"], default="cue")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "graph"])
     ap.add_argument("--path", default="auto", choices=["auto", "plain", "fused", "persist", "resident"])
     ap.add_argument("--depth", type=int, default=0, help="temporal depth on the fused path (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -258,6 +258,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload == "graph":
+        return run_reference_graph(args)
     w = workload(args.workload)
     import numpy as np
     import oracle
@@ -340,6 +342,8 @@ def main():
 
     if args.workload == "c4":
         return main_batch(args, torch, cue, dev, rank, world, dist, barrier)
+    if args.workload == "graph":
+        return main_graph(args, torch, dev, rank, world, dist, barrier)
     w = workload(args.workload, rank)
     if args.run_steps:
         w.nsteps = args.run_steps
@@ -636,6 +640,198 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
             "cpu_model": cpu_model()}
         line["cpu_baseline_threads"] = oracle_threads_sample("c4", ws[0].n_cells, nsteps, sample)
     b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------------------ connectivity
+GRAPH_METRIC = "cue connectivity pipeline: cones/s (bin neurons + connect cones + adjacency list + BFS)"
+GRAPH_UNIT = "cones/s"
+GRAPH_LAUNCHES = 7 + 1 + 10 + 1        # kernels per pipeline: binning, connections, adjacency list, BFS
+
+
+def graph_describe(gw):
+    return {"workload": f"connectivity: {gw.n_neurons} neurons uniform on 2048x2048, {gw.n_cones} cones "
+                        f"grown up to 48 from them (95% active), radius {gw.radius}, "
+                        f"{gw.grid[0]}x{gw.grid[1]} cells",
+            "neurons": gw.n_neurons, "cones": gw.n_cones, "radius": gw.radius, "cell": gw.cell,
+            "grid": list(gw.grid)}
+
+
+def graph_oracle_sample(gw, budget_s):
+    """The FP64 oracle's connectivity on the first S cones (S sized to the budget): binning of
+    every neuron, the brute-force pair test of the S cones, the adjacency list, BFS.
+    Returns (S, seconds, pairs)."""
+    import oracle
+    probe = 256
+    t0 = time.perf_counter()
+    oracle.connect(gw.pos[:, :probe], gw.owner[:probe], gw.active[:probe], gw.npos, gw.radius, cap=1 << 16)
+    per_cone = (time.perf_counter() - t0) / probe
+    S = int(max(probe, min(gw.n_cones, budget_s / max(per_cone, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.bin_points(gw.npos, gw.cell, gw.grid)
+    src, dst = oracle.connect(gw.pos[:, :S], gw.owner[:S], gw.active[:S], gw.npos, gw.radius, cap=8 * S + 1024)
+    row, col = oracle.csr(gw.n_neurons, src, dst)
+    oracle.bfs(row, col, gw.source)
+    return S, time.perf_counter() - t0, int(src.size)
+
+
+def run_reference_graph(args):
+    from paper_1405_3331_gb300 import workloads as W
+    gw = W.config_graph()
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    S, secs, pairs = graph_oracle_sample(gw, budget)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        graph_oracle_sample(gw, budget)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = S * args.steps / total
+    sample = (f"first {S} of {gw.n_cones} cones per step (all {gw.n_neurons} neurons binned; pair test "
+              f"against every neuron; adjacency list and BFS of their edges), FP64")
+    line = {
+        "impl": "reference", "metric": GRAPH_METRIC, "value": value, "unit": GRAPH_UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": graph_describe(gw),
+        "cpu_baseline": {"value": value, "unit": GRAPH_UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count(), "cpu_model": cpu_model()},
+        "e2e": {"value": value, "unit": GRAPH_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main_graph(args, torch, dev, rank, world, dist, barrier):
+    """The connectivity stage (cue_graph.h) as one step: bin the neurons, connect the cones to
+    them, build the adjacency list of the connection graph, BFS from neuron 0; every call on one
+    stream with preallocated workspaces, each stage bracketed by CUDA events."""
+    import ctypes as ct
+
+    import numpy as np
+
+    from paper_1405_3331_gb300 import cue
+    from paper_1405_3331_gb300 import graph as G
+    from paper_1405_3331_gb300 import workloads as W
+    gw = W.config_graph(seed=7 + 100 * rank)
+    L = G._lib()
+    m, n = gw.n_neurons, gw.n_cones
+    ncell = gw.grid[0] * gw.grid[1]
+    cap = 4 * n                                     # ~0.8 connections per cone expected
+    t = lambda a, dt: torch.as_tensor(a, dtype=dt).to(dev)
+    npos, pos = t(gw.npos, torch.float32), t(gw.pos, torch.float32)
+    owner, active = t(gw.owner, torch.int32), t(gw.active, torch.uint8)
+    i32 = lambda k: torch.empty(k, dtype=torch.int32, device=dev)
+    cell_of, sid, start, end = i32(m), i32(m), i32(ncell), i32(ncell)
+    src, dst, cnt = i32(cap), i32(cap), i32(1)
+    row, col, medges, level = i32(m + 1), i32(cap), i32(1), i32(m)
+    nb_bin, nb_csr, nb_bfs = (int(L.cue_bin_workspace_bytes(m, ncell)), int(L.cue_csr_workspace_bytes(m, cap)),
+                              int(L.cue_bfs_workspace_bytes(m)))
+    ws = [torch.empty(nb + 256, dtype=torch.uint8, device=dev) for nb in (nb_bin, nb_csr, nb_bfs)]
+    wp = [(b.data_ptr() + 255) & ~255 for b in ws]
+    grid3 = (ct.c_int32 * 3)(gw.grid[0], gw.grid[1], 1)
+    stream = torch.cuda.Stream(dev)
+    st = stream.cuda_stream
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def stages(ev=None):
+        calls = [
+            lambda: L.cue_bin_points(2, m, npos.data_ptr(), gw.cell, grid3, cell_of.data_ptr(), sid.data_ptr(),
+                                     start.data_ptr(), end.data_ptr(), wp[0], nb_bin, st),
+            lambda: L.cue_connect(2, n, pos.data_ptr(), owner.data_ptr(), active.data_ptr(), m, npos.data_ptr(),
+                                  gw.radius, gw.cell, grid3, sid.data_ptr(), start.data_ptr(), end.data_ptr(), cap,
+                                  src.data_ptr(), dst.data_ptr(), cnt.data_ptr(), st),
+            lambda: L.cue_csr_build(m, cap, cnt.data_ptr(), src.data_ptr(), dst.data_ptr(), row.data_ptr(),
+                                    col.data_ptr(), medges.data_ptr(), wp[1], nb_csr, st),
+            lambda: L.cue_bfs(m, row.data_ptr(), col.data_ptr(), gw.source, level.data_ptr(), wp[2], nb_bfs, st),
+        ]
+        for i, f in enumerate(calls):
+            if ev is not None:
+                ev[i].record(stream)
+            cue._check(f(), ("cue_bin_points", "cue_connect", "cue_csr_build", "cue_bfs")[i])
+        if ev is not None:
+            ev[4].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        stages()
+    cue._check(L.cue_graph_status(wp[2], st), "cue_graph_status")
+    pairs, edges = int(cnt.item()), int(medges.item())
+    if pairs > cap:
+        raise RuntimeError(f"{pairs} connections exceed the preallocated {cap}")
+    lv = level.cpu().numpy()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_id_for(dev.index or 0))
+    barrier()
+    sampler.start()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stages(evs[k])
+    barrier()
+    clocks = sampler.stop()
+    cue._check(L.cue_graph_status(wp[2], st), "cue_graph_status")
+    stage_ms = [sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps for i in range(4)]
+    local_ms = sum(e[0].elapsed_time(e[4]) for e in evs)
+    total_ms, value = aggregate(local_ms, n, args.steps, world, dist, dev)
+    hbm, peak_kind = peaks()
+    # compulsory bytes of each stage: every input read once, every output written once
+    alg = [16 * m + 8 * ncell,                                    # neurons in; cell, order, cell ranges out
+           13 * n + 8 * ncell + 12 * m + 8 * pairs,               # cones + the binned neurons in; pairs out
+           8 * pairs + 4 * (m + 1) + 4 * edges,                   # pairs in; adjacency list out
+           4 * (m + 1) + 4 * edges + 4 * m]                       # adjacency list in; levels out
+    names = ["bin_points", "connect", "csr_build", "bfs"]
+    top = max(range(4), key=lambda i: stage_ms[i])
+    achieved = alg[top] / (stage_ms[top] / 1e3) / 1e9
+    line = {
+        "metric": GRAPH_METRIC, "value": value, "unit": GRAPH_UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 positions, f64 distances, int32 graph", "data": "synthetic",
+        "config": dict(graph_describe(gw), l2="flushed between timed steps (512 MiB write)",
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "stages_ms": dict(zip(names, stage_ms)),
+        "connections": pairs, "edges": edges, "bfs_reached": int((lv >= 0).sum()), "bfs_levels": int(lv.max()) + 1,
+        "bfs_edges_per_s": edges / (stage_ms[3] / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": names[top], "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg[top], "avg_launch_us": stage_ms[top] * 1e3,
+                     "note": "compulsory bytes of the slowest stage; the working set (about 60 MB) stays in L2 "
+                             "and the stages are latency-bound (atomics, scans, a barrier per BFS level)"},
+        "clocks": clocks, "gpu_launches": GRAPH_LAUNCHES * args.steps,
+    }
+    if not args.no_e2e:
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                for a in (gw.npos, gw.pos, gw.owner, gw.active)]
+        lv_host = torch.empty(m, dtype=torch.int32).pin_memory()
+        reps = max(1, min(args.steps, 3))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                for d, h in zip((npos, pos, owner, active), host):
+                    d.copy_(h, non_blocking=True)
+            stages()
+            with torch.cuda.stream(stream):
+                lv_host.copy_(level, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        line["e2e"] = {"value": world * n * reps / (tot / 1e3), "unit": GRAPH_UNIT,
+                       "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host),
+                       "d2h_bytes_per_step": m * 4, "ms_per_step": tot / reps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        S, secs, _ = graph_oracle_sample(gw, args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": S / secs, "unit": GRAPH_UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {S} of {n} cones (all {m} neurons binned; pair test against every neuron; "
+                      f"adjacency list and BFS of their edges), FP64, one thread",
+            "seconds": secs, "host_cores": os.cpu_count(), "cpu_model": cpu_model()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -368,19 +368,24 @@ def bin_points(pos, cell, grid):
     return cell_of, sid, start, end
 
 
-def connect(pos, owner, active, npos, radius):
-    """(owner, neuron) pairs of active cones within ``radius`` of a neuron other than their own."""
+def connect(pos, owner, active, npos, radius, cap=None):
+    """(owner, neuron) pairs of active cones within ``radius`` of a neuron other than their own.
+    ``cap`` sizes the output (default: every pair could connect); a larger count is re-run with
+    room for all of it."""
     pos, npos = _f64(pos), _f64(npos)
     dim, n = pos.shape
     m = npos.shape[1]
     owner = _i32(owner)
     act = np.ascontiguousarray(np.ones(n) if active is None else active, dtype=np.uint8)
-    cap = n * max(m, 1)
-    src = np.empty(max(cap, 1), np.int32)
-    dst = np.empty(max(cap, 1), np.int32)
-    k = _load().orc_connect(dim, n, _ptr(pos), _ptr(owner), _ptr(act), m, _ptr(npos), float(radius), cap,
-                            _ptr(src), _ptr(dst))
-    return src[:k].copy(), dst[:k].copy()
+    cap = n * max(m, 1) if cap is None else int(cap)
+    while True:
+        src = np.empty(max(cap, 1), np.int32)
+        dst = np.empty(max(cap, 1), np.int32)
+        k = _load().orc_connect(dim, n, _ptr(pos), _ptr(owner), _ptr(act), m, _ptr(npos), float(radius), cap,
+                                _ptr(src), _ptr(dst))
+        if k <= cap:
+            return src[:k].copy(), dst[:k].copy()
+        cap = k
 
 
 def csr(nv, src, dst):

@@ -255,3 +255,46 @@ def hbm_probe_3d(seed=6) -> Workload:
     """3D 512^3 (512 MiB per buffer), C3 physics."""
     return make("probe-3d-512", 3, 512, 512, 512, D=1.0, lam=0.01, dt=0.15, n_src=128,
                 emit=(0.5, 2.0), n_axons=65536, nsteps=200, seed=seed, philox_seed=7)
+
+
+@dataclasses.dataclass
+class GraphWorkload:
+    """Inputs of the connectivity stage: neurons, the growth cones grown from them, and the
+    uniform grid that bins the neurons."""
+    name: str
+    npos: np.ndarray        # float32 [2, n_neurons]
+    pos: np.ndarray         # float32 [2, n_cones]
+    owner: np.ndarray       # int32 [n_cones]: the neuron each cone grows from
+    active: np.ndarray      # uint8 [n_cones]
+    radius: float           # connection distance (the sum of the two radii)
+    cell: float             # grid cell side (>= radius)
+    grid: tuple             # cells per axis
+    source: int = 0         # BFS source vertex
+
+    @property
+    def n_neurons(self) -> int:
+        return int(self.npos.shape[1])
+
+    @property
+    def n_cones(self) -> int:
+        return int(self.pos.shape[1])
+
+
+def config_graph(seed=7, extent=2048.0, n_neurons=262144, cones_per_neuron=4, reach=48.0,
+                 radius=2.0) -> GraphWorkload:
+    """Connectivity on the 2048^2 domain: neurons uniform in it, each with `cones_per_neuron`
+    cones that have grown up to `reach` from it (uniform direction, uniform distance, clamped
+    into the domain); 95% of the cones still growing; cells of side `radius`."""
+    rng = np.random.default_rng(seed)
+    hi = extent - 1.0
+    npos = rng.uniform(0.0, hi, (2, n_neurons))
+    owner = np.repeat(np.arange(n_neurons, dtype=np.int32), cones_per_neuron)
+    n = owner.size
+    ang = rng.uniform(0.0, 2.0 * np.pi, n)
+    dist = rng.uniform(0.0, reach, n)
+    pos = npos[:, owner] + np.stack([np.cos(ang), np.sin(ang)]) * dist
+    pos = np.clip(pos, 0.0, hi)
+    active = (rng.uniform(0.0, 1.0, n) < 0.95).astype(np.uint8)
+    side = int(np.ceil(extent / radius))
+    return GraphWorkload(name=f"graph-2d-{int(extent)}", npos=npos.astype(np.float32), pos=pos.astype(np.float32),
+                         owner=owner, active=active, radius=radius, cell=radius, grid=(side, side))

@@ -126,3 +126,48 @@ def test_pipeline_from_a_simulation(g):
     np.testing.assert_array_equal(col.cpu().numpy()[: wc.size], wc)
     np.testing.assert_array_equal(lev, oracle.bfs(wr, wc, 0))
     assert wc.size > 100 and (lev > 1).any()
+
+
+def test_connectivity_at_the_benchmark_size(g):
+    """The bench's connectivity workload (262,144 neurons, 1,048,576 cones): binning of every
+    neuron against the oracle; the connections of the cones of the first 1,000 neurons against
+    the oracle's brute-force pair test (as a set); the adjacency list and BFS levels of the whole
+    graph by properties that hold at any size (rows sorted and distinct and covering exactly the
+    distinct connections; every level one more than some predecessor's, no edge skipping one)."""
+    import torch
+    from paper_1405_3331_gb300 import workloads as W
+    gw = W.config_graph()
+    m, n = gw.n_neurons, gw.n_cones
+    binned = g.bin_points(_t(gw.npos, torch.float32), gw.cell, gw.grid)
+    want = oracle.bin_points(gw.npos.astype(np.float64), np.float32(gw.cell), gw.grid)
+    for x, y, what in zip(binned, want, ("cell_of", "sorted_id", "cell_start", "cell_end")):
+        np.testing.assert_array_equal(x.cpu().numpy(), y, err_msg=what)
+    src, dst, cnt = g.connect(_t(gw.pos, torch.float32), _t(gw.owner, torch.int32), _t(gw.active, torch.uint8),
+                              _t(gw.npos, torch.float32), gw.radius, gw.cell, gw.grid, binned, cap=4 * n)
+    k = int(cnt.item())
+    assert 0.5 * n < k < 1.2 * n, k
+    s, d = src.cpu().numpy()[:k], dst.cpu().numpy()[:k]
+    first = 1000
+    cones = np.flatnonzero(gw.owner < first)
+    ws_, wd_ = oracle.connect(gw.pos[:, cones].astype(np.float64), gw.owner[cones], gw.active[cones],
+                              gw.npos.astype(np.float64), gw.radius, cap=16 * cones.size)
+    sel = s < first
+    assert sorted(zip(s[sel].tolist(), d[sel].tolist())) == sorted(zip(ws_.tolist(), wd_.tolist()))
+    row, col, mm = g.csr(m, src, dst, cnt)
+    row, e = row.cpu().numpy(), int(mm.item())
+    col = col.cpu().numpy()[:e]
+    assert row[0] == 0 and row[-1] == e and np.all(np.diff(row) >= 0)
+    u = np.repeat(np.arange(m), np.diff(row))
+    assert np.all((u[1:] != u[:-1]) | (col[1:] > col[:-1]))          # each row ascending, distinct
+    pairs = np.unique(s.astype(np.int64) * m + d)
+    np.testing.assert_array_equal(np.sort(u.astype(np.int64) * m + col), pairs)
+    lev = g.bfs(_t(row, torch.int32), _t(col, torch.int32), gw.source).cpu().numpy()
+    assert lev[gw.source] == 0 and (lev >= 0).sum() > m // 2
+    lu, lv = lev[u], lev[col]
+    reach = lu >= 0
+    assert np.all(lv[reach] >= 0) and np.all(lv[reach] <= lu[reach] + 1)   # no edge skips a level
+    best = np.full(m, np.iinfo(np.int64).max)
+    np.minimum.at(best, col[reach], lu[reach].astype(np.int64) + 1)
+    hit = lev > 0
+    np.testing.assert_array_equal(best[hit], lev[hit])                      # each level from a predecessor
+    assert np.all(lev[lev < 0] == -1) and not np.any((lev < 0) & (best < np.iinfo(np.int64).max))
