@@ -340,45 +340,41 @@ CsrLayout csr_layout(int nv, int ne_cap)
 // ---------------------------------------------------------------- breadth-first search
 // Fig. 5's arrays: F (frontier), X (visited, here level >= 0), C (cost =
 // level).  Fig. 5 sets F[nid] in the same pass that reads F, so a vertex found
-// at this level could be expanded within it; the levels stay exact here by
-// marking neighbours in a separate array U and committing U to F and C after
-// a grid barrier (the level synchronisation the text describes).  Three flag
-// words rotate: level L sets flag[L % 3] when it finds a vertex, and clears
-// flag[(L + 1) % 3], last read two barriers earlier.
+// at this level could be expanded within it; the levels stay exact here with
+// two frontier arrays: level L expands the vertices of F[L % 2] and writes the
+// vertices it finds into F[(L + 1) % 2], each claimed once by a compare-and-swap
+// of its level from -1 to L + 1, then the grid meets at one barrier (the level
+// synchronisation the text describes).  Three flag words rotate: level L sets
+// flag[L % 3] when it finds a vertex and clears flag[(L + 1) % 3], last read
+// after the barrier before the previous one.
 __global__ void __launch_bounds__(256) bfs_kernel(int nv, const int *__restrict__ row, const int *__restrict__ col,
-                                                  int source, int *level, uint8_t *F, uint8_t *U, int *flag,
+                                                  int source, int *level, uint8_t *F0, uint8_t *F1, int *flag,
                                                   PBar *bar, unsigned expected, long long limit, unsigned *status)
 {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     for (int v = t0; v < nv; v += stride) {
         level[v] = v == source ? 0 : -1;
-        F[v] = v == source;
-        U[v] = 0;
+        F0[v] = v == source;
+        F1[v] = 0;
     }
     if (!grid_barrier(bar, expected, limit, status)) return;
     for (int L = 0; L < nv; ++L) {
+        uint8_t *Fc = (L & 1) ? F1 : F0, *Fn = (L & 1) ? F0 : F1;
+        bool found = false;
         for (int v = t0; v < nv; v += stride) {
-            if (!__ldcg(F + v)) continue;
-            F[v] = 0;
+            if (!__ldcg(Fc + v)) continue;
+            Fc[v] = 0;
             const int e1 = row[v + 1];
             for (int e = row[v]; e < e1; ++e) {
                 const int u = col[e];
-                if (__ldcg(level + u) < 0) U[u] = 1;
+                if (__ldcg(level + u) < 0 && atomicCAS(level + u, -1, L + 1) == -1) {
+                    Fn[u] = 1;
+                    found = true;
+                }
             }
         }
         if (t0 == 0) flag[(L + 1) % 3] = 0;
-        if (!grid_barrier(bar, expected, limit, status)) return;
-        bool found = false;
-        for (int u = t0; u < nv; u += stride) {
-            if (!__ldcg(U + u)) continue;
-            U[u] = 0;
-            if (__ldcg(level + u) < 0) {
-                level[u] = L + 1;
-                F[u] = 1;
-                found = true;
-            }
-        }
         if (__syncthreads_or(found) && threadIdx.x == 0) flag[L % 3] = 1;
         if (!grid_barrier(bar, expected, limit, status)) return;
         if (!__ldcg(flag + L % 3)) break;

@@ -84,7 +84,7 @@ def test_bfs_matches_oracle(g, shape):
     if shape == "random":
         nv, ne = 20000, 60000
         src, dst = rng.integers(0, nv, ne), rng.integers(0, nv, ne)
-    elif shape == "path":                                  # 5,000 levels: 10,001 barriers in one launch
+    elif shape == "path":                                  # 5,000 levels: 5,001 barriers in one launch
         nv = 5000
         src, dst = np.arange(nv - 1), np.arange(1, nv)
     elif shape == "star":
