@@ -72,10 +72,12 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(const __grid_c
 {
     extern __shared__ __align__(16) float smem[];
     const FieldDesc &f = A.f;
-    const int cells = f.nx * f.ny;                    // a multiple of 4 (nx % 4 == 0)
+    const int nx = f.nx, ny = f.ny;
+    const float alpha = f.alpha, beta = f.beta, dt = f.dt;
+    const int cells = nx * ny;                        // a multiple of 4 (nx % 4 == 0)
     const int nq = cells >> 2;                        // float4 groups
-    const int Q = f.nx >> 2;                          // float4 groups per row
-    const int nrw = (f.ny + 31) >> 5;                 // words of the per-row source bitmap
+    const int Q = nx >> 2;                            // float4 groups per row
+    const int nrw = (ny + 31) >> 5;                   // words of the per-row source bitmap
     float *buf0 = smem, *buf1 = smem + cells;
     int *s_cell = reinterpret_cast<int *>(smem + 2 * cells);
     float *s_emit = smem + 2 * cells + A.n_src;
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(const __grid_c
     for (int k = tid; k < A.n_src; k += kResThreads) {
         const int c = s_cell[k];
         if (c >= 0) {
-            const int y = c / f.nx;
+            const int y = c / nx;
             atomicOr(s_rows + (y >> 5), 1u << (y & 31));
         }
     }
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(const __grid_c
     // the field loop's work items: column blocks of 32 groups x bands of `rows` rows
     const int ncb = (Q + 31) >> 5;
     const int R = A.rows;
-    const int n_items = ncb * ((f.ny + R - 1) / R);
+    const int n_items = ncb * ((ny + R - 1) / R);
 
     // cone state of this lane, in registers for the whole call
     const int a = (warp - A.field_warps) * 32 + lane;
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(const __grid_c
             const float4 *c4 = reinterpret_cast<const float4 *>(cur);
             float4 *o4 = reinterpret_cast<float4 *>(nxt);
             for (int it = warp; it < n_items; it += A.field_warps) {    // warp-uniform
-                const int cb = it % ncb, y0 = (it / ncb) * R, y1 = min(y0 + R, f.ny);
+                const int cb = it % ncb, y0 = (it / ncb) * R, y1 = min(y0 + R, ny);
                 const int x4 = cb * 32 + lane;        // this lane's group in the row
                 const bool xin = x4 < Q;
                 const bool need_l = lane == 0 && x4 > 0, need_r = lane == 31 && x4 + 1 < Q;
@@ -150,26 +152,26 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(const __grid_c
                 unsigned bits = 0;
 #pragma unroll 4
                 for (int y = y0; y < y1; ++y) {
-                    const float4 vp = col[(y + 1 < f.ny ? y + 1 : y) * Q];
+                    const float4 vp = col[(y + 1 < ny ? y + 1 : y) * Q];
                     if (((y - y0) & 31) == 0) bits = row_bits(s_rows, nrw, y);
                     float l = __shfl_up_sync(kFullR, vc.w, 1);
                     float r = __shfl_down_sync(kFullR, vc.x, 1);
-                    if (need_l) l = cur[y * f.nx + 4 * x4 - 1];
-                    if (need_r) r = cur[y * f.nx + 4 * x4 + 4];
+                    if (need_l) l = cur[y * nx + 4 * x4 - 1];
+                    if (need_r) r = cur[y * nx + 4 * x4 + 4];
                     if (wall_l) l = vc.x;             // a wall: the missing neighbour is the node itself
                     if (wall_r) r = vc.w;
                     float4 o;
-                    o.x = node_update2(vc.x, l, vc.y, vm.x, vp.x, f.alpha, f.beta);
-                    o.y = node_update2(vc.y, vc.x, vc.z, vm.y, vp.y, f.alpha, f.beta);
-                    o.z = node_update2(vc.z, vc.y, vc.w, vm.z, vp.z, f.alpha, f.beta);
-                    o.w = node_update2(vc.w, vc.z, r, vm.w, vp.w, f.alpha, f.beta);
+                    o.x = node_update2(vc.x, l, vc.y, vm.x, vp.x, alpha, beta);
+                    o.y = node_update2(vc.y, vc.x, vc.z, vm.y, vp.y, alpha, beta);
+                    o.z = node_update2(vc.z, vc.y, vc.w, vm.z, vp.z, alpha, beta);
+                    o.w = node_update2(vc.w, vc.z, r, vm.w, vp.w, alpha, beta);
                     const int q = y * Q + x4;
                     if constexpr (MAP) {
                         const float4 m = __ldg(reinterpret_cast<const float4 *>(A.map) + (xin ? q : 0));
-                        o.x = fmaf(f.dt, m.x, o.x);
-                        o.y = fmaf(f.dt, m.y, o.y);
-                        o.z = fmaf(f.dt, m.z, o.z);
-                        o.w = fmaf(f.dt, m.w, o.w);
+                        o.x = fmaf(dt, m.x, o.x);
+                        o.y = fmaf(dt, m.y, o.y);
+                        o.z = fmaf(dt, m.z, o.z);
+                        o.w = fmaf(dt, m.w, o.w);
                     }
                     if (bits & 1u) {                  // the row's sources at these nodes, in source order
                         for (int k = 0; k < A.n_src; ++k) {
@@ -195,7 +197,6 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(const __grid_c
             if (act) {
                 ++n_live;
                 const float *Cs = cur;
-                const int nx = f.nx;
                 auto ld = [&](int i, int j, int) { return Cs[i + nx * j]; };
                 act = cone_step_rule<2>(f, A.c, ld, xi, p, d, A.src_xyz, A.n_src, stop ? A.n_src : 0);
                 const float big = 3.402823466e38f;
@@ -271,14 +272,19 @@ int run_resident_if_supported(Sim &s, int nsteps)
     }
     const size_t smem = resident_smem_bytes(s);
     const bool map = s.src_map != nullptr;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[map]) {
+    // the shared-memory allowance is a per-device function attribute: set it
+    // once on every device this process launches the kernel on
+    static unsigned long long attr_set[2] = {0ull, 0ull};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CUE_ERR_CUDA;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!(attr_set[map] & bit)) {
         cudaError_t e = map ? cudaFuncSetAttribute(resident_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    resident_smem_limit())
                             : cudaFuncSetAttribute(resident_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    resident_smem_limit());
         if (e != cudaSuccess) return CUE_ERR_CUDA;
-        attr_set[map] = true;
+        attr_set[map] |= bit;
     }
     ResArgs A{};
     A.f = s.fd;
