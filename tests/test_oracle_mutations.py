@@ -1,7 +1,8 @@
 """The oracle's pins against planted mistakes, CPU only.
 
 Each mutant is a plausible slip in oracle/cue_oracle.c — a flipped sign, a
-dropped neighbour, h for h^2, a transposed index, a swapped weight, a wrong
+dropped neighbour, h for h^2, a transposed index, a swapped weight, a window
+wall decided by the local index, a wrong
 constant of the generator, the field stepped before the cones, a stop tested
 before the move, an off-by-one in a wall, a binning or a graph step, the
 adjoint's decay, parameter scaling or reverse-mode projections — planted in a copy of the oracle, which is
@@ -100,6 +101,14 @@ MUTANTS = [
     ("decay quadratic",
      "Cn[c] = ci + alpha * flux - decay * ci;",
      "Cn[c] = ci + alpha * flux - decay * ci * ci;", FIELD_CONE),
+    ("window wall by local index", "if (gi > 0)      flux += Wp[c - sx] - ci;",
+     "if (i > 0)      flux += Wp[c - sx] - ci;", FIELD_CONE),
+    ("window top wall one row early", "if (gj < ny - 1) flux += Wp[c + sy] - ci;",
+     "if (gj < ny - 2) flux += Wp[c + sy] - ci;", FIELD_CONE),
+    ("window decay sign", "out[i + (int64_t)wx * (j + (int64_t)wy * k)] = ci + alpha * flux - decay * ci;",
+     "out[i + (int64_t)wx * (j + (int64_t)wy * k)] = ci + alpha * flux + decay * ci;", FIELD_CONE),
+    ("window source decoded transposed", "gj = (cell / nx) % ny, gk = cell / (nx * ny);",
+     "gj = (cell / ny) % nx, gk = cell / (nx * ny);", FIELD_CONE),
     ("SNR turn direction", "(snr + xi[0] > 0.0) ? -cp->snr_turn : cp->snr_turn",
      "(snr + xi[0] > 0.0) ? cp->snr_turn : -cp->snr_turn", SNR),
     ("SNR window without its upper edge", "if (Cp >= cp->snr_cmin && Cp <= cp->snr_cmax) {",
