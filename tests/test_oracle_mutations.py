@@ -1,14 +1,14 @@
 """The oracle's pins against planted mistakes, CPU only.
 
-Each mutant is a plausible slip in oracle/cue_oracle.c — a flipped sign, a
+Each mutant is a plausible slip in oracle/cue_oracle.c: a flipped sign, a
 dropped neighbour, h for h^2, a transposed index, a swapped weight, a window
-wall decided by the local index, a wrong
-constant of the generator, the field stepped before the cones, a stop tested
-before the move, an off-by-one in a wall, a binning or a graph step, the
-adjoint's decay, parameter scaling or reverse-mode projections — planted in a copy of the oracle, which is
-compiled and run against the pins that cover that part.  Every mutant must make
-at least one pin fail.  (Clamping the cell index to N-1 instead of N-2 is left
-out: it only ever gives the extra node weight 0, so it computes the same
+wall decided by the local index, a wrong constant of the generator, the field
+stepped before the cones, a stop tested before the move, an off-by-one in a
+wall, a binning or a graph step, the adjoint's decay, parameter scaling or
+reverse-mode projections.  Each is planted alone in a copy of the oracle, which
+is compiled and run against the pins that cover that part; every mutant must
+make at least one pin fail.  (Clamping the cell index to N-1 instead of N-2 is
+left out: it only ever gives the extra node weight 0, so it computes the same
 values.)
 """
 import concurrent.futures as cf
