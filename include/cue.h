@@ -253,7 +253,8 @@ uint64_t cue_launch_count(const cue_sim *sim);
 /* With CUE_OPT_TIME_KERNEL on: synchronise the stream and return the summed
  * device time (ms, from CUDA events on the handle's stream) and the number of
  * launches of the dominant field kernel (the fused kernel on the fused path,
- * the field stencil on the plain path) since the previous call; resets both. */
+ * the field stencil on the plain path, the one launch per call of the
+ * persistent and resident paths) since the previous call; resets both. */
 int cue_kernel_time(cue_sim *sim, double *total_ms, uint64_t *launches);
 
 /* Synchronise the stream and return the number of cone updates (active
