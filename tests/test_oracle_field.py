@@ -329,3 +329,40 @@ def test_windowed_field_step_equals_the_full_step(dim):
         got = oracle.field_window(g, _padded_window(C, origin, size), origin, cells, emit)
         sl = tuple(slice(o, o + s) for o, s in zip(reversed(origin), reversed(size)))
         np.testing.assert_array_equal(got, full[sl])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_steady_state_follows_the_continuum_greens_function(dim):
+    """A point source emitting e per step, run to its steady state on a grid whose walls lie
+    many screening lengths l = sqrt(D / lambda) away: a few nodes from the source the field
+    follows the free-space solution of D lap C - lambda C = -(e / dt) delta, namely
+    (e/dt) / (2 pi D) K0(r / l) in 2D and (e/dt) / (4 pi D r) exp(-r / l) in 3D, to the
+    discretisation error of the 5- / 7-point operator, which shrinks away from the source."""
+    from scipy.special import k0
+    D, lam, e = 1.0, 0.04, 1.0
+    n, dt, rs, tol = (121, 0.2, (4, 6, 8, 10, 14), 1e-2) if dim == 2 else (61, 0.15, (6, 8, 10, 14, 18), 2.5e-2)
+    g = oracle.Grid(dim, n, n, n if dim == 3 else 1, h=1.0, D=D, lam=lam, dt=dt)
+    c = n // 2
+    cell = c + n * c + (n * n * c if dim == 3 else 0)
+    shape = (n,) * dim
+    ell = np.sqrt(D / lam)
+    none = (np.zeros((dim, 0)), np.zeros((dim, 0)), np.zeros(0, np.uint8))
+    C, *_ = oracle.run(g, oracle.Cone(), np.zeros(shape), 0, int(12 / (lam * dt)), [cell], [e], None, *none)
+
+    def along(axis, r):
+        idx = [c] * dim
+        idx[axis] += r
+        return C[tuple(reversed(idx))]
+
+    def green(r):
+        if dim == 2:
+            return e / dt / (2 * np.pi * D) * k0(r / ell)
+        return e / dt / (4 * np.pi * D * r) * np.exp(-r / ell)
+
+    errs = []
+    for r in (3,) + rs:
+        vals = [along(ax, r) for ax in range(dim)] + [along(0, -r)]
+        np.testing.assert_allclose(vals, vals[0], rtol=1e-12)          # the same in every axis direction
+        errs.append(abs(vals[0] / green(r) - 1.0))
+    assert max(errs[1:]) <= tol, errs
+    assert errs[0] > errs[1] > errs[3]                                 # O(h^2 / r^2) near the source
