@@ -116,7 +116,7 @@ def test_bilinear_corners_by_hand():
 
 # --------------------------------------------------------------- noise
 def test_box_muller_noise_is_standard_normal():
-    n = 400_000
+    n = 1_000_000
     axon = np.arange(n, dtype=np.uint32) % 50_000
     step = (np.arange(n, dtype=np.uint32) // 50_000) * 7 + 3
     xi = oracle.noise(0x5EED0002, axon, step, 3)
