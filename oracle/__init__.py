@@ -20,6 +20,7 @@ from .oracle import (  # noqa: F401
     run,
     endpoint_loss,
     adjoint,
+    adjoint_from_states,
     bin_points,
     connect,
     csr,

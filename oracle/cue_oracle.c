@@ -638,48 +638,27 @@ static void cone_step_adjoint(const orc_grid *g, const orc_cone *cp, const doubl
     }
 }
 
-/* Forward T clamp-mode steps from (C0, pos0, dir0), then the adjoint.
- * Returns the loss; writes dL/dD, dL/dlambda, dL/de_k (n_src), dL/dM (cells).
- * pos0/dir0/targets are SoA [dim][n].  Memory: (T+1) fields and cone states.
- * state_binary32 != 0 stores every forward state (field, positions, directions) rounded to
- * binary32: a perturbation of exactly the size single-precision storage makes, used by the
- * tests to measure how strongly a case's gradients depend on it.  0 is the oracle proper. */
-double orc_adjoint(const orc_grid *g, const orc_cone *cp, const double *C0,
-                   const int32_t *src_cell, const double *src_emit, int n_src, const double *src_map,
-                   int n, const double *pos0, const double *dir0, const double *targets, int T,
-                   double *gD, double *glam, double *gsrc, double *gmap, double *Cs, double *Ps, double *Ds,
-                   double *work, int state_binary32)
+/* The backward pass alone, over given forward states: Cs holds C^n (nodes
+ * values each) and Ps / Ds hold p^n / d^n (SoA [dim][n] each) for
+ * n = 0..T.  Returns the loss at p^T; writes dL/dD, dL/dlambda, dL/de_k
+ * (n_src) and dL/dM (nodes).  `work` holds 3 * nodes doubles.  Fed the
+ * states of the oracle's own forward run this is exactly orc_adjoint's
+ * backward; fed another program's stored states it gives the derivative that
+ * program's backward pass must produce from them (the same states in, so the
+ * forward's rounding drops out of the comparison). */
+double orc_adjoint_from_states(const orc_grid *g, const orc_cone *cp, const int32_t *src_cell, int n_src, int n,
+                               const double *targets, int T, const double *Cs, const double *Ps,
+                               const double *Ds, double *gD, double *glam, double *gsrc, double *gmap,
+                               double *work)
 {
     const int dim = g->dim;
     const int64_t nn = nodes_of(g);
     const size_t cs = (size_t)dim * n;
-    uint8_t *act = (uint8_t *)work;                  /* n bytes (all stay active) */
-    double *mu = (double *)((uint8_t *)work + ((n + 15) / 16) * 16);
-    double *mu2 = mu + nn, *lapC = mu2 + nn;
-    /* forward, storing every state */
-    memcpy(Cs, C0, (size_t)nn * sizeof(double));
-    memcpy(Ps, pos0, cs * sizeof(double));
-    memcpy(Ds, dir0, cs * sizeof(double));
-    for (int a = 0; a < n; ++a) act[a] = 1;
-    for (int s = 0; s < T; ++s) {
-        memcpy(Ps + (size_t)(s + 1) * cs, Ps + (size_t)s * cs, cs * sizeof(double));
-        memcpy(Ds + (size_t)(s + 1) * cs, Ds + (size_t)s * cs, cs * sizeof(double));
-        orc_cone_step(g, cp, Cs + (size_t)s * nn, (uint32_t)s, n, Ps + (size_t)(s + 1) * cs,
-                      Ds + (size_t)(s + 1) * cs, act, src_cell, n_src);
-        orc_field_step(g, Cs + (size_t)s * nn, Cs + (size_t)(s + 1) * nn, src_cell, src_emit, n_src, src_map);
-        if (state_binary32) {
-            double *Cn = Cs + (size_t)(s + 1) * nn, *Pn = Ps + (size_t)(s + 1) * cs, *Dn = Ds + (size_t)(s + 1) * cs;
-            for (int64_t i = 0; i < nn; ++i) Cn[i] = (double)(float)Cn[i];
-            for (size_t i = 0; i < cs; ++i) {
-                Pn[i] = (double)(float)Pn[i];
-                Dn[i] = (double)(float)Dn[i];
-            }
-        }
-    }
+    double *mu = work, *mu2 = mu + nn, *lapC = mu2 + nn;
     /* loss and its adjoint at T */
     double loss = 0.0;
     const double *PT = Ps + (size_t)T * cs;
-    double *pbar = (double *)malloc(cs * sizeof(double)), *dbar = (double *)malloc(cs * sizeof(double));
+    double *pbar = (double *)malloc((cs + 1) * sizeof(double)), *dbar = (double *)malloc((cs + 1) * sizeof(double));
     for (int a = 0; a < n; ++a)
         for (int k = 0; k < dim; ++k) {
             double e = PT[(size_t)k * n + a] - targets[(size_t)k * n + a];
@@ -687,7 +666,7 @@ double orc_adjoint(const orc_grid *g, const orc_cone *cp, const double *C0,
             pbar[(size_t)k * n + a] = 2.0 * e / n;
             dbar[(size_t)k * n + a] = 0.0;
         }
-    loss /= n;
+    if (n > 0) loss /= n;
     const double alpha_dD = g->dt / (g->h * g->h);
     *gD = 0.0;
     *glam = 0.0;
@@ -732,6 +711,47 @@ double orc_adjoint(const orc_grid *g, const orc_cone *cp, const double *C0,
     free(pbar);
     free(dbar);
     return loss;
+}
+
+/* Forward T clamp-mode steps from (C0, pos0, dir0), then the adjoint.
+ * Returns the loss; writes dL/dD, dL/dlambda, dL/de_k (n_src), dL/dM (cells).
+ * pos0/dir0/targets are SoA [dim][n].  Memory: (T+1) fields and cone states.
+ * state_binary32 != 0 stores every forward state (field, positions, directions) rounded to
+ * binary32: a perturbation of exactly the size single-precision storage makes, used by the
+ * tests to measure how strongly a case's gradients depend on it.  0 is the oracle proper.
+ * The backward pass is orc_adjoint_from_states over the stored states. */
+double orc_adjoint(const orc_grid *g, const orc_cone *cp, const double *C0,
+                   const int32_t *src_cell, const double *src_emit, int n_src, const double *src_map,
+                   int n, const double *pos0, const double *dir0, const double *targets, int T,
+                   double *gD, double *glam, double *gsrc, double *gmap, double *Cs, double *Ps, double *Ds,
+                   double *work, int state_binary32)
+{
+    const int dim = g->dim;
+    const int64_t nn = nodes_of(g);
+    const size_t cs = (size_t)dim * n;
+    uint8_t *act = (uint8_t *)work;                  /* n bytes (all stay active) */
+    double *mu = (double *)((uint8_t *)work + ((n + 15) / 16) * 16);
+    /* forward, storing every state */
+    memcpy(Cs, C0, (size_t)nn * sizeof(double));
+    memcpy(Ps, pos0, cs * sizeof(double));
+    memcpy(Ds, dir0, cs * sizeof(double));
+    for (int a = 0; a < n; ++a) act[a] = 1;
+    for (int s = 0; s < T; ++s) {
+        memcpy(Ps + (size_t)(s + 1) * cs, Ps + (size_t)s * cs, cs * sizeof(double));
+        memcpy(Ds + (size_t)(s + 1) * cs, Ds + (size_t)s * cs, cs * sizeof(double));
+        orc_cone_step(g, cp, Cs + (size_t)s * nn, (uint32_t)s, n, Ps + (size_t)(s + 1) * cs,
+                      Ds + (size_t)(s + 1) * cs, act, src_cell, n_src);
+        orc_field_step(g, Cs + (size_t)s * nn, Cs + (size_t)(s + 1) * nn, src_cell, src_emit, n_src, src_map);
+        if (state_binary32) {
+            double *Cn = Cs + (size_t)(s + 1) * nn, *Pn = Ps + (size_t)(s + 1) * cs, *Dn = Ds + (size_t)(s + 1) * cs;
+            for (int64_t i = 0; i < nn; ++i) Cn[i] = (double)(float)Cn[i];
+            for (size_t i = 0; i < cs; ++i) {
+                Pn[i] = (double)(float)Pn[i];
+                Dn[i] = (double)(float)Dn[i];
+            }
+        }
+    }
+    return orc_adjoint_from_states(g, cp, src_cell, n_src, n, targets, T, Cs, Ps, Ds, gD, glam, gsrc, gmap, mu);
 }
 
 /* Loss of the forward run alone (for finite differences). */

@@ -125,6 +125,9 @@ def _load():
             lib.orc_adjoint.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, P, P, ct.c_int, P, ct.c_int,
                                         P, P, P, ct.c_int, P, P, P, P, P, P, P, P, ct.c_int]
             lib.orc_adjoint.restype = ct.c_double
+            lib.orc_adjoint_from_states.argtypes = [ct.POINTER(_Grid), ct.POINTER(_Cone), P, ct.c_int, ct.c_int, P,
+                                                    ct.c_int, P, P, P, P, P, P, P, P]
+            lib.orc_adjoint_from_states.restype = ct.c_double
             lib.orc_bin_points.argtypes = [ct.c_int, ct.c_int, P, ct.c_double, P, P, P, P, P]
             lib.orc_connect.argtypes = [ct.c_int, ct.c_int, P, P, P, ct.c_int, P, ct.c_double, ct.c_int, P, P]
             lib.orc_connect.restype = ct.c_int
@@ -344,6 +347,31 @@ def adjoint(grid: Grid, cone: Cone, C0, src_cell, src_emit, src_map, pos, dir, t
                                _ptr(smap), n, _ptr(pos), _ptr(dirs), _ptr(tg), T, ct.byref(gD), ct.byref(gl),
                                _ptr(gsrc), _ptr(gmap), _ptr(Cs), _ptr(Ps), _ptr(Ds), _ptr(work),
                                1 if state_binary32 else 0)
+    return float(loss), gD.value, gl.value, gsrc, gmap
+
+
+def adjoint_from_states(grid: Grid, cone: Cone, src_cell, targets, C_states, pos_states, dir_states):
+    """The oracle's backward pass alone over given forward states: ``C_states`` (T + 1,
+    *field shape), ``pos_states`` / ``dir_states`` (T + 1, dim, n).  Returns (loss, dL/dD,
+    dL/dlambda, dL/de (n_src,), dL/dM (field-shaped)) as :func:`adjoint` does.  Fed the
+    states of another program's forward run it gives the gradients that program's backward
+    pass must produce from exactly those states."""
+    Cs = _f64(C_states)
+    Ps, Ds, tg = _f64(pos_states), _f64(dir_states), _f64(targets)
+    T = Cs.shape[0] - 1
+    if T < 0 or Ps.shape[0] != T + 1 or Ds.shape[0] != T + 1:
+        raise ValueError("states: T + 1 fields, positions and directions")
+    n = Ps.shape[2]
+    cell = _i32(src_cell)
+    nn = Cs[0].size
+    work = np.zeros(3 * nn)
+    gD, gl = ct.c_double(), ct.c_double()
+    gsrc = np.zeros(cell.shape[0])
+    gmap = np.zeros(Cs.shape[1:])
+    g, c = grid._c(), cone._c()
+    loss = _load().orc_adjoint_from_states(ct.byref(g), ct.byref(c), _ptr(cell), cell.shape[0], n, _ptr(tg), T,
+                                           _ptr(Cs), _ptr(Ps), _ptr(Ds), ct.byref(gD), ct.byref(gl), _ptr(gsrc),
+                                           _ptr(gmap), _ptr(work))
     return float(loss), gD.value, gl.value, gsrc, gmap
 
 

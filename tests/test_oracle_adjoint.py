@@ -109,3 +109,50 @@ def test_binary32_storage_knob_only_rounds_the_stored_states():
     y = oracle.adjoint(g, c_still, C0z, cells[:0], emit[:0], np.zeros_like(smap), pos32, d_axis, tg, T,
                        state_binary32=True)
     assert x[0] == y[0]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_backward_over_given_states_equals_the_full_adjoint(dim):
+    """The backward pass alone (``adjoint_from_states``), fed states gathered one step at a
+    time by the plain forward (``oracle.run``, not the adjoint's own storing loop), returns
+    exactly the full adjoint's loss and gradients: the state layout (T + 1, dim, n) and the
+    step indexing of the stored states are the ones the backward reads."""
+    g, c, C0, cells, emit, smap, pos, d, tg, T = _problem(dim, seed=8, T=25)
+    full = oracle.adjoint(g, c, C0, cells, emit, smap, pos, d, tg, T)
+    n = pos.shape[1]
+    Cs, Ps, Ds = [C0.copy()], [pos.copy()], [d.copy()]
+    C, p, dd, act = C0.copy(), pos.copy(), d.copy(), np.ones(n, np.uint8)
+    for s in range(T):
+        C, p, dd, act = oracle.run(g, c, C, s, 1, cells, emit, smap, p, dd, act)
+        Cs.append(C)
+        Ps.append(p)
+        Ds.append(dd)
+    assert act.all()
+    part = oracle.adjoint_from_states(g, c, cells, tg, np.stack(Cs), np.stack(Ps), np.stack(Ds))
+    assert part[0] == full[0] and part[1] == full[1] and part[2] == full[2]
+    np.testing.assert_array_equal(part[3], full[3])
+    np.testing.assert_array_equal(part[4], full[4])
+
+
+def test_backward_over_given_states_follows_the_states_it_is_given():
+    """Fed states of another run (here: the forward stored in binary32 by hand), the backward
+    pass returns the ``state_binary32`` adjoint, not the oracle's own: it reads only the states
+    it is given, and its loss is the given endpoint's."""
+    g, c, C0, cells, emit, smap, pos, d, tg, T = _problem(2, seed=9, T=20)
+    n = pos.shape[1]
+    Cs, Ps, Ds = [C0.copy()], [pos.copy()], [d.copy()]
+    C, p, dd, act = C0.copy(), pos.copy(), d.copy(), np.ones(n, np.uint8)
+    for s in range(T):
+        C, p, dd, act = oracle.run(g, c, C, s, 1, cells, emit, smap, p, dd, act)
+        C, p, dd = (x.astype(np.float32).astype(np.float64) for x in (C, p, dd))
+        Cs.append(C)
+        Ps.append(p)
+        Ds.append(dd)
+    part = oracle.adjoint_from_states(g, c, cells, tg, np.stack(Cs), np.stack(Ps), np.stack(Ds))
+    r32 = oracle.adjoint(g, c, C0, cells, emit, smap, pos, d, tg, T, state_binary32=True)
+    own = oracle.adjoint(g, c, C0, cells, emit, smap, pos, d, tg, T)
+    assert part[0] == r32[0] and part[1] == r32[1] and part[2] == r32[2]
+    np.testing.assert_array_equal(part[4], r32[4])
+    assert part[1] != own[1]
+    e = np.stack(Ps)[-1] - tg
+    assert part[0] == pytest.approx(float((e * e).sum()) / n, rel=1e-15)
