@@ -171,19 +171,34 @@ int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone,
              float *d_pos, float *d_dir, uint8_t *d_active, int32_t n_axons,
              void *d_workspace, size_t ws_bytes, void *stream);
 
-/* Advance the field only (rows a1, a2), nsteps >= 0 times; increments the
- * field step counter and flips the current buffer once per step. */
+/* Advance the field only, nsteps >= 0 times: the cue field on the fixed
+ * Eulerian grid of Sec. 5.2, diffusing at its own rate from sources placed
+ * pseudo-randomly (Sec. 4.3), written as the explicit update in the file
+ * header (axis-neighbour stencil, decay, then the point emissions and the
+ * rate map).  Increments the field step counter and flips the current buffer
+ * once per step.  Errors: CUE_ERR_ARG (nsteps < 0), CUE_ERR_STATE (step
+ * counter past 2^32 - 1), CUE_ERR_CUDA; device-side problems via
+ * cue_status. */
 int cue_step(cue_sim *sim, int32_t nsteps);
 
-/* Advance the cones only (rows a3-a6) nsteps times on the current field,
- * which is held fixed; step k uses Philox counter step = cone counter + k.
- * Increments the cone step counter.  cone_step(1) followed by cue_step(1)
- * equals sim_run(1). */
+/* Advance the cones only, nsteps times, on the current field (held fixed):
+ * the growth-cone steering of Sec. 3.5 -- the sensed cue gradient (Sec. 3.5,
+ * the cone senses the concentration change across its width) is added to the
+ * current direction (Eq. 6-7) together with Gaussian noise (Sec. 3.5, the
+ * N(SNR,1) decision; Sec. 5.1 stateless counter-based generator; Sec. 3.2
+ * Box-Muller), normalised, and the cone advances a fixed distance; it stops
+ * when it leaves the bounds (Sec. 3.4) or comes within stop_radius of a
+ * source, a squared-distance test (Sec. 3.3).  Step k uses Philox counter
+ * step = cone counter + k.  Increments the cone step counter.  cone_step(1)
+ * followed by cue_step(1) equals sim_run(1).  Errors as cue_step. */
 int cone_step(cue_sim *sim, int32_t nsteps);
 
-/* Advance cones and field together nsteps times (rows a1-a6): at each step
- * the cones read C^n and the field becomes C^{n+1}.  Requires the cone and
- * field counters to be equal (else CUE_ERR_STATE); advances both. */
+/* Advance cones and field together nsteps times: the coupled model of
+ * Sec. 3.5 (cone step, Eq. 6-7) and Sec. 5.2 (field step) as above; at each
+ * step the cones read C^n and the field becomes C^{n+1}.  Requires the cone
+ * and field counters to be equal (else CUE_ERR_STATE); advances both.  The
+ * library picks the kernel (CUE_OPT_PATH); every path gives the same values
+ * bit for bit.  Errors as cue_step. */
 int sim_run(cue_sim *sim, int32_t nsteps);
 
 /*
@@ -217,6 +232,37 @@ int sim_run(cue_sim *sim, int32_t nsteps);
  */
 int sim_adjoint(cue_sim *sim, const float *d_targets, int32_t nsteps, int32_t ckpt_every, void *d_adj_ws,
                 size_t adj_ws_bytes, float *d_gD, float *d_glambda, float *d_gsrc, float *d_gmap, float *d_loss);
+
+/* The endpoint loss L = (1/n_axons) sum_a |p_a - t_a|^2 of the handle's
+ * current cone positions (the loss sim_adjoint differentiates), written to
+ * d_loss (one float) on the handle's stream.  d_targets: dim*n_axons floats,
+ * SoA like pos.  Errors: CUE_ERR_ARG, CUE_ERR_CUDA. */
+int cue_endpoint_loss(cue_sim *sim, const float *d_targets, float *d_loss);
+
+/* Change the field physics of a handle: the diffusion coefficient D and the
+ * decay rate lambda of the field step (Sec. 5.2 grid model; Sec. 4.3 gives
+ * each cue its own diffusion rate).  Takes effect at the next step; the cone
+ * parameters, steering rule, buffers and counters stay.  Errors: CUE_ERR_ARG
+ * (non-finite or negative values), CUE_ERR_UNSTABLE (D dt / h^2 > 1/(2 dim)
+ * or lambda dt > 1; the handle is left unchanged). */
+int cue_set_physics(cue_sim *sim, float D, float lambda);
+
+/*
+ * cue_adjoint_trace: a diagnostic hook for checking the backward pass on its
+ * own.  With non-NULL buffers, every later sim_adjoint call on this handle
+ * also copies out the FP32 forward states its backward pass reads (the states
+ * recomputed from each checkpoint, exactly as the backward kernels see them):
+ *   d_fields : >= (nsteps + 1) * cells floats; state n at d_fields + n*cells
+ *   d_cones  : >= (nsteps + 1) * 2 * dim * n_axons floats; state n holds
+ *              pos^n then dir^n (each SoA, as d_pos) at
+ *              d_cones + n * 2 * dim * n_axons
+ * for n = 0..nsteps relative to the call's first step.  max_states is the
+ * number of states the buffers hold; a sim_adjoint call with
+ * nsteps + 1 > max_states returns CUE_ERR_ARG.  Both NULL turns the trace off.
+ * The buffers are the caller's.  The copies are queued on the handle's stream.
+ * Errors: CUE_ERR_ARG (one buffer NULL, max_states < 2).
+ */
+int cue_adjoint_trace(cue_sim *sim, float *d_fields, float *d_cones, int64_t max_states);
 
 /* Bytes of adjoint workspace sim_adjoint needs (0 for invalid arguments). */
 size_t cue_adjoint_workspace_bytes(const cue_params *params, int32_t n_src, int32_t n_axons, int32_t nsteps,
@@ -286,14 +332,17 @@ void cue_destroy(cue_sim *sim);
  * Scratch: one file-scope device array of cue_static_scratch_bytes()
  * (4 MiB), held by every GPU that loads the library until the process exits.
  * Problems needing more (cue_workspace_bytes) are rejected with
- * CUE_ERR_SCRATCH.  No cudaMalloc, cudaFree or allocating library routine is
- * called.  The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls on a device share the array and it
- * keeps the last call's contents (the parts that must start at zero are
- * cleared by each call); calls whose GPU work overlaps in time race on it.
- * Device-side status (non-finite values, skipped sources) is recorded in the
- * array but not reported by this call.
+ * CUE_ERR_SCRATCH before anything is queued.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  Every call looks up the array's
+ * device address in the current context (cudaGetSymbolAddress); the first
+ * lookup on a device loads the module there, so make the first call on a
+ * device before any stream capture.  All calls on a device share the array
+ * and it keeps the last call's contents (the parts that must start at zero,
+ * the status word among them, are cleared by each call); calls whose GPU work
+ * overlaps in time race on it.  Device-side problems (non-finite values,
+ * skipped sources, a bounded wait that ran out) are recorded in the array's
+ * status word: read it with cue_static_status after the call and before the
+ * next one, which clears it.
  */
 int sim_run_static(const cue_params *params, const cone_params *cone, float *d_field_a, float *d_field_b,
                    const int32_t *d_src_cell, const float *d_src_emit, int32_t n_src, const float *d_src_map,
@@ -302,6 +351,13 @@ int sim_run_static(const cue_params *params, const cone_params *cone, float *d_f
 
 /* Size in bytes of sim_run_static's device scratch array. */
 size_t cue_static_scratch_bytes(void);
+
+/* Status of the last sim_run_static call on the current device: synchronises
+ * `stream` (the stream that call was given), then returns and clears the
+ * status word of the fixed scratch array: CUE_OK, CUE_ERR_NONFINITE,
+ * CUE_ERR_TIMEOUT, CUE_ERR_BOUNDS or CUE_ERR_CUDA.  Allocates nothing.  Like
+ * sim_run_static it has no counterpart in the paper. */
+int cue_static_status(void *stream);
 
 /* Static description of a status code. */
 const char *cue_strerror(int code);

@@ -350,8 +350,47 @@ int sim_adjoint(cue_sim *s, const float *d_targets, int32_t nsteps, int32_t ckpt
     if (s->cd.steer != 0) return CUE_ERR_ARG;                                    // vector addition only
     if (s->cone_step != s->field_step) return CUE_ERR_STATE;
     if (s->field_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
+    if (s->adj_trace_field && (int64_t)nsteps + 1 > s->adj_trace_cap) return CUE_ERR_ARG;
     return run_adjoint(*s, d_targets, nsteps, ckpt_every, d_adj_ws, adj_ws_bytes, d_gD, d_glambda, d_gsrc, d_gmap,
                        d_loss);
+}
+
+int cue_endpoint_loss(cue_sim *s, const float *d_targets, float *d_loss)
+{
+    if (!s || !d_loss || (s->n_axons > 0 && !d_targets)) return CUE_ERR_ARG;
+    return cuda_err(launch_endpoint_loss(*s, d_targets, d_loss));
+}
+
+int cue_set_physics(cue_sim *s, float D, float lambda)
+{
+    if (!s || !std::isfinite(D) || !std::isfinite(lambda) || D < 0.0f || lambda < 0.0f) return CUE_ERR_ARG;
+    cue_params p = s->params;
+    p.D = D;
+    p.lambda = lambda;
+    FieldDesc f;
+    ConeDesc c;
+    const int rc = make_descs(p, s->cone, f, c);
+    if (rc != CUE_OK) return rc;
+    s->params = p;
+    s->fd = f;                   // the cone descriptor (and its steering rule) stays
+    s->persist_ready = false;    // the persistent path's instance record holds the field descriptor
+    return CUE_OK;
+}
+
+int cue_adjoint_trace(cue_sim *s, float *d_fields, float *d_cones, int64_t max_states)
+{
+    if (!s) return CUE_ERR_ARG;
+    if (!d_fields && !d_cones) {
+        s->adj_trace_field = nullptr;
+        s->adj_trace_cone = nullptr;
+        s->adj_trace_cap = 0;
+        return CUE_OK;
+    }
+    if (!d_fields || !d_cones || max_states < 2) return CUE_ERR_ARG;
+    s->adj_trace_field = d_fields;
+    s->adj_trace_cone = d_cones;
+    s->adj_trace_cap = max_states;
+    return CUE_OK;
 }
 
 int cue_get_state(const cue_sim *s, int64_t *field_step, int64_t *cone_step_out, int32_t *cur_buffer)

@@ -149,6 +149,11 @@ struct Sim {
     // resident path
     bool resident_used = false;
 
+    // adjoint trace (cue_adjoint_trace): copies of the forward states the backward pass reads
+    float *adj_trace_field = nullptr;   // [max_states][cells]
+    float *adj_trace_cone = nullptr;    // [max_states][pos, dir][dim * n_axons]
+    int64_t adj_trace_cap = 0;
+
     // persistent path
     bool persist_ready = false, persist_used = false;
     int persist_rows = 0;         // option (0 = heuristic)
@@ -249,6 +254,8 @@ int run_coupled(Sim &s, int nsteps);
 size_t adjoint_workspace_bytes(const cue_params &p, int n_src, int n_axons, int nsteps, int ckpt_every);
 int run_adjoint(Sim &s, const float *targets, int nsteps, int ckpt_every, void *ws, size_t ws_bytes, float *gD,
                 float *gl, float *gsrc, float *gmap, float *loss);
+// The endpoint loss of the handle's current cone state (one launch).
+cudaError_t launch_endpoint_loss(Sim &s, const float *targets, float *loss);
 
 // ---- launchers (each returns cudaGetLastError() after its launches) ----
 // One field step Cin -> Cout.  With `sources_done` non-null the kernel may also

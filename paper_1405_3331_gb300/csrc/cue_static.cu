@@ -8,36 +8,29 @@
 // share it and it keeps the last call's contents; cue_init clears the parts
 // that must start at zero (status word, cone counter, tile counts).  Calls
 // whose GPU work overlaps (two streams, or two host threads) race on it.
-#include <mutex>
-
+// The status word sits at the start of the array (the workspace layout puts
+// it at offset 0); cue_static_status reads and clears it.
 #include "cue_internal.h"
 
 namespace {
 
 constexpr size_t kStaticScratchBytes = 4u << 20;   // 4 MiB
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_lock;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device, resolved once per
-// device (host code may not use the symbol itself: on the host it names a
-// stand-in object, not device memory).
+// Device address of g_static_scratch in the current context.  Host code may
+// not use the symbol itself: on the host it names a stand-in object, not
+// device memory.  The address is looked up on every call (the lookup
+// allocates nothing), so a reset device or another current context never
+// sees an address resolved elsewhere.  The first lookup on a device loads the
+// module there, which is why the first call must come before any stream
+// capture.
 int scratch_for_current_device(void **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return CUE_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return CUE_ERR_ARG;
-    std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) return CUE_ERR_CUDA;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return CUE_ERR_CUDA;
+    *out = p;
     return CUE_OK;
 }
 
@@ -71,6 +64,26 @@ int sim_run_static(const cue_params *params, const cone_params *cone, float *d_f
     cue_destroy(h);
     if (rc == CUE_OK) *cur_buffer_out = cur;
     return rc;
+}
+
+int cue_static_status(void *stream)
+{
+    void *ws = nullptr;
+    int rc = scratch_for_current_device(&ws);
+    if (rc != CUE_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, ws, sizeof(word), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && word) {
+        e = cudaMemsetAsync(ws, 0, sizeof(word), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) return CUE_ERR_CUDA;
+    if (word & cue::kStatusNonFinite) return CUE_ERR_NONFINITE;
+    if (word & cue::kStatusTimeout) return CUE_ERR_TIMEOUT;
+    if (word & cue::kStatusBounds) return CUE_ERR_BOUNDS;
+    return CUE_OK;
 }
 
 }  // extern "C"

@@ -14,13 +14,18 @@
 //          linear in C^n (its adjoint scatters into mu, now dL/dC^n) and
 //          multilinear in p (adds into pbar).
 // Memory: the forward keeps (C, p, d) every ckpt_every steps; each segment is
-// recomputed with the plain kernels, storing every step, then walked
-// backwards (two kernels per step).
+// recomputed storing every step (one persistent launch on 2D grids with
+// nx % 4 == 0, else a cone and a field launch per step), then walked
+// backwards: one persistent cooperative launch per segment (adj_persist_kernel:
+// field warps advance the adjoint field, cone warps scatter the cone adjoint,
+// one bounded grid barrier per step), or, where that launch does not apply, a
+// field launch and a cone launch per step.
 //
 // Precision: the adjoint field is double-float (two FP32 planes carried with
-// error-free transformations, so GB300 runs it at FP32 rate); the cone adjoint
-// and the per-thread partial sums are FP32; block totals of the dD and dlambda
-// sums, the per-source sums and the segment totals of the rate-map sum are
+// error-free transformations, so GB300 runs it at FP32 rate); the cone reverse
+// mode is FP64 at the FP32 forward values, with dL/d(p, d) kept in FP64; the
+// per-thread partial sums of the dD and dlambda products are FP32, their block
+// totals, the per-source sums and the segment totals of the rate-map sum
 // FP64.
 #include <algorithm>
 
@@ -841,6 +846,30 @@ __global__ void __launch_bounds__(256) adj_loss_kernel(int n, int dim, const flo
     block_add2<false>(s, 0.0f, loss_acc);
 }
 
+// The endpoint loss alone, L = (1/n) sum_a |p_a - t_a|^2, by one block:
+// per-thread FP32 sums over a grid-stride share of the cones, block total in
+// FP64, written as FP32 (no accumulator left behind in device memory).
+__global__ void __launch_bounds__(1024) loss_only_kernel(int n, int dim, const float *__restrict__ P,
+                                                         const float *__restrict__ T, float *out)
+{
+    __shared__ double sw[32];
+    float s = 0.0f;
+    for (int a = threadIdx.x; a < n; a += blockDim.x)
+        for (int i = 0; i < dim; ++i) {
+            const float e = P[(size_t)i * n + a] - T[(size_t)i * n + a];
+            s = fmaf(e, e, s);
+        }
+    double v = warp_sum((double)s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sw[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sw[lane] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) *out = n > 0 ? (float)(v / (double)n) : 0.0f;
+    }
+}
+
 // Scale the accumulators into the caller's outputs (block 0 sums the field
 // kernel's per-block dD / dlambda slots).
 __global__ void __launch_bounds__(256) adj_finalize_kernel(FieldDesc f, int n_axons, const double *acc, int n_src,
@@ -998,6 +1027,13 @@ void launch_adj_field(Sim &s, const float *mu_in, float *mu_out, const float *C,
 
 }  // namespace
 
+cudaError_t launch_endpoint_loss(Sim &s, const float *targets, float *loss)
+{
+    loss_only_kernel<<<1, 1024, 0, s.stream>>>(s.n_axons, s.fd.dim, s.pos, targets, loss);
+    s.launches++;
+    return cudaGetLastError();
+}
+
 size_t adjoint_workspace_bytes(const cue_params &p, int n_src, int n_axons, int nsteps, int ckpt_every)
 {
     if (nsteps <= 0 || ckpt_every <= 0) return 0;
@@ -1099,6 +1135,12 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
                 !ok(launch_field_and_sources(s, sgC + cells * m, sgC + cells * (m + 1))))
                 return CUE_ERR_CUDA;
         }
+        if (s.adj_trace_field &&
+            (!ok(cudaMemcpyAsync(s.adj_trace_field + cells * (size_t)j * k, sgC, sizeof(float) * cells * (len + 1),
+                                 cudaMemcpyDeviceToDevice, st)) ||
+             !ok(cudaMemcpyAsync(s.adj_trace_cone + 2 * cone_n * (size_t)j * k, sgP,
+                                 sizeof(float) * 2 * cone_n * (len + 1), cudaMemcpyDeviceToDevice, st))))
+            return CUE_ERR_CUDA;
         if (persist_bw) {
             A.segC = sgC;
             A.segP = sgP;

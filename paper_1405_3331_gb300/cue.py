@@ -54,7 +54,8 @@ class cue_snr_params(ct.Structure):
 EXPORTED = ("cue_set_steering", "cue_workspace_bytes", "cue_init", "cue_step", "cone_step", "sim_run", "cue_get_state",
             "cue_set_state", "cue_set_stream", "cue_set_option", "cue_launch_count", "cue_status",
             "cue_destroy", "cue_strerror", "cue_kernel_time", "cue_cone_updates", "cue_get_option", "sim_run_static",
-            "cue_static_scratch_bytes", "sim_adjoint", "cue_adjoint_workspace_bytes")
+            "cue_static_scratch_bytes", "cue_static_status", "sim_adjoint", "cue_adjoint_workspace_bytes",
+            "cue_adjoint_trace", "cue_endpoint_loss", "cue_set_physics")
 
 
 class cue_params(ct.Structure):
@@ -114,8 +115,16 @@ def lib():
             L.sim_adjoint.restype = ct.c_int
             L.cue_adjoint_workspace_bytes.argtypes = [ct.POINTER(cue_params), I32, I32, I32, I32]
             L.cue_adjoint_workspace_bytes.restype = SZ
+            L.cue_adjoint_trace.argtypes = [P, P, P, I64]
+            L.cue_adjoint_trace.restype = ct.c_int
+            L.cue_endpoint_loss.argtypes = [P, P, P]
+            L.cue_endpoint_loss.restype = ct.c_int
+            L.cue_set_physics.argtypes = [P, ct.c_float, ct.c_float]
+            L.cue_set_physics.restype = ct.c_int
             L.cue_static_scratch_bytes.argtypes = []
             L.cue_static_scratch_bytes.restype = SZ
+            L.cue_static_status.argtypes = [P]
+            L.cue_static_status.restype = ct.c_int
             L.cue_launch_count.argtypes = [P]
             L.cue_launch_count.restype = ct.c_uint64
             L.cue_status.argtypes = [P]
@@ -236,8 +245,25 @@ def sim_adjoint(h, targets: int, nsteps: int, ckpt_every: int, ws: int, ws_bytes
                              gmap or None, loss)
 
 
+def cue_endpoint_loss(h, targets: int, loss: int) -> int:
+    return lib().cue_endpoint_loss(h, targets or None, loss)
+
+
+def cue_set_physics(h, D: float, lam: float) -> int:
+    return lib().cue_set_physics(h, D, lam)
+
+
+def cue_adjoint_trace(h, fields: int, cones: int, max_states: int) -> int:
+    return lib().cue_adjoint_trace(h, fields or None, cones or None, max_states)
+
+
 def cue_static_scratch_bytes() -> int:
     return int(lib().cue_static_scratch_bytes())
+
+
+def cue_static_status(stream: int) -> int:
+    """Synchronise ``stream``, then return and clear the status word of sim_run_static's scratch."""
+    return lib().cue_static_status(stream or None)
 
 
 def cue_destroy(h) -> None:
@@ -398,17 +424,27 @@ class Simulation:
         return (self.fields[cur].cpu().numpy(), self.pos.cpu().numpy(), self.dir.cpu().numpy(),
                 self.active.cpu().numpy(), fs, cs)
 
-    def adjoint(self, targets, nsteps: int, ckpt_every: int = 64, want_map: bool = True):
+    def adjoint(self, targets, nsteps: int, ckpt_every: int = 64, want_map: bool = True, trace: bool = False):
         """Gradients of L = mean_a |p_a(T) - t_a|^2 after ``nsteps`` more steps (no-stopping
-        runs only).  Returns a dict of device tensors: loss, dD, dlambda, dsrc, dmap (or None).
+        runs only).  Returns a dict of device tensors: loss, dD, dlambda, dsrc, dmap (or None);
+        with ``trace`` also ``trace_C`` (nsteps + 1, *shape) and ``trace_cone`` (nsteps + 1, 2,
+        dim, n_axons): the FP32 forward states the backward pass read (cue_adjoint_trace).
         The handle advances by ``nsteps``, as with sim_run."""
         torch = self.torch
         dev = self.device
         tg = torch.as_tensor(targets, dtype=torch.float32, device=dev).contiguous()
+        tr = None
+        if trace:
+            tr = (torch.empty((nsteps + 1,) + tuple(self.fields[0].shape), dtype=torch.float32, device=dev),
+                  torch.empty((nsteps + 1, 2, self.dim, self.n_axons), dtype=torch.float32, device=dev))
+            _check(cue_adjoint_trace(self.h, tr[0].data_ptr(), tr[1].data_ptr(), nsteps + 1), "cue_adjoint_trace")
         nbytes = cue_adjoint_workspace_bytes(self.params, self.n_src, self.n_axons, nsteps, ckpt_every)
         if nbytes == 0:
             raise CueError(CUE_ERR_ARG, "cue_adjoint_workspace_bytes")
-        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        ws = getattr(self, "_adj_ws", None)           # one adjoint workspace, reused while it is big enough
+        if ws is None or ws.numel() < nbytes + 256:
+            ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+            self._adj_ws = ws
         ws_ptr = (ws.data_ptr() + 255) & ~255
         out = {k: torch.zeros((), dtype=torch.float32, device=dev) for k in ("loss", "dD", "dlambda")}
         out["dsrc"] = torch.zeros(max(self.n_src, 1), dtype=torch.float32, device=dev)
@@ -416,9 +452,13 @@ class Simulation:
         rc = sim_adjoint(self.h, tg.data_ptr(), nsteps, ckpt_every, ws_ptr, nbytes, out["dD"].data_ptr(),
                          out["dlambda"].data_ptr(), out["dsrc"].data_ptr() if self.n_src else 0,
                          out["dmap"].data_ptr() if want_map else 0, out["loss"].data_ptr())
+        if trace:
+            _check(cue_adjoint_trace(self.h, 0, 0, 0), "cue_adjoint_trace")
         _check(rc, "sim_adjoint")
         self._adj_keep = (ws, tg)            # keep the buffers alive until the stream has used them
         out["dsrc"] = out["dsrc"][: self.n_src]
+        if trace:
+            out["trace_C"], out["trace_cone"] = tr
         return out
 
     def run_host(self, C, pos, dir, active, nsteps: int, out=None):

@@ -72,3 +72,20 @@ def ambiguous_cones(w, C, step, pos, dir, active, margin=1e-4):
         amb |= (np.abs(d2 - r2) <= margin * r2 * 10).any(axis=1)
     amb &= active.astype(bool)
     return amb
+
+
+def compare_cones(w, C, step, pos0, dir0, act0, got_pos, got_dir, got_act):
+    """One cone step of the GPU (got_*) against the oracle's from the same state (C, pos0, dir0,
+    act0 at Philox step `step`): stop flags identical, positions to POS_RTOL, directions to 1e-5,
+    cones whose decision rounding may flip excluded (at most 1%, or 2) and counted."""
+    want_pos, want_dir, want_act = oracle.cone_step(grid_of(w), cone_of(w), C.astype(np.float64), step,
+                                                    pos0, dir0, act0, w.src_cell)
+    amb = ambiguous_cones(w, C.astype(np.float64), step, pos0, dir0, act0)
+    keep = ~amb
+    assert amb.sum() <= max(2, 0.01 * act0.sum()), amb.sum()
+    np.testing.assert_array_equal(got_act[keep], want_act[keep])
+    err = pos_rel_err(got_pos[:, keep], want_pos[:, keep])
+    assert (err.max() if err.size else 0.0) <= POS_RTOL, err.max()
+    derr = np.abs(got_dir[:, keep] - want_dir[:, keep]).max() if keep.any() else 0.0
+    assert derr <= 1e-5, derr
+    return int(amb.sum())

@@ -206,6 +206,52 @@ def test_autograd_function_gives_the_adjoint_gradients(cue):
     np.testing.assert_allclose(smap.grad.cpu().numpy(), 3 * ref["dmap"], rtol=1e-5, atol=1e-12)
 
 
+def test_autograd_problem_reuses_its_buffers_and_skips_the_adjoint_without_grad(cue):
+    """An EndpointProblem called repeatedly gives the same loss and gradients bit for bit
+    (its state is reset on the device each call), new parameter values take effect (D and
+    lambda through cue_set_physics, emissions and map copied device to device), and under
+    no_grad the forward alone (coupled steps + the loss kernel) gives the adjoint's loss."""
+    import torch
+    from paper_1405_3331_gb300.autograd import EndpointProblem
+    w = _copy64(seed=57, nsteps=60)
+    dev = torch.device("cuda:0")
+    prob = EndpointProblem(w, w.targets, 60, 16, device=dev)
+    D = torch.tensor(w.D, dtype=torch.float32, device=dev, requires_grad=True)
+    lam = torch.tensor(w.lam, dtype=torch.float32, device=dev, requires_grad=True)
+    emit = torch.as_tensor(w.src_emit, device=dev).clone().requires_grad_(True)
+    smap = torch.as_tensor(w.src_map, device=dev).clone().requires_grad_(True)
+    L1 = prob(D, lam, emit, smap)
+    L1.backward()
+    g1 = [t.grad.clone() for t in (D, lam, emit, smap)]
+    for t in (D, lam, emit, smap):
+        t.grad = None
+    L2 = prob(D, lam, emit, smap)
+    L2.backward()
+    assert float(L1) == float(L2)
+    for a, t in zip(g1, (D, lam, emit, smap)):
+        assert torch.equal(a, t.grad)
+    ref = _gpu(cue, w, 60, 16)
+    assert _rel(float(L1.detach()), float(ref["loss"])) < 1e-6
+    assert _rel(float(g1[0]), float(ref["dD"])) < 1e-6
+    with torch.no_grad():
+        L0 = prob(D, lam, emit, smap)
+    assert _rel(float(L0), float(ref["loss"])) < 1e-6
+    # other parameter values: the same as a fresh handle built with them
+    w2 = W.config_c5(seed=57, n=64, n_src=2, n_axons=64, nsteps=60)
+    w2.D, w2.lam = 0.8, 0.02
+    w2.src_emit = (w.src_emit * 1.5).astype(np.float32)
+    ref2 = _gpu(cue, w2, 60, 16)
+    D2 = torch.tensor(0.8, dtype=torch.float32, device=dev, requires_grad=True)
+    lam2 = torch.tensor(0.02, dtype=torch.float32, device=dev, requires_grad=True)
+    e2 = torch.as_tensor(w2.src_emit, device=dev).clone().requires_grad_(True)
+    L3 = prob(D2, lam2, e2, smap)
+    L3.backward()
+    assert float(L3) == float(ref2["loss"])
+    assert float(D2.grad) == float(ref2["dD"])
+    np.testing.assert_array_equal(e2.grad.cpu().numpy(), ref2["dsrc"])
+    prob.close()
+
+
 def test_adjoint_refuses_runs_that_stop(cue):
     w = W.make("stop", 2, 32, 32, n_src=2, n_axons=8, C0="smooth", seed=55, targets=True)   # wall stop
     sim = cue.Simulation(w)
@@ -294,3 +340,61 @@ def test_adjoint_full_horizon_on_the_small_copy_is_reported(cue, record_property
     print("full-horizon 64x64 adjoint, relative differences:",
           {"gpu_vs_oracle": [_rel(float(g["dD"]), gD), _rel(float(g["dlambda"]), gl), _relmax(g["dsrc"], gsrc)],
            "oracle_vs_fd": [_rel(gD, fd["dD"]), _rel(gl, fd["dlambda"]), _relmax(gsrc, fd_src)]})
+
+
+def _gpu_traced(cue, w, nsteps, k, path=None):
+    sim = cue.Simulation(w) if path is None else cue.Simulation(w, path=path)
+    g = sim.adjoint(w.targets, nsteps, k, trace=True)
+    sim.check()
+    out = {key: (None if v is None else v.cpu().numpy()) for key, v in g.items()}
+    out["pos_end"] = sim.pos.cpu().numpy()
+    sim.close()
+    return out
+
+
+@pytest.mark.parametrize("seed,path", [(50, None), (51, None), (50, "plain")])
+def test_adjoint_backward_over_the_gpu_states_full_horizon(cue, seed, path):
+    """The backward pass held to 1e-4 over the adjoint workload's whole horizon: the 64x64 copy,
+    2,000 steps, checkpoint every 64.  The forward of an FP32 run and of the FP64 oracle part
+    ways over this horizon (cones circle the sources; see the reported test above), so the
+    backward kernels are compared on the identical states instead: the FP32 states the GPU
+    recomputed from its checkpoints and walked back (cue_adjoint_trace) go into the oracle's
+    backward pass alone (FP64), and the GPU gradients must match it -- dD, dlambda and every
+    e_k to 1e-4 relative, every rate-map entry to 1e-4 of the largest, the loss to 1e-6.
+    Run on the persistent backward (one launch per segment) and on the per-step launches."""
+    w, T = _copy64(seed=seed), 2000
+    g = _gpu_traced(cue, w, T, 64, path=cue.CUE_PATH_PLAIN if path == "plain" else None)
+    Cs = g["trace_C"].astype(np.float64)
+    Ps, Ds = g["trace_cone"][:, 0], g["trace_cone"][:, 1]
+    # the trace is the run: it starts at the initial state and ends where the forward ended
+    np.testing.assert_array_equal(g["trace_C"][0], w.field0())
+    np.testing.assert_array_equal(Ps[0], w.pos)
+    np.testing.assert_array_equal(Ds[0], w.dir)
+    np.testing.assert_array_equal(Ps[-1], g["pos_end"])
+    grid = oracle.Grid(2, w.nx, w.ny, h=w.h, D=w.D, lam=w.lam, dt=w.dt)
+    loss, gD, gl, gsrc, gmap = oracle.adjoint_from_states(grid, cone_of(w), w.src_cell, w.targets, Cs, Ps, Ds)
+    assert _rel(float(g["loss"]), loss) < 1e-6
+    assert _rel(float(g["dD"]), gD) < ADJ_RTOL, (float(g["dD"]), gD)
+    assert _rel(float(g["dlambda"]), gl) < ADJ_RTOL, (float(g["dlambda"]), gl)
+    for k in range(w.n_src):
+        assert _rel(float(g["dsrc"][k]), gsrc[k]) < ADJ_RTOL, (k, float(g["dsrc"][k]), gsrc[k])
+    assert _relmax(g["dmap"], gmap) < ADJ_RTOL
+
+
+def test_adjoint_backward_over_the_gpu_states_3d(cue):
+    """The same identical-state comparison in 3D (trilinear sample, 3-component noise), over
+    600 steps with checkpoints every 50: gradients to 1e-4 of the oracle's backward pass."""
+    w = W.make("adj3d-long", 3, 20, 16, 12, dt=0.15, n_src=3, n_axons=40, C0="smooth", seed=56, wall_mode=1,
+               src_map=True, targets=True)
+    T = 600
+    g = _gpu_traced(cue, w, T, 50)
+    Cs = g["trace_C"].astype(np.float64)
+    Ps, Ds = g["trace_cone"][:, 0], g["trace_cone"][:, 1]
+    np.testing.assert_array_equal(Ps[-1], g["pos_end"])
+    grid = oracle.Grid(3, w.nx, w.ny, w.nz, h=w.h, D=w.D, lam=w.lam, dt=w.dt)
+    loss, gD, gl, gsrc, gmap = oracle.adjoint_from_states(grid, cone_of(w), w.src_cell, w.targets, Cs, Ps, Ds)
+    assert _rel(float(g["loss"]), loss) < 1e-6
+    assert _rel(float(g["dD"]), gD) < ADJ_RTOL
+    assert _rel(float(g["dlambda"]), gl) < ADJ_RTOL
+    assert _relmax(g["dsrc"], gsrc) < ADJ_RTOL
+    assert _relmax(g["dmap"], gmap) < ADJ_RTOL

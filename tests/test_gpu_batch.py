@@ -10,7 +10,9 @@ autotuner has measured its candidates (it must restore the state it found).
 import numpy as np
 import pytest
 
+import oracle
 from paper_1405_3331_gb300 import workloads as W
+from parity import FIELD_RTOL, compare_cones, field_rel_err, grid_of
 
 pytestmark = pytest.mark.gpu
 
@@ -174,3 +176,30 @@ def test_long_per_step_runs_replay_a_bounded_graph(cue, batch_mod):
     assert a.cone_updates() == g.cone_updates()
     a.close()
     g.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("sample", ["c4-16", "mixed"])
+def test_batched_step_matches_oracle(cue, batch_mod, sample, mode):
+    """Every instance's batched step against the FP64 oracle's from the identical state: the
+    batch runs 6 steps, each instance's state is copied out, then one more batched step must
+    match one oracle step from that copy (field to FIELD_RTOL, cones as in the single-instance
+    parity tests).  Samples: sixteen instances of the 512-instance workload, and the mixed set
+    (nx % 4 = 0..3, stop radius, wall clamp, a rate map, no sources or cones)."""
+    ws = W.config_c4(n_instances=16, nsteps=8) if sample == "c4-16" else _mixed()
+    b = batch_mod.Batch(ws)
+    b.set_option(batch_mod.CUE_BOPT_MODE, mode)
+    after = 6
+    b.run(after)
+    b.check()
+    before = [b.snapshot(i) for i in range(len(ws))]
+    b.run(1)
+    b.check()
+    for i, w in enumerate(ws):
+        C, pos, dirs, act = before[i]
+        C1, pos1, dirs1, act1 = b.snapshot(i)
+        want = oracle.field_step(grid_of(w), C.astype(np.float64), w.src_cell, w.src_emit, w.src_map)
+        assert field_rel_err(C1, want) <= FIELD_RTOL, w.name
+        if w.n_axons:
+            compare_cones(w, C, after, pos, dirs, act, pos1, dirs1, act1)
+    b.close()

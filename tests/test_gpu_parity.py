@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_1405_3331_gb300 import workloads as W
-from parity import (FIELD_RTOL, POS_RTOL, ambiguous_cones, cone_of, field_rel_err, grid_of,
+from parity import (FIELD_RTOL, POS_RTOL, ambiguous_cones, compare_cones, cone_of, field_rel_err, grid_of,
                     pos_rel_err)
 
 pytestmark = pytest.mark.gpu
@@ -79,18 +79,7 @@ def test_field_step_matches_oracle(cue, name):
     sim.close()
 
 
-def _compare_cones(w, C, step, pos0, dir0, act0, got_pos, got_dir, got_act):
-    want_pos, want_dir, want_act = oracle.cone_step(grid_of(w), cone_of(w), C.astype(np.float64), step,
-                                                    pos0, dir0, act0, w.src_cell)
-    amb = ambiguous_cones(w, C.astype(np.float64), step, pos0, dir0, act0)
-    keep = ~amb
-    assert amb.sum() <= max(2, 0.01 * act0.sum()), amb.sum()
-    np.testing.assert_array_equal(got_act[keep], want_act[keep])
-    err = pos_rel_err(got_pos[:, keep], want_pos[:, keep])
-    assert (err.max() if err.size else 0.0) <= POS_RTOL, err.max()
-    derr = np.abs(got_dir[:, keep] - want_dir[:, keep]).max() if keep.any() else 0.0
-    assert derr <= 1e-5, derr
-    return int(amb.sum())
+_compare_cones = compare_cones
 
 
 @pytest.mark.parametrize("name", CASES)
