@@ -39,8 +39,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cue", "reference"], default="cue")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "graph"])
-    ap.add_argument("--path", default="auto", choices=["auto", "plain", "fused", "persist", "resident"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2x", "c3", "c4", "c5", "graph"])
+    ap.add_argument("--path", default="auto", choices=list(PATHS))
     ap.add_argument("--depth", type=int, default=0, help="temporal depth on the fused path (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -48,9 +48,16 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--run-steps", type=int, default=0,
                     help="time steps per benchmark step (0 = the workload's own count); for profiling")
+    ap.add_argument("--subs", default="clustered,c3,batched,adjoint,whole_run",
+                    help="with the default workload: sub-figures added to its line (comma list of clustered, c3, "
+                         "batched, adjoint, whole_run; empty for none)")
+    ap.add_argument("--whole-run-cones", type=int, default=2048,
+                    help="cones the oracle follows over a whole run (the first ones)")
     # internal: time the oracle with its field rows over threads, in a process of its own
     # (no CUDA context, no second OpenMP runtime next to PyTorch's): WORKLOAD:NSTEPS:THREADS
     ap.add_argument("--oracle-threads-sample", default="", help=argparse.SUPPRESS)
+    # internal: the oracle over a whole run in a process of its own: WORKLOAD:NCONES:OUT
+    ap.add_argument("--oracle-whole-run", default="", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -60,6 +67,8 @@ def workload(name, rank=0):
         return W.config_c1(seed=0 + 100 * rank)
     if name == "c2":
         return W.config_c2(seed=1 + 100 * rank)
+    if name == "c2x":
+        return W.config_c2_clustered(seed=8 + 100 * rank)
     if name == "c3":
         return W.config_c3(seed=2 + 100 * rank)
     if name == "c5":
@@ -312,13 +321,142 @@ def aggregate(local_ms, units_per_step, steps, world, dist=None, device=None):
 
 
 # ------------------------------------------------------------------ GPU arm
+PATHS = ("auto", "plain", "fused", "persist", "resident")
+
+
+def path_code(cue, name):
+    return {"auto": cue.CUE_PATH_AUTO, "plain": cue.CUE_PATH_PLAIN, "fused": cue.CUE_PATH_FUSED,
+            "persist": cue.CUE_PATH_PERSIST, "resident": cue.CUE_PATH_RESIDENT}[name]
+
+
+class Runner:
+    """One simulation handle over a workload, with its initial state kept on the device so that
+    every benchmark step restarts from it (reset and L2 flush outside the timed events)."""
+
+    def __init__(self, cue, torch, dev, w, path="auto", depth=0, flush=None):
+        self.cue, self.torch, self.w = cue, torch, w
+        self.sim = cue.Simulation(w, device=dev, path=path_code(cue, path))
+        if depth:
+            self.sim.set_option(cue.CUE_OPT_TEMPORAL_DEPTH, depth)
+        self.stream = self.sim.stream
+        s = self.sim
+        self.init = (s.fields[0].clone(), s.pos.clone(), s.dir.clone(), s.active.clone())
+        self.flush = flush
+
+    def reset(self):
+        s, torch = self.sim, self.torch
+        with torch.cuda.stream(self.stream):
+            for dst, src in zip((s.fields[0], s.pos, s.dir, s.active), self.init):
+                dst.copy_(src)
+        self.cue._check(self.cue.cue_set_state(s.h, 0, 0, 0), "cue_set_state")
+
+    def timed_runs(self, steps, warmup, barrier, sampler=None, sample_period=16):
+        """``warmup`` untimed runs, then ``steps`` timed whole runs.  Returns a dict with the
+        per-run device times, the launches of the timed region, the cone updates of one run and
+        the CUDA-event times of every ``sample_period``-th launch of the dominant kernel."""
+        torch, sim, w = self.torch, self.sim, self.w
+        for i in range(max(warmup, 3)):
+            self.reset()
+            if i == max(warmup, 3) - 1:
+                sim.cone_updates()
+            sim.sim_run(w.nsteps)
+        sim.check()
+        cone_updates = sim.cone_updates()
+        path = sim_path_used(sim)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sim.set_option(self.cue.CUE_OPT_TIME_KERNEL, 1 if path in ("persist", "resident") else sample_period)
+        sim.kernel_time()
+        barrier()
+        if sampler is not None:
+            sampler.start()
+        launches0 = sim.launches()
+        for k in range(steps):
+            with torch.cuda.stream(self.stream):
+                self.flush.zero_()
+            self.reset()
+            evs[k][0].record(self.stream)
+            sim.sim_run(w.nsteps)
+            evs[k][1].record(self.stream)
+        barrier()
+        clocks = sampler.stop() if sampler is not None else None
+        launches = sim.launches() - launches0
+        kern_ms, kern_n = sim.kernel_time()
+        sim.set_option(self.cue.CUE_OPT_TIME_KERNEL, 0)
+        sim.check()
+        return {"run_ms": [a.elapsed_time(b) for a, b in evs], "launches": launches, "cone_updates": cone_updates,
+                "sampled_ms": kern_ms, "sampled_n": kern_n, "clocks": clocks, "path": path}
+
+    def close(self):
+        self.sim.close()
+
+
+def dominant_kernel(sim, w):
+    """(name, launches of the dominant kernel in one run, steps one launch covers)."""
+    path = sim_path_used(sim)
+    if path == "fused":
+        K = sim.get_option(sim_cue().CUE_INFO_DEPTH)
+        return "fused", (w.nsteps + K - 1) // K, K
+    if path in ("persist", "resident"):
+        return path, 1, w.nsteps
+    return ("step3d" if w.dim == 3 else "field"), w.nsteps, 1
+
+
+def sim_cue():
+    from paper_1405_3331_gb300 import cue
+    return cue
+
+
+def roofline_single(sim, w, rec, ms_per_run, hbm, peak_kind, work):
+    """Roofline of the dominant kernel.  achieved = 8 B per node update (12 B with a rate map;
+    the 3D step launch also moves its cones' state) x the node updates one launch makes, over
+    the launch's time.  The launch time is the timed runs' device time over the dominant
+    kernel's launches in them: on these paths the dominant kernel is all but all of a run (the
+    committed launch lists), so launches x time never exceeds the run.  The CUDA-event figure of
+    sampled launches is kept beside it (events between back-to-back launches inflate it)."""
+    name, per_run, K = dominant_kernel(sim, w)
+    bpc = 12 if w.src_map is not None else 8
+    units = w.n_cells * K
+    alg = bpc * units
+    if name == "step3d":
+        alg += w.n_axons * (4 * w.dim * 4 + 1)
+    avg_s = ms_per_run / per_run / 1e3
+    achieved = alg / avg_s / 1e9
+    # compulsory traffic: a launch reads and writes its field once however many steps it covers
+    one_pass = bpc * w.n_cells * (1 if name == "fused" else K)
+    r = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+         "traffic": recorded_traffic({"step3d": "field"}.get(name, name), work), "kernel": name,
+         "peak_kind": peak_kind, "launches_per_run": per_run, "steps_per_launch": K,
+         "node_updates_per_launch": units, "algorithmic_bytes_per_launch": alg,
+         "avg_launch_us": avg_s * 1e6,
+         "launch_time": "device time of the timed runs / launches of the dominant kernel in them",
+         "compulsory_bytes_per_launch": one_pass, "compulsory_gbs": one_pass / avg_s / 1e9,
+         "compulsory_frac": one_pass / avg_s / 1e9 / hbm}
+    if rec["sampled_n"]:
+        r["sampled_launch_us"] = rec["sampled_ms"] / rec["sampled_n"] * 1e3
+    if name == "resident":
+        r["note"] = ("one block holds the grid in shared memory for the whole run: HBM is read and "
+                     "written once per launch; a step is bound by one SM's shared-memory and issue rate")
+    return r
+
+
+def single_summary(runner, rec, hbm, peak_kind, work, world=1):
+    w = runner.w
+    ms = statistics.median(rec["run_ms"])
+    return {"workload": describe(w)["workload"], "path": rec["path"], "value": world * w.n_cells * w.nsteps / (ms / 1e3),
+            "unit": UNIT, "ms_per_run": ms, "runs": len(rec["run_ms"]),
+            "axon_steps_per_s": world * rec["cone_updates"] / (ms / 1e3),
+            "roofline": roofline_single(runner.sim, w, rec, ms, hbm, peak_kind, work),
+            "gpu_launches_per_run": rec["launches"] / max(1, len(rec["run_ms"]))}
+
+
 def main():
     args = parse_args()
     if args.oracle_threads_sample:
         return oracle_threads_child(args.oracle_threads_sample)
+    if args.oracle_whole_run:
+        return oracle_whole_run_child(args.oracle_whole_run)
     if args.impl == "reference":
         return run_reference(args)
-    import numpy as np
     import torch
     from paper_1405_3331_gb300 import build as cue_build
     cue_build.build()
@@ -347,139 +485,66 @@ def main():
     w = workload(args.workload, rank)
     if args.run_steps:
         w.nsteps = args.run_steps
-    path = {"auto": cue.CUE_PATH_AUTO, "plain": cue.CUE_PATH_PLAIN, "fused": cue.CUE_PATH_FUSED,
-            "persist": cue.CUE_PATH_PERSIST, "resident": cue.CUE_PATH_RESIDENT}[args.path]
-    sim = cue.Simulation(w, device=dev, path=path)
-    if args.depth:
-        sim.set_option(cue.CUE_OPT_TEMPORAL_DEPTH, args.depth)
-    stream = sim.stream
-    C0 = sim.fields[0].clone()
-    pos0, dir0, act0 = sim.pos.clone(), sim.dir.clone(), sim.active.clone()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-
-    def reset():
-        with torch.cuda.stream(stream):
-            sim.fields[0].copy_(C0)
-            sim.pos.copy_(pos0)
-            sim.dir.copy_(dir0)
-            sim.active.copy_(act0)
-        cue._check(cue.cue_set_state(sim.h, 0, 0, 0), "cue_set_state")
-
-    # warm-up (also counts the cone updates of one run: every run is identical)
-    for i in range(max(args.warmup, 3)):
-        reset()
-        if i == max(args.warmup, 3) - 1:
-            sim.cone_updates()
-        sim.sim_run(w.nsteps)
-    sim.check()
-    cone_updates_per_run = sim.cone_updates()
-
-    # timed region
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    sampler = ClockSampler(gpu_id_for(local))
-    # events around every 16th launch of the dominant kernel (every launch on the persistent
-    # and resident paths, where one launch is a whole run)
-    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 1 if sim_path_used(sim) in ("persist", "resident") else 16)
-    sim.kernel_time()
-    barrier()
-    sampler.start()
-    launches0 = sim.launches()
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        reset()
-        evs[k][0].record(stream)
-        sim.sim_run(w.nsteps)
-        evs[k][1].record(stream)
-    barrier()
-    clocks = sampler.stop()
-    launches = sim.launches() - launches0
-    kern_ms, kern_n = sim.kernel_time()
-    sim.set_option(cue.CUE_OPT_TIME_KERNEL, 0)
-    sim.check()
-    local_ms = sum(a.elapsed_time(b) for a, b in evs)
+    hbm, peak_kind = peaks()
+    run = Runner(cue, torch, dev, w, args.path, args.depth, flush)
+    rec = run.timed_runs(args.steps, args.warmup, barrier, ClockSampler(gpu_id_for(local)))
+    local_ms = sum(rec["run_ms"])
     cells_per_run = w.n_cells * w.nsteps
     total_ms, value = aggregate(local_ms, cells_per_run, args.steps, world, dist, dev)
-    axon_steps = world * cone_updates_per_run * args.steps / (total_ms / 1e3)
-
-    # roofline of the dominant kernel
-    hbm, peak_kind = peaks()
-    fused = kern_n > 0 and sim_path_used(sim) == "fused"
-    bytes_per_cell = 12 if w.src_map is not None else 8
-    if kern_n:
-        steps_per_launch = (w.nsteps / (launches_per_run(sim, w)))
-        # compulsory field traffic of one launch: the fused kernel reads and writes the field once
-        # for its K steps; the plain kernel once per step; the persistent and resident kernels
-        # once per step of the whole run they cover
-        per_launch_passes = steps_per_launch if sim_path_used(sim) in ("persist", "resident") else 1
-        alg_bytes = bytes_per_cell * w.n_cells * per_launch_passes
-        if w.dim == 3 and sim_path_used(sim) == "plain":
-            # the 3D step launch also moves the cones: position and direction read and
-            # written, the active flag read (the sampled field nodes are counted in the field)
-            alg_bytes += w.n_axons * (4 * w.dim * 4 + 1)
-        avg_s = kern_ms / kern_n / 1e3
-        achieved = alg_bytes / avg_s / 1e9
-    else:
-        steps_per_launch, alg_bytes, avg_s, achieved = 0, 0, 0, 0.0
-    kname = {"fused": "fused", "persist": "persist", "resident": "resident"}.get(sim_path_used(sim), "field")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm if hbm else None,
-                "traffic": recorded_traffic(kname, args.workload),
-                "kernel": kname, "peak_kind": peak_kind, "launches": kern_n,
-                "avg_launch_us": avg_s * 1e6, "steps_per_launch": steps_per_launch,
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "effective_gbs": bytes_per_cell * w.n_cells * steps_per_launch / avg_s / 1e9 if avg_s else 0}
-    # a temporally blocked launch moves its field through HBM once for K steps: the bytes an
-    # unblocked kernel would move for the same node updates, against the same peak
-    roofline["effective_frac"] = roofline["effective_gbs"] / hbm if hbm else None
-    if kname == "resident":
-        roofline["note"] = ("one block holds the grid in shared memory for the whole run: HBM is read "
-                            "and written once per launch, and a step is bound by one SM's shared-memory "
-                            "and issue rate; achieved counts 8 B per node update as for the other kernels")
-
+    ms_run = total_ms / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_run, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(describe(w), parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                       path=sim_path_used(sim)),
-        "axon_steps_per_s": axon_steps, "cone_updates_per_run": cone_updates_per_run,
-        "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+        "config": describe(w),
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU", "path": rec["path"],
+        "axon_steps_per_s": world * rec["cone_updates"] * args.steps / (total_ms / 1e3),
+        "cone_updates_per_run": rec["cone_updates"],
+        "roofline": roofline_single(run.sim, w, rec, ms_run, hbm, peak_kind, args.workload),
+        "clocks": rec["clocks"], "gpu_launches": rec["launches"],
     }
 
     # end to end through the public API from pinned host buffers
     if not args.no_e2e:
-        Ch = w.field0()
-        host = [torch.from_numpy(a).pin_memory() for a in (Ch, w.pos, w.dir, w.active)]
-        out = tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in host)
-        sim.run_host(*host, w.nsteps, out=out)     # warm
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = max(1, min(args.steps, 3))
-        barrier()
-        tot = 0.0
-        for _ in range(reps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            e0.record(stream)
-            sim.run_host(*host, w.nsteps, out=out)
-            e1.record(stream)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-        h2d = sum(t.numel() * t.element_size() for t in host)
-        d2h = sum(t.numel() * t.element_size() for t in out)
-        line["e2e"] = {"value": world * cells_per_run * reps / (tot / 1e3), "unit": UNIT,
-                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                       "ms_per_step": tot / reps}
+        line["e2e"] = e2e_single(torch, run, args.steps, barrier, world)
 
-    # adjoint workload: gradients of the endpoint loss against the forward run's own time
-    if w.targets is not None and w.wall_mode == 1 and rank == 0:
-        line["adjoint"] = adjoint_timing(cue, torch, sim, w, reset, stream, flush, total_ms / args.steps)
+    subs = [s for s in args.subs.split(",") if s] if (args.workload == "c2" and not args.run_steps) else []
+    if rank == 0 and "whole_run" in subs:
+        final_c2 = final_state(run)
+    run.close()
+    if rank == 0:
+        # the rest of the metric on the same GPU: the same grid with its cones clustered, the 3D
+        # workload, the batch against the one-instance-per-launch solver, the adjoint against
+        # the forward solvers
+        if "clustered" in subs:
+            wx = workload("c2x")
+            rx = Runner(cue, torch, dev, wx, flush=flush)
+            recx = rx.timed_runs(3, 2, barrier)
+            line["clustered"] = single_summary(rx, recx, hbm, peak_kind, "c2x")
+            line["clustered"]["ms_per_run_vs_uniform"] = line["clustered"]["ms_per_run"] / ms_run
+            rx.close()
+        if "c3" in subs:
+            w3 = workload("c3")
+            r3 = Runner(cue, torch, dev, w3, flush=flush)
+            rec3 = r3.timed_runs(3, 2, barrier)
+            line["c3"] = single_summary(r3, rec3, hbm, peak_kind, "c3")
+            if "whole_run" in subs:
+                final_c3 = final_state(r3)
+            r3.close()
+        if "batched" in subs:
+            line["batched"] = batch_summary(args, torch, cue, dev, rank, barrier, flush, hbm, peak_kind)
+        if "adjoint" in subs:
+            line["adjoint"] = adjoint_summary(cue, torch, dev, flush, barrier, hbm, peak_kind)
+    if w.targets is not None and w.wall_mode == 1 and rank == 0 and args.workload == "c5":
+        r5 = Runner(cue, torch, dev, w, flush=flush)
+        line["adjoint"] = adjoint_timing(cue, torch, r5, w, ms_run)
+        r5.close()
 
-    # HBM probe: plain field kernel on 2D 8192^2 (256 MiB per buffer), never L2-resident
+    # HBM probes: the unblocked field kernels on grids that cannot stay in L2
     if not args.no_probe and rank == 0:
         line["hbm_probe"] = hbm_probe(cue, torch, dev, hbm)
-        if w.dim == 3:
+        if w.dim == 3 or "c3" in subs:
             line["hbm_probe_3d"] = hbm_probe(cue, torch, dev, hbm, dim=3)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -490,7 +555,11 @@ def main():
             "sample": sample + ", one thread", "seconds": secs, "host_cores": os.cpu_count(),
             "cpu_model": cpu_model()}
         line["cpu_baseline_threads"] = oracle_threads_sample(args.workload, w.n_cells, nsteps, sample)
-    sim.close()
+    if rank == 0 and "whole_run" in subs:
+        # FP32-vs-FP64 after the full runs (oracle in a child process over every host core)
+        line["whole_run"] = {"c2": whole_run_report("c2", final_c2, args.whole_run_cones)}
+        if "c3" in subs:
+            line["whole_run"]["c3"] = whole_run_report("c3", final_c3, args.whole_run_cones)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -498,58 +567,183 @@ def main():
     return 0
 
 
-def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
-    """512 independent 2D instances of uneven sizes and physics, 1,000 coupled steps, in one
-    persistent launch replayed from a captured CUDA graph, launch shape chosen by the autotuner.
-    One benchmark step = the whole batch from its initial state."""
+def e2e_single(torch, run, steps, barrier, world):
+    """The same runs through Simulation.run_host: state from pinned host buffers, field and
+    cones back into pinned host buffers, copies inside the timed events."""
+    w, sim = run.w, run.sim
+    host = [torch.from_numpy(a).pin_memory() for a in (w.field0(), w.pos, w.dir, w.active)]
+    out = tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in host)
+    sim.run_host(*host, w.nsteps, out=out)     # warm
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(steps, 3))
+    barrier()
+    tot = 0.0
+    for _ in range(reps):
+        with torch.cuda.stream(run.stream):
+            run.flush.zero_()
+        e0.record(run.stream)
+        sim.run_host(*host, w.nsteps, out=out)
+        e1.record(run.stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return {"value": world * w.n_cells * w.nsteps * reps / (tot / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in host),
+            "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in out), "ms_per_step": tot / reps}
+
+
+def final_state(run):
+    """State after the last timed full run (numpy): field, initial and final cone positions, active."""
+    C, pos, dirs, act, fs, cs = run.sim.snapshot()
+    assert fs == run.w.nsteps
+    return {"C": C, "pos": pos, "act": act}
+
+
+# ------------------------------------------------------------------ batched workload
+def build_batch(torch, dev, ws):
     from paper_1405_3331_gb300 import batch as B
-    from paper_1405_3331_gb300 import workloads as W
-    ws = W.config_c4(seed=3 + 100 * rank)
-    T = args.run_steps or ws[0].nsteps
-    cells = sum(w.n_cells for w in ws)
     b = B.Batch(ws, device=dev)
-    stream = b.stream
     init = [(b.fields[i][0].clone(), b.pos[i].clone(), b.dir[i].clone(), b.active[i].clone())
             for i in range(len(ws))]
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def reset():
-        with torch.cuda.stream(stream):
+        with torch.cuda.stream(b.stream):
             for i, (C, p, d, a) in enumerate(init):
                 b.fields[i][0].copy_(C)
                 b.pos[i].copy_(p)
                 b.dir[i].copy_(d)
                 b.active[i].copy_(a)
         b.reset_state(0, 0)
+    return b, init, reset
 
-    rows, bpsm, tuned_ms = b.autotune(10)
-    mode = b.get_option(B.CUE_BOPT_MODE)
-    b.set_option(B.CUE_BOPT_GRAPH, 1)
-    for _ in range(max(args.warmup, 3)):
+
+def batch_timed(torch, b, reset, T, steps, warmup, barrier, flush, sampler=None):
+    for _ in range(max(warmup, 3)):
         reset()
         b.run(T)
     b.check()
     b.cone_updates()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sampler = ClockSampler(gpu_id_for(dev.index or 0))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier()
-    sampler.start()
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
+    if sampler is not None:
+        sampler.start()
+    for k in range(steps):
+        with torch.cuda.stream(b.stream):
             flush.zero_()
         reset()
-        evs[k][0].record(stream)
+        evs[k][0].record(b.stream)
         b.run(T)
-        evs[k][1].record(stream)
+        evs[k][1].record(b.stream)
     barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler is not None else None
     b.check()
-    cone_updates = b.cone_updates() / args.steps
-    local_ms = sum(x.elapsed_time(y) for x, y in evs)
+    return [x.elapsed_time(y) for x, y in evs], b.cone_updates() / steps, clocks
+
+
+def batch_mode_name(B, b):
+    mode = b.get_option(B.CUE_BOPT_MODE)
+    rows = b.get_option(B.CUE_BOPT_ROWS)
+    depth = b.get_option(B.CUE_BOPT_DEPTH)
+    if mode == 1:
+        return "persist", "one persistent launch per run", 1
+    if mode == 3:
+        return "blocked", f"one temporally blocked launch per {depth} steps", depth
+    return "step", ("per time step one launch over every instance's cone chunks and streamed field tiles"
+                    if rows > 4 else "per time step one launch over the cone chunks and one over the field tiles"), 1
+
+
+def batch_roofline(B, b, cells, T, ms_run, hbm, peak_kind):
+    name, _, K = batch_mode_name(B, b)
+    per_run = 1 if name == "persist" else (T + K - 1) // K
+    avg_s = ms_run / per_run / 1e3
+    alg = 8.0 * cells * (T if name == "persist" else K)
+    one_pass = 8.0 * cells * (T if name == "persist" else 1)
+    return {"bound": "hbm", "achieved": alg / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": alg / avg_s / 1e9 / hbm, "traffic": recorded_traffic(name, "c4"), "kernel": name,
+            "peak_kind": peak_kind, "launches_per_run": per_run, "steps_per_launch": T if name == "persist" else K,
+            "algorithmic_bytes_per_launch": alg, "avg_launch_us": avg_s * 1e6,
+            "launch_time": "device time of the timed runs / launches of the dominant kernel in them",
+            "compulsory_bytes_per_launch": one_pass, "compulsory_frac": one_pass / avg_s / 1e9 / hbm}
+
+
+def sequential_rate(torch, cue, dev, ws, path, Tb=100):
+    """Every instance alone, one after another, ``Tb`` steps each (a rate, so runs of other
+    lengths compare directly); each Simulation has its own stream, so instances may overlap on
+    the GPU, which only favours this baseline."""
+    sims = [cue.Simulation(w, device=dev, path=path) for w in ws]
+    for sm in sims:
+        sm.sim_run(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sm in sims:
+        sm.sim_run(Tb)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for sm in sims:
+        sm.check()
+        sm.close()
+    return sum(w.n_cells for w in ws) * Tb / dt
+
+
+def batch_summary(args, torch, cue, dev, rank, barrier, flush, hbm, peak_kind):
+    """The 512-instance workload (sub-figure of the default line): autotuned, graph-replayed,
+    against the one-instance-per-launch plain solver and one sim_run per instance."""
+    from paper_1405_3331_gb300 import batch as B
+    from paper_1405_3331_gb300 import workloads as W
+    ws = W.config_c4(seed=3 + 100 * rank)
+    T = ws[0].nsteps
+    cells = sum(w.n_cells for w in ws)
+    b, init, reset = build_batch(torch, dev, ws)
+    tuned = b.autotune(16)
+    b.set_option(B.CUE_BOPT_GRAPH, 1)
+    run_ms, cone_updates, _ = batch_timed(torch, b, reset, T, 3, 2, barrier, flush)
+    ms = statistics.median(run_ms)
+    value = cells * T / (ms / 1e3)
+    plain = sequential_rate(torch, cue, dev, ws, cue.CUE_PATH_PLAIN)
+    auto = sequential_rate(torch, cue, dev, ws, cue.CUE_PATH_AUTO)
+    name, launch, K = batch_mode_name(B, b)
+    out = {"workload": f"batched: {len(ws)} independent 2D instances (sides U{{64..1024}}, {cells / 1e6:.1f} M "
+                       f"cells, {sum(w.n_axons for w in ws)} cones), {T} steps",
+           "value": value, "unit": UNIT, "ms_per_run": ms, "runs": len(run_ms),
+           "axon_steps_per_s": cone_updates / (ms / 1e3),
+           "launch": launch + ", replayed from a CUDA graph", "autotuned": autotune_record(B, b, tuned),
+           "roofline": batch_roofline(B, b, cells, T, ms, hbm, peak_kind),
+           "vs_plain_per_instance": {"value": plain, "unit": UNIT, "speedup": value / plain,
+                                     "sample": f"all {len(ws)} instances x 100 steps, each instance its own "
+                                               "cone and field launches per step"},
+           "vs_sequential_sim_run": {"value": auto, "unit": UNIT, "speedup": value / auto,
+                                     "sample": f"all {len(ws)} instances x 100 steps, one sim_run per instance "
+                                               "in turn (the library's own path choice)"}}
+    b.close()
+    return out
+
+
+def autotune_record(B, b, tuned):
+    rows, bpsm, ms = tuned[:3]
+    name, _, depth = batch_mode_name(B, b)
+    return {"mode": name, "rows": rows, "blocks_per_sm": bpsm, "depth": depth, "probe_ms_per_step": ms,
+            "candidates": "persistent (rows 1, 2, 4 x blocks per SM 1..3), one launch per step (rows 2..16), "
+                          "temporally blocked (depth 2, 4, 8)"}
+
+
+def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
+    """512 independent 2D instances of uneven sizes and physics, 1,000 coupled steps, replayed
+    from a captured CUDA graph, run mode, tile shape and temporal depth chosen by the
+    autotuner.  One benchmark step = the whole batch from its initial state."""
+    from paper_1405_3331_gb300 import batch as B
+    from paper_1405_3331_gb300 import workloads as W
+    ws = W.config_c4(seed=3 + 100 * rank)
+    T = args.run_steps or ws[0].nsteps
+    cells = sum(w.n_cells for w in ws)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    b, init, reset = build_batch(torch, dev, ws)
+    tuned = b.autotune(16)
+    b.set_option(B.CUE_BOPT_GRAPH, 1)
+    run_ms, cone_updates, clocks = batch_timed(torch, b, reset, T, args.steps, args.warmup, barrier, flush,
+                                               ClockSampler(gpu_id_for(dev.index or 0)))
+    local_ms = sum(run_ms)
     total_ms, value = aggregate(local_ms, cells * T, args.steps, world, dist, dev)
     hbm, peak_kind = peaks()
-    per_launch_s = total_ms / args.steps / 1e3
-    achieved = 8.0 * cells * T / per_launch_s / 1e9
+    name, launch, K = batch_mode_name(B, b)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -557,65 +751,33 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
         "config": {"workload": f"batched: {len(ws)} independent 2D instances (sides U{{64..1024}}, "
                                f"{cells / 1e6:.1f} M cells, {sum(w.n_axons for w in ws)} cones), {T} steps",
                    "instances": len(ws), "cells": cells, "steps_per_run": T,
-                   "launch": ("one persistent launch per run" if mode == 1 else
-                              ("per time step one launch over every instance's cone chunks and streamed field "
-                               "tiles" if rows > 4 else
-                               "per time step one launch over the cone chunks and one over the field tiles"))
-                             + ", replayed from a CUDA graph",
-                   "autotuned": {"rows": rows, "blocks_per_sm": bpsm, "probe_ms_per_step": tuned_ms},
-                   "l2": "flushed between timed steps (512 MiB write); 1.2 GB working set",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "l2": "flushed between timed steps (512 MiB write); 1.2 GB working set"},
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        "launch": launch + ", replayed from a CUDA graph", "autotuned": autotune_record(B, b, tuned),
         "axon_steps_per_s": world * cone_updates * args.steps / (total_ms / 1e3),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": recorded_traffic("persist" if mode == 1 else "step", "c4"),
-                     "kernel": "persist" if mode == 1 else "step launches (per run)", "peak_kind": peak_kind,
-                     "launches": args.steps, "avg_launch_us": per_launch_s * 1e6, "steps_per_launch": T,
-                     "algorithmic_bytes_per_launch": 8.0 * cells * T},
-        # persistent: the kernel + the step advance; per step: one launch per time step (streamed tiles
-        # with the cone chunks) or two (cone chunks, then tiles), + the advance
+        "roofline": batch_roofline(B, b, cells, T, total_ms / args.steps, hbm, peak_kind),
         "clocks": clocks,
-        "gpu_launches": args.steps * (2 if mode == 1 else (T if rows > 4 else 2 * T) + 1),
+        "gpu_launches": args.steps * (2 if name == "persist" else
+                                      ((T + K - 1) // K if name == "blocked" else
+                                       (T if b.get_option(B.CUE_BOPT_ROWS) > 4 else 2 * T)) + 1),
     }
-    # the one-instance-per-launch plain solver on the first 32 instances (100 steps each), and
-    # the same instances one after another through sim_run on the library's own path choice
-    # every instance, 100 steps each (a rate, so the batch's 1,000-step runs compare directly); each
-    # Simulation has its own stream, so instances may overlap on the GPU: a conservative baseline
-    sub = ws
-    sub_cells = sum(w.n_cells for w in sub)
-    Tb = 100
-
-    def sequential_rate(path):
-        sims = [cue.Simulation(w, device=dev, path=path) for w in sub]
-        for sm in sims:
-            sm.sim_run(2)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for sm in sims:
-            sm.sim_run(Tb)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        for sm in sims:
-            sm.check()
-            sm.close()
-        return sub_cells * Tb / dt
-
-    plain_rate = sequential_rate(cue.CUE_PATH_PLAIN)
-    auto_rate = sequential_rate(cue.CUE_PATH_AUTO)
-    line["baseline_sequential_sim_run"] = {
-        "value": auto_rate, "unit": UNIT, "speedup": value / world / auto_rate,
-        "sample": f"all {len(sub)} instances x {Tb} steps, one sim_run per instance in turn (resident, "
-                  "persistent or fused path as the library picks)"}
+    plain = sequential_rate(torch, cue, dev, ws, cue.CUE_PATH_PLAIN)
+    auto = sequential_rate(torch, cue, dev, ws, cue.CUE_PATH_AUTO)
     line["baseline_plain_per_instance"] = {
-        "value": plain_rate, "unit": UNIT, "speedup": value / world / plain_rate,
-        "sample": f"all {len(sub)} instances x {Tb} steps, each instance its own cone and field launches per step"}
+        "value": plain, "unit": UNIT, "speedup": value / world / plain,
+        "sample": f"all {len(ws)} instances x 100 steps, each instance its own cone and field launches per step"}
+    line["baseline_sequential_sim_run"] = {
+        "value": auto, "unit": UNIT, "speedup": value / world / auto,
+        "sample": f"all {len(ws)} instances x 100 steps, one sim_run per instance in turn (the library's own "
+                  "path choice)"}
     if not args.no_e2e:
         # end to end: every instance's state from pinned host memory, the run, the fields back
         host = [tuple(t.cpu().pin_memory() for t in st) for st in init]
         outs = [torch.empty_like(h[0]).pin_memory() for h in host]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
-        e0.record(stream)
-        with torch.cuda.stream(stream):
+        e0.record(b.stream)
+        with torch.cuda.stream(b.stream):
             for i, (C, p, d, a) in enumerate(host):
                 b.fields[i][0].copy_(C, non_blocking=True)
                 b.pos[i].copy_(p, non_blocking=True)
@@ -624,10 +786,10 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
         b.reset_state()
         b.run(T)
         cur = b.get_option(B.CUE_BINFO_CUR)
-        with torch.cuda.stream(stream):
+        with torch.cuda.stream(b.stream):
             for i in range(len(ws)):
                 outs[i].copy_(b.fields[i][cur], non_blocking=True)
-        e1.record(stream)
+        e1.record(b.stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         line["e2e"] = {"value": cells * T / (ms / 1e3), "unit": UNIT,
@@ -647,6 +809,134 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+# ------------------------------------------------------------------ adjoint workload
+def adjoint_summary(cue, torch, dev, flush, barrier, hbm, peak_kind):
+    """The adjoint workload (1024^2, 32 sources, 4,096 cones, 2,000 steps, checkpoint every 64):
+    sim_adjoint against the fastest forward run (the library's own path) and the plain forward
+    solver (one cone and one field launch per step) of the same workload."""
+    from paper_1405_3331_gb300 import workloads as W
+    w = W.config_c5()
+    fwd = Runner(cue, torch, dev, w, flush=flush)
+    frec = fwd.timed_runs(3, 2, barrier)
+    plain = Runner(cue, torch, dev, w, path="plain", flush=flush)
+    prec = plain.timed_runs(3, 2, barrier)
+    plain.close()
+    out = adjoint_timing(cue, torch, fwd, w, statistics.median(frec["run_ms"]))
+    # the same gradients with the whole run stored once (ckpt_every >= nsteps: no recompute,
+    # nsteps + 1 states of workspace)
+    stored = adjoint_timing(cue, torch, fwd, w, out["forward_ms_per_run"], k=w.nsteps)
+    out["stored_run"] = {k: stored[k] for k in ("ms_per_run", "ratio_to_forward", "ckpt_every")}
+    out["stored_run"]["workspace_bytes"] = cue.cue_adjoint_workspace_bytes(fwd.sim.params, fwd.sim.n_src,
+                                                                           fwd.sim.n_axons, w.nsteps, w.nsteps)
+    out["forward_path"] = frec["path"]
+    out["plain_forward_ms_per_run"] = statistics.median(prec["run_ms"])
+    out["ratio_to_plain_forward"] = out["ms_per_run"] / out["plain_forward_ms_per_run"]
+    out["stored_run"]["ratio_to_plain_forward"] = out["stored_run"]["ms_per_run"] / out["plain_forward_ms_per_run"]
+    out["forward_roofline"] = roofline_single(fwd.sim, w, frec, out["forward_ms_per_run"], hbm, peak_kind, "c5")
+    fwd.close()
+    return out
+
+
+def adjoint_timing(cue, torch, run, w, forward_ms, k=64, reps=3):
+    """Time sim_adjoint (forward with checkpoints every k steps, recompute, backward) on the
+    runner's workload from its initial state; the ratio divides by the timed forward run."""
+    sim = run.sim
+    run.reset()
+    sim.adjoint(w.targets, w.nsteps, k)          # warm (and the workspace)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        with torch.cuda.stream(run.stream):
+            run.flush.zero_()
+        run.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(run.stream)
+        g = sim.adjoint(w.targets, w.nsteps, k)
+        e1.record(run.stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    sim.check()
+    ms = statistics.median(times)
+    return {"workload": describe(w)["workload"] + ", gradients of the endpoint loss",
+            "ms_per_run": ms, "runs": reps, "forward_ms_per_run": forward_ms, "ratio_to_forward": ms / forward_ms,
+            "ckpt_every": k, "loss": float(g["loss"]), "dL_dD": float(g["dD"]),
+            "dL_dlambda": float(g["dlambda"]), "dL_de_max": float(g["dsrc"].abs().max()),
+            "dL_dM_max": float(g["dmap"].abs().max())}
+
+
+# ------------------------------------------------------------------ whole runs against the oracle
+def oracle_whole_run_child(spec):
+    """Child process: the oracle over the whole run of WORKLOAD (field on every host core, the
+    first NCONES cones; cones never interact, so a prefix of them follows exactly the paths it
+    follows among all of them, its Philox counters being the cone indices); saves the final
+    field and cone state to OUT (.npz) and prints {"seconds", "threads"}."""
+    name, ncones, out = spec.split(":", 2)
+    import numpy as np
+    import oracle
+    w = workload(name)
+    n = min(int(ncones), w.n_axons)
+    used = oracle.set_threads(os.cpu_count() or 1)
+    g = oracle.Grid(w.dim, w.nx, w.ny, w.nz if w.dim == 3 else 1, h=w.h, D=w.D, lam=w.lam, dt=w.dt)
+    c = oracle.Cone(w.w_prev, w.w_grad, w.w_noise, w.step_len, w.stop_radius, w.grad_eps, w.wall_mode, w.seed)
+    t0 = time.perf_counter()
+    C, pos, dirs, act = oracle.run(g, c, w.field0().astype(np.float64), 0, w.nsteps, w.src_cell, w.src_emit,
+                                   w.src_map, w.pos[:, :n], w.dir[:, :n], w.active[:n])
+    secs = time.perf_counter() - t0
+    np.savez(out, C=C, pos=pos, act=act)
+    print(json.dumps({"seconds": secs, "threads": used, "cones": n}), flush=True)
+    return 0
+
+
+def whole_run_report(name, gpu, ncones):
+    """FP32 GPU run against the FP64 oracle after the workload's full run: the field error (the
+    field does not depend on the cones), and the cones' endpoint distributions (displacement
+    from the start) -- quantiles and a two-sample Kolmogorov-Smirnov test -- plus how many of the
+    same cones end within 1e-3 of the oracle's endpoint.  Whole-run trajectories are chaotic in
+    rounding, so the endpoint figures are a report, not a pass criterion."""
+    import numpy as np
+    w = workload(name)
+    with tempfile.TemporaryDirectory() as d:
+        out = os.path.join(d, "orc.npz")
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-whole-run",
+                                f"{name}:{ncones}:{out}"], capture_output=True, text=True, timeout=1200)
+            meta = json.loads(r.stdout.strip().splitlines()[-1])
+            ref = dict(np.load(out))
+        except Exception as e:
+            return {"unavailable": f"oracle whole run failed: {type(e).__name__}"}
+        wall = time.perf_counter() - t0
+    n = meta["cones"]
+    Cg, Cr = gpu["C"].astype(np.float64), ref["C"]
+    scale = np.abs(Cr).max()
+    rel = np.abs(Cg - Cr) / np.maximum(np.abs(Cr), 1e-6 * scale)
+    p0 = w.pos[:, :n].astype(np.float64)
+    dg = np.linalg.norm(gpu["pos"][:, :n].astype(np.float64) - p0, axis=0)
+    dr = np.linalg.norm(ref["pos"] - p0, axis=0)
+    gap = np.linalg.norm(gpu["pos"][:, :n].astype(np.float64) - ref["pos"], axis=0)
+    q = [0.1, 0.5, 0.9]
+    try:
+        from scipy.stats import ks_2samp
+        ks = ks_2samp(dg, dr)
+        ks_rec = {"statistic": float(ks.statistic), "pvalue": float(ks.pvalue)}
+    except Exception as e:
+        ks_rec = {"unavailable": type(e).__name__}
+    return {"workload": describe(w)["workload"],
+            "field": {"max_rel_err": float(rel.max()),
+                      "rel_l2_err": float(np.linalg.norm(Cg - Cr) / max(np.linalg.norm(Cr), 1e-300)),
+                      "denominator": "max(|C64|, 1e-6 max|C64|)"},
+            "endpoints": {"cones": n, "of": w.n_axons,
+                          "displacement_quantiles_gpu": [float(x) for x in np.quantile(dg, q)],
+                          "displacement_quantiles_oracle": [float(x) for x in np.quantile(dr, q)],
+                          "quantiles": q, "ks_2samp": ks_rec,
+                          "same_endpoint_within_1e-3": float((gap <= 1e-3).mean()),
+                          "median_endpoint_gap": float(np.median(gap)),
+                          "stopped_gpu": float(1 - gpu["act"][:n].mean()),
+                          "stopped_oracle": float(1 - ref["act"].mean())},
+            "oracle": {"seconds": meta["seconds"], "threads": meta["threads"], "wall_s": wall,
+                       "kind": "FP64 oracle, field rows over every host core, the first cones"}}
 
 
 # ------------------------------------------------------------------ connectivity
@@ -839,54 +1129,6 @@ def main_graph(args, torch, dev, rank, world, dist, barrier):
     if dist is not None:
         dist.destroy_process_group()
     return 0
-
-
-def adjoint_timing(cue, torch, sim, w, reset, stream, flush, forward_ms):
-    """Time sim_adjoint (forward with checkpoints every 64 steps, recompute, adjoint) on the
-    same workload; the ratio divides by the timed forward run."""
-    k = 64
-    reset()
-    sim.adjoint(w.targets, w.nsteps, k)          # warm
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        flush.zero_()
-    reset()
-    e0.record(stream)
-    g = sim.adjoint(w.targets, w.nsteps, k)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    # the plain forward solver (one cone and one field launch per step) on the same workload
-    plain = cue.Simulation(w, device=sim.device, path=cue.CUE_PATH_PLAIN)
-    plain.sim_run(w.nsteps)
-    torch.cuda.synchronize()
-    plain.load(C=w.field0(), pos=w.pos, dir=w.dir, active=w.active, step=0)
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(plain.stream)
-    plain.sim_run(w.nsteps)
-    p1.record(plain.stream)
-    p1.synchronize()
-    plain_ms = p0.elapsed_time(p1)
-    plain.check()
-    plain.close()
-    return {"ms_per_run": ms, "forward_ms_per_run": forward_ms, "ratio_to_forward": ms / forward_ms,
-            "plain_forward_ms_per_run": plain_ms, "ratio_to_plain_forward": ms / plain_ms,
-            "ckpt_every": k, "loss": float(g["loss"]), "dL_dD": float(g["dD"]),
-            "dL_dlambda": float(g["dlambda"]), "dL_de_max": float(g["dsrc"].abs().max()),
-            "dL_dM_max": float(g["dmap"].abs().max())}
-
-
-def launches_per_run(sim, w):
-    """Launches of the dominant kernel in one run (K steps per launch on the fused path, the
-    whole run per launch on the persistent and resident paths)."""
-    from paper_1405_3331_gb300 import cue
-    if sim.fused_active():
-        K = sim.get_option(cue.CUE_INFO_DEPTH)
-        return (w.nsteps + K - 1) // K
-    if sim_path_used(sim) in ("persist", "resident"):
-        return 1
-    return w.nsteps
 
 
 def sim_path_used(sim):

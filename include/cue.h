@@ -210,12 +210,15 @@ int sim_run(cue_sim *sim, int32_t nsteps);
  * because stopping is a discrete event without a derivative.
  *
  * The call runs the coupled model nsteps forward from the handle's state,
- * keeping (C, p, d) every ckpt_every steps, computes L, then walks back: each
- * segment is recomputed storing every step, and the adjoint field
+ * keeping (C, p, d) every ckpt_every steps and storing every state of the last
+ * segment, computes L, then walks back: each earlier segment is recomputed
+ * from its checkpoint storing every step, and the adjoint field
  * mu = dL/dC^n is advanced backwards with the (symmetric) field operator while
  * the cone adjoint -- back through the clamp, the step length, the
  * normalisation Jacobians and the multilinear gradient sample -- scatters into
- * it.  Parameter gradients: dL/dD = dt/h^2 sum_n <mu^{n+1}, lap C^n>,
+ * it.  With ckpt_every >= nsteps the whole run is stored once (nsteps + 1
+ * states in the workspace) and nothing is recomputed: a workspace-for-time
+ * trade the caller makes through ckpt_every.  Parameter gradients: dL/dD = dt/h^2 sum_n <mu^{n+1}, lap C^n>,
  * dL/dlambda = -dt sum_n <mu^{n+1}, C^n>, dL/de_k = sum_n mu^{n+1}[cell_k],
  * dL/dM = dt sum_n mu^{n+1}.
  *

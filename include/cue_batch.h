@@ -8,10 +8,12 @@
  * cones.  The paper steps one environment; running many in one launch is this
  * library's own addition.  All instances' field tiles and cone chunks form
  * one work list, instance by instance.  A cue_batch_run call runs it in one
- * of two modes (CUE_BOPT_MODE; the autotuner picks): one cooperative launch
+ * of three modes (CUE_BOPT_MODE; the autotuner picks): one cooperative launch
  * in which every block takes items each step and the blocks meet at a
- * bounded grid barrier between steps, or one ordinary launch per step with
- * one item per block; either can be replayed from a captured CUDA graph.
+ * bounded grid barrier between steps; one ordinary launch per step with one
+ * item per block; or temporally blocked launches, each advancing every
+ * instance's field tiles and their cones several steps in shared memory.  Any
+ * of them can be replayed from a captured CUDA graph.
  * Per node and per cone the arithmetic is cue.h's plain path, so an instance
  * here evolves bit for bit as it would alone (source cells distinct).
  *
@@ -70,20 +72,26 @@ cue_batch *cue_batch_create(int32_t n, const cue_instance *inst, void *d_ws, siz
                             int32_t *err);
 
 /* Advance every instance by nsteps coupled steps (cones on C^n, then
- * C^n -> C^{n+1}).  One cooperative launch (CUE_BOPT_MODE 1) or two launches
- * per step (mode 2), or one graph replay of those when CUE_BOPT_GRAPH is on
- * (the graph is captured at the first call with a given nsteps and replayed
- * afterwards; the step counter and buffer parity live on the device, so a
- * replay needs no new arguments). */
+ * C^n -> C^{n+1}).  One cooperative launch (CUE_BOPT_MODE 1), one or two
+ * launches per step (mode 2), or (mode 3) the cones binned to field tiles and
+ * then one temporally blocked launch per CUE_BOPT_DEPTH steps -- each field
+ * tile of each instance loaded once into shared memory with its halo and
+ * advanced that many steps there with its cones -- or one graph replay of
+ * those when CUE_BOPT_GRAPH is on (the graph is captured at the first call
+ * with a given nsteps and replayed afterwards; the step counter, buffer
+ * parity and bin round live on the device, so a replay needs no new
+ * arguments). */
 int cue_batch_run(cue_batch *b, int32_t nsteps);
 
 /* Time each candidate launch shape (rows per thread 1, 2, 4 x blocks per SM
- * 1..3 of the persistent launch, and rows 2, 4, 8, 16 of one launch per step) on
+ * 1..3 of the persistent launch, rows 2, 4, 8, 16 of one launch per step, and
+ * temporal depths 2, 4, 8 of the blocked mode when CUE_BINFO_BLOCKED is 1) on
  * probe_steps steps from the current state, restoring the state after every
- * candidate, and keep the fastest.  Needs the backup area (see
- * cue_batch_workspace_bytes).  Synchronises the stream.  Writes the chosen
- * rows, blocks per SM (0: one launch per step) and the best time per step
- * (ms) when non-null. */
+ * candidate, and keep the fastest (CUE_BOPT_MODE and CUE_BOPT_DEPTH then say
+ * which).  Needs the backup area (see cue_batch_workspace_bytes).
+ * Synchronises the stream.  Writes the chosen rows and blocks per SM (both 0
+ * for the blocked mode; blocks 0 alone: one launch per step) and the best
+ * time per step (ms) when non-null. */
 int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows, int32_t *blocks_per_sm,
                        double *ms_per_step);
 
@@ -99,11 +107,19 @@ int cue_batch_set_state(cue_batch *b, int64_t step, int32_t cur);
 #define CUE_BOPT_MODE    4    /* 1: one persistent launch per run (grid barrier     */
                               /* between steps); 2: per step one launch over every  */
                               /* instance's cone chunks and one over every tile;    */
-                              /* 0: library choice (1 unless the autotuner picked 2) */
+                              /* 3: temporally blocked, one launch per DEPTH steps  */
+                              /* (CUE_ERR_ARG when CUE_BINFO_BLOCKED is 0);         */
+                              /* 0: library choice (1 unless the autotuner picked)  */
+#define CUE_BOPT_DEPTH   5    /* steps per launch of mode 3 (1..8; 0: library       */
+                              /* choice, 4)                                         */
 #define CUE_BINFO_ITEMS  16   /* work-list length (field tiles + cone chunks)       */
 #define CUE_BINFO_STEP   17   /* steps taken so far (host mirror)                   */
 #define CUE_BINFO_CUR    18   /* current buffer of every instance: 0 = field_a      */
+                              /* (modes 1, 2 flip it every step, mode 3 once per    */
+                              /* launch of DEPTH steps)                              */
 #define CUE_BINFO_GRID   19   /* blocks of the last launch                          */
+#define CUE_BINFO_BLOCKED 20  /* 1 when every instance can run in mode 3 (its depth-8 */
+                              /* tile geometry exists and it has <= 256 sources)    */
 
 int cue_batch_set_option(cue_batch *b, int32_t option, int64_t value);
 int cue_batch_get_option(const cue_batch *b, int32_t option, int64_t *value);

@@ -1,6 +1,7 @@
 """Python binding of include/cue_batch.h: many independent 2D simulations of
-uneven sizes stepped together by one persistent launch (argument marshalling
-over PyTorch-owned device buffers; every step runs in libcue.so)."""
+uneven sizes stepped together -- one persistent launch, one launch per step, or
+temporally blocked launches (argument marshalling over PyTorch-owned device
+buffers; every step runs in libcue.so)."""
 from __future__ import annotations
 
 import ctypes as ct
@@ -15,10 +16,12 @@ CUE_BOPT_ROWS = 1
 CUE_BOPT_BLOCKS = 2
 CUE_BOPT_GRAPH = 3
 CUE_BOPT_MODE = 4
+CUE_BOPT_DEPTH = 5
 CUE_BINFO_ITEMS = 16
 CUE_BINFO_STEP = 17
 CUE_BINFO_CUR = 18
 CUE_BINFO_GRID = 19
+CUE_BINFO_BLOCKED = 20
 
 EXPORTED = ("cue_batch_workspace_bytes", "cue_batch_create", "cue_batch_run", "cue_batch_autotune",
             "cue_batch_set_state", "cue_batch_set_option", "cue_batch_get_option", "cue_batch_status",

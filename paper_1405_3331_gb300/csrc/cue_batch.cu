@@ -1,7 +1,8 @@
 // cue_batch.cu -- C ABI of batched runs (include/cue_batch.h): many
 // independent 2D instances stepped by the persistent engine of k_persist.cu,
-// optionally through a captured CUDA graph, with a measuring autotuner for
-// the launch shape.
+// by one launch per step, or by the temporally blocked kernel of k_blocked.cu,
+// optionally through a captured CUDA graph, with a measuring autotuner for the
+// run mode, the launch shape and the temporal depth.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -23,9 +24,36 @@ struct BatchLayout {
     size_t ctrl, bar, counters, inst, items, step_items, src_xyz, backup, total;
     size_t items_cap;
     std::vector<size_t> xyz_off, ent_off, key_off, bk_field, bk_cone;   // per instance
+    // temporally blocked mode (sized for the deepest accepted depth, which has the most tiles)
+    bool blk_ok = false;
+    size_t blk_inst, blk_items, blk_chunks, blk_counts, blk_ids, blk_done;
+    size_t blk_tiles_cap = 0, blk_chunks_cap = 0, blk_bins_cap = 0;
 };
 
+constexpr int kBlockedMaxDepth = 8;    // deepest temporal block of the batched blocked mode
+constexpr int kBlockedDefaultDepth = 4;
+
 size_t inst_cells(const cue_instance &I) { return (size_t)I.pitch * I.params.ny; }
+
+// Every instance can run on the temporally blocked kernel: its depth-8 tile
+// geometry exists, its sources fit the tile lists, and TMA maps can be made.
+bool blocked_capable(int n, const cue_instance *in)
+{
+    if (!encode_field_map_available()) return false;
+    for (int i = 0; i < n; ++i) {
+        const cue_instance &I = in[i];
+        if (I.params.dim != 2 || I.n_src > kBlockedMaxSrc || I.pitch % 4 != 0) return false;
+        cue_params p = I.params;
+        p.nz = 1;
+        FieldDesc f;
+        ConeDesc c;
+        FusedGeom g;
+        if (make_descs(p, I.cone, f, c) != CUE_OK) return false;
+        if (!fused_geometry(f, c.step_len, c.stop_r2, I.n_axons > 0, kBlockedMaxDepth, g)) return false;
+        if ((long long)g.ntx * g.nty * std::max(I.n_axons, 1) > (1LL << 30)) return false;
+    }
+    return true;
+}
 
 BatchLayout batch_layout(int n, const cue_instance *in, bool backup)
 {
@@ -59,6 +87,36 @@ BatchLayout batch_layout(int n, const cue_instance *in, bool backup)
         off += align256(sizeof(PSrc) * ns);
         L.key_off[i] = off;
         off += align256(sizeof(int) * ns);
+    }
+    // blocked mode: instance table, (instance, tile) items, cone chunks for the binning,
+    // bin counts (two rounds) and bins that hold every cone of an instance (two rounds)
+    L.blk_ok = blocked_capable(n, in);
+    if (L.blk_ok) {
+        for (int i = 0; i < n; ++i) {
+            FieldDesc f;
+            ConeDesc c;
+            cue_params p = in[i].params;
+            p.nz = 1;
+            FusedGeom g;
+            make_descs(p, in[i].cone, f, c);
+            fused_geometry(f, c.step_len, c.stop_r2, in[i].n_axons > 0, kBlockedMaxDepth, g);
+            const size_t tiles = (size_t)g.ntx * g.nty;
+            L.blk_tiles_cap += tiles;
+            L.blk_bins_cap += tiles * (size_t)std::max(in[i].n_axons, 0);
+            L.blk_chunks_cap += (size_t)(std::max(in[i].n_axons, 0) + 255) / 256;
+        }
+        L.blk_inst = off;
+        off += align256(sizeof(BInst) * (size_t)n);
+        L.blk_items = off;
+        off += align256(sizeof(int2) * std::max<size_t>(L.blk_tiles_cap, 1));
+        L.blk_chunks = off;
+        off += align256(sizeof(int2) * std::max<size_t>(L.blk_chunks_cap, 1));
+        L.blk_counts = off;
+        off += align256(sizeof(int) * 2 * std::max<size_t>(L.blk_tiles_cap, 1));
+        L.blk_ids = off;
+        off += align256(sizeof(int) * 2 * std::max<size_t>(L.blk_bins_cap, 1));
+        L.blk_done = off;
+        off += 256;
     }
     L.backup = off;
     L.bk_field.resize(n);
@@ -120,7 +178,12 @@ struct cue_batch {
     unsigned char *ws = nullptr;
     cudaStream_t stream = nullptr;
     int rows = 0, bpsm = 0;          // options (0 = library choice)
-    int mode = 0;                    // option: 0 library choice (persistent unless tuned), 1 persistent, 2 per step
+    int mode = 0;                    // option: 0 library choice (persistent unless tuned), 1 persistent, 2 per step,
+                                     // 3 temporally blocked
+    int depth = 0;                   // option: steps per blocked launch (0 = library choice)
+    int blk_K = 0;                   // depth the blocked tables were staged for (0 = not staged)
+    int blk_items = 0, blk_chunks = 0, blk_tiles = 0;
+    size_t blk_bins = 0;
     int rows_used = 0;
     int n_items = 0;
     int n_step_tiles = 0, n_step_chunks = 0;
@@ -141,6 +204,14 @@ struct cue_batch {
     PItem *d_items() const { return reinterpret_cast<PItem *>(ws + L.items); }
     PItem *d_step_items() const { return reinterpret_cast<PItem *>(ws + L.step_items); }
     bool per_step() const { return mode == 2; }
+    bool blocked() const { return mode == 3; }
+    int blocked_depth() const { return depth > 0 ? depth : kBlockedDefaultDepth; }
+    BInst *d_binst() const { return reinterpret_cast<BInst *>(ws + L.blk_inst); }
+    int2 *d_blk_items() const { return reinterpret_cast<int2 *>(ws + L.blk_items); }
+    int2 *d_blk_chunks() const { return reinterpret_cast<int2 *>(ws + L.blk_chunks); }
+    int *blk_counts() const { return reinterpret_cast<int *>(ws + L.blk_counts); }
+    int *blk_ids() const { return reinterpret_cast<int *>(ws + L.blk_ids); }
+    int *blk_done() const { return reinterpret_cast<int *>(ws + L.blk_done); }
 };
 
 namespace {
@@ -216,8 +287,94 @@ int stage_list(cue_batch *b)
     return CUE_OK;
 }
 
+// The blocked mode's instance table (tensor maps of both buffers, tile geometry
+// for depth K, first tile and first bin of each instance), its (instance, tile)
+// items instance by instance, and the cone chunks of the binning launch.
+int stage_blocked(cue_batch *b, int K)
+{
+    if (!b->L.blk_ok) return CUE_ERR_ARG;
+    if (b->blk_K == K) return CUE_OK;
+    std::vector<BInst> bi(b->n);
+    std::vector<int2> items, chunks;
+    int tile_base = 0;
+    size_t bin_base = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const cue_instance &I = b->in[i];
+        const PInst &P = b->insts[i];
+        BInst &B = bi[i];
+        std::memset(static_cast<void *>(&B), 0, sizeof(BInst));
+        FusedGeom g;
+        if (!fused_geometry(P.f, P.c.step_len, P.c.stop_r2, I.n_axons > 0, K, g)) return CUE_ERR_ARG;
+        if (!encode_field_map(&B.map[0], I.field_a, I.params.nx, I.params.ny, I.pitch) ||
+            !encode_field_map(&B.map[1], I.field_b, I.params.nx, I.params.ny, I.pitch))
+            return CUE_ERR_CUDA;
+        B.f = P.f;
+        B.c = P.c;
+        B.g = g;
+        B.field[0] = I.field_a;
+        B.field[1] = I.field_b;
+        B.rate_map = I.src_map;
+        B.src_cell = I.src_cell;
+        B.src_emit = I.src_emit;
+        B.src_xyz = P.src_xyz;
+        B.pos = I.pos;
+        B.dir = I.dir;
+        B.active = I.active;
+        B.counter = P.counter;
+        B.pitch = I.pitch;
+        B.n_src = I.n_src;
+        B.n_axons = I.n_axons;
+        B.tile_base = tile_base;
+        B.bin_base = bin_base;
+        const int tiles = g.ntx * g.nty;
+        for (int t = 0; t < tiles; ++t) items.push_back(make_int2(i, t));
+        for (int a0 = 0; a0 < I.n_axons; a0 += 256) chunks.push_back(make_int2(i, a0));
+        tile_base += tiles;
+        bin_base += (size_t)tiles * (size_t)std::max(I.n_axons, 0);
+    }
+    if (items.size() > b->L.blk_tiles_cap || chunks.size() > b->L.blk_chunks_cap || bin_base > b->L.blk_bins_cap)
+        return CUE_ERR_WORKSPACE;
+    if (cudaMemcpyAsync(b->d_binst(), bi.data(), sizeof(BInst) * bi.size(), cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        (!items.empty() && cudaMemcpyAsync(b->d_blk_items(), items.data(), sizeof(int2) * items.size(),
+                                           cudaMemcpyHostToDevice, b->stream) != cudaSuccess) ||
+        (!chunks.empty() && cudaMemcpyAsync(b->d_blk_chunks(), chunks.data(), sizeof(int2) * chunks.size(),
+                                            cudaMemcpyHostToDevice, b->stream) != cudaSuccess) ||
+        cudaMemsetAsync(b->blk_done(), 0, sizeof(int), b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)       // the host vectors are released below
+        return CUE_ERR_CUDA;
+    b->blk_items = (int)items.size();
+    b->blk_chunks = (int)chunks.size();
+    b->blk_tiles = tile_base;
+    b->blk_bins = bin_base;
+    b->blk_K = K;
+    drop_graph(b);
+    return CUE_OK;
+}
+
+// A run of the blocked mode: both rounds of bin counts cleared, the bin round
+// reset, every cone binned, then ceil(nsteps / K) blocked launches (the last
+// one shorter); the kernels advance the step control themselves.
+cudaError_t launch_blocked(cue_batch *b, int nsteps)
+{
+    const int K = b->blk_K;
+    cudaError_t e = cudaMemsetAsync(b->blk_counts(), 0, sizeof(int) * 2 * (size_t)std::max(b->blk_tiles, 1),
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&b->ctrl()->pad[0], 0, sizeof(uint32_t), b->stream);
+    if (e == cudaSuccess)
+        e = blocked_bin(b->d_binst(), b->d_blk_chunks(), b->blk_chunks, b->blk_counts(), b->blk_ids(), b->blk_bins,
+                        b->blk_tiles, b->ctrl(), b->stream);
+    for (int done = 0; e == cudaSuccess && done < nsteps; done += K)
+        e = blocked_launch(b->d_binst(), b->d_blk_items(), b->blk_items, std::min(K, nsteps - done), b->ctrl(),
+                           b->blk_counts(), b->blk_ids(), b->blk_bins, b->blk_tiles, b->blk_done(), b->status(),
+                           b->stream);
+    b->grid = b->blk_items;
+    return e;
+}
+
 cudaError_t launch_direct(cue_batch *b, int nsteps)
 {
+    if (b->blocked()) return launch_blocked(b, nsteps);
     if (b->per_step()) {
         b->grid = b->n_step_tiles;
         return step_launch(b->d_inst(), b->d_step_items(), b->n_step_chunks, b->d_step_items() + b->n_step_chunks,
@@ -261,9 +418,9 @@ constexpr int kStepGraphMax = 1024;
 
 int run_batch(cue_batch *b, int nsteps)
 {
-    int rc = stage_list(b);
+    int rc = b->blocked() ? stage_blocked(b, b->blocked_depth()) : stage_list(b);
     if (rc != CUE_OK) return rc;
-    if (b->use_graph && b->per_step() && nsteps > kStepGraphMax) {
+    if (b->use_graph && (b->per_step() || b->blocked()) && nsteps > kStepGraphMax) {
         for (int i = 0; i < nsteps / kStepGraphMax && rc == CUE_OK; ++i) rc = run_graph(b, kStepGraphMax);
         if (rc == CUE_OK && nsteps % kStepGraphMax)
             rc = launch_direct(b, nsteps % kStepGraphMax) == cudaSuccess ? CUE_OK : CUE_ERR_CUDA;
@@ -274,7 +431,18 @@ int run_batch(cue_batch *b, int nsteps)
     }
     if (rc != CUE_OK) return rc;
     b->step += nsteps;
-    b->cur ^= (nsteps & 1);
+    if (b->blocked()) {             // one buffer flip per blocked launch, K steps each, per run piece
+        const int K = b->blk_K;
+        long long flips = 0;
+        if (b->use_graph && nsteps > kStepGraphMax)
+            flips = (long long)(nsteps / kStepGraphMax) * ((kStepGraphMax + K - 1) / K) +
+                    (nsteps % kStepGraphMax + K - 1) / K;
+        else
+            flips = (nsteps + K - 1) / K;
+        b->cur ^= (int)(flips & 1);
+    } else {
+        b->cur ^= (nsteps & 1);
+    }
     return CUE_OK;
 }
 
@@ -447,40 +615,48 @@ int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows_out, int
     const long long step0 = b->step;
     int rc = save_state(b, counter);
     if (rc != CUE_OK) return rc;
-    const int keep_rows = b->rows, keep_bpsm = b->bpsm, keep_mode = b->mode;
+    const int keep_rows = b->rows, keep_bpsm = b->bpsm, keep_mode = b->mode, keep_depth = b->depth;
     const bool keep_graph = b->use_graph;
     b->use_graph = false;
     const int maxb = std::max(1, std::min(3, persist_max_blocks_per_sm()));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CUE_ERR_CUDA;
     double best = 1e30;
-    int best_rows = 0, best_b = 0;
+    int best_rows = 0, best_b = 0, best_mode = 1, best_depth = 0;
+    auto probe = [&](int mode, int rows, int bb, int depth) {
+        b->rows = rows;
+        b->bpsm = bb;
+        b->mode = mode;
+        b->depth = depth;
+        rc = run_batch(b, std::min(probe_steps, 2 * std::max(depth, 1)));   // warm: stages the tables, first touch
+        if (rc == CUE_OK) rc = restore_state(b, cur0, step0, counter);
+        if (rc != CUE_OK) return;
+        float ms = 0.f;
+        if (cudaEventRecord(e0, b->stream) != cudaSuccess) rc = CUE_ERR_CUDA;
+        if (rc == CUE_OK) rc = run_batch(b, probe_steps);
+        if (rc == CUE_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = CUE_ERR_CUDA;
+        if (rc == CUE_OK && ms / probe_steps < best) {
+            best = ms / probe_steps;
+            best_rows = rows;
+            best_b = bb;
+            best_mode = mode;
+            best_depth = depth;
+        }
+        if (rc == CUE_OK) rc = restore_state(b, cur0, step0, counter);
+    };
     const int rows_c[5] = {1, 2, 4, 8, 16};
-    // candidates: the persistent launch (rows 1, 2, 4 x blocks per SM 1..maxb) and one
-    // launch per step (rows 2..16; "blocks per SM" 0)
+    // candidates: the persistent launch (rows 1, 2, 4 x blocks per SM 1..maxb), one
+    // launch per step (rows 2..16; "blocks per SM" 0), and the temporally blocked
+    // launch (depth 2, 4, 8; rows and blocks 0) where every instance can take it
     for (int ri = 0; ri < 5 && rc == CUE_OK; ++ri)
         for (int bb = 0; bb <= maxb && rc == CUE_OK; ++bb) {
             if ((bb == 0 && rows_c[ri] == 1) || (bb > 0 && rows_c[ri] > 4)) continue;
-            b->rows = rows_c[ri];
-            b->bpsm = bb;
-            b->mode = bb == 0 ? 2 : 1;
-            rc = run_batch(b, 1);                              // warm: stages the list, first touch
-            if (rc == CUE_OK) rc = restore_state(b, cur0, step0, counter);
-            if (rc != CUE_OK) break;
-            float ms = 0.f;
-            if (cudaEventRecord(e0, b->stream) != cudaSuccess) rc = CUE_ERR_CUDA;
-            if (rc == CUE_OK) rc = run_batch(b, probe_steps);
-            if (rc == CUE_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess ||
-                                 cudaEventSynchronize(e1) != cudaSuccess ||
-                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                rc = CUE_ERR_CUDA;
-            if (rc == CUE_OK && ms / probe_steps < best) {
-                best = ms / probe_steps;
-                best_rows = rows_c[ri];
-                best_b = bb;
-            }
-            if (rc == CUE_OK) rc = restore_state(b, cur0, step0, counter);
+            probe(bb == 0 ? 2 : 1, rows_c[ri], bb, 0);
         }
+    for (int K = 2; b->L.blk_ok && K <= kBlockedMaxDepth && rc == CUE_OK; K *= 2) probe(3, 0, 0, K);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->use_graph = keep_graph;
@@ -488,17 +664,21 @@ int cue_batch_autotune(cue_batch *b, int32_t probe_steps, int32_t *rows_out, int
         b->rows = keep_rows;
         b->bpsm = keep_bpsm;
         b->mode = keep_mode;
+        b->depth = keep_depth;
         return rc;
     }
     b->rows = best_rows;
     b->bpsm = best_b;
-    b->mode = best_b == 0 ? 2 : 1;
+    b->mode = best_mode;
+    b->depth = best_depth;
     b->list_ready = false;
     drop_graph(b);
     if (rows_out) *rows_out = best_rows;
     if (bpsm_out) *bpsm_out = best_b;
     if (ms_out) *ms_out = best;
-    return stage_list(b);
+    rc = stage_list(b);
+    if (rc == CUE_OK && b->blocked()) rc = stage_blocked(b, b->blocked_depth());
+    return rc;
 }
 
 int cue_batch_set_state(cue_batch *b, int64_t step, int32_t cur)
@@ -535,8 +715,14 @@ int cue_batch_set_option(cue_batch *b, int32_t option, int64_t value)
         if (!b->use_graph) drop_graph(b);
         return CUE_OK;
     case CUE_BOPT_MODE:
-        if (value < 0 || value > 2) return CUE_ERR_ARG;
+        if (value < 0 || value > 3) return CUE_ERR_ARG;
+        if (value == 3 && !b->L.blk_ok) return CUE_ERR_ARG;
         b->mode = (int)value;
+        drop_graph(b);
+        return CUE_OK;
+    case CUE_BOPT_DEPTH:
+        if (value < 0 || value > kBlockedMaxDepth) return CUE_ERR_ARG;
+        b->depth = (int)value;
         drop_graph(b);
         return CUE_OK;
     default:
@@ -555,7 +741,9 @@ int cue_batch_get_option(const cue_batch *b, int32_t option, int64_t *value)
     case CUE_BINFO_STEP: *value = b->step; return CUE_OK;
     case CUE_BINFO_CUR: *value = b->cur; return CUE_OK;
     case CUE_BINFO_GRID: *value = b->grid; return CUE_OK;
-    case CUE_BOPT_MODE: *value = b->per_step() ? 2 : 1; return CUE_OK;
+    case CUE_BOPT_MODE: *value = b->blocked() ? 3 : b->per_step() ? 2 : 1; return CUE_OK;
+    case CUE_BOPT_DEPTH: *value = b->blocked_depth(); return CUE_OK;
+    case CUE_BINFO_BLOCKED: *value = b->L.blk_ok ? 1 : 0; return CUE_OK;
     default: return CUE_ERR_ARG;
     }
 }

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <vector>
 
@@ -16,23 +17,33 @@ namespace cue {
 //   [0,   256)  status word (unsigned) at 0, cone-update counter (u64) at 8
 //   [256, ...)  source coordinates, FP32 [3][n_src]
 //   [...]       fused-path scratch (two rounds each): per-tile cone counts,
-//               fixed-capacity per-tile bins of cone ids, a spill list of
+//               per-tile bins of cone ids (bin_cap each), a spill list of
 //               (cone, tile) for overfull tiles and its count.  n_tiles is an
-//               upper bound over every tile geometry.
-constexpr int kFusedBinCap = 512;   // cone ids per tile bin (the fused kernel's register slots)
+//               upper bound over every tile geometry.  bin_cap is n_axons (a
+//               tile's bin holds any number of its cones, so the spill list
+//               stays empty) while the bins fit in kFusedBinBudget, else
+//               kFusedBinCap.
+constexpr int kFusedBinCap = 512;   // cone ids a CTA keeps in registers (2 slots x 256 threads)
+constexpr size_t kFusedBinBudget = size_t(256) << 20;   // bytes of bins (both rounds) that buy bin_cap = n_axons
 
 struct WorkspaceLayout {
     size_t status_off = 0;
     size_t src_xyz_off = 0;
     size_t bin_count_off = 0;    // 2 x n_tiles int32 (double-buffered counts)
     size_t bin_ctl_off = 0;      // spill counts (2 int32) and a finished-tile counter
-    size_t bin_list_off = 0;     // 2 x n_tiles x kFusedBinCap int32 (cone ids by tile)
+    size_t bin_list_off = 0;     // 2 x n_tiles x bin_cap int32 (cone ids by tile)
     size_t spill_off = 0;        // 2 x n_axons int2 (cone, tile) that did not fit their bin
     size_t persist_off = 0;      // persistent path: barrier, two instance records, work list
     size_t persist_items_cap = 0;
     size_t persist_src_off = 0;  // persistent path: binned sources (PSrc) and their tile keys
+    // 3D one-launch step: cones binned to the launch's boxes (two rounds each):
+    // counts [2][boxes3], ids [2][boxes3][cap3], overflow ids [2][n_axons], overflow
+    // counts (2) and a finished-box counter
+    size_t bin3_count_off = 0, bin3_list_off = 0, bin3_ovf_off = 0, bin3_ctl_off = 0;
+    int boxes3 = 0, cap3 = 0;
     size_t total = 0;
     int n_tiles = 0;
+    int bin_cap = 0;             // cone ids per tile bin
 };
 
 // Tile geometry of the fused path.
@@ -172,6 +183,8 @@ struct Sim {
     alignas(64) unsigned char tmap[2][128];   // CUtensorMap per field buffer (as TMA source)
     alignas(64) unsigned char tmap3[2][128];  // 3D plane maps of the field buffers
     bool tmap3_ready = false;
+    long long bin3_round = 0;                 // round of the 3D cone bins the next step reads
+    bool bin3_valid = false;                  // the current round's bins hold every active cone
 
     int *bin_count() const { return reinterpret_cast<int *>(ws + wl.bin_count_off); }
     int *bin_ctl() const { return reinterpret_cast<int *>(ws + wl.bin_ctl_off); }
@@ -248,6 +261,39 @@ int field_fused_if_supported(Sim &s, int nsteps);
 void timing_begin(Sim &s);
 void timing_end(Sim &s);
 
+// ---- temporally blocked batch mode (k_blocked.cu) ----
+constexpr int kBlockedMaxSrc = 256;   // point sources per instance on this mode
+// One instance of a batch in the blocked mode (device table; the tensor maps
+// give the struct their 128-byte alignment, which the workspace's 256-byte
+// offsets keep).
+struct BInst {
+    CUtensorMap map[2];               // TMA source maps of field_a / field_b (nx x ny, row pitch)
+    FieldDesc f;
+    ConeDesc c;
+    FusedGeom g;                      // tile geometry for the launch's depth
+    float *field[2];
+    const float *rate_map;            // [ny][pitch] or null
+    const int32_t *src_cell;
+    const float *src_emit;
+    const float *src_xyz;
+    float *pos, *dir;
+    uint8_t *active;
+    unsigned long long *counter;
+    size_t bin_base;                  // this instance's first bin (tile 0) in one round of ids
+    int pitch, n_src, n_axons, tile_base;
+};
+// Tile geometry of the temporally blocked kernels for depth K (false if none).
+bool fused_geometry(const FieldDesc &f, float step_len, float stop_r2, bool cones, int K, FusedGeom &g);
+// Encode a 2D TMA source map of an nx x ny FP32 field with rows `pitch` floats apart.
+bool encode_field_map(void *map128, float *base, int nx, int ny, int pitch);
+bool encode_field_map_available();
+size_t blocked_smem_bytes();
+cudaError_t blocked_bin(const BInst *d_insts, const int2 *d_chunks, int n_chunks, int *counts, int *ids,
+                        size_t bin_total, int total_tiles, const PCtrl *ctrl, cudaStream_t stream);
+cudaError_t blocked_launch(const BInst *d_insts, const int2 *d_items, int n_items, int K, PCtrl *ctrl, int *counts,
+                           int *ids, size_t bin_total, int total_tiles, int *done, unsigned *status,
+                           cudaStream_t stream);
+
 // ---- coupled steps without the public entry point's checks (cue_api.cu)
 int run_coupled(Sim &s, int nsteps);
 // ---- adjoint (k_adjoint.cu)
@@ -270,6 +316,11 @@ cudaError_t launch_cone_step_io(Sim &s, const float *C, uint32_t step, const flo
                                 float *pout, float *dout);
 // 3D field step through the TMA plane pipeline (k_field3d.cu)
 bool field3d_tma_prepare(Sim &s);
+// Boxes (CTAs) of the 3D step launch and each box's z chunk, for a grid of
+// nx x ny x nz nodes on a device of `sms` SMs.
+void field3d_boxes(int nx, int ny, int nz, int sms, int *boxes, int *zchunk);
+// Bin every active cone into the 3D boxes of the current round (start of a run).
+cudaError_t launch_bin3(Sim &s);
 // cones_done (optional): the field blocks also step the cones on the input
 // buffer (cone step index s.cone_step) when one thread each covers them, and
 // *cones_done says whether they did; sources_done (optional): the field

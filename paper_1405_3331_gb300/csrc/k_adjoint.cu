@@ -13,10 +13,12 @@
 //          + w_n xi, g = bilinear/trilinear gradient of C^n at p; the gradient is
 //          linear in C^n (its adjoint scatters into mu, now dL/dC^n) and
 //          multilinear in p (adds into pbar).
-// Memory: the forward keeps (C, p, d) every ckpt_every steps; each segment is
-// recomputed storing every step (one persistent launch on 2D grids with
-// nx % 4 == 0, else a cone and a field launch per step), then walked
-// backwards: one persistent cooperative launch per segment (adj_persist_kernel:
+// Memory: the forward keeps (C, p, d) every ckpt_every steps and runs its last
+// segment as a stored trajectory; every other segment is recomputed from its
+// checkpoint storing every step (one persistent launch on 2D grids with
+// nx % 4 == 0, else a cone and a field launch per step).  With ckpt_every >=
+// nsteps the whole run is stored once and nothing is recomputed.  Each segment
+// is then walked backwards: one persistent cooperative launch per segment (adj_persist_kernel:
 // field warps advance the adjoint field, cone warps scatter the cone adjoint,
 // one bounded grid barrier per step), or, where that launch does not apply, a
 // field launch and a cone launch per step.
@@ -129,18 +131,6 @@ __device__ __forceinline__ DF df_mul(DF a, float c)
 
 __device__ __forceinline__ DF df_of(float hi, float lo) { return two_sum(hi, lo); }   // renormalise
 
-// atomically mu += c as a double-float: the float atomic returns the old high
-// part, from which this thread recovers the exact rounding error of the
-// addition (round-to-nearest, as the atomic rounds) and adds it to the low
-// plane.  Whatever the order of the atomics, hi + sum(lo) stays the exact sum
-// up to the low plane's own rounding.
-__device__ __forceinline__ void atomic_add_df(float *hi, float *lo, float c)
-{
-    const float old = atomicAdd(hi, c);
-    const float e = two_sum(old, c).lo;
-    if (e != 0.0f) atomicAdd(lo, e);
-}
-
 // One backward field step on an nx % 4 == 0 2D grid, laid out like the
 // forward's float4 kernel (32 lanes x 4 nodes in x, 8 warps of `rows` rows):
 //   mu_out = A mu_in (A is the forward stencil: the no-flux operator is
@@ -156,6 +146,20 @@ __device__ __forceinline__ DF df_update(DF m, DF l, DF r, DF u, DF d, float alph
     const DF lp = df_add(sum, df_mul(m, -4.0f));
     *lap = lp.hi + lp.lo;
     return df_add(df_mul(m, beta), df_mul(sum, alpha));
+}
+
+// The segment's rate-map sum of four nodes, Sseg += mu, as a double-float (high
+// and low planes): the adjoint at a source or in a cone's orbit swings between
+// large values of either sign from step to step, and their sum is a small
+// remainder that a single float would hold only to its rounding.
+__device__ __forceinline__ void seg_sum_add(float4 *hi, float4 *lo, const DF &m0, const DF &m1, const DF &m2,
+                                            const DF &m3)
+{
+    const float4 h = *hi, l = *lo;
+    const DF a0 = df_add(df_of(h.x, l.x), m0), a1 = df_add(df_of(h.y, l.y), m1);
+    const DF a2 = df_add(df_of(h.z, l.z), m2), a3 = df_add(df_of(h.w, l.w), m3);
+    *hi = make_float4(a0.hi, a1.hi, a2.hi, a3.hi);
+    *lo = make_float4(a0.lo, a1.lo, a2.lo, a3.lo);
 }
 
 __global__ void __launch_bounds__(256) adj_field2d_vec4(FieldDesc f, const float *__restrict__ mu_in,
@@ -177,6 +181,7 @@ __global__ void __launch_bounds__(256) adj_field2d_vec4(FieldDesc f, const float
     float4 *ohi4 = reinterpret_cast<float4 *>(mu_out);
     float4 *olo4 = reinterpret_cast<float4 *>(mu_out + cells);
     float4 *s4 = reinterpret_cast<float4 *>(Sseg);
+    float4 *s4lo = reinterpret_cast<float4 *>(Sseg + cells);
     float tD = 0.f, tL = 0.f;
     if (y0 < f.ny) {                               // warp-uniform
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -227,14 +232,7 @@ __global__ void __launch_bounds__(256) adj_field2d_vec4(FieldDesc f, const float
                 const float v0 = m0.hi + m0.lo, v1 = m1.hi + m1.lo, v2 = m2.hi + m2.lo, v3 = m3.hi + m3.lo;
                 tD = fmaf(L0, c.x, fmaf(L1, c.y, fmaf(L2, c.z, fmaf(L3, c.w, tD))));
                 tL = fmaf(v0, c.x, fmaf(v1, c.y, fmaf(v2, c.z, fmaf(v3, c.w, tL))));
-                if (Sseg) {
-                    float4 sv = s4[at];
-                    sv.x += v0;
-                    sv.y += v1;
-                    sv.z += v2;
-                    sv.w += v3;
-                    s4[at] = sv;
-                }
+                if (Sseg) seg_sum_add(s4 + at, s4lo + at, m0, m1, m2, m3);
                 ohi4[at] = make_float4(o0.hi, o1.hi, o2.hi, o3.hi);
                 olo4[at] = make_float4(o0.lo, o1.lo, o2.lo, o3.lo);
             }
@@ -279,19 +277,25 @@ __global__ void __launch_bounds__(256) adj_field_scalar(FieldDesc f, const float
         const float cc = C[c];
         tD = fmaf(lp.hi + lp.lo, cc, tD);
         tL = fmaf(v, cc, tL);
-        if (Sseg) Sseg[c] += v;
+        if (Sseg) {
+            const DF sv = df_add(df_of(Sseg[c], Sseg[n + c]), m);
+            Sseg[c] = sv.hi;
+            Sseg[n + c] = sv.lo;
+        }
         mu_out[c] = o.hi;
         mu_out[n + c] = o.lo;
     }
     block_add2<true>(tD, tL, acc);
 }
 
-// End of a segment: S += Sseg in FP64, Sseg = 0.
+// End of a segment: S += Sseg in FP64 (Sseg double-float: high plane, then
+// low plane), Sseg = 0.
 __global__ void __launch_bounds__(256) adj_fold_kernel(size_t n, float *Sseg, double *S)
 {
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
-        S[c] += (double)Sseg[c];
+        S[c] += (double)Sseg[c] + (double)Sseg[n + c];
         Sseg[c] = 0.0f;
+        Sseg[n + c] = 0.0f;
     }
 }
 
@@ -301,122 +305,9 @@ __device__ __forceinline__ size_t node_index(const FieldDesc &f, int i, int j, i
     return (size_t)i + (size_t)f.nx * ((size_t)j + (size_t)f.ny * k);
 }
 
-// Backward through one clamp-mode cone step.  p, d: state at step n;
-// pbar, dbar: in dL/d(p,d)^{n+1}, out dL/d(p,d)^n; the field part is scattered
-// into mu (atomic adds).
-template <int DIM>
-__device__ __forceinline__ void cone_adjoint(const FieldDesc &f, const ConeDesc &c, const float *__restrict__ C,
-                                             uint32_t axon, uint32_t step, const float *p, const float *d,
-                                             float *pbar, float *dbar, float *mu)
-{
-    const size_t sy = f.nx, sz = (size_t)f.nx * f.ny;
-    float *mu_lo = mu + sz * f.nz;                    // low plane of the double-float field
-    auto ld = [&](int i, int j, int k) { return __ldg(C + (size_t)i + sy * j + sz * k); };
-    // forward recomputation with the forward's own functions (same decisions)
-    float g[DIM];
-    sample_gradient<DIM>(f, c, p, ld, g);
-    float gn2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) gn2 = fmaf(g[i], g[i], gn2);
-    const bool has_g = gn2 > c.eps2;
-    const float ginv = has_g ? rsqrtf(gn2) : 0.0f;
-    float xi[DIM];
-    cone_noise<DIM>(c.key0, c.key1, axon, step, xi);
-    float v[DIM], vn2 = 0.f, ghat[DIM];
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) {
-        ghat[i] = g[i] * ginv;
-        v[i] = c.w_prev * d[i] + c.w_grad * ghat[i] + c.w_noise * xi[i];
-        vn2 = fmaf(v[i], v[i], vn2);
-    }
-    const bool has_v = vn2 > 1e-30f;
-    const float vinv = has_v ? rsqrtf(vn2) : 0.0f;
-    float dn[DIM];
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) dn[i] = has_v ? v[i] * vinv : d[i];
-    const float hi[3] = {c.hi0, c.hi1, c.hi2};
-    // adjoint
-    float qbar[DIM], dnbar[DIM];
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) {
-        const float q = fmaf(c.step_len, dn[i], p[i]);
-        qbar[i] = (q < 0.0f || q > hi[i]) ? 0.0f : pbar[i];
-        dnbar[i] = fmaf(c.step_len, qbar[i], dbar[i]);
-    }
-    float vbar[DIM];
-    if (has_v) {
-        float dot = 0.f;
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) dot = fmaf(dn[i], dnbar[i], dot);
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-            vbar[i] = (dnbar[i] - dn[i] * dot) * vinv;
-            dbar[i] = c.w_prev * vbar[i];
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-            vbar[i] = 0.f;
-            dbar[i] = dnbar[i];
-        }
-    }
-    float gbar[DIM];
-    {
-        float dot = 0.f;
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) dot = fmaf(ghat[i], c.w_grad * vbar[i], dot);
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) gbar[i] = has_g ? (c.w_grad * vbar[i] - ghat[i] * dot) * ginv : 0.0f;
-    }
-    // back through the sample: bilinear / trilinear weights (position) and the
-    // node central differences (field)
-    int lo[3] = {0, 0, 0};
-    float fr[3] = {0.f, 0.f, 0.f};
-    cell_of<DIM>(f, p, lo, fr);
-    const int ext[3] = {f.nx, f.ny, f.nz};
-    float pb[DIM];
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) pb[i] = qbar[i];
-    const int kc = DIM == 3 ? 2 : 1;
-    for (int e = 0; e < kc; ++e)
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const int idx[3] = {lo[0] + a, lo[1] + b, lo[2] + e};
-                const float w1[3] = {a ? fr[0] : 1.0f - fr[0], b ? fr[1] : 1.0f - fr[1],
-                                     DIM == 3 ? (e ? fr[2] : 1.0f - fr[2]) : 1.0f};
-                const float sg[3] = {a ? 1.0f : -1.0f, b ? 1.0f : -1.0f, e ? 1.0f : -1.0f};
-                const float w = w1[0] * w1[1] * w1[2];
-                // node gradient at this corner (ghost = edge) and the scatter of gbar
-                float gnode[DIM];
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    int ip[3] = {idx[0], idx[1], idx[2]}, im[3] = {idx[0], idx[1], idx[2]};
-                    ip[k] = min(ip[k] + 1, ext[k] - 1);
-                    im[k] = max(im[k] - 1, 0);
-                    gnode[k] = (ld(ip[0], ip[1], ip[2]) - ld(im[0], im[1], im[2])) * c.inv2h;
-                    const float coef = gbar[k] * w * c.inv2h;
-                    const size_t jp = node_index(f, ip[0], ip[1], ip[2]), jm = node_index(f, im[0], im[1], im[2]);
-                    atomic_add_df(mu + jp, mu_lo + jp, coef);
-                    atomic_add_df(mu + jm, mu_lo + jm, -coef);
-                }
-#pragma unroll
-                for (int m = 0; m < DIM; ++m) {
-                    float dwm = sg[m] * f.inv_h;
-#pragma unroll
-                    for (int q = 0; q < DIM; ++q)
-                        if (q != m) dwm *= w1[q];
-                    float s = 0.f;
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) s = fmaf(gbar[k], gnode[k], s);
-                    pb[m] = fmaf(dwm, s, pb[m]);
-                }
-            }
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) pbar[i] = pb[i];
-}
-
-// 2D specialisation: the 12-node patch gathered for the forward recomputation
+// Backward through one clamp-mode 2D cone step.  p, d: state at step n;
+// pbar, dbar: in dL/d(p,d)^{n+1}, out dL/d(p,d)^n; the field part is
+// scattered into mu.  The 12-node patch gathered for the forward recomputation
 // also gives the corner node gradients (position derivative), and the field
 // adjoint is summed per patch node in registers, then scattered with 12
 // independent double-float atomics (instead of reloading the nodes and
@@ -433,9 +324,159 @@ __device__ __forceinline__ double rsqrt_d(double x)
     return y * (1.5 - 0.5 * x * y * y);
 }
 
-__device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc &c, const float *__restrict__ C,
-                                              uint32_t axon, uint32_t step, const float *p, const float *d,
-                                              double *pbar, double *dbar, float *mu)
+// Double-float accumulation of an FP64 value c into (hi, lo): c rounded to
+// FP32 goes to the high plane; its rounding error plus the exact rounding
+// error of that add (recovered from the returned old value, as the atomic
+// rounds to nearest) goes to the low plane.  Whatever the order of the
+// atomics, hi + sum(lo) stays the exact sum up to the low plane's rounding.
+__device__ __forceinline__ void atomic_add_df64(float *hi, float *lo, double c)
+{
+    const float ch = (float)c;
+    const float old = atomicAdd(hi, ch);
+    const float r = two_sum(old, ch).lo + (float)(c - (double)ch);
+    if (r != 0.0f) atomicAdd(lo, r);
+}
+
+// Backward through one clamp-mode 3D cone step, the reverse mode in FP64 at
+// the FP32 state it is given (the decisions -- gradient threshold, blend
+// threshold, clamp -- and the noise are the FP32 forward's; inv_hd = 1/h in
+// FP64).  pbar, dbar: FP64, in dL/d(p,
+// d)^{n+1}, out dL/d(p, d)^n; the field part is scattered into mu.
+__device__ __forceinline__ void cone_adjoint3(const FieldDesc &f, const ConeDesc &c, double inv_hd,
+                                              const float *__restrict__ C, uint32_t axon, uint32_t step,
+                                              const float *p, const float *d, double *pbar, double *dbar, float *mu)
+{
+    constexpr int DIM = 3;
+    const size_t sy = f.nx, sz = (size_t)f.nx * f.ny;
+    float *mu_lo = mu + sz * f.nz;
+    auto ld = [&](int i, int j, int k) { return __ldg(C + (size_t)i + sy * j + sz * k); };
+    // the forward step in FP32, for its decisions
+    float g[DIM], xi[DIM];
+    sample_gradient<DIM>(f, c, p, ld, g);
+    cone_noise<DIM>(c.key0, c.key1, axon, step, xi);
+    float gn2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) gn2 = fmaf(g[i], g[i], gn2);
+    const bool has_g = gn2 > c.eps2;
+    const float ginv = has_g ? rsqrtf(gn2) : 0.0f;
+    float vf[DIM], vn2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        vf[i] = c.w_prev * d[i] + c.w_grad * (g[i] * ginv) + c.w_noise * xi[i];
+        vn2 = fmaf(vf[i], vf[i], vn2);
+    }
+    const bool has_v = vn2 > 1e-30f;
+    const float vinv = has_v ? rsqrtf(vn2) : 0.0f;
+    const float hi[3] = {c.hi0, c.hi1, c.hi2};
+    bool clamped[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        const float q = fmaf(c.step_len, has_v ? vf[i] * vinv : d[i], p[i]);
+        clamped[i] = q < 0.0f || q > hi[i];
+    }
+    // the sample in FP64: cell, fractions, corner node gradients, weights
+    int lo[3] = {0, 0, 0};
+    float frf[3] = {0.f, 0.f, 0.f};
+    cell_of<DIM>(f, p, lo, frf);
+    const int ext[3] = {f.nx, f.ny, f.nz};
+    const double i2h = (double)c.inv2h;
+    double fr[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) fr[i] = (double)p[i] * inv_hd - (double)lo[i];
+    double G[8][DIM], W[8];
+    double gd[DIM] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int cidx = 0; cidx < 8; ++cidx) {
+        const int a = cidx & 1, b = (cidx >> 1) & 1, e = cidx >> 2;
+        const int idx[3] = {lo[0] + a, lo[1] + b, lo[2] + e};
+        W[cidx] = (a ? fr[0] : 1.0 - fr[0]) * (b ? fr[1] : 1.0 - fr[1]) * (e ? fr[2] : 1.0 - fr[2]);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            int ip[3] = {idx[0], idx[1], idx[2]}, im[3] = {idx[0], idx[1], idx[2]};
+            ip[k] = min(ip[k] + 1, ext[k] - 1);
+            im[k] = max(im[k] - 1, 0);
+            G[cidx][k] = ((double)ld(ip[0], ip[1], ip[2]) - (double)ld(im[0], im[1], im[2])) * i2h;
+            gd[k] += W[cidx] * G[cidx][k];
+        }
+    }
+    double ghat[DIM] = {0.0, 0.0, 0.0}, ginvd = 0.0;
+    if (has_g) {
+        ginvd = rsqrt_d(gd[0] * gd[0] + gd[1] * gd[1] + gd[2] * gd[2]);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) ghat[i] = gd[i] * ginvd;
+    }
+    double vd[DIM], dn[DIM], vinvd = 0.0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+        vd[i] = (double)c.w_prev * (double)d[i] + (double)c.w_grad * ghat[i] + (double)c.w_noise * (double)xi[i];
+    if (has_v) vinvd = rsqrt_d(vd[0] * vd[0] + vd[1] * vd[1] + vd[2] * vd[2]);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) dn[i] = has_v ? vd[i] * vinvd : (double)d[i];
+    double qbar[DIM], dnbar[DIM], vbar[DIM], gbar[DIM] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        qbar[i] = clamped[i] ? 0.0 : pbar[i];
+        dnbar[i] = (double)c.step_len * qbar[i] + dbar[i];
+    }
+    if (has_v) {
+        const double dot = dn[0] * dnbar[0] + dn[1] * dnbar[1] + dn[2] * dnbar[2];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            vbar[i] = (dnbar[i] - dn[i] * dot) * vinvd;
+            dbar[i] = (double)c.w_prev * vbar[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            vbar[i] = 0.0;
+            dbar[i] = dnbar[i];
+        }
+    }
+    if (has_g) {
+        const double wg = (double)c.w_grad;
+        const double dot = ghat[0] * (wg * vbar[0]) + ghat[1] * (wg * vbar[1]) + ghat[2] * (wg * vbar[2]);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) gbar[i] = (wg * vbar[i] - ghat[i] * dot) * ginvd;
+    }
+    // back through the sample: position (weight derivatives) and field (node differences)
+    double pb[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) pb[i] = qbar[i];
+    const double ih = inv_hd;
+#pragma unroll
+    for (int cidx = 0; cidx < 8; ++cidx) {
+        const int a = cidx & 1, b = (cidx >> 1) & 1, e = cidx >> 2;
+        const double w1[3] = {a ? fr[0] : 1.0 - fr[0], b ? fr[1] : 1.0 - fr[1], e ? fr[2] : 1.0 - fr[2]};
+        const double sg[3] = {a ? 1.0 : -1.0, b ? 1.0 : -1.0, e ? 1.0 : -1.0};
+        const double sdot = gbar[0] * G[cidx][0] + gbar[1] * G[cidx][1] + gbar[2] * G[cidx][2];
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) {
+            double dwm = sg[m] * ih;
+#pragma unroll
+            for (int q = 0; q < DIM; ++q)
+                if (q != m) dwm *= w1[q];
+            pb[m] += dwm * sdot;
+        }
+        if (!has_g) continue;
+        const int idx[3] = {lo[0] + a, lo[1] + b, lo[2] + e};
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            int ip[3] = {idx[0], idx[1], idx[2]}, im[3] = {idx[0], idx[1], idx[2]};
+            ip[k] = min(ip[k] + 1, ext[k] - 1);
+            im[k] = max(im[k] - 1, 0);
+            const double coef = gbar[k] * W[cidx] * i2h;
+            const size_t jp = node_index(f, ip[0], ip[1], ip[2]), jm = node_index(f, im[0], im[1], im[2]);
+            atomic_add_df64(mu + jp, mu_lo + jp, coef);
+            atomic_add_df64(mu + jm, mu_lo + jm, -coef);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) pbar[i] = pb[i];
+}
+
+__device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc &c, double inv_hd,
+                                              const float *__restrict__ C, uint32_t axon, uint32_t step,
+                                              const float *p, const float *d, double *pbar, double *dbar, float *mu)
 {
     const size_t sy = f.nx;
     auto ld = [&](int i, int j, int) { return __ldg(C + (size_t)i + sy * j); };
@@ -468,10 +509,22 @@ __device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc
         const float q = fmaf(c.step_len, dnf, p[i]);
         clamped[i] = q < 0.0f || q > (i ? c.hi1 : c.hi0);
     }
-    // the reverse mode in FP64 at those values: the adjoint of the endpoint
-    // loss cancels heavily between cones and steps, and the per-cone work is
-    // small next to the field's
-    const double gd[2] = {(double)g[0], (double)g[1]};
+    // the reverse mode in FP64 at that state: the adjoint of the endpoint loss
+    // cancels heavily between cones and steps, and near a cue maximum or a
+    // source the sampled gradient is a small difference of larger node values,
+    // so the linearisation point -- sample and normalised gradient -- is formed
+    // in FP64 from the FP32 node values and position (inv_hd = 1/h in FP64);
+    // the per-cone work is small next to the field's
+    const double i2h = (double)c.inv2h;
+    const double frx = (double)p[0] * inv_hd - (double)lo[0], fry = (double)p[1] * inv_hd - (double)lo[1];
+    const double wx0 = 1.0 - frx, wx1 = frx, wy0 = 1.0 - fry, wy1 = fry;
+    const double w00 = wx0 * wy0, w10 = wx1 * wy0, w01 = wx0 * wy1, w11 = wx1 * wy1;
+    const double gx00 = ((double)v[2] - v[0]) * i2h, gx10 = ((double)v[3] - v[1]) * i2h;
+    const double gx01 = ((double)v[6] - v[4]) * i2h, gx11 = ((double)v[7] - v[5]) * i2h;
+    const double gy00 = ((double)v[5] - v[8]) * i2h, gy10 = ((double)v[6] - v[9]) * i2h;
+    const double gy01 = ((double)v[10] - v[1]) * i2h, gy11 = ((double)v[11] - v[2]) * i2h;
+    const double gd[2] = {w00 * gx00 + w10 * gx10 + w01 * gx01 + w11 * gx11,
+                          w00 * gy00 + w10 * gy10 + w01 * gy01 + w11 * gy11};
     double ghat[2] = {0.0, 0.0}, ginvd = 0.0;
     if (has_g) {
         ginvd = rsqrt_d(gd[0] * gd[0] + gd[1] * gd[1]);
@@ -513,18 +566,11 @@ __device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc
 #pragma unroll
         for (int i = 0; i < 2; ++i) gbar[i] = (wg * vbar[i] - ghat[i] * dot) * ginvd;
     }
-    // corner weights and node gradients (corner (a, b) = node (x_a, y_b))
-    const double i2h = (double)c.inv2h;
-    const double wx0 = 1.0 - (double)fr[0], wx1 = (double)fr[0], wy0 = 1.0 - (double)fr[1], wy1 = (double)fr[1];
-    const double w00 = wx0 * wy0, w10 = wx1 * wy0, w01 = wx0 * wy1, w11 = wx1 * wy1;
-    const double gx00 = ((double)v[2] - v[0]) * i2h, gx10 = ((double)v[3] - v[1]) * i2h;
-    const double gx01 = ((double)v[6] - v[4]) * i2h, gx11 = ((double)v[7] - v[5]) * i2h;
-    const double gy00 = ((double)v[5] - v[8]) * i2h, gy10 = ((double)v[6] - v[9]) * i2h;
-    const double gy01 = ((double)v[10] - v[1]) * i2h, gy11 = ((double)v[11] - v[2]) * i2h;
-    // position: g(p) = sum_c w_c(p) G_c, dw/dp from the bilinear weights
+    // position: g(p) = sum_c w_c(p) G_c (corner (a, b) = node (x_a, y_b)), dw/dp
+    // from the bilinear weights
     const double s00 = gbar[0] * gx00 + gbar[1] * gy00, s10 = gbar[0] * gx10 + gbar[1] * gy10;
     const double s01 = gbar[0] * gx01 + gbar[1] * gy01, s11 = gbar[0] * gx11 + gbar[1] * gy11;
-    const double ih = (double)f.inv_h;
+    const double ih = inv_hd;
     pbar[0] = ih * (wy0 * (s10 - s00) + wy1 * (s11 - s01)) + qbar[0];
     pbar[1] = ih * (wx0 * (s01 - s00) + wx1 * (s11 - s10)) + qbar[1];
     if (!has_g) return;
@@ -571,6 +617,7 @@ __device__ __forceinline__ void cone_adjoint2(const FieldDesc &f, const ConeDesc
 struct AdjP {
     FieldDesc f;
     ConeDesc c;
+    double inv_h64;               // 1/h in FP64 (the cone reverse mode)
     int n;                        // cones
     int n_src;
     const int32_t *src_cell;
@@ -689,7 +736,6 @@ __device__ __forceinline__ void adj_rows(const AdjP &A, const float *Yin, const 
         if (xin) {
             const float4 c = __ldg(reinterpret_cast<const float4 *>(Cm) + at);
             float4 *s4 = A.Sseg ? reinterpret_cast<float4 *>(A.Sseg) + at : nullptr;
-            const float4 sv0 = s4 ? *s4 : z4;
             float L0, L1, L2, L3;
             const DF o0 = df_update2(cu[0], l, cu[1], up[0], dn[0], f.alpha, f.beta, &L0);
             const DF o1 = df_update2(cu[1], cu[0], cu[2], up[1], dn[1], f.alpha, f.beta, &L1);
@@ -699,7 +745,7 @@ __device__ __forceinline__ void adj_rows(const AdjP &A, const float *Yin, const 
                         v3 = cu[3].hi + cu[3].lo;
             tD = fmaf(L0, c.x, fmaf(L1, c.y, fmaf(L2, c.z, fmaf(L3, c.w, tD))));
             tL = fmaf(v0, c.x, fmaf(v1, c.y, fmaf(v2, c.z, fmaf(v3, c.w, tL))));
-            if (s4) *s4 = make_float4(sv0.x + v0, sv0.y + v1, sv0.z + v2, sv0.w + v3);
+            if (s4) seg_sum_add(s4, reinterpret_cast<float4 *>(A.Sseg + cells) + at, cu[0], cu[1], cu[2], cu[3]);
             reinterpret_cast<float4 *>(Yout)[at] = make_float4(o0.hi, o1.hi, o2.hi, o3.hi);
             reinterpret_cast<float4 *>(Yout + cells)[at] = make_float4(o0.lo, o1.lo, o2.lo, o3.lo);
             reinterpret_cast<float4 *>(Xz)[at] = z4;
@@ -756,7 +802,7 @@ __global__ void __launch_bounds__(256, 2) adj_persist_kernel(AdjP A, int len, ui
                     pb[i] = __ldcg(A.pbar + (size_t)i * A.n + a);
                     db[i] = __ldcg(A.dbar + (size_t)i * A.n + a);
                 }
-                cone_adjoint2(A.f, A.c, Cm, (uint32_t)a, g, p, d, pb, db, Xout);
+                cone_adjoint2(A.f, A.c, A.inv_h64, Cm, (uint32_t)a, g, p, d, pb, db, Xout);
                 for (int i = 0; i < 2; ++i) {
                     A.pbar[(size_t)i * A.n + a] = pb[i];
                     A.dbar[(size_t)i * A.n + a] = db[i];
@@ -805,22 +851,11 @@ __global__ void __launch_bounds__(256) adj_cone_kernel(FieldDesc f, ConeDesc c, 
         pb[i] = pbar[(size_t)i * n + a];
         db[i] = dbar[(size_t)i * n + a];
     }
-    if constexpr (DIM == 2) {
-        cone_adjoint2(f, c, C, (uint32_t)a, step, p, d, pb, db, mu_out);
-    } else {
-        float pf[DIM], df_[DIM];
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-            pf[i] = (float)pb[i];
-            df_[i] = (float)db[i];
-        }
-        cone_adjoint<DIM>(f, c, C, (uint32_t)a, step, p, d, pf, df_, mu_out);
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-            pb[i] = pf[i];
-            db[i] = df_[i];
-        }
-    }
+    const double inv_hd = 1.0 / (double)f.h;
+    if constexpr (DIM == 2)
+        cone_adjoint2(f, c, inv_hd, C, (uint32_t)a, step, p, d, pb, db, mu_out);
+    else
+        cone_adjoint3(f, c, inv_hd, C, (uint32_t)a, step, p, d, pb, db, mu_out);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
         pbar[(size_t)i * n + a] = pb[i];
@@ -966,18 +1001,19 @@ AdjLayout adj_layout(const cue_params &p, int n_src, int n_axons, int nsteps, in
     const size_t cone = (size_t)2 * p.dim * (n_axons > 0 ? n_axons : 1);    // pos + dir
     L.nseg = (nsteps + k - 1) / k;
     size_t off = 0;
-    L.ckpt_c = off;
-    off += align256(sizeof(float) * cells * L.nseg);
+    L.ckpt_c = off;                               // checkpoints of every segment but the last
+    off += align256(sizeof(float) * cells * (L.nseg - 1));
     L.ckpt_p = off;
-    off += align256(sizeof(float) * cone * L.nseg);
+    off += align256(sizeof(float) * cone * (L.nseg - 1));
+    const size_t seg_states = (size_t)std::min(k, nsteps) + 1;
     L.seg_c = off;
-    off += align256(sizeof(float) * cells * (k + 1));
+    off += align256(sizeof(float) * cells * seg_states);
     L.seg_p = off;
-    off += align256(sizeof(float) * cone * (k + 1));
+    off += align256(sizeof(float) * cone * seg_states);
     L.mu = off;                                   // adjoint field: five double-float buffers (hi, lo planes):
     off += align256(sizeof(float) * cells * 10);  // Y[2] and X[3] of the persistent backward, or mu[2]
-    L.Sseg = off;                                 // this segment's sum of mu
-    off += align256(sizeof(float) * cells);
+    L.Sseg = off;                                 // this segment's sum of mu (double-float: hi, lo planes)
+    off += align256(sizeof(float) * cells * 2);
     L.S = off;                                    // FP64 sum over the segments (rate-map gradient)
     off += align256(sizeof(double) * cells);
     L.pbar = off;
@@ -1066,11 +1102,31 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
         !ok(cudaMemsetAsync(acc, 0, sizeof(double) * (4 + s.n_src), st)) ||
         !ok(cudaMemsetAsync(part, 0, sizeof(double) * 2 * (size_t)L.n_part, st)) ||
         (S && !ok(cudaMemsetAsync(S, 0, sizeof(double) * cells, st))) ||
-        (Sseg && !ok(cudaMemsetAsync(Sseg, 0, sizeof(float) * cells, st))))
+        (Sseg && !ok(cudaMemsetAsync(Sseg, 0, sizeof(float) * cells * 2, st))))
         return CUE_ERR_CUDA;
     const int64_t n0 = s.field_step;
-    // ---- forward with checkpoints (any path: fused and plain agree bit for bit)
-    for (int j = 0; j < L.nseg; ++j) {
+    // one segment's coupled steps storing every state in sgC / sgP (slot 0 holds
+    // its start): one persistent launch where the path runs, else a cone and a
+    // field launch per step
+    auto trajectory = [&](int len, int64_t nstart) -> int {
+        int rc = (s.path != CUE_PATH_PLAIN && persist_supported(s))
+                     ? run_persist_trajectory(s, sgC, sgP, (uint32_t)nstart, len)
+                     : 1;
+        if (rc < 0) return rc;
+        for (int m = 0; rc == 1 && m < len; ++m) {
+            float *Pm = sgP + 2 * cone_n * m, *Pn = sgP + 2 * cone_n * (m + 1);
+            if (!ok(launch_cone_step_io(s, sgC + cells * m, (uint32_t)(nstart + m), Pm, Pm + cone_n, Pn,
+                                        Pn + cone_n)) ||
+                !ok(launch_field_and_sources(s, sgC + cells * m, sgC + cells * (m + 1))))
+                return CUE_ERR_CUDA;
+        }
+        return CUE_OK;
+    };
+    // ---- forward: checkpoints every k steps on the fastest path; the last segment
+    // runs as a stored trajectory, which its backward then walks without a
+    // recompute (with k >= nsteps the whole run is one stored trajectory and
+    // nothing is recomputed)
+    for (int j = 0; j < L.nseg - 1; ++j) {
         const int len = std::min(k, nsteps - j * k);
         if (!ok(cudaMemcpyAsync(ckC + cells * j, s.field[s.cur], sizeof(float) * cells, cudaMemcpyDeviceToDevice,
                                 st)) ||
@@ -1080,6 +1136,31 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
             return CUE_ERR_CUDA;
         int rc = run_coupled(s, len);
         if (rc != CUE_OK) return rc;
+    }
+    {
+        const int jl = L.nseg - 1;
+        const int len = nsteps - jl * k;
+        if (!ok(cudaMemcpyAsync(sgC, s.field[s.cur], sizeof(float) * cells, cudaMemcpyDeviceToDevice, st)) ||
+            !ok(cudaMemcpyAsync(sgP, s.pos, sizeof(float) * cone_n, cudaMemcpyDeviceToDevice, st)) ||
+            !ok(cudaMemcpyAsync(sgP + cone_n, s.dir, sizeof(float) * cone_n, cudaMemcpyDeviceToDevice, st)))
+            return CUE_ERR_CUDA;
+        int rc = trajectory(len, n0 + (int64_t)jl * k);
+        if (rc != CUE_OK) return rc;
+        // the handle ends as after sim_run: C^T in the buffer that is then current,
+        // C^{T-1} in the other, the cones at step T
+        const int cur_end = s.cur ^ (len & 1);
+        if (!ok(cudaMemcpyAsync(s.field[cur_end], sgC + cells * len, sizeof(float) * cells,
+                                cudaMemcpyDeviceToDevice, st)) ||
+            !ok(cudaMemcpyAsync(s.field[cur_end ^ 1], sgC + cells * (len - 1), sizeof(float) * cells,
+                                cudaMemcpyDeviceToDevice, st)) ||
+            !ok(cudaMemcpyAsync(s.pos, sgP + 2 * cone_n * len, sizeof(float) * cone_n, cudaMemcpyDeviceToDevice,
+                                st)) ||
+            !ok(cudaMemcpyAsync(s.dir, sgP + 2 * cone_n * len + cone_n, sizeof(float) * cone_n,
+                                cudaMemcpyDeviceToDevice, st)))
+            return CUE_ERR_CUDA;
+        s.cur = cur_end;
+        s.field_step += len;
+        s.cone_step += len;
     }
     // ---- loss and its adjoint at the end
     if (n > 0) {
@@ -1094,6 +1175,7 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
     if (persist_bw) {
         A.f = f;
         A.c = s.cd;
+        A.inv_h64 = 1.0 / (double)f.h;
         A.n = n;
         A.n_src = s.n_src;
         A.src_cell = s.src_cell;
@@ -1119,21 +1201,13 @@ int run_adjoint(Sim &s, const float *targets, int nsteps, int k, void *ws, size_
     for (int j = L.nseg - 1; j >= 0; --j) {
         const int len = std::min(k, nsteps - j * k);
         const int64_t nstart = n0 + (int64_t)j * k;
-        if (!ok(cudaMemcpyAsync(sgC, ckC + cells * j, sizeof(float) * cells, cudaMemcpyDeviceToDevice, st)) ||
-            !ok(cudaMemcpyAsync(sgP, ckP + 2 * cone_n * j, sizeof(float) * 2 * cone_n, cudaMemcpyDeviceToDevice, st)))
-            return CUE_ERR_CUDA;
-        // recompute the segment, storing every step: one persistent launch where
-        // the path runs, else a cone and a field launch per step
-        int rc = (s.path != CUE_PATH_PLAIN && persist_supported(s))
-                     ? run_persist_trajectory(s, sgC, sgP, (uint32_t)nstart, len)
-                     : 1;
-        if (rc < 0) return rc;
-        for (int m = 0; rc == 1 && m < len; ++m) {
-            float *Pm = sgP + 2 * cone_n * m, *Pn = sgP + 2 * cone_n * (m + 1);
-            if (!ok(launch_cone_step_io(s, sgC + cells * m, (uint32_t)(nstart + m), Pm, Pm + cone_n, Pn,
-                                        Pn + cone_n)) ||
-                !ok(launch_field_and_sources(s, sgC + cells * m, sgC + cells * (m + 1))))
+        if (j < L.nseg - 1) {         // recompute the segment from its checkpoint, storing every step
+            if (!ok(cudaMemcpyAsync(sgC, ckC + cells * j, sizeof(float) * cells, cudaMemcpyDeviceToDevice, st)) ||
+                !ok(cudaMemcpyAsync(sgP, ckP + 2 * cone_n * j, sizeof(float) * 2 * cone_n, cudaMemcpyDeviceToDevice,
+                                    st)))
                 return CUE_ERR_CUDA;
+            int rc = trajectory(len, nstart);
+            if (rc != CUE_OK) return rc;
         }
         if (s.adj_trace_field &&
             (!ok(cudaMemcpyAsync(s.adj_trace_field + cells * (size_t)j * k, sgC, sizeof(float) * cells * (len + 1),

@@ -16,11 +16,15 @@
 // node per sub-step; cones move at most step_len per step and read a 4-node
 // footprint, so the halo is H = K + 1 + ceil((K-1) step_len / h) (the x halo
 // rounded up to 4 nodes for 16-byte TMA coordinates).  Each launch re-bins its
-// cones for the next one as they finish: fixed-capacity per-tile bins (as many
-// ids as the register slots) filled through atomic counters, cones of a full
-// bin going to a spill list that the tile scans; each tile clears its own
-// count once read, the last tile past its prologue clears the spill count.
-// No separate binning launch between fused launches.
+// cones for the next one as they finish: per-tile bins filled through atomic
+// counters.  A bin holds every cone of its tile whenever the bins fit the
+// workspace budget (then no cone ever spills, however the cones cluster); the
+// first 512 ids of a bin ride in registers for the whole launch, the rest are
+// stepped from global memory.  Only on grids too large for such bins does a
+// bin hold 512 ids, cones of a full bin going to a spill list that every tile
+// scans.  Each tile clears its own count once read, the last tile past its
+// prologue clears the spill count.  No separate binning launch between fused
+// launches.
 //
 // Model: cue field on an Eulerian grid (Sec. 5.2) with sources of their own
 // rates (Sec. 4.3); cone steering by vector addition (Sec. 3.5, Eq. 6-7) with
@@ -34,191 +38,16 @@
 #include <cmath>
 
 #include "cue_internal.h"
+#include "cue_tile.cuh"
 
 namespace cue {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kW = 256;               // loaded columns per tile: a warp spans a row, 2 float4 per lane
-constexpr int kThreads = 256;         // 8 warps
-constexpr int kWarps = kThreads / 32;
+using namespace tile;
+
 constexpr int kMaxTileSrc = 256;      // sources per tile (and in total on this path)
-constexpr long long kWaitLimit = 1LL << 22;
-constexpr int kBand = 12;             // rows swept by each warp per sub-step
-constexpr int kRows = kWarps * kBand; // loaded rows per tile (96)
 constexpr int kFusedMinTX = 128;      // smallest interior tile the path accepts
 constexpr int kFusedMinTY = 32;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: gives up after kWaitLimit polls instead of hanging the GPU.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase)
-{
-    for (long long i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, phase)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-struct Row {
-    float4 a, b;   // columns 4*lane .. +3 and 128 + 4*lane .. +3 of the tile
-};
-
-__device__ __forceinline__ Row ld_row(const float4 *S4, int r, int lane)
-{
-    return Row{S4[r * (kW / 4) + lane], S4[r * (kW / 4) + 32 + lane]};
-}
-
-__device__ __forceinline__ void st_row(float4 *S4, int r, int lane, const Row &v)
-{
-    S4[r * (kW / 4) + lane] = v.a;
-    S4[r * (kW / 4) + 32 + lane] = v.b;
-}
-
-// New values of a 4-node group from its old values and neighbours, with the
-// arithmetic of node_update2: horizontal pairs summed as scalars, the rest two
-// nodes at a time with the packed FP32x2 instructions (each lane of a pair
-// rounds exactly like the scalar form).
-__device__ __forceinline__ float4 update4(float L, const float4 &c, float R, const float4 &u, const float4 &d,
-                                          float2 alpha2, float2 beta2)
-{
-    float2 h01 = make_float2(L + c.y, c.x + c.z);
-    float2 h23 = make_float2(c.y + c.w, c.z + R);
-    float2 s01 = __fadd2_rn(h01, __fadd2_rn(make_float2(u.x, u.y), make_float2(d.x, d.y)));
-    float2 s23 = __fadd2_rn(h23, __fadd2_rn(make_float2(u.z, u.w), make_float2(d.z, d.w)));
-    float2 o01 = __ffma2_rn(alpha2, s01, __fmul2_rn(beta2, make_float2(c.x, c.y)));
-    float2 o23 = __ffma2_rn(alpha2, s23, __fmul2_rn(beta2, make_float2(c.z, c.w)));
-    return make_float4(o01.x, o01.y, o23.x, o23.y);
-}
-
-// Per-lane wall flags: the x walls (global x = 0 and nx-1) fall on the first /
-// last component of one of the lane's two float4 groups.
-struct LaneWalls {
-    bool l_a, r_a, l_b, r_b;
-};
-
-// New values of row `cur` from the old rows above/at/below.  x neighbours come
-// from adjacent lanes.  The tile's two outermost columns take whatever the
-// shuffle wraps around (they are outside the valid region after the first
-// sub-step anyway); a node on an x wall uses itself as its missing neighbour.
-__device__ __forceinline__ Row update_row(const Row &up, const Row &cur, const Row &dn, int lane,
-                                          const LaneWalls &w, float2 alpha2, float2 beta2)
-{
-    float aL = __shfl_sync(kFull, cur.a.w, (lane + 31) & 31);
-    float aR = __shfl_sync(kFull, lane == 0 ? cur.b.x : cur.a.x, (lane + 1) & 31);
-    float bL = __shfl_sync(kFull, lane == 31 ? cur.a.w : cur.b.w, (lane + 31) & 31);
-    float bR = __shfl_sync(kFull, cur.b.x, (lane + 1) & 31);
-    aL = w.l_a ? cur.a.x : aL;
-    aR = w.r_a ? cur.a.w : aR;
-    bL = w.l_b ? cur.b.x : bL;
-    bR = w.r_b ? cur.b.w : bR;
-    Row o;
-    o.a = update4(aL, cur.a, aR, up.a, dn.a, alpha2, beta2);
-    o.b = update4(bL, cur.b, bR, up.b, dn.b, alpha2, beta2);
-    return o;
-}
-
-__device__ __forceinline__ float comp(const float4 &v, int k)
-{
-    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
-}
-
-__device__ __forceinline__ void set_comp(float4 &v, int k, float e)
-{
-    if (k == 0) v.x = e;
-    else if (k == 1) v.y = e;
-    else if (k == 2) v.z = e;
-    else v.w = e;
-}
-
-// Sources of one warp band, consumed in row order.
-struct BandSources {
-    const int *t_col, *t_row;
-    const float *t_e;
-    int begin, end;
-};
-
-// One sub-step of the in-place sweep over the warp's band of kBand rows
-// starting at r0.  `above` / `below` are the old rows just outside the band,
-// read before the CTA barrier that precedes the sweep.  On WALL tiles (a y
-// wall inside the loaded rows), rows outside the domain are not stored and the
-// ghost row beyond each y wall is rewritten with the new edge row, so the
-// next sub-step sees the edge node as its own missing neighbour.
-template <bool WALL>
-__device__ __forceinline__ void sweep_band(float4 *S4, int lane, int r0, const Row &above, const Row &below,
-                                           const LaneWalls &lw, float2 alpha2, float2 beta2,
-                                           const BandSources &src, int oy, int ny)
-{
-    int sp = src.begin;
-    int srow = sp < src.end ? src.t_row[sp] : 1 << 30;
-    Row up = above;
-    Row cur = ld_row(S4, r0, lane);
-    Row dn = ld_row(S4, r0 + 1, lane);
-#pragma unroll
-    for (int i = 0; i < kBand; ++i) {
-        const int r = r0 + i;
-        Row nxt;
-        if (i + 2 < kBand) nxt = ld_row(S4, r + 2, lane);
-        else if (i + 2 == kBand) nxt = below;
-        Row o = update_row(up, cur, dn, lane, lw, alpha2, beta2);
-        while (srow == r) {
-            const int col = src.t_col[sp];
-            const float e = src.t_e[sp];
-            const int q = col >> 2;
-            if ((q & 31) == lane) {
-                if (q < 32) set_comp(o.a, col & 3, comp(o.a, col & 3) + e);
-                else set_comp(o.b, col & 3, comp(o.b, col & 3) + e);
-            }
-            ++sp;
-            srow = sp < src.end ? src.t_row[sp] : 1 << 30;
-        }
-        if (WALL) {
-            const int gy = oy + r;
-            if (gy >= 0 && gy < ny) st_row(S4, r, lane, o);
-            if (gy == 0 && r > 0) st_row(S4, r - 1, lane, o);               // top ghost row
-            if (gy == ny - 1 && r + 1 < kRows) st_row(S4, r + 1, lane, o);  // bottom ghost row
-        } else {
-            st_row(S4, r, lane, o);
-        }
-        up = cur;
-        cur = dn;
-        dn = nxt;
-    }
-}
 
 struct FusedArgs {
     FieldDesc f;
@@ -243,6 +72,7 @@ struct FusedArgs {
     int2 *spill_next;
     int *spill_cnt_next;
     int *done;                                 // tiles past their prologue: the last clears spill_cnt_cur
+    int bin_cap;                               // ids per tile bin (this launch's and the next's)
     const int32_t *src_cell;
     const float *src_emit;
     int n_src;
@@ -296,8 +126,8 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     // this tile's cones into registers (overlaps the TMA load)
     __shared__ int s_nspill;
     if (tid == 0) s_nspill = A.cones_on ? *A.spill_cnt_cur : 0;
-    const int n_bin = A.cones_on ? min(A.cnt_cur[t], kFusedBinCap) : 0;
-    const int *bin = A.bins_cur + (size_t)t * kFusedBinCap;
+    const int n_bin = A.cones_on ? min(A.cnt_cur[t], A.bin_cap) : 0;
+    const int *bin = A.bins_cur + (size_t)t * A.bin_cap;
     int ca[kConeSlots];
     bool cl[kConeSlots];
     float cp[kConeSlots][2], cdir[kConeSlots][2];
@@ -407,7 +237,8 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     const int stop_stride = g.local_stop ? kMaxTileSrc : A.n_src;
     const int n_stop = stop_on ? (g.local_stop ? row_start[kRows] : A.n_src) : 0;
     // walls: x walls by per-lane flags; y walls by a ghost row inside the loaded rows
-    const LaneWalls lw{gxA == 0, gxA + 3 == f.nx - 1, gxB == 0, gxB + 3 == f.nx - 1};
+    const LaneWalls lw = lane_walls(gxA, gxB, f.nx);      // nx % 4 == 0 on this path: walls on group edges
+    const BandMap no_map{};
     const int gt = (oy <= -1) ? -oy - 1 : -1;                       // tile row of global y = -1
     const int gb = (oy + kRows - 1 >= f.ny) ? f.ny - oy : -1;       // tile row of global y = ny
     const bool wall = gt >= 0 || gb >= 0;
@@ -484,6 +315,25 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
                 }
             }
         }
+        // cones of the bin beyond the register slots, then the spilled cones of this
+        // tile: state read from and written back to global memory every sub-step
+        // (warp-uniform trip counts: count_active is a warp-collective ballot)
+        for (int base = kFusedBinCap; base < n_bin; base += kThreads) {
+            const int i = base + tid;
+            const int a = i < n_bin ? bin[i] : -1;
+            bool live = a >= 0 && A.active[a] != 0;
+            count_active(A.counter, live);
+            if (live) {
+                float p[2] = {A.pos[a], A.pos[n + a]};
+                float d[2] = {A.dir[a], A.dir[n + a]};
+                bool alive = step_cone((uint32_t)a, step, p, d, nullptr);
+                A.pos[a] = p[0];
+                A.pos[n + a] = p[1];
+                A.dir[a] = d[0];
+                A.dir[n + a] = d[1];
+                if (!alive) A.active[a] = 0;
+            }
+        }
         for (int base = 0; base < n_spill; base += kThreads) {   // spilled cones of this tile
             const int i = base + tid;
             const int2 e = i < n_spill ? A.spill_cur[i] : make_int2(-1, -1);
@@ -506,8 +356,8 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
         const Row below = ld_row(S4, r0 + kBand < kRows ? r0 + kBand : r0 + kBand - 1, lane);
         __syncthreads();
         // ---- phase B: in-place sweep of the band to C^{n+j+1}
-        if (wall) sweep_band<true>(S4, lane, r0, above, below, lw, alpha2, beta2, bsrc, oy, f.ny);
-        else sweep_band<false>(S4, lane, r0, above, below, lw, alpha2, beta2, bsrc, oy, f.ny);
+        if (wall) sweep_band<true, false, false>(S4, lane, r0, above, below, lw, alpha2, beta2, bsrc, oy, f.ny, no_map);
+        else sweep_band<false, false, false>(S4, lane, r0, above, below, lw, alpha2, beta2, bsrc, oy, f.ny, no_map);
         __syncthreads();
     }
 
@@ -515,8 +365,8 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     auto rebin = [&](int a, float px, float py) {
         const int tile = tile_of(f, g, px, py);
         const int slot = atomicAdd(&A.cnt_next[tile], 1);
-        if (slot < kFusedBinCap) {
-            A.bins_next[(size_t)tile * kFusedBinCap + slot] = a;
+        if (slot < A.bin_cap) {
+            A.bins_next[(size_t)tile * A.bin_cap + slot] = a;
         } else {
             const int k = atomicAdd(A.spill_cnt_next, 1);
             A.spill_next[k] = make_int2(a, tile);
@@ -534,6 +384,10 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
         if (A.cnt_next && cl[q]) rebin(a, cp[q][0], cp[q][1]);
     }
     if (A.cnt_next) {
+        for (int i = kFusedBinCap + tid; i < n_bin; i += kThreads) {
+            const int a = bin[i];
+            if (A.active[a]) rebin(a, A.pos[a], A.pos[n + a]);
+        }
         for (int i = tid; i < n_spill; i += kThreads) {
             const int2 e = A.spill_cur[i];
             if (e.y == t && A.active[e.x]) rebin(e.x, A.pos[e.x], A.pos[n + e.x]);
@@ -565,15 +419,15 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
 // ---------------------------------------------------------------- binning
 // Start of a run: every active cone into its tile's bin (or the spill list).
 __global__ void bin_count_kernel(FieldDesc f, FusedGeom g, int n, const float *__restrict__ pos,
-                                 const uint8_t *__restrict__ active, int *count, int *bins, int2 *spill,
-                                 int *spill_cnt)
+                                 const uint8_t *__restrict__ active, int *count, int *bins, int bin_cap,
+                                 int2 *spill, int *spill_cnt)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n || !active[a]) return;
     const int tile = tile_of(f, g, pos[a], pos[n + a]);
     const int slot = atomicAdd(&count[tile], 1);
-    if (slot < kFusedBinCap) {
-        bins[(size_t)tile * kFusedBinCap + slot] = a;
+    if (slot < bin_cap) {
+        bins[(size_t)tile * bin_cap + slot] = a;
     } else {
         const int k = atomicAdd(spill_cnt, 1);
         spill[k] = make_int2(a, tile);
@@ -655,6 +509,26 @@ bool choose_geometry(const FieldDesc &f, float step_len, float stop_r2, bool con
 
 }  // namespace
 
+bool fused_geometry(const FieldDesc &f, float step_len, float stop_r2, bool cones, int K, FusedGeom &g)
+{
+    return choose_geometry(f, step_len, stop_r2, cones, K, device_sm_count(), g);
+}
+
+bool encode_field_map_available() { return encode_fn() != nullptr; }
+
+bool encode_field_map(void *map128, float *base, int nx, int ny, int pitch)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)kW, (cuuint32_t)kRows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(reinterpret_cast<CUtensorMap *>(map128), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Upper bound on the tile count of any accepted geometry (interior at least
 // kFusedMinTX x kFusedMinTY), used to size the binning workspace independently
 // of the temporal depth.
@@ -724,7 +598,8 @@ static cudaError_t launch_bin_count(Sim &s)
     if (e != cudaSuccess) return e;
     bin_count_kernel<<<(s.n_axons + 255) / 256, 256, 0, s.stream>>>(
         s.fd, s.geom, s.n_axons, s.pos, s.active, s.bin_count() + r * s.wl.n_tiles,
-        s.bin_list() + (size_t)r * s.wl.n_tiles * kFusedBinCap, s.spill() + (size_t)r * s.n_axons, s.bin_ctl() + r);
+        s.bin_list() + (size_t)r * s.wl.n_tiles * s.wl.bin_cap, s.wl.bin_cap, s.spill() + (size_t)r * s.n_axons,
+        s.bin_ctl() + r);
     (void)n_tiles;
     s.launches++;
     return cudaGetLastError();
@@ -751,14 +626,15 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     A.dir = s.dir;
     A.active = s.active;
     A.cnt_cur = s.bin_count() + r * s.wl.n_tiles;
-    A.bins_cur = s.bin_list() + (size_t)r * s.wl.n_tiles * kFusedBinCap;
+    A.bins_cur = s.bin_list() + (size_t)r * s.wl.n_tiles * s.wl.bin_cap;
     A.spill_cur = s.spill() + (size_t)r * s.n_axons;
     A.spill_cnt_cur = s.bin_ctl() + r;
     A.cnt_next = with_cones ? s.bin_count() + rn * s.wl.n_tiles : nullptr;
-    A.bins_next = s.bin_list() + (size_t)rn * s.wl.n_tiles * kFusedBinCap;
+    A.bins_next = s.bin_list() + (size_t)rn * s.wl.n_tiles * s.wl.bin_cap;
     A.spill_next = s.spill() + (size_t)rn * s.n_axons;
     A.spill_cnt_next = s.bin_ctl() + rn;
     A.done = s.bin_ctl() + 2;
+    A.bin_cap = s.wl.bin_cap;
     A.src_cell = s.src_cell;
     A.src_emit = s.src_emit;
     A.n_src = s.n_src;

@@ -212,6 +212,21 @@ def config_c2(seed=1) -> Workload:
                 philox_seed=2)
 
 
+def config_c2_clustered(seed=8) -> Workload:
+    """The 2048^2 workload with its 16,384 cones starting clustered: four 48 x 48 node squares
+    (4,096 cones each, uniform inside) centred on four points of the grid, wall clamp and no
+    source stop, so no cone leaves the run and the cones stay crowded into a few field tiles."""
+    w = make("c2-2d-2048-clustered", 2, 2048, 2048, h=1.0, D=1.0, lam=0.005, dt=0.2, n_src=64,
+             emit=(0.5, 2.0), n_axons=16384, wall_mode=1, nsteps=5000, seed=seed, philox_seed=8)
+    rng = np.random.default_rng(seed + 1000)
+    centres = np.array([[512.0, 512.0], [1536.0, 512.0], [512.0, 1536.0], [1536.0, 1536.0]])
+    pos = np.empty((2, 16384))
+    for q in range(4):
+        pos[:, q * 4096:(q + 1) * 4096] = centres[q][:, None] + rng.uniform(-24.0, 24.0, (2, 4096))
+    w.pos = pos.astype(np.float32)
+    return w
+
+
 def config_c3(seed=2) -> Workload:
     return make("c3-3d-256", 3, 256, 256, 256, h=1.0, D=1.0, lam=0.01, dt=0.15, n_src=128,
                 emit=(0.5, 2.0), n_axons=65536, nsteps=2000, seed=seed, philox_seed=3)

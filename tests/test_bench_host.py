@@ -46,7 +46,7 @@ def test_committed_traffic_entries_are_well_formed():
         assert e["dram_bytes_per_launch"] > 0 and len(e["source_digest"]) == 16 and e["note"], key
 
 
-@pytest.mark.parametrize("flag,values", [("--workload", ["c1", "c2", "c3", "c4", "c5", "graph"]),
+@pytest.mark.parametrize("flag,values", [("--workload", ["c1", "c2", "c2x", "c3", "c4", "c5", "graph"]),
                                          ("--path", ["auto", "plain", "fused", "persist", "resident"])])
 def test_command_line_offers_every_workload_and_path(monkeypatch, flag, values):
     for v in values:

@@ -75,20 +75,30 @@ def test_batch_equals_each_instance_alone(cue, batch_mod, nsteps):
     b.close()
 
 
-@pytest.mark.parametrize("rows,blocks,mode", [(1, 1, 1), (2, 3, 1), (4, 2, 1), (1, 0, 2), (2, 0, 2), (4, 0, 2),
-                                              (8, 0, 2), (16, 0, 2)])
-def test_launch_shape_does_not_change_results(cue, batch_mod, rows, blocks, mode):
-    """Persistent launches of any shape and one launch per step give every instance exactly
-    the state it reaches alone on the plain path, and the same cone-update count."""
+@pytest.mark.parametrize("rows,blocks,mode,depth", [(1, 1, 1, 0), (2, 3, 1, 0), (4, 2, 1, 0), (1, 0, 2, 0),
+                                                    (2, 0, 2, 0), (4, 0, 2, 0), (8, 0, 2, 0), (16, 0, 2, 0),
+                                                    (0, 0, 3, 1), (0, 0, 3, 2), (0, 0, 3, 3), (0, 0, 3, 4),
+                                                    (0, 0, 3, 5), (0, 0, 3, 8)])
+def test_launch_shape_does_not_change_results(cue, batch_mod, rows, blocks, mode, depth):
+    """Persistent launches of any shape, one launch per step, and temporally blocked launches
+    of any depth (12 steps: ragged last launches for depths 5 and 8) give every instance
+    exactly the state it reaches alone on the plain path, and the same cone-update count."""
     ws = _mixed()
     b = batch_mod.Batch(ws)
-    b.set_option(batch_mod.CUE_BOPT_ROWS, rows)
+    assert b.get_option(batch_mod.CUE_BINFO_BLOCKED) == 1
+    if rows:
+        b.set_option(batch_mod.CUE_BOPT_ROWS, rows)
     b.set_option(batch_mod.CUE_BOPT_BLOCKS, blocks)
     b.set_option(batch_mod.CUE_BOPT_MODE, mode)
+    if depth:
+        b.set_option(batch_mod.CUE_BOPT_DEPTH, depth)
     b.run(12)
     b.check()
-    assert b.get_option(batch_mod.CUE_BOPT_ROWS) == rows
+    if rows:
+        assert b.get_option(batch_mod.CUE_BOPT_ROWS) == rows
     assert b.get_option(batch_mod.CUE_BOPT_MODE) == mode
+    if depth:
+        assert b.get_option(batch_mod.CUE_BOPT_DEPTH) == depth
     updates = b.cone_updates()
     want_updates = 0
     for i, w in enumerate(ws):
@@ -103,7 +113,7 @@ def test_launch_shape_does_not_change_results(cue, batch_mod, rows, blocks, mode
     b.close()
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_graph_replays_equal_direct_launches(cue, batch_mod, mode):
     ws = _mixed()
     a = batch_mod.Batch(ws)
@@ -128,9 +138,13 @@ def test_autotune_restores_the_state_and_keeps_a_valid_shape(cue, batch_mod):
     b.run(3)
     before = [b.snapshot(i) for i in range(len(ws))]
     updates_before = b.cone_updates()
-    rows, blocks, ms = b.autotune(4)
-    assert rows in (1, 2, 4, 8, 16) and 0 <= blocks <= 8 and ms > 0
-    assert b.get_option(batch_mod.CUE_BOPT_MODE) == (2 if blocks == 0 else 1)
+    rows, blocks, ms = b.autotune(8)
+    mode = b.get_option(batch_mod.CUE_BOPT_MODE)
+    assert ms > 0 and 0 <= blocks <= 8
+    if mode == 3:
+        assert rows == 0 and blocks == 0 and b.get_option(batch_mod.CUE_BOPT_DEPTH) in (2, 4, 8)
+    else:
+        assert rows in (1, 2, 4, 8, 16) and mode == (2 if blocks == 0 else 1)
     assert b.get_option(batch_mod.CUE_BINFO_STEP) == 3
     for i in range(len(ws)):
         _assert_same(b.snapshot(i), before[i], ws[i].name)
@@ -143,11 +157,14 @@ def test_autotune_restores_the_state_and_keeps_a_valid_shape(cue, batch_mod):
     b.close()
 
 
-def test_batched_workload_sample_equals_instances_alone(cue, batch_mod):
+@pytest.mark.parametrize("mode", [1, 3])
+def test_batched_workload_sample_equals_instances_alone(cue, batch_mod, mode):
     """Sixteen instances of the 512-instance batched workload (sides U{64..1024}, D ~ U[0.5, 2],
-    lambda log-uniform, dt = 0.2 / D, 4-64 sources, 256-4096 cones)."""
+    lambda log-uniform, dt = 0.2 / D, 4-64 sources, 256-4096 cones), persistent and
+    temporally blocked (depth 4: two launches)."""
     ws = W.config_c4(n_instances=16, nsteps=8)
     b = batch_mod.Batch(ws)
+    b.set_option(batch_mod.CUE_BOPT_MODE, mode)
     b.run(8)
     b.check()
     for i, w in enumerate(ws):
@@ -155,16 +172,17 @@ def test_batched_workload_sample_equals_instances_alone(cue, batch_mod):
     b.close()
 
 
-def test_long_per_step_runs_replay_a_bounded_graph(cue, batch_mod):
-    """A per-step run longer than one captured graph replays the graph and launches the
-    remainder; the result is that of direct launches, bit for bit."""
+@pytest.mark.parametrize("mode", [2, 3])
+def test_long_per_step_runs_replay_a_bounded_graph(cue, batch_mod, mode):
+    """A per-step or blocked run longer than one captured graph replays the graph and launches
+    the remainder; the result is that of direct launches, bit for bit."""
     ws = _mixed()
     a = batch_mod.Batch(ws)
-    a.set_option(batch_mod.CUE_BOPT_MODE, 2)
+    a.set_option(batch_mod.CUE_BOPT_MODE, mode)
     a.set_option(batch_mod.CUE_BOPT_ROWS, 8)
     a.run(2500)
     g = batch_mod.Batch(ws)
-    g.set_option(batch_mod.CUE_BOPT_MODE, 2)
+    g.set_option(batch_mod.CUE_BOPT_MODE, mode)
     g.set_option(batch_mod.CUE_BOPT_ROWS, 8)
     g.set_option(batch_mod.CUE_BOPT_GRAPH, 1)
     g.run(2500)
@@ -178,7 +196,7 @@ def test_long_per_step_runs_replay_a_bounded_graph(cue, batch_mod):
     g.close()
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("sample", ["c4-16", "mixed"])
 def test_batched_step_matches_oracle(cue, batch_mod, sample, mode):
     """Every instance's batched step against the FP64 oracle's from the identical state: the
@@ -202,4 +220,24 @@ def test_batched_step_matches_oracle(cue, batch_mod, sample, mode):
         assert field_rel_err(C1, want) <= FIELD_RTOL, w.name
         if w.n_axons:
             compare_cones(w, C, after, pos, dirs, act, pos1, dirs1, act1)
+    b.close()
+
+
+def test_blocked_mode_on_clustered_and_crowded_instances(cue, batch_mod):
+    """The blocked mode with every cone of an instance in one field tile (a 64 x 64 instance
+    with 4,000 cones, a 900 x 700 instance whose 3,000 cones start in one corner), wall clamp
+    and stop: bins beyond the 512 register slots, re-binning across tiles; bit for bit equal
+    to each instance alone, over 2 x 8 + 3 steps."""
+    rng = np.random.default_rng(90)
+    a = W.make("crowd", 2, 64, 64, n_src=4, n_axons=4000, C0="smooth", seed=91)
+    bw = W.make("corner", 2, 900, 700, n_src=12, n_axons=3000, C0="smooth", seed=92, wall_mode=1)
+    bw.pos = rng.uniform(2.0, 40.0, (2, 3000)).astype(np.float32)
+    ws = [a, bw]
+    b = batch_mod.Batch(ws)
+    b.set_option(batch_mod.CUE_BOPT_MODE, 3)
+    b.set_option(batch_mod.CUE_BOPT_DEPTH, 8)
+    b.run(19)
+    b.check()
+    for i, w in enumerate(ws):
+        _assert_same(b.snapshot(i), _alone(cue, w, 19), w.name)
     b.close()

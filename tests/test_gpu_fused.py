@@ -180,6 +180,31 @@ def test_all_cones_in_one_tile(cue):
     _assert_same(a.snapshot(), b.snapshot())
 
 
+def test_clustered_workload_equals_plain(cue):
+    """The clustered 2048^2 workload (16,384 cones in four 48 x 48 squares, wall clamp): every
+    crowded tile steps its overflow cones from global memory; three fused launches and a ragged
+    fourth equal the plain path bit for bit."""
+    w = W.config_c2_clustered()
+    a, b = _pair(cue, w, 8)
+    a.sim_run(29)
+    b.sim_run(29)
+    _assert_same(a.snapshot(), b.snapshot())
+
+
+def test_clustered_cones_spill_path_on_a_large_grid(cue):
+    """A grid large enough that per-tile bins holding every cone would pass the workspace
+    budget (4096^2, 8,448 cones): bins hold 512 ids and the rest of a crowded tile's cones go
+    to the spill list.  5,000 cones start in one tile and 3,448 spread over the grid; both
+    runs must equal the plain path bit for bit."""
+    w = W.make("spill-4096", 2, 4096, 4096, n_src=16, n_axons=8448, C0="smooth", seed=39, stop_radius=2.0)
+    rng = np.random.default_rng(39)
+    w.pos[:, :5000] = rng.uniform(1000, 1040, (2, 5000)).astype(np.float32)
+    a, b = _pair(cue, w, 8)
+    a.sim_run(19)
+    b.sim_run(19)
+    _assert_same(a.snapshot(), b.snapshot())
+
+
 def test_fused_unsupported_shapes_are_refused(cue):
     w = W.make("odd", 2, 257, 131, n_src=3, n_axons=10, C0="smooth", seed=38)
     sim = cue.Simulation(w)

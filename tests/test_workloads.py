@@ -104,3 +104,15 @@ def test_connectivity_workload():
     A = csr_matrix((np.ones(keep.sum()), (src[keep], dst[keep])), shape=(m, m))
     order = csgraph.breadth_first_order(A, gw.source, directed=True, return_predecessors=False)
     assert order.size > 0.9 * m
+
+
+def test_clustered_workload_recipe():
+    """2048^2 physics of the default workload; 16,384 cones in four 48 x 48 squares of 4,096,
+    wall clamp, no source stop."""
+    w = W.config_c2_clustered()
+    c2 = W.config_c2()
+    assert (w.nx, w.ny, w.D, w.lam, w.dt, w.n_src, w.n_axons) == (c2.nx, c2.ny, c2.D, c2.lam, c2.dt, 64, 16384)
+    assert w.wall_mode == 1 and w.stop_radius == 0.0
+    for q, (cx, cy) in enumerate([(512, 512), (1536, 512), (512, 1536), (1536, 1536)]):
+        p = w.pos[:, q * 4096:(q + 1) * 4096]
+        assert np.all(np.abs(p[0] - cx) <= 24) and np.all(np.abs(p[1] - cy) <= 24)
