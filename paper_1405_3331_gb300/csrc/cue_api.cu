@@ -34,22 +34,6 @@ WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons)
     off += align256(sizeof(int32_t) * 2 * nt * (w.n_tiles > 0 ? (size_t)w.bin_cap : 1));
     w.spill_off = off;
     off += align256(sizeof(int2) * 2 * (w.n_tiles > 0 ? na : 1));
-    if (p.dim == 3 && n_axons > 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-        int zc = 1;
-        field3d_boxes(p.nx, p.ny, p.nz, sms, &w.boxes3, &zc);
-        w.cap3 = std::min(n_axons, 512);
-        w.bin3_count_off = off;
-        off += align256(sizeof(int32_t) * 2 * (size_t)w.boxes3);
-        w.bin3_list_off = off;
-        off += align256(sizeof(int32_t) * 2 * (size_t)w.boxes3 * w.cap3);
-        w.bin3_ovf_off = off;
-        off += align256(sizeof(int32_t) * 2 * na);
-        w.bin3_ctl_off = off;
-        off += 256;
-    }
     w.persist_off = off;
     if (p.dim == 2 && p.nx >= 4) {
         w.persist_items_cap = (size_t)persist_tiles(p.nx, p.ny, 1) + (na + kPersistConeChunk - 1) / kPersistConeChunk;
@@ -149,11 +133,8 @@ int run_coupled(Sim &s, int nsteps)
     if (rc != 1) return rc;
     rc = run_fused_if_supported(s, nsteps);
     if (rc != 1) return rc;       // handled (0 = ok, < 0 = error)
-    // 3D with the TMA field kernel: cones, field and sources of a step in one launch,
-    // the cones binned to the launch's boxes (binned once per call, then re-binned by
-    // each launch as the cones move)
+    // 3D with the TMA field kernel: cones, field and sources of a step in one launch
     const bool merged3 = s.fd.dim == 3 && s.vec4 && field3d_tma_prepare(s);
-    if (merged3 && nsteps > 0 && s.n_axons > 0 && launch_bin3(s) != cudaSuccess) return CUE_ERR_CUDA;
     for (int k = 0; k < nsteps; ++k) {
         float *in = s.field[s.cur], *out = s.field[s.cur ^ 1];
         cudaError_t e;
@@ -309,10 +290,7 @@ int cue_init(cue_sim **out, const cue_params *params, const cone_params *cone, f
     cudaError_t e = cudaMemsetAsync(s->ws, 0, 256, s->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(s->ws + wl.bin_count_off, 0, wl.bin_list_off - wl.bin_count_off, s->stream);
-    if (e == cudaSuccess && wl.boxes3 > 0) {
-        e = cudaMemsetAsync(s->ws + wl.bin3_count_off, 0, sizeof(int32_t) * 2 * (size_t)wl.boxes3, s->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(s->ws + wl.bin3_ctl_off, 0, 256, s->stream);
-    }
+
     if (e == cudaSuccess) e = launch_src_xyz(*s);
     if (e != cudaSuccess) {
         delete s;

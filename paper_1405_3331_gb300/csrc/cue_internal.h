@@ -36,11 +36,6 @@ struct WorkspaceLayout {
     size_t persist_off = 0;      // persistent path: barrier, two instance records, work list
     size_t persist_items_cap = 0;
     size_t persist_src_off = 0;  // persistent path: binned sources (PSrc) and their tile keys
-    // 3D one-launch step: cones binned to the launch's boxes (two rounds each):
-    // counts [2][boxes3], ids [2][boxes3][cap3], overflow ids [2][n_axons], overflow
-    // counts (2) and a finished-box counter
-    size_t bin3_count_off = 0, bin3_list_off = 0, bin3_ovf_off = 0, bin3_ctl_off = 0;
-    int boxes3 = 0, cap3 = 0;
     size_t total = 0;
     int n_tiles = 0;
     int bin_cap = 0;             // cone ids per tile bin
@@ -183,8 +178,6 @@ struct Sim {
     alignas(64) unsigned char tmap[2][128];   // CUtensorMap per field buffer (as TMA source)
     alignas(64) unsigned char tmap3[2][128];  // 3D plane maps of the field buffers
     bool tmap3_ready = false;
-    long long bin3_round = 0;                 // round of the 3D cone bins the next step reads
-    bool bin3_valid = false;                  // the current round's bins hold every active cone
 
     int *bin_count() const { return reinterpret_cast<int *>(ws + wl.bin_count_off); }
     int *bin_ctl() const { return reinterpret_cast<int *>(ws + wl.bin_ctl_off); }
@@ -316,11 +309,6 @@ cudaError_t launch_cone_step_io(Sim &s, const float *C, uint32_t step, const flo
                                 float *pout, float *dout);
 // 3D field step through the TMA plane pipeline (k_field3d.cu)
 bool field3d_tma_prepare(Sim &s);
-// Boxes (CTAs) of the 3D step launch and each box's z chunk, for a grid of
-// nx x ny x nz nodes on a device of `sms` SMs.
-void field3d_boxes(int nx, int ny, int nz, int sms, int *boxes, int *zchunk);
-// Bin every active cone into the 3D boxes of the current round (start of a run).
-cudaError_t launch_bin3(Sim &s);
 // cones_done (optional): the field blocks also step the cones on the input
 // buffer (cone step index s.cone_step) when one thread each covers them, and
 // *cones_done says whether they did; sources_done (optional): the field

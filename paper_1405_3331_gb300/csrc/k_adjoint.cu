@@ -765,6 +765,9 @@ __device__ __forceinline__ void adj_rows(const AdjP &A, const float *Yin, const 
 __global__ void __launch_bounds__(256, 2) adj_persist_kernel(AdjP A, int len, uint32_t g0, PBar *bar,
                                                              unsigned expected, long long limit, unsigned *status)
 {
+    // each thread's dD and dlambda products, summed over the segment's steps in
+    // compensated FP32 (two_sum: hi + lo), reduced over the block once at the end
+    DF sD{0.f, 0.f}, sL{0.f, 0.f};
     for (int m = len - 1; m >= 0; --m) {
         const uint32_t g = g0 + (uint32_t)m;              // global step index
         const float *Yin = A.Y[(g + 1) & 1];
@@ -820,9 +823,12 @@ __global__ void __launch_bounds__(256, 2) adj_persist_kernel(AdjP A, int len, ui
                 r += n;
             }
         }
-        block_add2<true>(tD, tL, A.part);
+        sD = df_add(sD, DF{tD, 0.f});
+        sL = df_add(sL, DF{tL, 0.f});
         if (!grid_barrier(bar, expected, limit, status)) return;
     }
+    block_add2<true>(sD.hi, sL.hi, A.part);
+    block_add2<true>(sD.lo, sL.lo, A.part);
 }
 
 // One backward step of the cones (+ de_k += mu_in[cell_k] by the first threads).

@@ -319,20 +319,43 @@ __global__ void __launch_bounds__(kThreads, 2) blocked_kernel(const BlockedArgs 
             }
         }
         // cones of the bin beyond the register slots: state through global memory
-        for (int base = kFusedBinCap; base < n_bin; base += kThreads) {
-            const int i = base + tid;
-            const int a = i < n_bin ? bin[i] : -1;
-            const bool live = a >= 0 && I.active[a] != 0;
-            count_active(I.counter, live);
-            if (live) {
-                float p[2] = {I.pos[a], I.pos[n + a]};
-                float d[2] = {I.dir[a], I.dir[n + a]};
-                bool alive = step_cone((uint32_t)a, step, p, d, nullptr);
-                I.pos[a] = p[0];
-                I.pos[n + a] = p[1];
-                I.dir[a] = d[0];
-                I.dir[n + a] = d[1];
-                if (!alive) I.active[a] = 0;
+        // software-pipelined: the next round's cone state (and the ids two rounds ahead)
+        // are loaded while this round's cone steps, so a crowded tile is bound by its
+        // arithmetic rather than by chains of dependent loads
+        if (n_bin > kFusedBinCap) {
+            auto id_at = [&](int i) { return i < n_bin ? bin[i] : -1; };
+            int a_nn = id_at(kFusedBinCap + kThreads + tid);
+            int a_n = id_at(kFusedBinCap + tid);
+            bool live_n = a_n >= 0 && I.active[a_n] != 0;
+            float p_n[2] = {0.f, 0.f}, d_n[2] = {0.f, 0.f};
+            if (live_n) {
+                p_n[0] = I.pos[a_n];
+                p_n[1] = I.pos[n + a_n];
+                d_n[0] = I.dir[a_n];
+                d_n[1] = I.dir[n + a_n];
+            }
+            for (int base = kFusedBinCap; base < n_bin; base += kThreads) {
+                const int a = a_n;
+                const bool live = live_n;
+                float p[2] = {p_n[0], p_n[1]}, d[2] = {d_n[0], d_n[1]};
+                a_n = a_nn;                                   // next round: state in flight now
+                a_nn = id_at(base + 2 * kThreads + tid);        // the round after next
+                live_n = a_n >= 0 && I.active[a_n] != 0;
+                if (live_n) {
+                    p_n[0] = I.pos[a_n];
+                    p_n[1] = I.pos[n + a_n];
+                    d_n[0] = I.dir[a_n];
+                    d_n[1] = I.dir[n + a_n];
+                }
+                count_active(I.counter, live);             // warp-uniform trip count
+                if (live) {
+                    bool alive = step_cone((uint32_t)a, step, p, d, nullptr);
+                    I.pos[a] = p[0];
+                    I.pos[n + a] = p[1];
+                    I.dir[a] = d[0];
+                    I.dir[n + a] = d[1];
+                    if (!alive) I.active[a] = 0;
+                }
             }
         }
         // rows just outside this warp's band, read before anyone overwrites them

@@ -7,10 +7,8 @@
 // nodes per plane from shared memory (x neighbours by warp shuffle) and
 // writes them with one 16-byte store.  HBM traffic: one read and one write
 // per node (8 B per node update) plus the halo overlap.  A ninth warp per CTA
-// steps the growth cones of the CTA's box on the input field meanwhile (the
-// cones are binned to the launch's boxes at the start of a run and re-binned
-// by each launch as they move, so a cone's gathers read planes its own CTA
-// streams and find them in L2; the eight field warps synchronise among
+// steps the CTA's share of the growth cones on the input field meanwhile (its
+// gathers are dependent global loads; the eight field warps synchronise among
 // themselves on a named barrier and never wait for it), and after the last
 // plane the field warps add the point sources of the CTA's box.
 //
@@ -103,35 +101,7 @@ struct Field3Args {
     const int32_t *src_cell;
     const float *src_emit;
     int n_add;
-    // cones binned to the launch's boxes (binned != 0): block b steps the cones of its
-    // box's bin, then its share of the overflow list, and files each cone that is
-    // still active into the next round's bin of the box that now holds it
-    int binned, cap3;
-    int *cnt_cur, *ids_cur, *ovf_cur, *ovf_cnt_cur;
-    int *cnt_next, *ids_next, *ovf_next, *ovf_cnt_next;
-    int *done3;
 };
-
-// Box (launch block) holding position p: the x-y column tile and the z chunk.
-__device__ __forceinline__ int box_of3(const FieldDesc &f, int ntx, int nty, int zchunk, const float *p)
-{
-    const int ix = clampi((int)floorf(p[0] * f.inv_h), 0, f.nx - 1);
-    const int iy = clampi((int)floorf(p[1] * f.inv_h), 0, f.ny - 1);
-    const int iz = clampi((int)floorf(p[2] * f.inv_h), 0, f.nz - 1);
-    return ix / kTX + ntx * (iy / kBY + nty * (iz / zchunk));
-}
-
-// File cone a into the next round's bin of box b (the overflow list when the bin is full).
-__device__ __forceinline__ void rebin3(const Field3Args &A, int a, int b)
-{
-    const int slot = atomicAdd(&A.cnt_next[b], 1);
-    if (slot < A.cap3) {
-        A.ids_next[(size_t)b * A.cap3 + slot] = a;
-    } else {
-        const int k = atomicAdd(A.ovf_cnt_next, 1);
-        A.ovf_next[k] = a;
-    }
-}
 
 // Cone a (inr: a is one of this block's cones): the plain cone kernel's step
 // (same functions, same order), with the source coordinates of the stop test
@@ -165,7 +135,6 @@ __device__ __forceinline__ void cone_one3(const Field3Args &A, int a, bool inr)
     }
     if (!alive) A.active[a] = 0;
     if (bad) flag_status(A.status, kStatusNonFinite);
-    if (A.binned && alive) rebin3(A, a, box_of3(f, A.ntx, A.nty, A.zchunk, p));
 }
 
 // The field warps meet at named barrier 1 (kThreads3 threads), so the cone
@@ -222,29 +191,7 @@ __global__ void __launch_bounds__(CONES ? kLaunch3 : kThreads3, 4)
         return mbar_wait_bounded(&bar[k % kStages], (unsigned)((k / kStages) & 1));
     };
     if (CONES && warp == kThreads3 / 32) {        // the cone warp: this block's cones, alongside the field
-        if (A.binned) {
-            // the cones in this block's box: their gathers read the planes this block streams
-            const int cnt = min(A.cnt_cur[fb], A.cap3);
-            const int *bin = A.ids_cur + (size_t)fb * A.cap3;
-            for (int base = 0; base < cnt; base += 32) {   // whole warp each round (the active count is a vote)
-                const int i = base + lane;
-                cone_one3(A, i < cnt ? bin[i] : 0, i < cnt);
-            }
-            const int ov = *A.ovf_cnt_cur, per = (ov + (int)gridDim.x - 1) / (int)gridDim.x;
-            const int o0 = min(fb * per, ov), o1 = min(o0 + per, ov);
-            for (int base = o0; base < o1; base += 32) {
-                const int i = base + lane;
-                cone_one3(A, i < o1 ? A.ovf_cur[i] : 0, i < o1);
-            }
-            if (lane == 0) {       // bin read: cleared for the step after next; the last block clears the overflow
-                A.cnt_cur[fb] = 0;
-                __threadfence();
-                if (atomicAdd(A.done3, 1) == (int)gridDim.x - 1) {
-                    *A.ovf_cnt_cur = 0;
-                    *A.done3 = 0;
-                }
-            }
-        } else if (A.cone_per > 0) {
+        if (A.cone_per > 0) {
             const int first = fb * A.cone_per;
             const int cnt = min(A.cone_per, A.n - first);
             for (int base = 0; base < cnt; base += 32)  // whole warp each round (the active count is a vote)
@@ -334,24 +281,6 @@ __global__ void __launch_bounds__(CONES ? kLaunch3 : kThreads3, 4)
     }
 }
 
-// Start of a run: every active cone into the bin of its box (overflow past cap3).
-__global__ void __launch_bounds__(256) bin3_kernel(FieldDesc f, int ntx, int nty, int zchunk, int n,
-                                                  const float *__restrict__ pos, const uint8_t *__restrict__ active,
-                                                  int cap3, int *cnt, int *ids, int *ovf, int *ovf_cnt)
-{
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n || !active[a]) return;
-    const float p[3] = {pos[a], pos[(size_t)n + a], pos[2 * (size_t)n + a]};
-    const int b = box_of3(f, ntx, nty, zchunk, p);
-    const int slot = atomicAdd(&cnt[b], 1);
-    if (slot < cap3) {
-        ids[(size_t)b * cap3 + slot] = a;
-    } else {
-        const int k = atomicAdd(ovf_cnt, 1);
-        ovf[k] = a;
-    }
-}
-
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -381,47 +310,6 @@ int sm_count3()
 }
 
 }  // namespace
-
-void field3d_boxes(int nx, int ny, int nz, int sms, int *boxes, int *zchunk)
-{
-    // at most one wave (four CTAs per SM resident): a CTA left for a second wave would
-    // stream its whole chunk after the others; each CTA marches a chunk of z planes
-    const long long cols = (long long)((nx + kTX - 1) / kTX) * ((ny + kBY - 1) / kBY);
-    long long chunks = 4LL * sms / cols;
-    if (chunks < 1) chunks = 1;
-    if (chunks > nz) chunks = nz;
-    const int zc = (int)((nz + chunks - 1) / chunks);
-    chunks = (nz + zc - 1) / zc;
-    *zchunk = zc;
-    *boxes = (int)(cols * chunks);
-}
-
-static int *bin3_count(Sim &s, int r) { return reinterpret_cast<int *>(s.ws + s.wl.bin3_count_off) + r * s.wl.boxes3; }
-static int *bin3_ids(Sim &s, int r)
-{
-    return reinterpret_cast<int *>(s.ws + s.wl.bin3_list_off) + (size_t)r * s.wl.boxes3 * s.wl.cap3;
-}
-static int *bin3_ovf(Sim &s, int r) { return reinterpret_cast<int *>(s.ws + s.wl.bin3_ovf_off) + (size_t)r * s.n_axons; }
-static int *bin3_ctl(Sim &s) { return reinterpret_cast<int *>(s.ws + s.wl.bin3_ctl_off); }   // ovf counts [2], done
-
-cudaError_t launch_bin3(Sim &s)
-{
-    s.bin3_valid = false;
-    int boxes = 0, zc = 1;
-    field3d_boxes(s.fd.nx, s.fd.ny, s.fd.nz, sm_count3(), &boxes, &zc);
-    if (s.wl.boxes3 <= 0 || boxes > s.wl.boxes3 || s.n_axons <= 0) return cudaSuccess;   // index slices instead
-    const int r = (int)(s.bin3_round & 1);
-    cudaError_t e = cudaMemsetAsync(bin3_count(s, 0), 0, sizeof(int) * 2 * (size_t)s.wl.boxes3, s.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bin3_ctl(s), 0, 256, s.stream);
-    if (e != cudaSuccess) return e;
-    bin3_kernel<<<(s.n_axons + 255) / 256, 256, 0, s.stream>>>(
-        s.fd, (s.fd.nx + kTX - 1) / kTX, (s.fd.ny + kBY - 1) / kBY, zc, s.n_axons, s.pos, s.active, s.wl.cap3,
-        bin3_count(s, r), bin3_ids(s, r), bin3_ovf(s, r), bin3_ctl(s) + r);
-    s.launches++;
-    e = cudaGetLastError();
-    if (e == cudaSuccess) s.bin3_valid = true;
-    return e;
-}
 
 // Tensor maps of the two field buffers as TMA sources; false if unavailable.
 bool field3d_tma_prepare(Sim &s)
@@ -478,32 +366,22 @@ cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout, bool *cones_d
     A.ntx = (s.fd.nx + kTX - 1) / kTX;
     A.nty = (s.fd.ny + kBY - 1) / kBY;
     A.status = s.status();
-    int boxes = 0;
-    field3d_boxes(s.fd.nx, s.fd.ny, s.fd.nz, sm_count3(), &boxes, &A.zchunk);
-    const unsigned grid = (unsigned)boxes;
-    // the cones ride along: the cones of each block's box when the bins hold every active
-    // cone, else an equal slice of the cone indices (at most 8 rounds of the cone warp)
+    // at most one wave (four CTAs per SM resident): a CTA left for a second wave would
+    // stream its whole chunk after the others; each CTA marches a chunk of z planes
+    const long long cols = (long long)A.ntx * A.nty;
+    long long chunks = 4LL * sm_count3() / cols;
+    if (chunks < 1) chunks = 1;
+    if (chunks > s.fd.nz) chunks = s.fd.nz;
+    A.zchunk = (int)((s.fd.nz + chunks - 1) / chunks);
+    chunks = (s.fd.nz + A.zchunk - 1) / A.zchunk;
+    const unsigned grid = (unsigned)(cols * chunks);
+    // the cones ride along (at most 8 rounds of the cone warp per block)
     const long long per = ((long long)s.n_axons + grid - 1) / grid;
-    A.binned = (cones_done && s.n_axons > 0 && s.bin3_valid && boxes <= s.wl.boxes3) ? 1 : 0;
-    A.cone_per = (!A.binned && cones_done && s.n_axons > 0 && per <= kThreads3) ? (int)per : 0;
-    if (A.binned) {
-        const int r = (int)(s.bin3_round & 1), rn = r ^ 1;
-        A.cap3 = s.wl.cap3;
-        A.cnt_cur = bin3_count(s, r);
-        A.ids_cur = bin3_ids(s, r);
-        A.ovf_cur = bin3_ovf(s, r);
-        A.ovf_cnt_cur = bin3_ctl(s) + r;
-        A.cnt_next = bin3_count(s, rn);
-        A.ids_next = bin3_ids(s, rn);
-        A.ovf_next = bin3_ovf(s, rn);
-        A.ovf_cnt_next = bin3_ctl(s) + rn;
-        A.done3 = bin3_ctl(s) + 2;
-    }
-    if (cones_done) *cones_done = A.binned || A.cone_per > 0 || s.n_axons == 0;
+    A.cone_per = (cones_done && s.n_axons > 0 && per <= kThreads3) ? (int)per : 0;
+    if (cones_done) *cones_done = A.cone_per > 0 || s.n_axons == 0;
     const int smem = 128 + kStages * kStageStride * (int)sizeof(float);
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(s.tmap3[in_buffer]);
-    const bool cones = A.binned || A.cone_per > 0;
-    if (A.binned) s.bin3_round++;              // this launch fills the other round
+    const bool cones = A.cone_per > 0;
     if (s.src_map) {
         if (cones) field3d_tma_kernel<true, true><<<grid, kLaunch3, smem, s.stream>>>(*map, A);
         else field3d_tma_kernel<true, false><<<grid, kThreads3, smem, s.stream>>>(*map, A);

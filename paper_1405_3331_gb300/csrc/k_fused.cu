@@ -318,20 +318,43 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
         // cones of the bin beyond the register slots, then the spilled cones of this
         // tile: state read from and written back to global memory every sub-step
         // (warp-uniform trip counts: count_active is a warp-collective ballot)
-        for (int base = kFusedBinCap; base < n_bin; base += kThreads) {
-            const int i = base + tid;
-            const int a = i < n_bin ? bin[i] : -1;
-            bool live = a >= 0 && A.active[a] != 0;
-            count_active(A.counter, live);
-            if (live) {
-                float p[2] = {A.pos[a], A.pos[n + a]};
-                float d[2] = {A.dir[a], A.dir[n + a]};
-                bool alive = step_cone((uint32_t)a, step, p, d, nullptr);
-                A.pos[a] = p[0];
-                A.pos[n + a] = p[1];
-                A.dir[a] = d[0];
-                A.dir[n + a] = d[1];
-                if (!alive) A.active[a] = 0;
+        // software-pipelined: the next round's cone state (and the ids two rounds ahead)
+        // are loaded while this round's cone steps, so a crowded tile is bound by its
+        // arithmetic rather than by chains of dependent loads
+        if (n_bin > kFusedBinCap) {
+            auto id_at = [&](int i) { return i < n_bin ? bin[i] : -1; };
+            int a_nn = id_at(kFusedBinCap + kThreads + tid);
+            int a_n = id_at(kFusedBinCap + tid);
+            bool live_n = a_n >= 0 && A.active[a_n] != 0;
+            float p_n[2] = {0.f, 0.f}, d_n[2] = {0.f, 0.f};
+            if (live_n) {
+                p_n[0] = A.pos[a_n];
+                p_n[1] = A.pos[n + a_n];
+                d_n[0] = A.dir[a_n];
+                d_n[1] = A.dir[n + a_n];
+            }
+            for (int base = kFusedBinCap; base < n_bin; base += kThreads) {
+                const int a = a_n;
+                const bool live = live_n;
+                float p[2] = {p_n[0], p_n[1]}, d[2] = {d_n[0], d_n[1]};
+                a_n = a_nn;                                   // next round: state in flight now
+                a_nn = id_at(base + 2 * kThreads + tid);        // the round after next
+                live_n = a_n >= 0 && A.active[a_n] != 0;
+                if (live_n) {
+                    p_n[0] = A.pos[a_n];
+                    p_n[1] = A.pos[n + a_n];
+                    d_n[0] = A.dir[a_n];
+                    d_n[1] = A.dir[n + a_n];
+                }
+                count_active(A.counter, live);             // warp-uniform trip count
+                if (live) {
+                    bool alive = step_cone((uint32_t)a, step, p, d, nullptr);
+                    A.pos[a] = p[0];
+                    A.pos[n + a] = p[1];
+                    A.dir[a] = d[0];
+                    A.dir[n + a] = d[1];
+                    if (!alive) A.active[a] = 0;
+                }
             }
         }
         for (int base = 0; base < n_spill; base += kThreads) {   // spilled cones of this tile

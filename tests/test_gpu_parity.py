@@ -338,9 +338,9 @@ def test_vector_and_tma_field_kernels_equal_the_any_size_kernel(cue, name):
 @pytest.mark.parametrize("name", ["3d-40x36x20", "c3-256"])
 def test_merged_3d_step_equals_separate_launches(cue, name):
     """With the TMA field kernel a 3D step (cones, field, sources) is one launch (each field
-    block steps the cones binned to its box while its planes stream; one binning launch per
-    call); with a one-float offset it is three.  Same arithmetic in the same order: the
-    whole state agrees bit for bit after several steps (sources sit on distinct nodes)."""
+    block steps a slice of the cones while its first planes load); with a one-float offset
+    it is three.  Same arithmetic in the same order: the whole state
+    agrees bit for bit after several steps (sources sit on distinct nodes)."""
     w = _case(name)
     a = cue.Simulation(w, path=cue.CUE_PATH_PLAIN)
     b = cue.Simulation(w, path=cue.CUE_PATH_PLAIN, field_offset=1)
@@ -349,7 +349,7 @@ def test_merged_3d_step_equals_separate_launches(cue, name):
     b.sim_run(4)
     a.check()
     b.check()
-    assert a.launches() - l0a == 1 + 4
+    assert a.launches() - l0a == 4
     assert b.launches() - l0b == 12
     for x, y in zip(a.snapshot()[:4], b.snapshot()[:4]):
         np.testing.assert_array_equal(x, y)
@@ -358,12 +358,11 @@ def test_merged_3d_step_equals_separate_launches(cue, name):
 
 
 @pytest.mark.parametrize("layout", ["crowded", "stop"])
-def test_binned_3d_cones_over_many_steps(cue, layout):
-    """The 3D step's per-box cone bins over 37 steps in two calls (re-binned by every
-    launch): 'crowded' puts 3,000 of 3,500 cones in one box (its bin holds 512, the rest go
-    through the overflow list that every block shares out); 'stop' uses a source-stop
-    radius, so cones leave the bins as they stop.  Bit for bit equal to the separate cone
-    and field launches."""
+def test_one_launch_3d_cones_over_many_steps(cue, layout):
+    """The one-launch 3D step over 150 steps in two calls with crowded cones ('crowded':
+    3,000 of 3,500 cones in one z plane of one column tile, gathering the same nodes) and
+    with a source-stop radius ('stop': cones drop out as they stop).  Bit for bit equal to
+    the separate cone and field launches."""
     if layout == "crowded":
         w = W.make("3d-crowd", 3, 64, 48, 40, dt=0.15, n_src=6, n_axons=3500, C0="smooth", seed=61)
         rng = np.random.default_rng(61)
@@ -374,7 +373,7 @@ def test_binned_3d_cones_over_many_steps(cue, layout):
                    stop_radius=2.5)
     a = cue.Simulation(w, path=cue.CUE_PATH_PLAIN)
     b = cue.Simulation(w, path=cue.CUE_PATH_PLAIN, field_offset=1)
-    for n in (20, 17):
+    for n in (70, 80):
         a.sim_run(n)
         b.sim_run(n)
     a.check()
