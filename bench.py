@@ -41,7 +41,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["cue", "reference"], default="cue")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2x", "c3", "c4", "c5", "graph"])
     ap.add_argument("--path", default="auto", choices=list(PATHS))
-    ap.add_argument("--depth", type=int, default=0, help="temporal depth on the fused path (0 = auto)")
+    ap.add_argument("--depth", type=int, default=0,
+                    help="temporal depth on the fused path, or of the blocked batch mode with --workload c4 "
+                         "(0 = auto / autotuned)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
@@ -321,12 +323,12 @@ def aggregate(local_ms, units_per_step, steps, world, dist=None, device=None):
 
 
 # ------------------------------------------------------------------ GPU arm
-PATHS = ("auto", "plain", "fused", "persist", "resident")
+PATHS = ("auto", "plain", "fused", "persist", "resident", "cluster")
 
 
 def path_code(cue, name):
     return {"auto": cue.CUE_PATH_AUTO, "plain": cue.CUE_PATH_PLAIN, "fused": cue.CUE_PATH_FUSED,
-            "persist": cue.CUE_PATH_PERSIST, "resident": cue.CUE_PATH_RESIDENT}[name]
+            "persist": cue.CUE_PATH_PERSIST, "resident": cue.CUE_PATH_RESIDENT, "cluster": cue.CUE_PATH_CLUSTER}[name]
 
 
 class Runner:
@@ -364,7 +366,8 @@ class Runner:
         cone_updates = sim.cone_updates()
         path = sim_path_used(sim)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        sim.set_option(self.cue.CUE_OPT_TIME_KERNEL, 1 if path in ("persist", "resident") else sample_period)
+        sim.set_option(self.cue.CUE_OPT_TIME_KERNEL, 1 if path in ("persist", "resident", "cluster")
+                       else sample_period)
         sim.kernel_time()
         barrier()
         if sampler is not None:
@@ -396,7 +399,7 @@ def dominant_kernel(sim, w):
     if path == "fused":
         K = sim.get_option(sim_cue().CUE_INFO_DEPTH)
         return "fused", (w.nsteps + K - 1) // K, K
-    if path in ("persist", "resident"):
+    if path in ("persist", "resident", "cluster"):
         return path, 1, w.nsteps
     return ("step3d" if w.dim == 3 else "field"), w.nsteps, 1
 
@@ -736,7 +739,12 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
     cells = sum(w.n_cells for w in ws)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     b, init, reset = build_batch(torch, dev, ws)
-    tuned = b.autotune(16)
+    if args.depth:                       # a fixed blocked depth (profiling): no autotuner
+        b.set_option(B.CUE_BOPT_MODE, 3)
+        b.set_option(B.CUE_BOPT_DEPTH, args.depth)
+        tuned = (0, 0, 0.0)
+    else:
+        tuned = b.autotune(16)
     b.set_option(B.CUE_BOPT_GRAPH, 1)
     run_ms, cone_updates, clocks = batch_timed(torch, b, reset, T, args.steps, args.warmup, barrier, flush,
                                                ClockSampler(gpu_id_for(dev.index or 0)))
@@ -1133,8 +1141,8 @@ def main_graph(args, torch, dev, rank, world, dist, barrier):
 
 def sim_path_used(sim):
     from paper_1405_3331_gb300 import cue
-    return {cue.CUE_PATH_FUSED: "fused", cue.CUE_PATH_PERSIST: "persist",
-            cue.CUE_PATH_RESIDENT: "resident"}.get(sim.last_path(), "plain")
+    return {cue.CUE_PATH_FUSED: "fused", cue.CUE_PATH_PERSIST: "persist", cue.CUE_PATH_RESIDENT: "resident",
+            cue.CUE_PATH_CLUSTER: "cluster"}.get(sim.last_path(), "plain")
 
 
 def hbm_probe(cue, torch, dev, hbm, dim=2):

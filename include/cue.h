@@ -119,7 +119,8 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
 #define CUE_INFO_DEPTH         18  /* temporal depth the fused path runs with                 */
 #define CUE_INFO_GRID          19  /* blocks of the last persistent launch                    */
 #define CUE_PATH_AUTO   0          /* library picks: fused for grids of at least one tile per
-                                      SM, else resident, else persistent, else plain         */
+                                      SM, else resident, else cluster, else persistent, else
+                                      plain                                                  */
 #define CUE_PATH_PLAIN  1          /* one launch per half-step: cone kernel, field kernel  */
 #define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel       */
 #define CUE_PATH_PERSIST 3         /* 2D, nx % 4 == 0: one cooperative launch for the whole
@@ -129,6 +130,12 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
                                       shared memory (128^2: 128 KB), at most 256 cones and
                                       1024 sources: one block holds the grid in shared
                                       memory and the cones in registers for the whole call  */
+#define CUE_PATH_CLUSTER 5         /* 2D, nx % 4 == 0, ny >= 16, a band of ny / 8 rows (both
+                                      buffers plus two halo rows) within one block's shared
+                                      memory, at most 2048 cones and 1024 sources: a cluster
+                                      of 8 blocks holds the grid in distributed shared
+                                      memory, one band each, for the whole call; one
+                                      cluster barrier per step                               */
 
 /* Parameters of the SNR turn rule (Sec. 3.5, Eq. 5; 2D).  Inside the
  * detectable window c_min <= C(p) <= c_max the cone turns by `turn` radians to

@@ -122,12 +122,17 @@ int run_coupled(Sim &s, int nsteps)
     s.fused_used = false;
     s.persist_used = false;
     s.resident_used = false;
+    s.cluster_used = false;
     // AUTO: the temporally blocked kernel when the grid gives every SM a tile;
-    // else one block with the grid in shared memory when it fits; else the
-    // persistent launch (small grids, or a rate map); else plain.
+    // else one block with the grid in shared memory when it fits (its step is
+    // the shortest: no cluster barrier, no remote loads); else a cluster of CTAs
+    // with the grid in their distributed shared memory; else the persistent
+    // launch (larger small grids, or a rate map); else plain.
     const bool small = !fused_supported(s) || fused_tile_count(s.params) < sm_count_api();
     int rc = 1;
     if (s.path == CUE_PATH_RESIDENT || (s.path == CUE_PATH_AUTO && small)) rc = run_resident_if_supported(s, nsteps);
+    if (rc != 1) return rc;
+    if (s.path == CUE_PATH_CLUSTER || (s.path == CUE_PATH_AUTO && small)) rc = run_cluster_if_supported(s, nsteps);
     if (rc != 1) return rc;
     if (s.path == CUE_PATH_PERSIST || (s.path == CUE_PATH_AUTO && small)) rc = run_persist_if_supported(s, nsteps);
     if (rc != 1) return rc;
@@ -458,8 +463,9 @@ int cue_set_option(cue_sim *s, int32_t option, int64_t value)
     switch (option) {
     case CUE_OPT_PATH:
         if (value != CUE_PATH_AUTO && value != CUE_PATH_PLAIN && value != CUE_PATH_FUSED &&
-            value != CUE_PATH_PERSIST && value != CUE_PATH_RESIDENT)
+            value != CUE_PATH_PERSIST && value != CUE_PATH_RESIDENT && value != CUE_PATH_CLUSTER)
             return CUE_ERR_ARG;
+        if (value == CUE_PATH_CLUSTER && !cluster_supported(*s)) return CUE_ERR_ARG;
         if (value == CUE_PATH_FUSED && !fused_supported(*s)) return CUE_ERR_ARG;
         if (value == CUE_PATH_PERSIST && !persist_supported(*s)) return CUE_ERR_ARG;
         if (value == CUE_PATH_RESIDENT && !resident_supported(*s)) return CUE_ERR_ARG;
@@ -526,6 +532,7 @@ int cue_get_option(const cue_sim *s, int32_t option, int64_t *value)
         *value = s->fused_used      ? CUE_PATH_FUSED
                  : s->persist_used  ? CUE_PATH_PERSIST
                  : s->resident_used ? CUE_PATH_RESIDENT
+                 : s->cluster_used  ? CUE_PATH_CLUSTER
                                     : CUE_PATH_PLAIN;
         return CUE_OK;
     case CUE_OPT_PERSIST_ROWS: *value = s->persist_rows; return CUE_OK;

@@ -152,8 +152,9 @@ struct Sim {
     double timed_ms = 0.0;
     uint64_t timed_launches = 0;
 
-    // resident path
+    // resident and cluster paths
     bool resident_used = false;
+    bool cluster_used = false;
 
     // adjoint trace (cue_adjoint_trace): copies of the forward states the backward pass reads
     float *adj_trace_field = nullptr;   // [max_states][cells]
@@ -239,6 +240,15 @@ bool resident_supported(const Sim &s);
 // Runs nsteps on the resident path when selected (or AUTO) and supported:
 // CUE_OK / negative error when it ran, 1 when the caller should fall back.
 int run_resident_if_supported(Sim &s, int nsteps);
+
+// ---- small 2D grids spread over a thread-block cluster (k_cluster.cu) ----
+constexpr int kClusterSize = 8;           // CTAs per cluster (portable size), one band of rows each
+constexpr int kClusterThreads = 256;      // threads per CTA; one cone per thread at most
+constexpr int kClusterMaxSources = 1024;
+bool cluster_supported(const Sim &s);
+// Runs nsteps on the cluster path when selected (or AUTO) and supported:
+// CUE_OK / negative error when it ran, 1 when the caller should fall back.
+int run_cluster_if_supported(Sim &s, int nsteps);
 
 // ---- fused, temporally blocked path (k_fused.cu) ----
 constexpr int kMaxTemporalDepth = 16;

@@ -45,6 +45,7 @@ CUE_PATH_PLAIN = 1
 CUE_PATH_FUSED = 2
 CUE_PATH_PERSIST = 3
 CUE_PATH_RESIDENT = 4
+CUE_PATH_CLUSTER = 5
 
 class cue_snr_params(ct.Structure):
     _fields_ = [("gain", ct.c_float), ("width", ct.c_float), ("kd", ct.c_float), ("c_min", ct.c_float),
@@ -371,8 +372,8 @@ class Simulation:
         return self.get_option(CUE_INFO_LAST_PATH) == CUE_PATH_FUSED
 
     def last_path(self) -> int:
-        """CUE_PATH_PLAIN, CUE_PATH_FUSED, CUE_PATH_PERSIST or CUE_PATH_RESIDENT: the path of the
-        last sim_run."""
+        """CUE_PATH_PLAIN, CUE_PATH_FUSED, CUE_PATH_PERSIST, CUE_PATH_RESIDENT or CUE_PATH_CLUSTER:
+        the path of the last sim_run."""
         return self.get_option(CUE_INFO_LAST_PATH)
 
     def launches(self) -> int:

@@ -112,13 +112,14 @@ def test_auto_takes_the_resident_path_where_it_applies(cue):
         sim.check()
         assert sim.last_path() == cue.CUE_PATH_RESIDENT, name
         sim.close()
-    # too many cones for the cone warps, or both buffers beyond one block's shared memory
+    # too many cones for the cone warps, or both buffers beyond one block's shared memory: the
+    # resident path is refused (AUTO takes the cluster path there)
     for w in (W.make("cones", 2, 128, 128, n_src=4, n_axons=257, seed=78),
               W.make("big", 2, 256, 192, n_src=4, n_axons=64, seed=79)):
         sim = cue.Simulation(w)
         sim.sim_run(2)
         sim.check()
-        assert sim.last_path() == cue.CUE_PATH_PERSIST, w.name
+        assert sim.last_path() == cue.CUE_PATH_CLUSTER, w.name
         with pytest.raises(cue.CueError) as e:
             sim.set_option(cue.CUE_OPT_PATH, cue.CUE_PATH_RESIDENT)
         assert e.value.code == cue.CUE_ERR_ARG
