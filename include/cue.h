@@ -113,14 +113,19 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
 #define CUE_OPT_BARRIER_PHANTOM 8  /* diagnostic: the persistent grid barrier also waits for
                                       this many arrivals that never come, so its bounded
                                       wait runs out (tests the timeout path); 0 = off       */
+#define CUE_OPT_CLUSTER_CTAS    9  /* value: blocks per cluster of the cluster path: 0 = the
+                                      library picks (16 where it fits and the device can
+                                      schedule it, else 8), or 8 or 16; results do not
+                                      depend on it                                           */
 /* read-only values for cue_get_option */
 #define CUE_INFO_LAST_PATH     16  /* CUE_PATH_*: path the last sim_run took                  */
 #define CUE_INFO_TILE          17  /* fused tile interior: TX | TY << 16 (0 if not prepared) */
 #define CUE_INFO_DEPTH         18  /* temporal depth the fused path runs with                 */
-#define CUE_INFO_GRID          19  /* blocks of the last persistent launch                    */
+#define CUE_INFO_GRID          19  /* blocks of the last persistent or cluster launch         */
 #define CUE_PATH_AUTO   0          /* library picks: fused for grids of at least one tile per
-                                      SM, else resident, else cluster, else persistent, else
-                                      plain                                                  */
+                                      SM; else cluster for 2D grids of at least 4096 nodes
+                                      with at most 128 cones and 16384 nodes per block; else
+                                      resident; else persistent; else plain                 */
 #define CUE_PATH_PLAIN  1          /* one launch per half-step: cone kernel, field kernel  */
 #define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel       */
 #define CUE_PATH_PERSIST 3         /* 2D, nx % 4 == 0: one cooperative launch for the whole
@@ -130,12 +135,13 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
                                       shared memory (128^2: 128 KB), at most 256 cones and
                                       1024 sources: one block holds the grid in shared
                                       memory and the cones in registers for the whole call  */
-#define CUE_PATH_CLUSTER 5         /* 2D, nx % 4 == 0, ny >= 16, a band of ny / 8 rows (both
-                                      buffers plus two halo rows) within one block's shared
-                                      memory, at most 2048 cones and 1024 sources: a cluster
-                                      of 8 blocks holds the grid in distributed shared
-                                      memory, one band each, for the whole call; one
-                                      cluster barrier per step                               */
+#define CUE_PATH_CLUSTER 5         /* 2D, nx % 4 == 0, ny >= 2G, a band of ceil(ny / G) rows
+                                      (both buffers plus two halo rows) within one block's
+                                      shared memory, at most 512 G cones and 1024 sources: a
+                                      cluster of G = 16 blocks (where the device schedules
+                                      one; else G = 8, see CUE_OPT_CLUSTER_CTAS) holds the
+                                      grid in distributed shared memory, one band each, for
+                                      the whole call; one cluster barrier per step           */
 
 /* Parameters of the SNR turn rule (Sec. 3.5, Eq. 5; 2D).  Inside the
  * detectable window c_min <= C(p) <= c_max the cone turns by `turn` radians to

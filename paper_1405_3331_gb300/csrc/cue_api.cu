@@ -124,15 +124,16 @@ int run_coupled(Sim &s, int nsteps)
     s.resident_used = false;
     s.cluster_used = false;
     // AUTO: the temporally blocked kernel when the grid gives every SM a tile;
-    // else one block with the grid in shared memory when it fits (its step is
-    // the shortest: no cluster barrier, no remote loads); else a cluster of CTAs
-    // with the grid in their distributed shared memory; else the persistent
-    // launch (larger small grids, or a rate map); else plain.
+    // else a cluster of CTAs with the grid in their distributed shared memory
+    // where its measured step is the shortest (cluster_preferred); else one
+    // block with the grid in shared memory; else the persistent launch (larger
+    // small grids, or many cones); else plain.
     const bool small = !fused_supported(s) || fused_tile_count(s.params) < sm_count_api();
     int rc = 1;
-    if (s.path == CUE_PATH_RESIDENT || (s.path == CUE_PATH_AUTO && small)) rc = run_resident_if_supported(s, nsteps);
+    if (s.path == CUE_PATH_CLUSTER || (s.path == CUE_PATH_AUTO && small && cluster_preferred(s)))
+        rc = run_cluster_if_supported(s, nsteps);
     if (rc != 1) return rc;
-    if (s.path == CUE_PATH_CLUSTER || (s.path == CUE_PATH_AUTO && small)) rc = run_cluster_if_supported(s, nsteps);
+    if (s.path == CUE_PATH_RESIDENT || (s.path == CUE_PATH_AUTO && small)) rc = run_resident_if_supported(s, nsteps);
     if (rc != 1) return rc;
     if (s.path == CUE_PATH_PERSIST || (s.path == CUE_PATH_AUTO && small)) rc = run_persist_if_supported(s, nsteps);
     if (rc != 1) return rc;
@@ -487,6 +488,18 @@ int cue_set_option(cue_sim *s, int32_t option, int64_t value)
         if (value < 0 || value > 1024) return CUE_ERR_ARG;
         s->persist_phantom = (int)value;
         return CUE_OK;
+    case CUE_OPT_CLUSTER_CTAS: {
+        if (value != 0 && value != kClusterSize && value != kClusterSizeLarge) return CUE_ERR_ARG;
+        const int old = s->cluster_opt;
+        s->cluster_opt = (int)value;
+        s->cluster_pick = -1;
+        if (s->path == CUE_PATH_CLUSTER && !cluster_supported(*s)) {   // keep the selected path runnable
+            s->cluster_opt = old;
+            s->cluster_pick = -1;
+            return CUE_ERR_ARG;
+        }
+        return CUE_OK;
+    }
     case CUE_OPT_TEMPORAL_DEPTH:
         if (value < 0 || value > kMaxTemporalDepth) return CUE_ERR_ARG;
         s->temporal_depth = (int)value;
@@ -539,7 +552,8 @@ int cue_get_option(const cue_sim *s, int32_t option, int64_t *value)
     case CUE_OPT_PERSIST_BLOCKS: *value = s->persist_bpsm; return CUE_OK;
     case CUE_OPT_WAIT_LIMIT: *value = s->persist_limit; return CUE_OK;
     case CUE_OPT_BARRIER_PHANTOM: *value = s->persist_phantom; return CUE_OK;
-    case CUE_INFO_GRID: *value = s->persist_grid; return CUE_OK;
+    case CUE_OPT_CLUSTER_CTAS: *value = s->cluster_opt; return CUE_OK;
+    case CUE_INFO_GRID: *value = s->cluster_used ? s->cluster_last : s->persist_grid; return CUE_OK;
     case CUE_INFO_TILE: *value = s->geom_ready ? (int64_t)s->geom.TX | ((int64_t)s->geom.TY << 16) : 0; return CUE_OK;
     case CUE_INFO_DEPTH: *value = s->geom_ready ? s->geom.K : 0; return CUE_OK;
     default: return CUE_ERR_ARG;

@@ -155,6 +155,9 @@ struct Sim {
     // resident and cluster paths
     bool resident_used = false;
     bool cluster_used = false;
+    int cluster_opt = 0;          // option: CTAs per cluster (0 = library picks, 8 or 16)
+    mutable int cluster_pick = -1;  // cached cluster_ctas() for cluster_opt (-1 = not yet asked)
+    int cluster_last = 0;         // CTAs of the last cluster launch
 
     // adjoint trace (cue_adjoint_trace): copies of the forward states the backward pass reads
     float *adj_trace_field = nullptr;   // [max_states][cells]
@@ -242,10 +245,19 @@ bool resident_supported(const Sim &s);
 int run_resident_if_supported(Sim &s, int nsteps);
 
 // ---- small 2D grids spread over a thread-block cluster (k_cluster.cu) ----
-constexpr int kClusterSize = 8;           // CTAs per cluster (portable size), one band of rows each
-constexpr int kClusterThreads = 256;      // threads per CTA; one cone per thread at most
+constexpr int kClusterSize = 8;           // CTAs per cluster at the portable size, one band of rows each
+constexpr int kClusterSizeLarge = 16;     // the non-portable size, where the device can schedule it
+constexpr int kClusterThreads = 1024;     // threads per CTA: field warps first, then one warp per 32 cones
+constexpr int kClusterMaxConeWarps = 16;  // cones per CTA at most 512 (16 warps stay on the field)
 constexpr int kClusterMaxSources = 1024;
 bool cluster_supported(const Sim &s);
+// CTAs per cluster the cluster path launches for this simulation (its option,
+// else the larger size that fits and the device can schedule); 0 = unsupported.
+int cluster_ctas(const Sim &s);
+// Whether AUTO takes the cluster path: supported, at least 4,096 nodes, at most
+// 128 cones and 16,384 nodes per CTA (the shapes on which it measured faster
+// than the single-block and persistent kernels).
+bool cluster_preferred(const Sim &s);
 // Runs nsteps on the cluster path when selected (or AUTO) and supported:
 // CUE_OK / negative error when it ran, 1 when the caller should fall back.
 int run_cluster_if_supported(Sim &s, int nsteps);

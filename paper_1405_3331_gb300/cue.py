@@ -36,6 +36,7 @@ CUE_OPT_PERSIST_ROWS = 5
 CUE_OPT_PERSIST_BLOCKS = 6
 CUE_OPT_WAIT_LIMIT = 7
 CUE_OPT_BARRIER_PHANTOM = 8
+CUE_OPT_CLUSTER_CTAS = 9
 CUE_INFO_LAST_PATH = 16
 CUE_INFO_TILE = 17
 CUE_INFO_DEPTH = 18

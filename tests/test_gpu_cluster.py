@@ -1,11 +1,13 @@
-"""The thread-block-cluster 2D path (a cluster of 8 CTAs holds the grid in
-distributed shared memory, one band of rows each, for a whole call).
+"""The thread-block-cluster 2D path (a cluster of 8 or 16 CTAs holds the grid
+in distributed shared memory, one band of rows each, for a whole call).
 
 Per node and per cone it computes the plain path's arithmetic in the same
 order, so the two must agree bit for bit (source cells are distinct in these
-workloads), both field buffers included; cones whose patch crosses a band
-edge read the neighbouring CTA's shared memory; calls must continue one
-another; AUTO must take it exactly where it applies.
+workloads), both field buffers included, at either cluster size; band edge
+rows reach the neighbouring CTA's halo through distributed shared memory
+stores, and cones whose patch crosses a band edge read the neighbour's
+shared memory; calls must continue one another; AUTO must take it exactly
+where it applies.
 """
 import math
 
@@ -54,8 +56,14 @@ CASES = ["c1-128", "16x16", "100x37-stop", "map-96x64-clamp", "256x192-2000cones
          "4x2000-tall"]
 
 
-def _run(cue, w, path, calls, snr=None):
+def _run(cue, w, path, calls, snr=None, ctas=0):
     sim = cue.Simulation(w, path=path)
+    if ctas:
+        try:
+            sim.set_option(cue.CUE_OPT_CLUSTER_CTAS, ctas)
+        except cue.CueError:
+            sim.close()
+            pytest.skip(f"no {ctas}-CTA cluster of this size can be scheduled on this device")
     if snr:
         sim.set_steering(snr)
     for k in calls:
@@ -76,33 +84,75 @@ def _assert_same(sa, sb):
             assert x == y, (what, x, y)
 
 
+@pytest.mark.parametrize("ctas", [8, 16])
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("nsteps", [1, 2, 37])
-def test_cluster_equals_plain_bitwise(cue, name, nsteps):
+def test_cluster_equals_plain_bitwise(cue, name, nsteps, ctas):
     w = _case(name)
+    if w.ny < 2 * ctas:
+        pytest.skip("a band per CTA needs two rows")
     a, pa = _run(cue, w, cue.CUE_PATH_PLAIN, [nsteps])
-    b, pb = _run(cue, w, cue.CUE_PATH_CLUSTER, [nsteps])
+    b, pb = _run(cue, w, cue.CUE_PATH_CLUSTER, [nsteps], ctas=ctas)
     assert pa == cue.CUE_PATH_PLAIN and pb == cue.CUE_PATH_CLUSTER
     _assert_same(a, b)
 
 
+@pytest.mark.parametrize("ctas", [8, 16])
 @pytest.mark.parametrize("name", ["c1-128", "100x37-stop"])
-def test_cluster_equals_resident_with_the_snr_rule(cue, name):
+def test_cluster_equals_resident_with_the_snr_rule(cue, name, ctas):
     w = _case(name)
     a, pa = _run(cue, w, cue.CUE_PATH_RESIDENT, [30], snr=SNR)
-    b, pb = _run(cue, w, cue.CUE_PATH_CLUSTER, [30], snr=SNR)
+    b, pb = _run(cue, w, cue.CUE_PATH_CLUSTER, [30], snr=SNR, ctas=ctas)
     assert pa == cue.CUE_PATH_RESIDENT and pb == cue.CUE_PATH_CLUSTER
     _assert_same(a, b)
 
 
-def test_cluster_whole_c1_run_equals_resident(cue):
+@pytest.mark.parametrize("ctas", [8, 16])
+def test_cluster_whole_c1_run_equals_resident(cue, ctas):
     """The 128^2 workload's 500 steps in one call: cluster and resident paths agree bit for
     bit over the whole run (the cones wander across every band edge)."""
     w = W.config_c1()
     a, _ = _run(cue, w, cue.CUE_PATH_RESIDENT, [500])
-    b, pb = _run(cue, w, cue.CUE_PATH_CLUSTER, [500])
+    b, pb = _run(cue, w, cue.CUE_PATH_CLUSTER, [500], ctas=ctas)
     assert pb == cue.CUE_PATH_CLUSTER
     _assert_same(a, b)
+
+
+def test_cluster_size_option(cue):
+    """CUE_OPT_CLUSTER_CTAS takes 0, 8 or 16; CUE_INFO_GRID reports the CTAs of the last
+    cluster launch; a size the grid cannot take (16 CTAs need 32 rows) is refused while the
+    cluster path is selected, and the old size kept."""
+    w = _case("c1-128")
+    sim = cue.Simulation(w, path=cue.CUE_PATH_CLUSTER)
+    assert sim.get_option(cue.CUE_OPT_CLUSTER_CTAS) == 0
+    for bad in (1, 4, 12, 32, -8):
+        with pytest.raises(cue.CueError):
+            sim.set_option(cue.CUE_OPT_CLUSTER_CTAS, bad)
+    sim.set_option(cue.CUE_OPT_CLUSTER_CTAS, 8)
+    sim.sim_run(2)
+    sim.check()
+    assert sim.get_option(cue.CUE_INFO_GRID) == 8
+    sim.close()
+    short = W.make("rows-24", 2, 64, 24, n_src=2, n_axons=8, C0="smooth", seed=184)
+    sim = cue.Simulation(short, path=cue.CUE_PATH_CLUSTER)
+    with pytest.raises(cue.CueError):
+        sim.set_option(cue.CUE_OPT_CLUSTER_CTAS, 16)
+    assert sim.get_option(cue.CUE_OPT_CLUSTER_CTAS) == 0
+    sim.sim_run(1)
+    sim.check()
+    assert sim.get_option(cue.CUE_INFO_GRID) == 8
+    sim.close()
+
+
+def test_cones_beyond_one_warp_per_band(cue):
+    """4,000 cones on 8 CTAs (16 cone warps each, the most a CTA takes) and 8,000 on 16:
+    every cone lane of every CTA busy, bit for bit equal to the plain path."""
+    for ctas, n in ((8, 4000), (16, 8000)):
+        w = W.make(f"cones-{n}", 2, 128, 160, n_src=12, n_axons=n, C0="smooth", seed=185 + ctas, stop_radius=1.0)
+        a, _ = _run(cue, w, cue.CUE_PATH_PLAIN, [9])
+        b, pb = _run(cue, w, cue.CUE_PATH_CLUSTER, [9], ctas=ctas)
+        assert pb == cue.CUE_PATH_CLUSTER
+        _assert_same(a, b)
 
 
 def test_calls_continue_one_another(cue):
@@ -115,8 +165,8 @@ def test_calls_continue_one_another(cue):
 
 
 def test_auto_takes_the_cluster_path_where_it_applies(cue):
-    """Beyond one block's shared memory (or its 256 cones), up to the cluster's."""
-    for w in (_case("256x192-2000cones"),
+    """At least 4,096 nodes, at most 128 cones and 16,384 nodes per CTA."""
+    for w in (_case("c1-128"), _case("map-96x64-clamp"), _case("256x192-2000cones"),
               W.make("map-300x212", 2, 300, 212, n_src=9, n_axons=500, C0="smooth", seed=183, src_map="random",
                      wall_mode=1)):
         sim = cue.Simulation(w)
@@ -124,16 +174,26 @@ def test_auto_takes_the_cluster_path_where_it_applies(cue):
         sim.check()
         assert sim.last_path() == cue.CUE_PATH_CLUSTER, w.name
         sim.close()
-    # fewer than 16 rows (a band per CTA needs two), or too many cones for one per thread
-    for w, want in ((W.make("short", 2, 64, 12, n_src=2, n_axons=8, seed=178), cue.CUE_PATH_RESIDENT),
-                    (W.make("cones", 2, 128, 128, n_src=4, n_axons=2049, seed=179), cue.CUE_PATH_PERSIST)):
+    # below 4,096 nodes or 16 rows: the single block; more cones per CTA: the persistent
+    # kernel, though the cluster path can still be selected where it fits
+    for w, want, selectable in (
+            (W.make("short", 2, 64, 12, n_src=2, n_axons=8, seed=178), cue.CUE_PATH_RESIDENT, False),
+            (W.make("64x48", 2, 64, 48, n_src=2, n_axons=8, seed=186), cue.CUE_PATH_RESIDENT, True),
+            (W.make("64x1000", 2, 64, 1000, n_src=20, n_axons=3000, seed=187), cue.CUE_PATH_PERSIST, True),
+            (W.make("cones", 2, 128, 128, n_src=4, n_axons=8193, seed=179), cue.CUE_PATH_PERSIST, False)):
         sim = cue.Simulation(w)
         sim.sim_run(2)
         sim.check()
         assert sim.last_path() == want, w.name
-        with pytest.raises(cue.CueError) as e:
+        if selectable:
             sim.set_option(cue.CUE_OPT_PATH, cue.CUE_PATH_CLUSTER)
-        assert e.value.code == cue.CUE_ERR_ARG
+            sim.sim_run(1)
+            sim.check()
+            assert sim.last_path() == cue.CUE_PATH_CLUSTER, w.name
+        else:
+            with pytest.raises(cue.CueError) as e:
+                sim.set_option(cue.CUE_OPT_PATH, cue.CUE_PATH_CLUSTER)
+            assert e.value.code == cue.CUE_ERR_ARG
         sim.close()
 
 

@@ -86,9 +86,9 @@ def test_tile_and_grid_shape_do_not_change_results(cue, rows, blocks):
 
 
 def test_auto_takes_the_persistent_path_for_small_grids_beyond_one_block(cue):
-    """Grids too small for the fused kernel whose bands do not fit one cluster's shared memory
-    (or with more cones than its threads take); smaller ones run on the cluster or resident
-    paths."""
+    """Grids too small for the fused kernel whose bands do not fit one cluster's shared memory,
+    or with more than 128 cones per cluster CTA (where the cluster path measured slower);
+    smaller ones run on the cluster or resident paths."""
     for name in ("c5-1024", "2d-1000x64"):
         sim = cue.Simulation(_case(name))
         sim.sim_run(3)

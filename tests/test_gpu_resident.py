@@ -106,11 +106,14 @@ def test_calls_continue_one_another(cue):
 
 
 def test_auto_takes_the_resident_path_where_it_applies(cue):
-    for name in ("c1-128", "map-96x64-clamp", "160x160-256cones"):
-        sim = cue.Simulation(_case(name))
+    """Grids below the cluster path's 4,096 nodes, or with fewer rows than its bands need."""
+    for w in (W.make("short", 2, 128, 12, n_src=3, n_axons=40, C0="smooth", seed=83),
+              W.make("64x48", 2, 64, 48, n_src=3, n_axons=40, C0="smooth", seed=84, src_map="random"),
+              W.make("32x32", 2, 32, 32, n_src=2, n_axons=16, C0="smooth", seed=85)):
+        sim = cue.Simulation(w)
         sim.sim_run(3)
         sim.check()
-        assert sim.last_path() == cue.CUE_PATH_RESIDENT, name
+        assert sim.last_path() == cue.CUE_PATH_RESIDENT, w.name
         sim.close()
     # too many cones for the cone warps, or both buffers beyond one block's shared memory: the
     # resident path is refused (AUTO takes the cluster path there)
