@@ -23,7 +23,7 @@ namespace cue {
 //               tile's bin holds any number of its cones, so the spill list
 //               stays empty) while the bins fit in kFusedBinBudget, else
 //               kFusedBinCap.
-constexpr int kFusedBinCap = 512;   // cone ids a CTA keeps in registers (2 slots x 256 threads)
+constexpr int kFusedBinCap = 512;   // ids per tile bin when the bins cannot hold every cone (large grids)
 constexpr size_t kFusedBinBudget = size_t(256) << 20;   // bytes of bins (both rounds) that buy bin_cap = n_axons
 
 struct WorkspaceLayout {
@@ -278,6 +278,8 @@ void timing_end(Sim &s);
 
 // ---- temporally blocked batch mode (k_blocked.cu) ----
 constexpr int kBlockedMaxSrc = 256;   // point sources per instance on this mode
+constexpr int kBlockedTileW = 256;    // loaded columns and rows of a blocked-mode tile
+constexpr int kBlockedTileRows = 96;
 // One instance of a batch in the blocked mode (device table; the tensor maps
 // give the struct their 128-byte alignment, which the workspace's 256-byte
 // offsets keep).

@@ -42,6 +42,8 @@
 #include "cue_tile.cuh"
 
 namespace cue {
+static_assert(kBlockedTileW == tile::kW && kBlockedTileRows == tile::kRows, "blocked tile shape");
+
 namespace {
 
 using namespace tile;

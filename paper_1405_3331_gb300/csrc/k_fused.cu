@@ -4,14 +4,24 @@
 //
 // Each CTA owns an interior tile of TX x TY nodes.  It loads the tile plus a
 // halo (HX columns, HY rows on each side) into shared memory with one TMA
-// tensor copy, then runs K sub-steps entirely in shared memory:
-//   phase A  the cones binned to this tile take step n+j, reading C^{n+j}
-//            from shared memory (multilinear gradient, Philox noise, blend,
-//            advance, stop tests), state read from / written to global;
-//   phase B  the field advances in place to C^{n+j+1}: each warp sweeps a
-//            band of full-width rows, keeping the rows above/at/below in
-//            registers (x neighbours by warp shuffle) and adding the point
-//            sources of each row as it goes.
+// tensor copy, then runs K sub-steps entirely in shared memory.  Its warps have
+// two roles that meet on two named barriers per sub-step:
+//   cone warps (2)   hold up to 192 of the tile's cones in registers; before
+//                    the first barrier each samples C^{n+j} at its cones (the
+//                    multilinear gradient from 12 patch nodes), after it the
+//                    rest of step n+j (Philox noise, blend, advance, stop tests),
+//                    which reads no field, runs while the field warps sweep;
+//   field warps (8)  before the first barrier step any further cones of the
+//                    bin (state in global memory) on C^{n+j}; after it each
+//                    sweeps a band of full-width rows in place to C^{n+j+1},
+//                    keeping the rows above/at/below in registers (x neighbours
+//                    by warp shuffle) and adding the point sources of each row.
+// The cone work thus overlaps the sweep instead of holding every warp at a
+// CTA barrier (measured on the 2048^2 workload: 35.9 -> 30.8 us per 8-step
+// launch; one cone warp, or three or four, were slower: one is starved of issue
+// slots by the sweeping warps, more lower the register budget of the sweep;
+// letting the cone warps also step the bin's further cones cost 2.5 us per
+// launch on the uniform workload and saved 2% on the clustered one).
 // After K sub-steps the interior is stored.  The valid region shrinks by one
 // node per sub-step; cones move at most step_len per step and read a 4-node
 // footprint, so the halo is H = K + 1 + ceil((K-1) step_len / h) (the x halo
@@ -19,8 +29,8 @@
 // cones for the next one as they finish: per-tile bins filled through atomic
 // counters.  A bin holds every cone of its tile whenever the bins fit the
 // workspace budget (then no cone ever spills, however the cones cluster); the
-// first 512 ids of a bin ride in registers for the whole launch, the rest are
-// stepped from global memory.  Only on grids too large for such bins does a
+// first 192 ids of a bin ride in the cone warps' registers for the whole launch,
+// the rest are stepped by the field warps from global memory.  Only on grids too large for such bins does a
 // bin hold 512 ids, cones of a full bin going to a spill list that every tile
 // scans.  Each tile clears its own count once read, the last tile past its
 // prologue clears the spill count.  No separate binning launch between fused
@@ -81,7 +91,17 @@ struct FusedArgs {
     unsigned long long *counter;
 };
 
-constexpr int kConeSlots = 2;          // cones held in registers per thread
+constexpr int kConeWarps = 2;          // warps that step the cones, after the 8 field warps
+constexpr int kConeSlots = 3;          // cones held in registers per lane of a cone warp
+constexpr int kRegCones = kConeSlots * 32 * kConeWarps;   // the first kRegCones ids of a bin ride in registers
+constexpr int kFusedThreads = kThreads + 32 * kConeWarps;
+
+// Named barriers between the field warps and the cone warps (every warp arrives
+// converged, from its own role's loop).
+__device__ __forceinline__ void role_sync(int id)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kFusedThreads) : "memory");
+}
 
 __device__ __forceinline__ int tile_of(const FieldDesc &f, const FusedGeom &g, float px, float py)
 {
@@ -90,8 +110,8 @@ __device__ __forceinline__ int tile_of(const FieldDesc &f, const FusedGeom &g, f
     return (iy / g.TY) * g.ntx + ix / g.TX;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                              const FusedArgs A)
+__global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                   const FusedArgs A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const FusedGeom &g = A.g;
@@ -106,13 +126,12 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     int *t_row = t_col + kMaxTileSrc;
     float *t_e = reinterpret_cast<float *>(t_row + kMaxTileSrc);
     float *t_xy = t_e + kMaxTileSrc;                            // [2][kMaxTileSrc] tile sources
-    int *cid = reinterpret_cast<int *>(t_xy + 2 * kMaxTileSrc);   // [kThreads] slot-0 cone ids
-    float *nzb = reinterpret_cast<float *>(cid + kThreads);       // [2 parity][2][kThreads] noise
 
     const int t = blockIdx.x;
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int ox = tx * g.TX - g.HX, oy = ty * g.TY - g.HY;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool cone_warp = warp >= kWarps;        // warps 0-7 sweep the field, warps 8-9 step the cones
     const int n = A.n_axons;
 
     if (tid == 0) mbar_init(bar, 1);
@@ -128,13 +147,16 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     if (tid == 0) s_nspill = A.cones_on ? *A.spill_cnt_cur : 0;
     const int n_bin = A.cones_on ? min(A.cnt_cur[t], A.bin_cap) : 0;
     const int *bin = A.bins_cur + (size_t)t * A.bin_cap;
+    // the cone warps' slots: bin entry (32 q + lane) kConeWarps + w in slot q of lane
+    // `lane` of cone warp w, so a tile's cones are shared out evenly (the rest of the
+    // bin, if any, is stepped by the field warps from global memory)
     int ca[kConeSlots];
     bool cl[kConeSlots];
     float cp[kConeSlots][2], cdir[kConeSlots][2];
 #pragma unroll
     for (int q = 0; q < kConeSlots; ++q) {
-        int i = tid + q * kThreads;
-        ca[q] = i < n_bin ? bin[i] : -1;
+        const int i = (32 * q + lane) * kConeWarps + (warp - kWarps);
+        ca[q] = cone_warp && i < n_bin ? bin[i] : -1;
         cl[q] = ca[q] >= 0;
         if (cl[q]) {
             cl[q] = A.active[ca[q]] != 0;
@@ -144,23 +166,10 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
             cdir[q][1] = A.dir[n + ca[q]];
         }
     }
-    // Noise of the slot-0 cones is drawn one sub-step ahead by the threads that
-    // hold no cone (it does not depend on the cone state), unless the tile is so
-    // full that few threads are free; the first sub-step's noise is drawn here,
-    // while the tile copy is in flight.
-    const int cnt0 = min(n_bin, kThreads);
-    const bool pre_noise = cnt0 > 0 && cnt0 <= kThreads - 64;
-    cid[tid] = ca[0];
-    if (pre_noise && ca[0] >= 0) {
-        float xi[2];
-        cone_noise<2>(A.c.key0, A.c.key1, (uint32_t)ca[0], A.step0, xi);
-        nzb[tid] = xi[0];
-        nzb[kThreads + tid] = xi[1];
-    }
 
     // point sources inside the loaded region, grouped by tile row
     const bool stop_on = A.cones_on && A.c.stop_r2 >= 0.0f && A.n_src > 0;
-    for (int s = tid; s < A.n_src; s += kThreads) {
+    for (int s = tid; s < A.n_src && tid < kThreads; s += kThreads) {
         int cell = A.src_cell[s];
         if (cell >= 0 && cell < f.nx * f.ny) {
             int gx = cell % f.nx, gy = cell / f.nx;
@@ -199,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     __syncthreads();
     for (int r = tid; r < kRows; r += kThreads) row_fill[r] = 0;
     __syncthreads();
-    for (int s = tid; s < A.n_src; s += kThreads) {
+    for (int s = tid; s < A.n_src && tid < kThreads; s += kThreads) {
         int cell = A.src_cell[s];
         if (cell >= 0 && cell < f.nx * f.ny) {
             int gx = cell % f.nx, gy = cell / f.nx;
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     }
     mbar_wait_bounded(bar, 0);              // completed phase: returns at once, acquires the tile
 
-    const int r0 = warp * kBand;
+    const int r0 = cone_warp ? 0 : warp * kBand;
     const int colA = 4 * lane, colB = 128 + 4 * lane;
     const int gxA = ox + colA, gxB = ox + colB;
     const float2 alpha2 = make_float2(f.alpha, f.alpha), beta2 = make_float2(f.beta, f.beta);
@@ -261,70 +270,95 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
     };
 
     auto ld_fast = [&](int i, int j, int) { return S[(j - oy) * kW + (i - ox)]; };
-    // one cone step on the shared-memory field (the plain kernel's arithmetic)
-    auto step_cone = [&](uint32_t a, uint32_t stp, float *p, float *d, const float *xi_in) {
+    // the field-dependent part of a cone step: the multilinear gradient at p from
+    // the 12 patch nodes in shared memory (the plain kernel's arithmetic)
+    auto grad_at = [&](const float *p, float *gr) {
         int lo[2];
-        float fr[2], v[kPatch2], gr[2], xi[2];
+        float fr[2], v[kPatch2];
         cell_of<2>(f, p, lo, fr);
         const bool inside = max(lo[0] - 1, 0) - ox >= 0 && min(lo[0] + 2, f.nx - 1) - ox < kW &&
                             max(lo[1] - 1, 0) - oy >= 0 && min(lo[1] + 2, f.ny - 1) - oy < kRows;
         if (inside) gather2(f, lo, ld_fast, v);
         else gather2(f, lo, ld, v);
         grad2(A.c, v, fr, gr);
-        if (xi_in) {
-            xi[0] = xi_in[0];
-            xi[1] = xi_in[1];
-        } else {
-            cone_noise<2>(A.c.key0, A.c.key1, a, stp, xi);
-        }
+    };
+    // one whole cone step on the shared-memory field
+    auto step_cone = [&](uint32_t a, uint32_t stp, float *p, float *d) {
+        float gr[2], xi[2];
+        grad_at(p, gr);
+        cone_noise<2>(A.c.key0, A.c.key1, a, stp, xi);
         return cone_finish_xi<2>(A.c, gr, xi, p, d, stop_xy, stop_stride, n_stop);
     };
-
-    bool stopped[kConeSlots];
-#pragma unroll
-    for (int q = 0; q < kConeSlots; ++q) stopped[q] = false;
-
-    for (int j = 0; j < A.K; ++j) {
-        const uint32_t step = A.step0 + j;
-        // ---- phase A: cones of this tile read C^{n+j}
-        if (pre_noise && tid >= cnt0 && j + 1 < A.K) {     // free threads: next sub-step's noise
-            float *nz_next = nzb + ((j + 1) & 1) * 2 * kThreads;
-            for (int i = tid - cnt0; i < cnt0; i += kThreads - cnt0) {
-                float xi[2];
-                cone_noise<2>(A.c.key0, A.c.key1, (uint32_t)cid[i], step + 1, xi);
-                nz_next[i] = xi[0];
-                nz_next[kThreads + i] = xi[1];
-            }
+    auto rebin = [&](int a, float px, float py) {
+        const int tile = tile_of(f, g, px, py);
+        const int slot = atomicAdd(&A.cnt_next[tile], 1);
+        if (slot < A.bin_cap) {
+            A.bins_next[(size_t)tile * A.bin_cap + slot] = a;
+        } else {
+            const int k = atomicAdd(A.spill_cnt_next, 1);
+            A.spill_next[k] = make_int2(a, tile);
         }
+    };
+
+    if (cone_warp) {
+        // ---- the cone warps.  Sub-step j: the slot cones sample C^{n+j} (their
+        // gradients), the first barrier lets the field warps overwrite it, and the
+        // rest of step n+j (noise, steering, advance, stop tests), which reads no
+        // field, runs while the field warps sweep; the second barrier ends the sub-step.
+        bool stopped[kConeSlots];
+#pragma unroll
+        for (int q = 0; q < kConeSlots; ++q) stopped[q] = false;
+        for (int j = 0; j < A.K; ++j) {
+            const uint32_t step = A.step0 + j;
+            float cg[kConeSlots][2];
+#pragma unroll
+            for (int q = 0; q < kConeSlots; ++q) {
+                cg[q][0] = cg[q][1] = 0.f;
+                if (cl[q]) grad_at(cp[q], cg[q]);
+            }
+            role_sync(1);
+#pragma unroll
+            for (int q = 0; q < kConeSlots; ++q) {
+                count_active(A.counter, cl[q]);
+                if (cl[q]) {
+                    float xi[2];
+                    cone_noise<2>(A.c.key0, A.c.key1, (uint32_t)ca[q], step, xi);
+                    if (!cone_finish_xi<2>(A.c, cg[q], xi, cp[q], cdir[q], stop_xy, stop_stride, n_stop)) {
+                        cl[q] = false;
+                        stopped[q] = true;
+                    }
+                }
+            }
+            role_sync(2);
+        }
+        // the slot cones back to global memory, binned for the next launch
 #pragma unroll
         for (int q = 0; q < kConeSlots; ++q) {
-            count_active(A.counter, cl[q]);
-            if (cl[q]) {
-                float xi_pre[2];
-                const float *xi_in = nullptr;
-                if (q == 0 && pre_noise) {
-                    const float *nz = nzb + (j & 1) * 2 * kThreads;
-                    xi_pre[0] = nz[tid];
-                    xi_pre[1] = nz[kThreads + tid];
-                    xi_in = xi_pre;
-                }
-                bool alive = step_cone((uint32_t)ca[q], step, cp[q], cdir[q], xi_in);
-                if (!alive) {
-                    cl[q] = false;
-                    stopped[q] = true;
-                }
-            }
+            const int a = ca[q];
+            if (a < 0) continue;
+            A.pos[a] = cp[q][0];
+            A.pos[n + a] = cp[q][1];
+            A.dir[a] = cdir[q][0];
+            A.dir[n + a] = cdir[q][1];
+            if (stopped[q]) A.active[a] = 0;
+            if (A.cnt_next && cl[q]) rebin(a, cp[q][0], cp[q][1]);
         }
-        // cones of the bin beyond the register slots, then the spilled cones of this
-        // tile: state read from and written back to global memory every sub-step
-        // (warp-uniform trip counts: count_active is a warp-collective ballot)
+        return;
+    }
+
+    // ---- the field warps
+    for (int j = 0; j < A.K; ++j) {
+        const uint32_t step = A.step0 + j;
+        // cones of the bin beyond the cone warps' slots, then the spilled cones of this
+        // tile: whole steps on C^{n+j}, state read from and written back to global memory
+        // (warp-uniform trip counts: count_active is a warp-collective ballot);
         // software-pipelined: the next round's cone state (and the ids two rounds ahead)
         // are loaded while this round's cone steps, so a crowded tile is bound by its
         // arithmetic rather than by chains of dependent loads
-        if (n_bin > kFusedBinCap) {
+        if (n_bin > kRegCones) {
             auto id_at = [&](int i) { return i < n_bin ? bin[i] : -1; };
-            int a_nn = id_at(kFusedBinCap + kThreads + tid);
-            int a_n = id_at(kFusedBinCap + tid);
+            int a_nn = id_at(kRegCones + kThreads + tid);
+            int a_n = id_at(kRegCones + tid);
             bool live_n = a_n >= 0 && A.active[a_n] != 0;
             float p_n[2] = {0.f, 0.f}, d_n[2] = {0.f, 0.f};
             if (live_n) {
@@ -333,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
                 d_n[0] = A.dir[a_n];
                 d_n[1] = A.dir[n + a_n];
             }
-            for (int base = kFusedBinCap; base < n_bin; base += kThreads) {
+            for (int base = kRegCones; base < n_bin; base += kThreads) {
                 const int a = a_n;
                 const bool live = live_n;
                 float p[2] = {p_n[0], p_n[1]}, d[2] = {d_n[0], d_n[1]};
@@ -348,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
                 }
                 count_active(A.counter, live);             // warp-uniform trip count
                 if (live) {
-                    bool alive = step_cone((uint32_t)a, step, p, d, nullptr);
+                    bool alive = step_cone((uint32_t)a, step, p, d);
                     A.pos[a] = p[0];
                     A.pos[n + a] = p[1];
                     A.dir[a] = d[0];
@@ -366,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
             if (live) {
                 float p[2] = {A.pos[a], A.pos[n + a]};
                 float d[2] = {A.dir[a], A.dir[n + a]};
-                bool alive = step_cone((uint32_t)a, step, p, d, nullptr);
+                bool alive = step_cone((uint32_t)a, step, p, d);
                 A.pos[a] = p[0];
                 A.pos[n + a] = p[1];
                 A.dir[a] = d[0];
@@ -377,37 +411,16 @@ __global__ void __launch_bounds__(kThreads, 2) fused2d_kernel(const __grid_const
         // rows just outside this warp's band, read before anyone overwrites them
         const Row above = ld_row(S4, r0 > 0 ? r0 - 1 : r0, lane);
         const Row below = ld_row(S4, r0 + kBand < kRows ? r0 + kBand : r0 + kBand - 1, lane);
-        __syncthreads();
-        // ---- phase B: in-place sweep of the band to C^{n+j+1}
+        role_sync(1);
+        // ---- in-place sweep of the band to C^{n+j+1}
         if (wall) sweep_band<true, false, false>(S4, lane, r0, above, below, lw, alpha2, beta2, bsrc, oy, f.ny, no_map);
         else sweep_band<false, false, false>(S4, lane, r0, above, below, lw, alpha2, beta2, bsrc, oy, f.ny, no_map);
-        __syncthreads();
+        role_sync(2);
     }
 
-    // ---- cones back to global memory, binned for the next launch
-    auto rebin = [&](int a, float px, float py) {
-        const int tile = tile_of(f, g, px, py);
-        const int slot = atomicAdd(&A.cnt_next[tile], 1);
-        if (slot < A.bin_cap) {
-            A.bins_next[(size_t)tile * A.bin_cap + slot] = a;
-        } else {
-            const int k = atomicAdd(A.spill_cnt_next, 1);
-            A.spill_next[k] = make_int2(a, tile);
-        }
-    };
-#pragma unroll
-    for (int q = 0; q < kConeSlots; ++q) {
-        const int a = ca[q];
-        if (a < 0) continue;
-        A.pos[a] = cp[q][0];
-        A.pos[n + a] = cp[q][1];
-        A.dir[a] = cdir[q][0];
-        A.dir[n + a] = cdir[q][1];
-        if (stopped[q]) A.active[a] = 0;
-        if (A.cnt_next && cl[q]) rebin(a, cp[q][0], cp[q][1]);
-    }
+    // ---- the other cones back to their bins for the next launch
     if (A.cnt_next) {
-        for (int i = kFusedBinCap + tid; i < n_bin; i += kThreads) {
+        for (int i = kRegCones + tid; i < n_bin; i += kThreads) {
             const int a = bin[i];
             if (A.active[a]) rebin(a, A.pos[a], A.pos[n + a]);
         }
@@ -489,7 +502,7 @@ int device_sm_count()
 size_t fused_smem_bytes(int R)
 {
     return 128 + (size_t)R * kW * sizeof(float) + sizeof(int) * (2 * R + 1) + sizeof(int) * 2 * kMaxTileSrc +
-           sizeof(float) * 3 * kMaxTileSrc + sizeof(int) * kThreads + sizeof(float) * 4 * kThreads;
+           sizeof(float) * 3 * kMaxTileSrc;
 }
 
 // Tile geometry for temporal depth K; returns false if the fused path cannot run.
@@ -666,7 +679,7 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     A.counter = s.cone_counter();
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(s.tmap[s.cur]);
     timing_begin(s);
-    fused2d_kernel<<<n_tiles, kThreads, fused_smem_bytes(g.R), s.stream>>>(*map, A);
+    fused2d_kernel<<<n_tiles, kFusedThreads, fused_smem_bytes(g.R), s.stream>>>(*map, A);
     timing_end(s);
     s.launches++;
     if (with_cones) s.bin_round++;
