@@ -134,38 +134,16 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_
     const bool cone_warp = warp >= kWarps;        // warps 0-7 sweep the field, warps 8-9 step the cones
     const int n = A.n_axons;
 
+    // Programmatic dependent launch: the next launch's CTAs may be scheduled as this
+    // launch's CTAs finish.  Up to griddepcontrol.wait a CTA reads only inputs that no
+    // kernel writes (the point sources), so that part of its prologue overlaps the
+    // previous launch's last tiles; the wait (a no-op in a launch without the
+    // attribute) returns once the previous launch has completed and its writes are
+    // visible.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid == 0) mbar_init(bar, 1);
     for (int r = tid; r < kRows; r += kThreads) row_fill[r] = 0;
     __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(bar, (unsigned)(kRows * kW * sizeof(float)));
-        tma_load_2d(S, &tmap, bar, ox, oy);
-    }
-
-    // this tile's cones into registers (overlaps the TMA load)
-    __shared__ int s_nspill;
-    if (tid == 0) s_nspill = A.cones_on ? *A.spill_cnt_cur : 0;
-    const int n_bin = A.cones_on ? min(A.cnt_cur[t], A.bin_cap) : 0;
-    const int *bin = A.bins_cur + (size_t)t * A.bin_cap;
-    // the cone warps' slots: bin entry (32 q + lane) kConeWarps + w in slot q of lane
-    // `lane` of cone warp w, so a tile's cones are shared out evenly (the rest of the
-    // bin, if any, is stepped by the field warps from global memory)
-    int ca[kConeSlots];
-    bool cl[kConeSlots];
-    float cp[kConeSlots][2], cdir[kConeSlots][2];
-#pragma unroll
-    for (int q = 0; q < kConeSlots; ++q) {
-        const int i = (32 * q + lane) * kConeWarps + (warp - kWarps);
-        ca[q] = cone_warp && i < n_bin ? bin[i] : -1;
-        cl[q] = ca[q] >= 0;
-        if (cl[q]) {
-            cl[q] = A.active[ca[q]] != 0;
-            cp[q][0] = A.pos[ca[q]];
-            cp[q][1] = A.pos[n + ca[q]];
-            cdir[q][0] = A.dir[ca[q]];
-            cdir[q][1] = A.dir[n + ca[q]];
-        }
-    }
 
     // point sources inside the loaded region, grouped by tile row
     const bool stop_on = A.cones_on && A.c.stop_r2 >= 0.0f && A.n_src > 0;
@@ -179,16 +157,6 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_
         }
     }
     __syncthreads();
-    const int n_spill = s_nspill;
-    if (A.cones_on && tid == 0) {
-        // every thread has read this tile's count: clear it for the launch after next;
-        // the last tile past this point clears the spill count (every tile holds it)
-        A.cnt_cur[t] = 0;
-        if (atomicAdd(A.done, 1) == (int)gridDim.x - 1) {
-            *A.spill_cnt_cur = 0;
-            *A.done = 0;
-        }
-    }
     if (warp == 0) {       // exclusive scan of the per-row counts
         int carry = 0;
         for (int base = 0; base < kRows; base += 32) {
@@ -221,6 +189,49 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_
                 t_xy[slot] = (float)gx * f.h;
                 t_xy[kMaxTileSrc + slot] = (float)gy * f.h;
             }
+        }
+    }
+
+    // from here on: what earlier launches wrote (the field, the cone bins and state)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (tid == 0) {
+        mbar_expect_tx(bar, (unsigned)(kRows * kW * sizeof(float)));
+        tma_load_2d(S, &tmap, bar, ox, oy);
+    }
+
+    // this tile's cones into registers (overlaps the TMA load)
+    __shared__ int s_nspill;
+    if (tid == 0) s_nspill = A.cones_on ? *A.spill_cnt_cur : 0;
+    const int n_bin = A.cones_on ? min(A.cnt_cur[t], A.bin_cap) : 0;
+    const int *bin = A.bins_cur + (size_t)t * A.bin_cap;
+    // the cone warps' slots: bin entry (32 q + lane) kConeWarps + w in slot q of lane
+    // `lane` of cone warp w, so a tile's cones are shared out evenly (the rest of the
+    // bin, if any, is stepped by the field warps from global memory)
+    int ca[kConeSlots];
+    bool cl[kConeSlots];
+    float cp[kConeSlots][2], cdir[kConeSlots][2];
+#pragma unroll
+    for (int q = 0; q < kConeSlots; ++q) {
+        const int i = (32 * q + lane) * kConeWarps + (warp - kWarps);
+        ca[q] = cone_warp && i < n_bin ? bin[i] : -1;
+        cl[q] = ca[q] >= 0;
+        if (cl[q]) {
+            cl[q] = A.active[ca[q]] != 0;
+            cp[q][0] = A.pos[ca[q]];
+            cp[q][1] = A.pos[n + ca[q]];
+            cdir[q][0] = A.dir[ca[q]];
+            cdir[q][1] = A.dir[n + ca[q]];
+        }
+    }
+    __syncthreads();
+    const int n_spill = s_nspill;
+    if (A.cones_on && tid == 0) {
+        // every thread has read this tile's count: clear it for the launch after next;
+        // the last tile past this point clears the spill count (every tile holds it)
+        A.cnt_cur[t] = 0;
+        if (atomicAdd(A.done, 1) == (int)gridDim.x - 1) {
+            *A.spill_cnt_cur = 0;
+            *A.done = 0;
         }
     }
 
@@ -678,11 +689,24 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     A.status = s.status();
     A.counter = s.cone_counter();
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(s.tmap[s.cur]);
+    // a programmatic dependent launch: its CTAs may start their source prologue while
+    // the previous kernel in the stream finishes (the kernel waits before reading it)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_tiles);
+    cfg.blockDim = dim3(kFusedThreads);
+    cfg.dynamicSmemBytes = fused_smem_bytes(g.R);
+    cfg.stream = s.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     timing_begin(s);
-    fused2d_kernel<<<n_tiles, kFusedThreads, fused_smem_bytes(g.R), s.stream>>>(*map, A);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, fused2d_kernel, *map, A);
     timing_end(s);
     s.launches++;
     if (with_cones) s.bin_round++;
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
