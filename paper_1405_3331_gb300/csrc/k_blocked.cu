@@ -102,17 +102,73 @@ __global__ void __launch_bounds__(kThreads, 2) blocked_kernel(const BlockedArgs 
     const FusedGeom &g = I.g;
     const int t = item.y;
     const int gt = I.tile_base + t;
-    const int cur = A.ctrl->cur;
-    const uint32_t step0 = A.ctrl->step0;
-    const int round = (int)A.ctrl->pad[0] & 1;
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int ox = tx * g.TX - g.HX, oy = ty * g.TY - g.HY;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = I.n_axons;
 
+    // a programmatic dependent launch: the next launch's CTAs may be scheduled as this
+    // launch's CTAs finish.  Up to griddepcontrol.wait a CTA reads only what no kernel
+    // writes (the instance table, the point sources), so that part of its prologue
+    // overlaps the previous launch's last tiles; the wait (a no-op without the launch
+    // attribute) returns once the previous launch has completed and its writes (step
+    // control, fields, cone bins and state) are visible.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid == 0) mbar_init(bar, 1);
     for (int r = tid; r < kRows; r += kThreads) row_fill[r] = 0;
     __syncthreads();
+    // point sources inside the loaded region, grouped by tile row
+    const bool stop_on = c.stop_r2 >= 0.0f && I.n_src > 0;
+    for (int s = tid; s < I.n_src; s += kThreads) {
+        int cell = I.src_cell[s];
+        if (cell >= 0 && cell < f.nx * f.ny) {
+            int gx = cell % f.nx, gy = cell / f.nx;
+            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) atomicAdd(&row_fill[gy - oy], 1);
+        } else if (t == 0) {
+            flag_status(A.status, kStatusBounds);      // skipped, reported by the instance's first tile
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {       // exclusive scan of the per-row counts
+        int carry = 0;
+        for (int base = 0; base < kRows; base += 32) {
+            int r = base + lane;
+            int v = r < kRows ? row_fill[r] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += y;
+            }
+            if (r < kRows) row_start[r] = carry + x - v;
+            carry += __shfl_sync(kFull, x, 31);
+        }
+        if (lane == 0) row_start[kRows] = carry;
+    }
+    __syncthreads();
+    for (int r = tid; r < kRows; r += kThreads) row_fill[r] = 0;
+    __syncthreads();
+    for (int s = tid; s < I.n_src; s += kThreads) {
+        int cell = I.src_cell[s];
+        if (cell >= 0 && cell < f.nx * f.ny) {
+            int gx = cell % f.nx, gy = cell / f.nx;
+            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) {
+                int r = gy - oy;
+                int slot = row_start[r] + atomicAdd(&row_fill[r], 1);
+                t_col[slot] = gx - ox;
+                t_row[slot] = r;
+                t_e[slot] = I.src_emit[s];
+                t_xy[slot] = (float)gx * f.h;
+                t_xy[kBlockedMaxSrc + slot] = (float)gy * f.h;
+            }
+        }
+    }
+
+    // from here on: what earlier launches wrote
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int cur = A.ctrl->cur;
+    const uint32_t step0 = A.ctrl->step0;
+    const int round = (int)A.ctrl->pad[0] & 1;
     if (tid == 0) {
         // the tensor map lives in global memory (written before the launch): make it
         // visible to the tensor-map proxy before the copy uses it
@@ -155,54 +211,8 @@ __global__ void __launch_bounds__(kThreads, 2) blocked_kernel(const BlockedArgs 
         nzb[kThreads + tid] = xi[1];
     }
 
-    // point sources inside the loaded region, grouped by tile row
-    const bool stop_on = c.stop_r2 >= 0.0f && I.n_src > 0;
-    for (int s = tid; s < I.n_src; s += kThreads) {
-        int cell = I.src_cell[s];
-        if (cell >= 0 && cell < f.nx * f.ny) {
-            int gx = cell % f.nx, gy = cell / f.nx;
-            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) atomicAdd(&row_fill[gy - oy], 1);
-        } else if (t == 0) {
-            flag_status(A.status, kStatusBounds);      // skipped, reported by the instance's first tile
-        }
-    }
     __syncthreads();
     if (tid == 0 && n > 0) cnt_cur[gt] = 0;           // read by every thread: cleared for the launch after next
-    if (warp == 0) {       // exclusive scan of the per-row counts
-        int carry = 0;
-        for (int base = 0; base < kRows; base += 32) {
-            int r = base + lane;
-            int v = r < kRows ? row_fill[r] : 0;
-            int x = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += y;
-            }
-            if (r < kRows) row_start[r] = carry + x - v;
-            carry += __shfl_sync(kFull, x, 31);
-        }
-        if (lane == 0) row_start[kRows] = carry;
-    }
-    __syncthreads();
-    for (int r = tid; r < kRows; r += kThreads) row_fill[r] = 0;
-    __syncthreads();
-    for (int s = tid; s < I.n_src; s += kThreads) {
-        int cell = I.src_cell[s];
-        if (cell >= 0 && cell < f.nx * f.ny) {
-            int gx = cell % f.nx, gy = cell / f.nx;
-            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) {
-                int r = gy - oy;
-                int slot = row_start[r] + atomicAdd(&row_fill[r], 1);
-                t_col[slot] = gx - ox;
-                t_row[slot] = r;
-                t_e[slot] = I.src_emit[s];
-                t_xy[slot] = (float)gx * f.h;
-                t_xy[kBlockedMaxSrc + slot] = (float)gy * f.h;
-            }
-        }
-    }
-
     // the last CTA to finish advances the step control (every CTA read it at its start)
     auto finish = [&]() {
         __syncthreads();
@@ -494,7 +504,20 @@ cudaError_t blocked_launch(const BInst *d_insts, const int2 *d_items, int n_item
     A.total_tiles = total_tiles;
     A.done = done;
     A.status = status;
-    blocked_kernel<<<n_items, kThreads, blocked_smem_bytes(), stream>>>(A);
+    // a programmatic dependent launch (see the kernel's prologue); inside a stream
+    // capture it becomes a programmatic edge of the graph
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_items);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = blocked_smem_bytes();
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, blocked_kernel, A);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -175,12 +175,18 @@ __global__ void __launch_bounds__(CONES ? kLaunch3 : kThreads3, 4)
     const int plo = max(zs - 1, 0), phi = min(ze, f.nz - 1);   // planes this CTA reads
     const unsigned bytes = kStageFloats * sizeof(float);
 
+    // a programmatic dependent launch: the next step's CTAs may be scheduled as this
+    // launch's CTAs finish; this one's set-up overlaps the previous launch's tail, and
+    // griddepcontrol.wait (a no-op without the launch attribute) returns once the
+    // previous launch has completed and its writes (the field, the cones) are visible
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     auto issue = [&](int p) {      // plane p into stage (p - plo) % kStages
         const int s = (p - plo) % kStages;
         mbar_expect_tx(&bar[s], bytes);
@@ -382,13 +388,24 @@ cudaError_t launch_field3d_tma(Sim &s, int in_buffer, float *Cout, bool *cones_d
     const int smem = 128 + kStages * kStageStride * (int)sizeof(float);
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(s.tmap3[in_buffer]);
     const bool cones = A.cone_per > 0;
-    if (s.src_map) {
-        if (cones) field3d_tma_kernel<true, true><<<grid, kLaunch3, smem, s.stream>>>(*map, A);
-        else field3d_tma_kernel<true, false><<<grid, kThreads3, smem, s.stream>>>(*map, A);
-    } else {
-        if (cones) field3d_tma_kernel<false, true><<<grid, kLaunch3, smem, s.stream>>>(*map, A);
-        else field3d_tma_kernel<false, false><<<grid, kThreads3, smem, s.stream>>>(*map, A);
-    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(cones ? kLaunch3 : kThreads3);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (s.src_map)
+        e = cones ? cudaLaunchKernelEx(&cfg, field3d_tma_kernel<true, true>, *map, A)
+                  : cudaLaunchKernelEx(&cfg, field3d_tma_kernel<true, false>, *map, A);
+    else
+        e = cones ? cudaLaunchKernelEx(&cfg, field3d_tma_kernel<false, true>, *map, A)
+                  : cudaLaunchKernelEx(&cfg, field3d_tma_kernel<false, false>, *map, A);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
