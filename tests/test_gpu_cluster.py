@@ -240,3 +240,21 @@ def test_nonfinite_is_reported(cue):
     sim.sim_run(2)
     assert sim.status() == cue.CUE_ERR_NONFINITE
     sim.close()
+
+
+def test_cluster_at_its_largest_grid(cue):
+    """1024 x 400 on 16 CTAs: bands of 25 rows, both buffers and the halo rows take
+    (25 + 2) x 1024 x 8 B = 221 KB of a CTA's 227 KB; bit for bit equal to the plain path,
+    every cone lane busy across band edges.  Sixteen more rows (bands of 26) no longer fit
+    in one block's shared memory, so the cluster path is refused there."""
+    w = W.make("1024x400", 2, 1024, 400, n_src=40, n_axons=2000, C0="smooth", seed=188, stop_radius=1.0)
+    a, _ = _run(cue, w, cue.CUE_PATH_PLAIN, [3])
+    b, pb = _run(cue, w, cue.CUE_PATH_CLUSTER, [3], ctas=16)
+    assert pb == cue.CUE_PATH_CLUSTER
+    _assert_same(a, b)
+    big = W.make("1024x416", 2, 1024, 416, n_src=4, n_axons=64, C0="smooth", seed=189)
+    sim = cue.Simulation(big)
+    with pytest.raises(cue.CueError) as e:
+        sim.set_option(cue.CUE_OPT_PATH, cue.CUE_PATH_CLUSTER)
+    assert e.value.code == cue.CUE_ERR_ARG
+    sim.close()
