@@ -398,6 +398,8 @@ def dominant_kernel(sim, w):
     path = sim_path_used(sim)
     if path == "fused":
         K = sim.get_option(sim_cue().CUE_INFO_DEPTH)
+        if w.dim == 3:          # an odd last step runs on the one-step kernel
+            return "fused3d", w.nsteps // K, K
         return "fused", (w.nsteps + K - 1) // K, K
     if path in ("persist", "resident", "cluster"):
         return path, 1, w.nsteps
@@ -425,7 +427,7 @@ def roofline_single(sim, w, rec, ms_per_run, hbm, peak_kind, work):
     avg_s = ms_per_run / per_run / 1e3
     achieved = alg / avg_s / 1e9
     # compulsory traffic: a launch reads and writes its field once however many steps it covers
-    one_pass = bpc * w.n_cells * (1 if name == "fused" else K)
+    one_pass = bpc * w.n_cells * (1 if name in ("fused", "fused3d") else K)
     r = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
          "traffic": recorded_traffic({"step3d": "field"}.get(name, name), work), "kernel": name,
          "peak_kind": peak_kind, "launches_per_run": per_run, "steps_per_launch": K,

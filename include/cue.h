@@ -97,7 +97,9 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
 /* ---- options (cue_set_option) ------------------------------------------ */
 #define CUE_OPT_PATH            1  /* value: CUE_PATH_*                                    */
 #define CUE_OPT_TEMPORAL_DEPTH  2  /* value: steps fused per launch on the fused path (1..16),
-                                      0 = library choice                                    */
+                                      0 = library choice; on 3D handles 2 selects the
+                                      blocked path under AUTO, other values the one-step
+                                      kernel                                                */
 #define CUE_OPT_ROWS_PER_THREAD 3  /* value: rows streamed per thread by the plain 2D field
                                       kernel (1..64), 0 = library choice                    */
 #define CUE_OPT_TIME_KERNEL     4  /* value v >= 1: bracket every v-th launch of the dominant
@@ -119,15 +121,21 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
                                       depend on it                                           */
 /* read-only values for cue_get_option */
 #define CUE_INFO_LAST_PATH     16  /* CUE_PATH_*: path the last sim_run took                  */
-#define CUE_INFO_TILE          17  /* fused tile interior: TX | TY << 16 (0 if not prepared) */
+#define CUE_INFO_TILE          17  /* fused tile interior: TX | TY << 16 (0 if not prepared);
+                                      3D: the blocked path's column tile                     */
 #define CUE_INFO_DEPTH         18  /* temporal depth the fused path runs with                 */
 #define CUE_INFO_GRID          19  /* blocks of the last persistent or cluster launch         */
-#define CUE_PATH_AUTO   0          /* library picks: fused for grids of at least one tile per
-                                      SM; else cluster for 2D grids of at least 4096 nodes
-                                      with at most 128 cones and 16384 nodes per block; else
-                                      resident; else persistent; else plain                 */
-#define CUE_PATH_PLAIN  1          /* one launch per half-step: cone kernel, field kernel  */
-#define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel       */
+#define CUE_PATH_AUTO   0          /* library picks: fused for 2D grids of at least one tile
+                                      per SM; else cluster for 2D grids of at least 4096
+                                      nodes with at most 128 cones and 16384 nodes per block;
+                                      else resident; else persistent; else plain (3D: one
+                                      launch per step)                                     */
+#define CUE_PATH_PLAIN  1          /* one launch per half-step: cone kernel, field kernel
+                                      (3D with nx % 4 == 0: one launch per step)           */
+#define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel; on 3D
+                                      handles (nx % 4 == 0, step_len <= h, at most 512
+                                      sources) two steps per launch, a run's odd last step
+                                      on the one-step kernel                               */
 #define CUE_PATH_PERSIST 3         /* 2D, nx % 4 == 0: one cooperative launch for the whole
                                       run; per step one pass over field tiles and cone
                                       chunks, then a bounded grid barrier                   */

@@ -20,6 +20,8 @@ WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons)
     w.src_xyz_off = off;
     off += align256(sizeof(float) * 3 * (size_t)(n_src > 0 ? n_src : 0));
     w.n_tiles = fused_tile_count(p);
+    Fused3Geom g3;
+    if (p.dim == 3 && fused3d_geometry(p, g3)) w.n_tiles = g3.boxes;   // the blocked 3D path's boxes
     const size_t nt = (size_t)(w.n_tiles > 0 ? w.n_tiles : 1);
     const size_t na = (size_t)(n_axons > 0 ? n_axons : 1);
     w.bin_count_off = off;
@@ -41,6 +43,10 @@ WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons)
         const size_t ns = (size_t)(n_src > 0 ? n_src : 0);
         w.persist_src_off = off;
         off += align256(sizeof(PSrc) * ns) + align256(sizeof(int) * ns);
+    }
+    if (p.dim == 3 && fused3d_geometry(p, g3)) {     // the blocked 3D path's copy of its intermediate step
+        w.inter_off = off;
+        off += align256(sizeof(float) * (size_t)p.nx * p.ny * p.nz);
     }
     w.total = off;
     return w;
@@ -136,6 +142,8 @@ int run_coupled(Sim &s, int nsteps)
     if (s.path == CUE_PATH_RESIDENT || (s.path == CUE_PATH_AUTO && small)) rc = run_resident_if_supported(s, nsteps);
     if (rc != 1) return rc;
     if (s.path == CUE_PATH_PERSIST || (s.path == CUE_PATH_AUTO && small)) rc = run_persist_if_supported(s, nsteps);
+    if (rc != 1) return rc;
+    rc = run_fused3d_if_supported(s, nsteps, true);
     if (rc != 1) return rc;
     rc = run_fused_if_supported(s, nsteps);
     if (rc != 1) return rc;       // handled (0 = ok, < 0 = error)
@@ -310,7 +318,10 @@ int cue_step(cue_sim *s, int32_t nsteps)
 {
     if (!s || nsteps < 0) return CUE_ERR_ARG;
     if (s->field_step + nsteps > 0xFFFFFFFFLL) return CUE_ERR_STATE;
-    int rc = field_fused_if_supported(*s, nsteps);
+    s->fused_used = false;
+    int rc = run_fused3d_if_supported(*s, nsteps, false);
+    if (rc != 1) return rc;
+    rc = field_fused_if_supported(*s, nsteps);
     if (rc != 1) return rc;
     s->fused_used = false;
     for (int k = 0; k < nsteps; ++k) {
@@ -467,7 +478,7 @@ int cue_set_option(cue_sim *s, int32_t option, int64_t value)
             value != CUE_PATH_PERSIST && value != CUE_PATH_RESIDENT && value != CUE_PATH_CLUSTER)
             return CUE_ERR_ARG;
         if (value == CUE_PATH_CLUSTER && !cluster_supported(*s)) return CUE_ERR_ARG;
-        if (value == CUE_PATH_FUSED && !fused_supported(*s)) return CUE_ERR_ARG;
+        if (value == CUE_PATH_FUSED && !fused_supported(*s) && !fused3d_supported(*s)) return CUE_ERR_ARG;
         if (value == CUE_PATH_PERSIST && !persist_supported(*s)) return CUE_ERR_ARG;
         if (value == CUE_PATH_RESIDENT && !resident_supported(*s)) return CUE_ERR_ARG;
         s->path = (int)value;
@@ -554,8 +565,14 @@ int cue_get_option(const cue_sim *s, int32_t option, int64_t *value)
     case CUE_OPT_BARRIER_PHANTOM: *value = s->persist_phantom; return CUE_OK;
     case CUE_OPT_CLUSTER_CTAS: *value = s->cluster_opt; return CUE_OK;
     case CUE_INFO_GRID: *value = s->cluster_used ? s->cluster_last : s->persist_grid; return CUE_OK;
-    case CUE_INFO_TILE: *value = s->geom_ready ? (int64_t)s->geom.TX | ((int64_t)s->geom.TY << 16) : 0; return CUE_OK;
-    case CUE_INFO_DEPTH: *value = s->geom_ready ? s->geom.K : 0; return CUE_OK;
+    case CUE_INFO_TILE:
+        if (s->fd.dim == 3) *value = s->geom3_ready ? (int64_t)128 | ((int64_t)s->geom3.TY << 16) : 0;
+        else *value = s->geom_ready ? (int64_t)s->geom.TX | ((int64_t)s->geom.TY << 16) : 0;
+        return CUE_OK;
+    case CUE_INFO_DEPTH:
+        if (s->fd.dim == 3) *value = s->geom3_ready ? 2 : 0;
+        else *value = s->geom_ready ? s->geom.K : 0;
+        return CUE_OK;
     default: return CUE_ERR_ARG;
     }
 }

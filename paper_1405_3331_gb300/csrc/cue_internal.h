@@ -36,6 +36,7 @@ struct WorkspaceLayout {
     size_t persist_off = 0;      // persistent path: barrier, two instance records, work list
     size_t persist_items_cap = 0;
     size_t persist_src_off = 0;  // persistent path: binned sources (PSrc) and their tile keys
+    size_t inter_off = 0;        // blocked 3D path: scratch copy of the field's intermediate step (0: none)
     size_t total = 0;
     int n_tiles = 0;
     int bin_cap = 0;             // cone ids per tile bin
@@ -51,6 +52,17 @@ struct FusedGeom {
     int ctas_per_sm;
     int local_stop;      // 1: the halo covers the source-stop radius, test tile sources only
 };
+
+// Box geometry of the temporally blocked 3D path (k_fused3d.cu): column tiles
+// of 128 x TY nodes in x-y, chunks of ZC planes in z, one CTA per box.
+struct Fused3Geom {
+    int TY = 0;
+    int ntx = 0, nty = 0;
+    int nchunk = 0, ZC = 0;
+    int boxes = 0;
+};
+// The geometry depends on the grid only (the workspace's bins are sized by it).
+bool fused3d_geometry(const cue_params &p, Fused3Geom &g);
 
 WorkspaceLayout workspace_layout(const cue_params &p, int n_src, int n_axons);
 // Device descriptors of one simulation (CUE_ERR_UNSTABLE when the explicit step is unstable).
@@ -182,6 +194,10 @@ struct Sim {
     alignas(64) unsigned char tmap[2][128];   // CUtensorMap per field buffer (as TMA source)
     alignas(64) unsigned char tmap3[2][128];  // 3D plane maps of the field buffers
     bool tmap3_ready = false;
+    // temporally blocked 3D path
+    Fused3Geom geom3{};
+    bool geom3_ready = false;
+    alignas(64) unsigned char tmap3b[2][128]; // 3D plane maps with the blocked path's box
 
     int *bin_count() const { return reinterpret_cast<int *>(ws + wl.bin_count_off); }
     int *bin_ctl() const { return reinterpret_cast<int *>(ws + wl.bin_ctl_off); }
@@ -193,6 +209,7 @@ struct Sim {
         return reinterpret_cast<unsigned long long *>(ws + wl.status_off + 8);
     }
     float *src_xyz() const { return reinterpret_cast<float *>(ws + wl.src_xyz_off); }
+    float *inter3() const { return wl.inter_off ? reinterpret_cast<float *>(ws + wl.inter_off) : nullptr; }
     PBar *persist_bar() const { return reinterpret_cast<PBar *>(ws + wl.persist_off); }
     PInst *persist_inst() const { return reinterpret_cast<PInst *>(ws + wl.persist_off + 256); }
     PItem *persist_items() const
@@ -271,6 +288,13 @@ bool fused_supported(const Sim &s);
 int run_fused_if_supported(Sim &s, int nsteps);
 // Same for field-only steps (cue_step).
 int field_fused_if_supported(Sim &s, int nsteps);
+
+// ---- temporally blocked 3D path (k_fused3d.cu): two steps per launch ----
+bool fused3d_supported(const Sim &s);
+// Runs nsteps (coupled when `cones`, else field only) on the blocked 3D path
+// when selected (or AUTO) and supported: CUE_OK / negative error when it ran,
+// 1 when the caller should use the one-launch-per-step kernels.
+int run_fused3d_if_supported(Sim &s, int nsteps, bool cones);
 
 // Bracket a launch of the dominant kernel with timing events (no-ops when off).
 void timing_begin(Sim &s);
