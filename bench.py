@@ -451,7 +451,9 @@ def single_summary(runner, rec, hbm, peak_kind, work, world=1):
             "unit": UNIT, "ms_per_run": ms, "runs": len(rec["run_ms"]),
             "axon_steps_per_s": world * rec["cone_updates"] / (ms / 1e3),
             "roofline": roofline_single(runner.sim, w, rec, ms, hbm, peak_kind, work),
-            "gpu_launches_per_run": rec["launches"] / max(1, len(rec["run_ms"]))}
+            "gpu_launches_per_run": rec["launches"] / max(1, len(rec["run_ms"])),
+            **({"helper_blocks": runner.sim.get_option(sim_cue().CUE_INFO_HELPERS)}
+               if rec["path"] == "fused" and w.dim == 2 else {})}
 
 
 def main():
@@ -509,6 +511,8 @@ def main():
         "roofline": roofline_single(run.sim, w, rec, ms_run, hbm, peak_kind, args.workload),
         "clocks": rec["clocks"], "gpu_launches": rec["launches"],
     }
+    if rec["path"] == "fused" and w.dim == 2:
+        line["helper_blocks"] = run.sim.get_option(cue.CUE_INFO_HELPERS)
 
     # end to end through the public API from pinned host buffers
     if not args.no_e2e:

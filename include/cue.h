@@ -125,6 +125,9 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
                                       3D: the blocked path's column tile                     */
 #define CUE_INFO_DEPTH         18  /* temporal depth the fused path runs with                 */
 #define CUE_INFO_GRID          19  /* blocks of the last persistent or cluster launch         */
+#define CUE_INFO_HELPERS       20  /* helper blocks of the last fused 2D launch: blocks that
+                                      share out the cones of crowded tiles (sized from the
+                                      crowding the previous run reported; 0 on the first)  */
 #define CUE_PATH_AUTO   0          /* library picks: fused for 2D grids of at least one tile
                                       per SM; else cluster for 2D grids of at least 4096
                                       nodes with at most 128 cones and 16384 nodes per block;

@@ -181,6 +181,11 @@ struct cue_sim : public cue::Sim {};
 
 namespace cue {
 
+void sim_no_host_alloc(cue_sim *h)
+{
+    if (h) h->adapt_helpers = false;
+}
+
 int make_descs(const cue_params &params, const cone_params &cone, FieldDesc &f, ConeDesc &c)
 {
     const int dim = params.dim;
@@ -565,6 +570,7 @@ int cue_get_option(const cue_sim *s, int32_t option, int64_t *value)
     case CUE_OPT_BARRIER_PHANTOM: *value = s->persist_phantom; return CUE_OK;
     case CUE_OPT_CLUSTER_CTAS: *value = s->cluster_opt; return CUE_OK;
     case CUE_INFO_GRID: *value = s->cluster_used ? s->cluster_last : s->persist_grid; return CUE_OK;
+    case CUE_INFO_HELPERS: *value = s->help_last; return CUE_OK;
     case CUE_INFO_TILE:
         if (s->fd.dim == 3) *value = s->geom3_ready ? (int64_t)128 | ((int64_t)s->geom3.TY << 16) : 0;
         else *value = s->geom_ready ? (int64_t)s->geom.TX | ((int64_t)s->geom.TY << 16) : 0;
@@ -616,6 +622,11 @@ void cue_destroy(cue_sim *s)
         cudaStreamSynchronize(s->stream);
         timing_free(*s);
     }
+    if (s->help_ev) {
+        cudaEventSynchronize(s->help_ev);       // the readback lands before its word goes
+        cudaEventDestroy(s->help_ev);
+    }
+    if (s->help_host) cudaFreeHost(s->help_host);
     delete s;
 }
 

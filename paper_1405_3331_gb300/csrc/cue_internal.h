@@ -187,6 +187,14 @@ struct Sim {
     int persist_grid = 0;
 
     // fused path
+    // helper CTAs for crowded tiles: the total need the last run reported, read back
+    // without blocking (pinned word + event) and applied to the next run
+    bool adapt_helpers = true;    // off for handles that must not allocate (sim_run_static)
+    int *help_host = nullptr;     // pinned host words: the run's largest need, the two round slots
+    cudaEvent_t help_ev = nullptr;
+    bool help_pending = false;
+    int help_next = 0;            // helpers the next run launches
+    int help_last = 0;            // helpers of the last fused launch (CUE_INFO_HELPERS)
     FusedGeom geom{};
     bool geom_ready = false;
     bool fused_used = false;
@@ -335,6 +343,8 @@ cudaError_t blocked_launch(const BInst *d_insts, const int2 *d_items, int n_item
                            int *ids, size_t bin_total, int total_tiles, int *done, unsigned *status,
                            cudaStream_t stream);
 
+// A handle that allocates nothing, not even the pinned word of the helper readback.
+void sim_no_host_alloc(cue_sim *h);
 // ---- coupled steps without the public entry point's checks (cue_api.cu)
 int run_coupled(Sim &s, int nsteps);
 // ---- adjoint (k_adjoint.cu)

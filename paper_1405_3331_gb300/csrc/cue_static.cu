@@ -56,6 +56,7 @@ int sim_run_static(const cue_params *params, const cone_params *cone, float *d_f
     rc = cue_init(&h, params, cone, d_field_a, d_field_b, d_src_cell, d_src_emit, n_src, d_src_map, d_pos, d_dir,
                   d_active, n_axons, ws, kStaticScratchBytes, stream);
     if (rc != CUE_OK) return rc;
+    cue::sim_no_host_alloc(h);          // no pinned readback word: this entry point allocates nothing
     rc = cue_set_state(h, step0, step0, 0);
     if (rc == CUE_OK) rc = sim_run(h, nsteps);
     int64_t fs = 0, cs = 0;

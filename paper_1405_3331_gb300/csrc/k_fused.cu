@@ -81,7 +81,12 @@ struct FusedArgs {
     int *bins_next;
     int2 *spill_next;
     int *spill_cnt_next;
-    int *done;                                 // tiles past their prologue: the last clears spill_cnt_cur
+    int *done;                                 // CTAs past their prologue: the last clears spill_cnt_cur
+    int n_help;                                // helper CTAs at the start of the grid (0: none)
+    int round;                                 // bin round this launch reads
+    int n_tiles;
+    int *need;                                 // [0] the run's largest per-launch helper need; [1 + round]
+                                               // the need of the bins filled for that round
     int bin_cap;                               // ids per tile bin (this launch's and the next's)
     const int32_t *src_cell;
     const float *src_emit;
@@ -91,10 +96,24 @@ struct FusedArgs {
     unsigned long long *counter;
 };
 
+constexpr int kHelpCap = 192;          // cones per CTA when a crowded tile's cones are shared out (its register slots)
+constexpr int kHelpMaxTiles = 2048;    // grids with more tiles run without helpers
+constexpr int kMaxHelpers = 128;
 constexpr int kConeWarps = 2;          // warps that step the cones, after the 8 field warps
 constexpr int kConeSlots = 3;          // cones held in registers per lane of a cone warp
 constexpr int kRegCones = kConeSlots * 32 * kConeWarps;   // the first kRegCones ids of a bin ride in registers
 constexpr int kFusedThreads = kThreads + 32 * kConeWarps;
+static_assert(kHelpCap <= kRegCones, "a helper's cones ride in the cone warps' registers");
+
+// The helper need of the bins this launch reads is complete (the launch that filled
+// them has finished): fold it into the run's maximum and clear its slot for the
+// launch after next.  Called once per launch, by the last CTA past its prologue.
+__device__ __forceinline__ void fold_need(const FusedArgs &A)
+{
+    int *slot = &A.need[1 + A.round];
+    if (*slot > A.need[0]) A.need[0] = *slot;
+    *slot = 0;
+}
 
 // Named barriers between the field warps and the cone warps (every warp arrives
 // converged, from its own role's loop).
@@ -110,6 +129,9 @@ __device__ __forceinline__ int tile_of(const FieldDesc &f, const FusedGeom &g, f
     return (iy / g.TY) * g.ntx + ix / g.TX;
 }
 
+// HELP: the launch may carry helper blocks (n_help > 0); without it the kernel is the
+// plain one-tile-per-block form.
+template <bool HELP>
 __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                    const FusedArgs A)
 {
@@ -127,93 +149,188 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_
     float *t_e = reinterpret_cast<float *>(t_row + kMaxTileSrc);
     float *t_xy = t_e + kMaxTileSrc;                            // [2][kMaxTileSrc] tile sources
 
-    const int t = blockIdx.x;
-    const int tx = t % g.ntx, ty = t / g.ntx;
-    const int ox = tx * g.TX - g.HX, oy = ty * g.TY - g.HY;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool cone_warp = warp >= kWarps;        // warps 0-7 sweep the field, warps 8-9 step the cones
     const int n = A.n_axons;
+    // Work item of this CTA.  Without helpers (n_help == 0) CTA b is tile b.  With
+    // helpers the first n_help CTAs are helpers: each takes a slice of kHelpCap cones
+    // of a crowded tile (a tile whose bin holds more than kHelpCap cones), sweeps that
+    // tile's field in its own shared memory and steps only its slice; the other CTAs
+    // are the tiles, in order, each stepping its first kHelpCap cones plus whatever
+    // its helpers do not cover.  Helpers past the work exit.
+    const bool stop_on = A.cones_on && A.c.stop_r2 >= 0.0f && A.n_src > 0;
+    const bool helper = HELP && (int)blockIdx.x < A.n_help;
+    int t = HELP ? (helper ? -1 : (int)blockIdx.x - A.n_help) : (int)blockIdx.x;   // a helper's tile comes from the plan
+    __shared__ int s_item[4];                      // helper: tile, slice; tile CTA: helpers it has
+
+    // Point sources inside the loaded region of tile (ox, oy), grouped by tile row.
+    auto build_sources = [&](int ox, int oy, bool report) {
+        for (int r = tid; r < kRows; r += kFusedThreads) row_fill[r] = 0;
+        __syncthreads();
+        for (int s = tid; s < A.n_src && tid < kThreads; s += kThreads) {
+            int cell = A.src_cell[s];
+            if (cell >= 0 && cell < f.nx * f.ny) {
+                int gx = cell % f.nx, gy = cell / f.nx;
+                if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) atomicAdd(&row_fill[gy - oy], 1);
+            } else if (report) {
+                flag_status(A.status, kStatusBounds);      // skipped, reported once per launch
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {       // exclusive scan of the per-row counts
+            int carry = 0;
+            for (int base = 0; base < kRows; base += 32) {
+                int r = base + lane;
+                int v = r < kRows ? row_fill[r] : 0;
+                int x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(kFull, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (r < kRows) row_start[r] = carry + x - v;
+                carry += __shfl_sync(kFull, x, 31);
+            }
+            if (lane == 0) row_start[kRows] = carry;
+        }
+        __syncthreads();
+        for (int r = tid; r < kRows; r += kFusedThreads) row_fill[r] = 0;
+        __syncthreads();
+        for (int s = tid; s < A.n_src && tid < kThreads; s += kThreads) {
+            int cell = A.src_cell[s];
+            if (cell >= 0 && cell < f.nx * f.ny) {
+                int gx = cell % f.nx, gy = cell / f.nx;
+                if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) {
+                    int r = gy - oy;
+                    int slot = row_start[r] + atomicAdd(&row_fill[r], 1);
+                    t_col[slot] = gx - ox;
+                    t_row[slot] = r;
+                    t_e[slot] = A.src_emit[s];
+                    t_xy[slot] = (float)gx * f.h;
+                    t_xy[kMaxTileSrc + slot] = (float)gy * f.h;
+                }
+            }
+        }
+    };
 
     // Programmatic dependent launch: the next launch's CTAs may be scheduled as this
-    // launch's CTAs finish.  Up to griddepcontrol.wait a CTA reads only inputs that no
-    // kernel writes (the point sources), so that part of its prologue overlaps the
+    // launch's CTAs finish.  Up to griddepcontrol.wait a tile CTA reads only inputs that
+    // no kernel writes (the point sources), so that part of its prologue overlaps the
     // previous launch's last tiles; the wait (a no-op in a launch without the
     // attribute) returns once the previous launch has completed and its writes are
-    // visible.
+    // visible.  A helper learns its tile from the bins, after the wait.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid == 0) mbar_init(bar, 1);
-    for (int r = tid; r < kRows; r += kThreads) row_fill[r] = 0;
-    __syncthreads();
-
-    // point sources inside the loaded region, grouped by tile row
-    const bool stop_on = A.cones_on && A.c.stop_r2 >= 0.0f && A.n_src > 0;
-    for (int s = tid; s < A.n_src && tid < kThreads; s += kThreads) {
-        int cell = A.src_cell[s];
-        if (cell >= 0 && cell < f.nx * f.ny) {
-            int gx = cell % f.nx, gy = cell / f.nx;
-            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) atomicAdd(&row_fill[gy - oy], 1);
-        } else if (t == 0) {
-            flag_status(A.status, kStatusBounds);      // skipped, reported once per launch
-        }
-    }
-    __syncthreads();
-    if (warp == 0) {       // exclusive scan of the per-row counts
-        int carry = 0;
-        for (int base = 0; base < kRows; base += 32) {
-            int r = base + lane;
-            int v = r < kRows ? row_fill[r] : 0;
-            int x = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += y;
-            }
-            if (r < kRows) row_start[r] = carry + x - v;
-            carry += __shfl_sync(kFull, x, 31);
-        }
-        if (lane == 0) row_start[kRows] = carry;
-    }
-    __syncthreads();
-    for (int r = tid; r < kRows; r += kThreads) row_fill[r] = 0;
-    __syncthreads();
-    for (int s = tid; s < A.n_src && tid < kThreads; s += kThreads) {
-        int cell = A.src_cell[s];
-        if (cell >= 0 && cell < f.nx * f.ny) {
-            int gx = cell % f.nx, gy = cell / f.nx;
-            if (gx >= ox && gx < ox + kW && gy >= oy && gy < oy + kRows) {
-                int r = gy - oy;
-                int slot = row_start[r] + atomicAdd(&row_fill[r], 1);
-                t_col[slot] = gx - ox;
-                t_row[slot] = r;
-                t_e[slot] = A.src_emit[s];
-                t_xy[slot] = (float)gx * f.h;
-                t_xy[kMaxTileSrc + slot] = (float)gy * f.h;
-            }
-        }
-    }
+    // a tile CTA's load coordinates, ready before the wait (the copy is the first thing after it)
+    const int tox = helper ? 0 : t % g.ntx * g.TX - g.HX, toy = helper ? 0 : t / g.ntx * g.TY - g.HY;
+    if (!helper) build_sources(tox, toy, t == 0);
 
     // from here on: what earlier launches wrote (the field, the cone bins and state)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (tid == 0) {
-        mbar_expect_tx(bar, (unsigned)(kRows * kW * sizeof(float)));
-        tma_load_2d(S, &tmap, bar, ox, oy);
+    auto issue_tile = [&](int x, int y) {
+        if (tid == 0) {
+            mbar_expect_tx(bar, (unsigned)(kRows * kW * sizeof(float)));
+            tma_load_2d(S, &tmap, bar, x, y);
+        }
+    };
+    if (!helper) issue_tile(tox, toy);              // a tile CTA's copy goes out first
+
+    // The helper plan: every tile's helper need (its cones past kHelpCap, kHelpCap per
+    // helper), scanned over the tiles in the order of the tile index.  Only helpers and
+    // crowded tiles (of a launch with helpers) compute it.
+    const int nb_own = (HELP && A.cones_on && !helper) ? min(A.cnt_cur[t], A.bin_cap) : 0;
+    const int need_own = nb_own > kHelpCap ? (nb_own - 1) / kHelpCap : 0;
+    if (HELP && A.cones_on && (helper || need_own > 0) && A.n_tiles <= kHelpMaxTiles) {
+        __shared__ int s_wsum[kFusedThreads / 32];
+        const int per = (A.n_tiles + kFusedThreads - 1) / kFusedThreads;
+        const int t_lo = min(tid * per, A.n_tiles), t_hi = min(t_lo + per, A.n_tiles);
+        auto need_of_tile = [&](int tt) {
+            const int nb = min(A.cnt_cur[tt], A.bin_cap);
+            return nb > kHelpCap ? (nb - 1) / kHelpCap : 0;
+        };
+        int mine = 0;
+        for (int tt = t_lo; tt < t_hi; ++tt) mine += need_of_tile(tt);
+        int x = mine;                                   // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_wsum[warp] = x;
+        if (tid == 0) {
+            s_item[0] = -1;
+            s_item[2] = 0;
+        }
+        __syncthreads();
+        int before = x - mine, total = 0;
+        for (int w = 0; w < kFusedThreads / 32; ++w) {
+            if (w < warp) before += s_wsum[w];
+            total += s_wsum[w];
+        }
+        const int used = min(total, A.n_help);
+        int pre = before;
+        for (int tt = t_lo; tt < t_hi; ++tt) {
+            const int nd = need_of_tile(tt);
+            if (helper) {
+                const int h = (int)blockIdx.x;
+                if (h >= pre && h < pre + nd && h < used) {
+                    s_item[0] = tt;
+                    s_item[1] = h - pre + 1;               // slice 1.. of the tile's bin
+                }
+            } else if (tt == t) {
+                s_item[2] = min(max(used - pre, 0), nd);   // helpers this tile has
+            }
+            pre += nd;
+        }
+        __syncthreads();
+        if (helper) t = s_item[0];
+    }
+    if (helper && t < 0) {                          // no work: count in and leave
+        if (tid == 0 && atomicAdd(A.done, 1) == (int)gridDim.x - 1) {
+            for (int tt = 0; tt < A.n_tiles; ++tt) A.cnt_cur[tt] = 0;
+            fold_need(A);
+            *A.spill_cnt_cur = 0;
+            *A.done = 0;
+        }
+        return;
+    }
+    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int ox = tx * g.TX - g.HX, oy = ty * g.TY - g.HY;
+    if (helper) {
+        issue_tile(ox, oy);
+        build_sources(ox, oy, false);
     }
 
-    // this tile's cones into registers (overlaps the TMA load)
+    // this CTA's cones into registers (overlaps the TMA load): its list is one or two
+    // ranges of the tile's bin -- a helper: slice s, [s kHelpCap, (s + 1) kHelpCap);
+    // a tile with helpers: [0, kHelpCap) and what follows its helpers' slices
     __shared__ int s_nspill;
     if (tid == 0) s_nspill = A.cones_on ? *A.spill_cnt_cur : 0;
-    const int n_bin = A.cones_on ? min(A.cnt_cur[t], A.bin_cap) : 0;
-    const int *bin = A.bins_cur + (size_t)t * A.bin_cap;
-    // the cone warps' slots: bin entry (32 q + lane) kConeWarps + w in slot q of lane
-    // `lane` of cone warp w, so a tile's cones are shared out evenly (the rest of the
-    // bin, if any, is stepped by the field warps from global memory)
+    const int n_bin_all = A.cones_on ? min(A.cnt_cur[t], A.bin_cap) : 0;
+    int b1 = 0, L1 = n_bin_all, b2 = 0, L2 = 0;
+    if (HELP && A.cones_on) {
+        if (helper) {
+            b1 = s_item[1] * kHelpCap;
+            L1 = min(kHelpCap, n_bin_all - b1);
+        } else if (n_bin_all > kHelpCap) {
+            L1 = kHelpCap;
+            b2 = kHelpCap * (1 + s_item[2]);
+            L2 = max(n_bin_all - b2, 0);
+        }
+    }
+    const int n_bin = L1 + L2;
+    const int *bin_base = A.bins_cur + (size_t)t * A.bin_cap;
+    auto bin_at = [&](int i) { return HELP ? bin_base[i < L1 ? b1 + i : b2 + (i - L1)] : bin_base[i]; };
+    // the cone warps' slots: list entry (32 q + lane) kConeWarps + w in slot q of lane
+    // `lane` of cone warp w, so a CTA's cones are shared out evenly (the rest of the
+    // list, if any, is stepped by the field warps from global memory)
     int ca[kConeSlots];
     bool cl[kConeSlots];
     float cp[kConeSlots][2], cdir[kConeSlots][2];
 #pragma unroll
     for (int q = 0; q < kConeSlots; ++q) {
         const int i = (32 * q + lane) * kConeWarps + (warp - kWarps);
-        ca[q] = cone_warp && i < n_bin ? bin[i] : -1;
+        ca[q] = cone_warp && i < n_bin ? bin_at(i) : -1;
         cl[q] = ca[q] >= 0;
         if (cl[q]) {
             cl[q] = A.active[ca[q]] != 0;
@@ -226,10 +343,14 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_
     __syncthreads();
     const int n_spill = s_nspill;
     if (A.cones_on && tid == 0) {
-        // every thread has read this tile's count: clear it for the launch after next;
-        // the last tile past this point clears the spill count (every tile holds it)
-        A.cnt_cur[t] = 0;
+        // every thread has read this tile's count: clear it for the launch after next
+        // (with helpers every CTA read every count: the last CTA past this point clears
+        // them all); the last CTA past this point clears the spill count
+        if (!HELP) A.cnt_cur[t] = 0;
         if (atomicAdd(A.done, 1) == (int)gridDim.x - 1) {
+            if (HELP)
+                for (int tt = 0; tt < A.n_tiles; ++tt) A.cnt_cur[tt] = 0;
+            fold_need(A);
             *A.spill_cnt_cur = 0;
             *A.done = 0;
         }
@@ -303,6 +424,9 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_
     auto rebin = [&](int a, float px, float py) {
         const int tile = tile_of(f, g, px, py);
         const int slot = atomicAdd(&A.cnt_next[tile], 1);
+        // a bin passing a multiple of kHelpCap cones needs one more helper: the run's
+        // total, from which the host sizes the next run's helpers
+        if (slot >= kHelpCap && slot % kHelpCap == 0) atomicAdd(&A.need[1 + (A.round ^ 1)], 1);
         if (slot < A.bin_cap) {
             A.bins_next[(size_t)tile * A.bin_cap + slot] = a;
         } else {
@@ -367,7 +491,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_
         // are loaded while this round's cone steps, so a crowded tile is bound by its
         // arithmetic rather than by chains of dependent loads
         if (n_bin > kRegCones) {
-            auto id_at = [&](int i) { return i < n_bin ? bin[i] : -1; };
+            auto id_at = [&](int i) { return i < n_bin ? bin_at(i) : -1; };
             int a_nn = id_at(kRegCones + kThreads + tid);
             int a_n = id_at(kRegCones + tid);
             bool live_n = a_n >= 0 && A.active[a_n] != 0;
@@ -432,7 +556,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_
     // ---- the other cones back to their bins for the next launch
     if (A.cnt_next) {
         for (int i = kRegCones + tid; i < n_bin; i += kThreads) {
-            const int a = bin[i];
+            const int a = bin_at(i);
             if (A.active[a]) rebin(a, A.pos[a], A.pos[n + a]);
         }
         for (int i = tid; i < n_spill; i += kThreads) {
@@ -441,7 +565,8 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused2d_kernel(const __grid_
         }
     }
 
-    // ---- store the interior
+    // ---- store the interior (a helper's copy of the tile is not stored)
+    if (helper) return;
     bool bad = false;
     for (int r = g.HY + warp; r < g.HY + g.TY; r += kWarps) {
         const int gy = oy + r;
@@ -627,8 +752,10 @@ static int prepare(Sim &s)
     s.geom = g;
     if (!make_maps(s)) return CUE_ERR_CUDA;
     size_t smem = fused_smem_bytes(g.R);
-    if (cudaFuncSetAttribute(fused2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(fused2d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(fused2d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
         return CUE_ERR_CUDA;
     s.geom_ready = true;
     return CUE_OK;
@@ -654,7 +781,7 @@ static cudaError_t launch_bin_count(Sim &s)
 
 // One launch of k <= K fused steps (cones on or off) from s.cur into s.cur^1.
 // With cones: the kernel reads the current round's bins and fills the next's.
-static cudaError_t launch_fused(Sim &s, int k, bool cones)
+static cudaError_t launch_fused(Sim &s, int k, bool cones, int n_help = 0)
 {
     const FusedGeom &g = s.geom;
     const int n_tiles = g.ntx * g.nty;
@@ -681,6 +808,10 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     A.spill_next = s.spill() + (size_t)rn * s.n_axons;
     A.spill_cnt_next = s.bin_ctl() + rn;
     A.done = s.bin_ctl() + 2;
+    A.need = s.bin_ctl() + 3;
+    A.round = r;
+    A.n_tiles = n_tiles;
+    A.n_help = with_cones ? n_help : 0;
     A.bin_cap = s.wl.bin_cap;
     A.src_cell = s.src_cell;
     A.src_emit = s.src_emit;
@@ -692,7 +823,7 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     // a programmatic dependent launch: its CTAs may start their source prologue while
     // the previous kernel in the stream finishes (the kernel waits before reading it)
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(n_tiles);
+    cfg.gridDim = dim3(n_tiles + A.n_help);
     cfg.blockDim = dim3(kFusedThreads);
     cfg.dynamicSmemBytes = fused_smem_bytes(g.R);
     cfg.stream = s.stream;
@@ -702,7 +833,8 @@ static cudaError_t launch_fused(Sim &s, int k, bool cones)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     timing_begin(s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, fused2d_kernel, *map, A);
+    cudaError_t e = A.n_help > 0 ? cudaLaunchKernelEx(&cfg, fused2d_kernel<true>, *map, A)
+                                 : cudaLaunchKernelEx(&cfg, fused2d_kernel<false>, *map, A);
     timing_end(s);
     s.launches++;
     if (with_cones) s.bin_round++;
@@ -720,13 +852,39 @@ int run_fused_if_supported(Sim &s, int nsteps)
     int rc = prepare(s);
     if (rc != CUE_OK) return s.path == CUE_PATH_FUSED ? rc : 1;
     if (nsteps > 0 && s.n_axons > 0 && launch_bin_count(s) != cudaSuccess) return CUE_ERR_CUDA;
+    // helpers: sized from the crowding the last run reported (its readback, if landed)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool adapt = s.adapt_helpers && s.n_axons > 0 && s.wl.bin_cap >= s.n_axons &&
+                       s.geom.ntx * s.geom.nty <= kHelpMaxTiles &&
+                       cudaStreamIsCapturing(s.stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+    if (adapt && s.help_pending && cudaEventQuery(s.help_ev) == cudaSuccess) {
+        // the largest per-launch need of the last run (its last launch's own count too)
+        const int need = std::max(s.help_host[0], std::max(s.help_host[1], s.help_host[2]));
+        s.help_next = std::min(std::max(need, 0), kMaxHelpers);
+        s.help_pending = false;
+    }
+    const int n_help = adapt ? s.help_next : 0;
+    s.help_last = 0;
     while (nsteps > 0) {
         int k = nsteps < s.geom.K ? nsteps : s.geom.K;
-        if (launch_fused(s, k, true) != cudaSuccess) return CUE_ERR_CUDA;
+        if (launch_fused(s, k, true, n_help) != cudaSuccess) return CUE_ERR_CUDA;
+        s.help_last = n_help;
         s.cur ^= 1;
         s.field_step += k;
         s.cone_step += k;
         nsteps -= k;
+    }
+    if (adapt && !s.help_pending) {     // read this run's last reported need back, without waiting
+        if (!s.help_host && cudaHostAlloc(reinterpret_cast<void **>(&s.help_host), 3 * sizeof(int),
+                                          cudaHostAllocDefault) != cudaSuccess)
+            s.help_host = nullptr;
+        if (s.help_host && !s.help_ev && cudaEventCreateWithFlags(&s.help_ev, cudaEventDisableTiming) != cudaSuccess)
+            s.help_ev = nullptr;
+        if (s.help_host && s.help_ev &&
+            cudaMemcpyAsync(s.help_host, s.bin_ctl() + 3, 3 * sizeof(int), cudaMemcpyDeviceToHost, s.stream) ==
+                cudaSuccess &&
+            cudaEventRecord(s.help_ev, s.stream) == cudaSuccess)
+            s.help_pending = true;
     }
     s.fused_used = true;
     return CUE_OK;

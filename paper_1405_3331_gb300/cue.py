@@ -41,6 +41,7 @@ CUE_INFO_LAST_PATH = 16
 CUE_INFO_TILE = 17
 CUE_INFO_DEPTH = 18
 CUE_INFO_GRID = 19
+CUE_INFO_HELPERS = 20
 CUE_PATH_AUTO = 0
 CUE_PATH_PLAIN = 1
 CUE_PATH_FUSED = 2

@@ -222,3 +222,61 @@ def test_fused_reports_nonfinite(cue):
     sim = cue.Simulation(w, path=cue.CUE_PATH_FUSED)
     sim.sim_run(8)
     assert sim.status() == cue.CUE_ERR_NONFINITE
+
+
+def _run_twice_with_helpers(cue, w, n, K=8):
+    """Two runs on each path: the fused handle's second run takes the helper count the
+    first run's crowding reported (its readback has landed after the synchronize)."""
+    import torch
+    a, b = _pair(cue, w, K)
+    a.sim_run(n)
+    b.sim_run(n)
+    torch.cuda.synchronize()
+    assert b.get_option(cue.CUE_INFO_HELPERS) == 0          # nothing reported before the first run
+    a.sim_run(n)
+    b.sim_run(n)
+    helpers = b.get_option(cue.CUE_INFO_HELPERS)
+    a.check()
+    b.check()
+    _assert_same(a.snapshot(), b.snapshot())
+    assert a.cone_updates() == b.cone_updates()
+    a.close()
+    b.close()
+    return helpers
+
+
+def test_clustered_workload_with_helpers_equals_plain(cue):
+    """The clustered 2048^2 workload: the second run shares each crowded tile's cones out
+    to helper blocks (192 per block, the cone warps' register slots) and must still equal the plain path bit for bit."""
+    helpers = _run_twice_with_helpers(cue, W.config_c2_clustered(), 21)
+    assert helpers > 0
+
+
+def test_helpers_all_cones_in_one_tile(cue):
+    w = _case("c1-128")
+    n = 5000
+    rng = np.random.default_rng(40)
+    w.pos = rng.uniform(60, 62, (2, n)).astype(np.float32)
+    w.dir = W._directions(rng, 2, n).astype(np.float32)
+    w.active = np.ones(n, np.uint8)
+    assert _run_twice_with_helpers(cue, w, 17) >= 10
+
+
+def test_helpers_fewer_than_needed(cue):
+    """60,000 cones in one tile need 312 helpers, more than the 128 a launch takes: the
+    tile's own block steps the cones past the helpers' slices."""
+    w = W.make("crowd-1024", 2, 1024, 512, n_src=8, n_axons=60000, C0="smooth", seed=41, wall_mode=1)
+    rng = np.random.default_rng(41)
+    w.pos = rng.uniform(300, 340, (2, 60000)).astype(np.float32)
+    assert _run_twice_with_helpers(cue, w, 9) == 128
+
+
+def test_uniform_workload_takes_no_helpers(cue):
+    import torch
+    w = _case("c2-2048")
+    sim = cue.Simulation(w, path=cue.CUE_PATH_FUSED)
+    sim.sim_run(16)
+    torch.cuda.synchronize()
+    sim.sim_run(16)
+    assert sim.get_option(cue.CUE_INFO_HELPERS) == 0
+    sim.close()
