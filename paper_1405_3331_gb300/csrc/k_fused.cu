@@ -35,6 +35,13 @@
 // scans.  Each tile clears its own count once read, the last tile past its
 // prologue clears the spill count.  No separate binning launch between fused
 // launches.
+// Crowded tiles: a launch may carry helper blocks at the start of its grid.
+// Each sweeps a crowded tile's field and steps one slice of kHelpCap of its
+// cones (a tile's own block steps the first slice and what its helpers do not
+// cover), so a tile holding thousands of cones no longer makes the launch wait
+// for one block.  The helper count comes from the crowding the previous run
+// reported (a count kept as cones are re-binned, read back without blocking).
+
 //
 // Model: cue field on an Eulerian grid (Sec. 5.2) with sources of their own
 // rates (Sec. 4.3); cone steering by vector addition (Sec. 3.5, Eq. 6-7) with
