@@ -541,6 +541,15 @@ def main():
             if "whole_run" in subs:
                 final_c3 = final_state(r3)
             r3.close()
+            # the opt-in temporally blocked 3D path (two steps per launch) on the same workload
+            r3b = Runner(cue, torch, dev, w3, path="fused", flush=flush)
+            rec3b = r3b.timed_runs(2, 1, barrier)
+            ms3b = statistics.median(rec3b["run_ms"])
+            line["c3"]["blocked_path"] = {
+                "path": rec3b["path"], "ms_per_run": ms3b, "value": w3.n_cells * w3.nsteps / (ms3b / 1e3),
+                "unit": UNIT, "vs_default_path": line["c3"]["ms_per_run"] / ms3b,
+                "roofline": roofline_single(r3b.sim, w3, rec3b, ms3b, hbm, peak_kind, "c3")}
+            r3b.close()
         if "batched" in subs:
             line["batched"] = batch_summary(args, torch, cue, dev, rank, barrier, flush, hbm, peak_kind)
         if "adjoint" in subs:

@@ -197,6 +197,11 @@ struct Sim {
     int help_last = 0;            // helpers of the last fused launch (CUE_INFO_HELPERS)
     FusedGeom geom{};
     bool geom_ready = false;
+    // point sources per fused tile region: the source cells on the host (copied once,
+    // when there are more than a tile's list holds) and the verdict for one depth
+    mutable std::vector<int32_t> src_cells_host;
+    mutable int src_fit_K = -1;
+    mutable bool src_fit_ok = false;
     bool fused_used = false;
     long long bin_round = 0;
     alignas(64) unsigned char tmap[2][128];   // CUtensorMap per field buffer (as TMA source)

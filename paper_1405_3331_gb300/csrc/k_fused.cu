@@ -62,7 +62,8 @@ namespace {
 
 using namespace tile;
 
-constexpr int kMaxTileSrc = 256;      // sources per tile (and in total on this path)
+constexpr int kMaxTileSrc = 256;      // sources inside one tile's loaded region
+constexpr int kMaxFusedSources = 1 << 16;   // sources in total on this path (each tile scans them all)
 constexpr int kFusedMinTX = 128;      // smallest interior tile the path accepts
 constexpr int kFusedMinTY = 32;
 
@@ -720,15 +721,56 @@ int fused_tile_count(const cue_params &p)
 
 static int default_depth(const Sim &s) { return s.temporal_depth > 0 ? s.temporal_depth : 8; }
 
+// Whether no tile's loaded region (kW x R nodes from (tx TX - HX, ty TY - HY)) holds
+// more than kMaxTileSrc point sources, the size of a tile's source list in shared
+// memory.  Up to kMaxTileSrc sources in total always fit; past that the source
+// cells are copied to the host once per handle (a synchronous copy) and counted
+// per region, once per geometry.  Inside a stream capture no copy is made and the
+// path is refused.
+static bool fused_sources_fit(const Sim &s, const FusedGeom &g)
+{
+    if (s.n_src <= kMaxTileSrc) return true;
+    if (s.src_fit_K == g.K) return s.src_fit_ok;
+    if (s.src_cells_host.empty()) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s.stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return false;
+        std::vector<int32_t> cells((size_t)s.n_src);
+        if (cudaStreamSynchronize(s.stream) != cudaSuccess ||
+            cudaMemcpy(cells.data(), s.src_cell, sizeof(int32_t) * cells.size(), cudaMemcpyDeviceToHost) !=
+                cudaSuccess)
+            return false;
+        s.src_cells_host.swap(cells);
+    }
+    std::vector<int> count((size_t)g.ntx * g.nty, 0);
+    bool ok = true;
+    for (int32_t cell : s.src_cells_host) {
+        if (cell < 0 || cell >= s.fd.nx * s.fd.ny) continue;     // skipped (and reported) by the kernel
+        const int gx = cell % s.fd.nx, gy = cell / s.fd.nx;
+        // tiles whose loaded region holds (gx, gy): tx TX - HX <= gx < tx TX - HX + kW
+        const int tx_lo = std::max(0, (gx + g.HX - kW + g.TX) / g.TX), tx_hi = std::min(g.ntx - 1, (gx + g.HX) / g.TX);
+        const int ty_lo = std::max(0, (gy + g.HY - g.R + g.TY) / g.TY), ty_hi = std::min(g.nty - 1, (gy + g.HY) / g.TY);
+        for (int ty = ty_lo; ty <= ty_hi && ok; ++ty)
+            for (int tx = tx_lo; tx <= tx_hi && ok; ++tx) {
+                const int ox = tx * g.TX - g.HX, oy = ty * g.TY - g.HY;
+                if (gx < ox || gx >= ox + kW || gy < oy || gy >= oy + g.R) continue;
+                if (++count[(size_t)ty * g.ntx + tx] > kMaxTileSrc) ok = false;
+            }
+    }
+    s.src_fit_K = g.K;
+    s.src_fit_ok = ok;
+    return ok;
+}
+
 bool fused_supported(const Sim &s)
 {
-    if (s.fd.dim != 2 || !s.vec4 || s.src_map || s.n_src > kMaxTileSrc || s.cd.steer != 0) return false;
+    if (s.fd.dim != 2 || !s.vec4 || s.src_map || s.n_src > kMaxFusedSources || s.cd.steer != 0) return false;
     if (!encode_fn()) return false;
     FusedGeom g;
     if (!choose_geometry(s.fd, s.cd.step_len, s.cd.stop_r2, s.n_axons > 0, default_depth(s), device_sm_count(), g))
         return false;
     long long tiles = (long long)g.ntx * g.nty;
     if (tiles > s.wl.n_tiles) return false;             // the workspace's bins are sized by fused_tile_count
+    if (!fused_sources_fit(s, g)) return false;
     return true;
 }
 

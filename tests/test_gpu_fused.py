@@ -280,3 +280,37 @@ def test_uniform_workload_takes_no_helpers(cue):
     sim.sim_run(16)
     assert sim.get_option(cue.CUE_INFO_HELPERS) == 0
     sim.close()
+
+
+def test_many_sources_spread_out_run_fused(cue):
+    """1,500 point sources in total, none of the tile regions holding more than its list's
+    256: the fused path takes them and equals the plain path bit for bit."""
+    w = W.make("src-1500", 2, 1024, 768, n_src=1500, n_axons=2000, C0="smooth", seed=42, stop_radius=1.5)
+    a, b = _pair(cue, w, 8)
+    a.sim_run(19)
+    b.sim_run(19)
+    assert b.fused_active()
+    _assert_same(a.snapshot(), b.snapshot())
+    a.close()
+    b.close()
+
+
+def test_sources_crowding_one_tile_are_refused(cue):
+    """300 sources inside one tile's region exceed its list: the fused path is refused and
+    AUTO runs the plain kernels."""
+    w = W.make("src-crowd", 2, 1024, 768, n_src=300, n_axons=100, C0="smooth", seed=43)
+    rng = np.random.default_rng(43)
+    xs = rng.choice(60, 300, replace=True) + 100
+    ys = rng.choice(40, 300, replace=True) + 100
+    cells = np.unique(ys * w.nx + xs).astype(np.int32)
+    while cells.size < 300:                                  # distinct cells in a 60 x 40 block
+        extra = (rng.integers(100, 140) * w.nx + rng.integers(100, 160))
+        cells = np.unique(np.append(cells, extra)).astype(np.int32)
+    w.src_cell = cells[:300]
+    sim = cue.Simulation(w)
+    with pytest.raises(cue.CueError):
+        sim.set_option(cue.CUE_OPT_PATH, cue.CUE_PATH_FUSED)
+    sim.sim_run(3)
+    assert not sim.fused_active()
+    sim.check()
+    sim.close()
