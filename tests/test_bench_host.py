@@ -42,7 +42,7 @@ def test_committed_traffic_entries_are_well_formed():
         entries = json.load(f)
     for key, e in entries.items():
         kernel, _, work = key.partition("@")
-        assert kernel and work in ("c1", "c2", "c3", "c4", "c5"), key
+        assert kernel and work in ("c1", "c2", "c2x", "c3", "c4", "c5"), key
         assert e["dram_bytes_per_launch"] > 0 and len(e["source_digest"]) == 16 and e["note"], key
 
 
