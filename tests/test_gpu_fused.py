@@ -314,3 +314,16 @@ def test_sources_crowding_one_tile_are_refused(cue):
     assert not sim.fused_active()
     sim.check()
     sim.close()
+
+
+def test_helpers_with_cones_stopping_at_sources(cue):
+    """A crowded tile whose cones stop at nearby sources as they go: helper slices step and
+    re-bin only the cones still moving, and the run equals the plain path bit for bit."""
+    w = W.make("crowd-stop", 2, 1024, 512, n_src=12, n_axons=6000, C0="smooth", seed=44, stop_radius=3.0)
+    rng = np.random.default_rng(44)
+    w.pos = rng.uniform(300, 360, (2, 6000)).astype(np.float32)
+    cells = np.unique(rng.integers(310, 350, 12) * w.nx + rng.integers(310, 350, 12)).astype(np.int32)
+    w.src_cell = cells
+    w.src_emit = np.ones(cells.size, np.float32)
+    helpers = _run_twice_with_helpers(cue, w, 13)
+    assert helpers > 0

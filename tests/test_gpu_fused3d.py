@@ -174,3 +174,27 @@ def test_auto_keeps_the_step_kernel(cue):
     a.sim_run(4)
     assert a.fused_active()
     a.close()
+
+
+def test_blocked_3d_crowded_box_with_stops(cue):
+    """3,000 cones in one box (past its 512 shared-memory slots) around sources with a stop
+    radius: cones stop in both sub-steps, in shared memory and in global memory."""
+    w = W.make("3d-crowd-stop", 3, 64, 48, 40, dt=0.15, n_src=8, n_axons=3500, C0="smooth", seed=77,
+               stop_radius=1.5)
+    rng = np.random.default_rng(77)
+    w.pos[:2, :3000] = rng.uniform(4.0, 12.0, (2, 3000)).astype(np.float32)
+    w.pos[2, :3000] = rng.uniform(5.1, 5.9, 3000).astype(np.float32)
+    xs, ys, zs = rng.integers(5, 12, 8), rng.integers(5, 12, 8), rng.integers(4, 8, 8)
+    w.src_cell = np.unique((zs * w.ny + ys) * w.nx + xs).astype(np.int32)
+    w.src_emit = np.ones(w.src_cell.size, np.float32)
+    a, b = _pair(cue, w)
+    for n in (6, 9):
+        a.sim_run(n)
+        b.sim_run(n)
+        a.check()
+        b.check()
+        _assert_same(a.snapshot(), b.snapshot())
+    assert a.cone_updates() == b.cone_updates()
+    assert int(b.snapshot()[3].sum()) < w.n_axons                 # some cones stopped
+    a.close()
+    b.close()
