@@ -135,7 +135,9 @@ typedef struct cue_sim cue_sim;   /* opaque, host-side */
                                       launch per step)                                     */
 #define CUE_PATH_PLAIN  1          /* one launch per half-step: cone kernel, field kernel
                                       (3D with nx % 4 == 0: one launch per step)           */
-#define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel; on 3D
+#define CUE_PATH_FUSED  2          /* temporally blocked field + cones in one kernel (2D:
+                                      nx % 4 == 0, no rate map, at most 65536 sources and
+                                      256 in any tile's loaded region); on 3D
                                       handles (nx % 4 == 0, step_len <= h, at most 512
                                       sources) two steps per launch, a run's odd last step
                                       on the one-step kernel                               */
