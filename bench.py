@@ -41,6 +41,12 @@ def parse_args():
     ap.add_argument("--impl", choices=["cue", "reference"], default="cue")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2x", "c3", "c4", "c5", "graph"])
     ap.add_argument("--path", default="auto", choices=list(PATHS))
+    ap.add_argument("--batch-mode", default="auto", choices=["auto", "persist", "step", "blocked"],
+                    help="batched workload: run mode (auto = the autotuner's choice)")
+    ap.add_argument("--batch-rows", type=int, default=0,
+                    help="with a fixed --batch-mode: rows per field tile (0 = library choice)")
+    ap.add_argument("--batch-blocks", type=int, default=0,
+                    help="with --batch-mode persist: blocks per SM (0 = library choice)")
     ap.add_argument("--depth", type=int, default=0,
                     help="temporal depth on the fused path, or of the blocked batch mode with --workload c4 "
                          "(0 = auto / autotuned)")
@@ -757,6 +763,11 @@ def main_batch(args, torch, cue, dev, rank, world, dist, barrier):
     if args.depth:                       # a fixed blocked depth (profiling): no autotuner
         b.set_option(B.CUE_BOPT_MODE, 3)
         b.set_option(B.CUE_BOPT_DEPTH, args.depth)
+        tuned = (0, 0, 0.0)
+    elif args.batch_mode in ("persist", "step"):     # a fixed mode (profiling): no autotuner
+        b.set_option(B.CUE_BOPT_MODE, 1 if args.batch_mode == "persist" else 2)
+        b.set_option(B.CUE_BOPT_ROWS, args.batch_rows)
+        b.set_option(B.CUE_BOPT_BLOCKS, args.batch_blocks)
         tuned = (0, 0, 0.0)
     else:
         tuned = b.autotune(16)
