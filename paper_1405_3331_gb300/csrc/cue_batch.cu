@@ -49,7 +49,7 @@ bool blocked_capable(int n, const cue_instance *in)
         ConeDesc c;
         FusedGeom g;
         if (make_descs(p, I.cone, f, c) != CUE_OK) return false;
-        if (!fused_geometry(f, c.step_len, c.stop_r2, I.n_axons > 0, kBlockedMaxDepth, g)) return false;
+        if (!blocked_geometry(f, c.step_len, c.stop_r2, I.n_axons > 0, kBlockedMaxDepth, g)) return false;
         if ((long long)g.ntx * g.nty * std::max(I.n_axons, 1) > (1LL << 30)) return false;
     }
     return true;
@@ -99,7 +99,7 @@ BatchLayout batch_layout(int n, const cue_instance *in, bool backup)
             p.nz = 1;
             FusedGeom g;
             make_descs(p, in[i].cone, f, c);
-            fused_geometry(f, c.step_len, c.stop_r2, in[i].n_axons > 0, kBlockedMaxDepth, g);
+            blocked_geometry(f, c.step_len, c.stop_r2, in[i].n_axons > 0, kBlockedMaxDepth, g);
             const size_t tiles = (size_t)g.ntx * g.nty;
             L.blk_tiles_cap += tiles;
             L.blk_bins_cap += tiles * (size_t)std::max(in[i].n_axons, 0);
@@ -305,7 +305,7 @@ int stage_blocked(cue_batch *b, int K)
         BInst &B = bi[i];
         std::memset(static_cast<void *>(&B), 0, sizeof(BInst));
         FusedGeom g;
-        if (!fused_geometry(P.f, P.c.step_len, P.c.stop_r2, I.n_axons > 0, K, g)) return CUE_ERR_ARG;
+        if (!blocked_geometry(P.f, P.c.step_len, P.c.stop_r2, I.n_axons > 0, K, g)) return CUE_ERR_ARG;
         if (!encode_field_map(&B.map[0], I.field_a, I.params.nx, I.params.ny, I.pitch) ||
             !encode_field_map(&B.map[1], I.field_b, I.params.nx, I.params.ny, I.pitch))
             return CUE_ERR_CUDA;
@@ -338,7 +338,7 @@ int stage_blocked(cue_batch *b, int K)
             // two), heaviest first so that no crowded tile is left for a group's last wave
             // (-> 704)
             const int tx = t % g.ntx, ty = t / g.ntx;
-            const int ox = tx * g.TX - g.HX, oy = ty * g.TY - g.HY;
+            const int ox = blocked_x(g, I.params.nx).origin(tx), oy = blocked_y(g, I.params.ny).origin(ty);
             const int nx = I.params.nx, ny = I.params.ny;
             const bool ragged = (nx & 3) != 0 && ox + kBlockedTileW > nx - 1;
             const bool wall = oy <= -1 || oy + kBlockedTileRows - 1 >= ny;

@@ -338,6 +338,42 @@ struct BInst {
 };
 // Tile geometry of the temporally blocked kernels for depth K (false if none).
 bool fused_geometry(const FieldDesc &f, float step_len, float stop_r2, bool cones, int K, FusedGeom &g);
+
+// Wall-aligned tiling of one axis of n nodes for the batch's blocked mode.  A
+// tile that holds a wall needs no halo on that side (the wall node is its own
+// missing neighbour), so the first tile starts at the wall and the last ends at
+// it: load extent W, halo H, interior T = W - 2H between two tiles, and `ghost`
+// rows kept beyond a wall (1 in y, where the sweep reads a ghost row; 0 in x,
+// where the lanes' wall flags stand in).  First interior F = W - ghost - H.
+// n <= W - 2 ghost: one tile from -ghost.  Otherwise tile 0 holds [0, F), tile
+// k >= 1 starts at F + (k - 1) T with origin start - H, and the last tile holds
+// the rest (at most F nodes, so its loaded region reaches its wall and ghost).
+struct AxisTiles {
+    int n, W, H, ghost;
+    __host__ __device__ int first() const { return W - ghost - H; }
+    __host__ __device__ int inner() const { return W - 2 * H; }
+    __host__ __device__ bool single() const { return n <= W - 2 * ghost; }
+    __host__ __device__ int count() const
+    {
+        if (single()) return 1;
+        const int rest = n - 2 * first();
+        return 2 + (rest > 0 ? (rest + inner() - 1) / inner() : 0);
+    }
+    __host__ __device__ int start(int k) const { return k == 0 ? 0 : first() + (k - 1) * inner(); }
+    __host__ __device__ int origin(int k) const { return k == 0 ? -ghost : start(k) - H; }
+    __host__ __device__ int end(int k) const { return k + 1 >= count() ? n : start(k + 1); }
+    __host__ __device__ int index(int i) const      // tile of node i (0 <= i < n)
+    {
+        if (single() || i < first()) return 0;
+        const int k = 1 + (i - first()) / inner();
+        const int last = count() - 1;
+        return k < last ? k : last;
+    }
+};
+__host__ __device__ inline AxisTiles blocked_x(const FusedGeom &g, int nx) { return AxisTiles{nx, g.W, g.HX, 0}; }
+__host__ __device__ inline AxisTiles blocked_y(const FusedGeom &g, int ny) { return AxisTiles{ny, g.R, g.HY, 1}; }
+// The fused geometry with the batch's wall-aligned tile counts in ntx / nty.
+bool blocked_geometry(const FieldDesc &f, float step_len, float stop_r2, bool cones, int K, FusedGeom &g);
 // Encode a 2D TMA source map of an nx x ny FP32 field with rows `pitch` floats apart.
 bool encode_field_map(void *map128, float *base, int nx, int ny, int pitch);
 bool encode_field_map_available();

@@ -2,7 +2,10 @@
 // instance of a batch K steps (field and cones, rows a1-a6 of each), one
 // HBM round trip of each instance's field per launch.
 //
-// The work list holds one item per (instance, field tile).  A CTA loads its
+// The work list holds one item per (instance, field tile).  Tiles are aligned
+// to the instance's walls (AxisTiles): a tile that holds a wall carries no halo
+// beyond it, so an instance up to 256 columns wide is one tile column and one
+// up to 94 rows high one tile row.  A CTA loads its
 // tile plus a halo from the instance's current buffer with one TMA tensor copy
 // (the instance's tensor maps live in the instance table in global memory;
 // rows are the instance's pitch apart, columns past nx read as zeros), runs K
@@ -68,7 +71,7 @@ __device__ __forceinline__ int tile_of_b(const BInst &I, float px, float py)
     const FieldDesc &f = I.f;
     int ix = clampi((int)floorf(px * f.inv_h), 0, f.nx - 1);
     int iy = clampi((int)floorf(py * f.inv_h), 0, f.ny - 1);
-    return (iy / I.g.TY) * I.g.ntx + ix / I.g.TX;
+    return blocked_y(I.g, f.ny).index(iy) * I.g.ntx + blocked_x(I.g, f.nx).index(ix);
 }
 
 // The first `real` (>= 1) components of a group are finite (the rest is row padding).
@@ -103,7 +106,8 @@ __global__ void __launch_bounds__(kThreads, 2) blocked_kernel(const BlockedArgs 
     const int t = item.y;
     const int gt = I.tile_base + t;
     const int tx = t % g.ntx, ty = t / g.ntx;
-    const int ox = tx * g.TX - g.HX, oy = ty * g.TY - g.HY;
+    const AxisTiles ax = blocked_x(g, f.nx), ay = blocked_y(g, f.ny);
+    const int ox = ax.origin(tx), oy = ay.origin(ty);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = I.n_axons;
 
@@ -432,12 +436,12 @@ __global__ void __launch_bounds__(kThreads, 2) blocked_kernel(const BlockedArgs 
             if (real > 2) row[gx + 2] = v.z;
         }
     };
-    for (int r = g.HY + warp; r < g.HY + g.TY; r += kWarps) {
-        const int gy = oy + r;
-        if (gy >= f.ny) break;
-        float *row = Cout + (size_t)gy * I.pitch;
-        if (colA >= g.HX && colA < g.HX + g.TX && gxA < f.nx) put(row, gxA, S4[r * (kW / 4) + lane]);
-        if (colB >= g.HX && colB < g.HX + g.TX && gxB < f.nx) put(row, gxB, S4[r * (kW / 4) + 32 + lane]);
+    // (the interior [ax.start, ax.end) x [ay.start, ay.end) of this tile, inside the grid)
+    const int cx0 = ax.start(tx) - ox, cx1 = ax.end(tx) - ox;
+    for (int r = ay.start(ty) - oy + warp; r < ay.end(ty) - oy; r += kWarps) {
+        float *row = Cout + (size_t)(oy + r) * I.pitch;
+        if (colA >= cx0 && colA < cx1) put(row, gxA, S4[r * (kW / 4) + lane]);
+        if (colB >= cx0 && colB < cx1) put(row, gxB, S4[r * (kW / 4) + 32 + lane]);
     }
     if (__any_sync(kFull, bad) && lane == 0) flag_status(A.status, kStatusNonFinite);
     finish();
@@ -461,6 +465,14 @@ __global__ void __launch_bounds__(256) blocked_bin_kernel(const BInst *__restric
 }
 
 }  // namespace
+
+bool blocked_geometry(const FieldDesc &f, float step_len, float stop_r2, bool cones, int K, FusedGeom &g)
+{
+    if (!fused_geometry(f, step_len, stop_r2, cones, K, g)) return false;
+    g.ntx = blocked_x(g, f.nx).count();
+    g.nty = blocked_y(g, f.ny).count();
+    return true;
+}
 
 size_t blocked_smem_bytes()
 {

@@ -241,3 +241,48 @@ def test_blocked_mode_on_clustered_and_crowded_instances(cue, batch_mod):
     for i, w in enumerate(ws):
         _assert_same(b.snapshot(i), _alone(cue, w, 19), w.name)
     b.close()
+
+
+def _tile_boundary_instances():
+    """Instances whose sides sit on either side of the blocked mode's tile-count steps at
+    depths 2, 5 and 8 (halo H = K + 1 + ceil((K - 1) step_len / h): 3, 7 and 13 rows, 4, 8
+    and 16 columns): one tile column up to 256 columns, one tile row up to 94 rows, then the
+    first and last tiles ending at the walls; nx % 4 = 0..3, clamp and stop walls, a rate
+    map, cones everywhere including the wall rows and columns."""
+    rng = np.random.default_rng(95)
+    sides = [(256, 94, 0), (257, 95, 1), (480, 164, 0), (481, 165, 1), (462, 150, 0), (463, 151, 1),
+             (705, 235, 0), (99, 300, 1), (1030, 96, 0), (134, 143, 1)]
+    out = []
+    for k, (nx, ny, clamp) in enumerate(sides):
+        w = W.make(f"edge{nx}x{ny}", 2, nx, ny, D=0.7 + 0.1 * k, lam=0.004, dt=0.2 / (0.7 + 0.1 * k), n_src=6 + k,
+                   n_axons=300 + 40 * k, C0="smooth", seed=200 + k, wall_mode=clamp,
+                   stop_radius=1.5 if k % 3 == 0 else 0.0, src_map="random" if k % 4 == 1 else False)
+        # a quarter of the cones on the walls' nodes and the nodes next to them
+        m = w.n_axons // 4
+        side = rng.integers(0, 4, m)
+        off = rng.uniform(0.0, 1.5, m)
+        along_x = rng.uniform(0.0, nx - 1.0, m)
+        along_y = rng.uniform(0.0, ny - 1.0, m)
+        x = np.where(side == 0, off, np.where(side == 1, nx - 1.0 - off, along_x))
+        y = np.where(side == 2, off, np.where(side == 3, ny - 1.0 - off, along_y))
+        w.pos[0, :m] = x.astype(np.float32)
+        w.pos[1, :m] = y.astype(np.float32)
+        out.append(w)
+    return out
+
+
+@pytest.mark.parametrize("depth", [2, 5, 8])
+def test_blocked_wall_aligned_tiles_at_count_boundaries(cue, batch_mod, depth):
+    """Wall-aligned tiles of the blocked mode: instances whose sides straddle every step of
+    the tile count (one tile, first and last tiles at the walls, middle tiles), bit for bit
+    equal to each instance alone on the plain path over 3 launches plus a ragged one."""
+    ws = _tile_boundary_instances()
+    b = batch_mod.Batch(ws)
+    b.set_option(batch_mod.CUE_BOPT_MODE, 3)
+    b.set_option(batch_mod.CUE_BOPT_DEPTH, depth)
+    nsteps = 3 * depth + 1
+    b.run(nsteps)
+    b.check()
+    for i, w in enumerate(ws):
+        _assert_same(b.snapshot(i), _alone(cue, w, nsteps), w.name)
+    b.close()
