@@ -29,6 +29,7 @@ constexpr int kBoxX = kTX + 2 * kHX;  // 136 floats = 544 bytes per row
 constexpr int kBY = 16;               // interior rows per tile
 constexpr int kBoxY = kBY + 2;
 constexpr int kStages = 4;
+constexpr int kAhead = kStages - 2;   // planes in flight beyond the three being read
 constexpr int kThreads3 = 256;        // field warps: 8 warps x 2 rows
 constexpr int kLaunch3 = kThreads3 + 32;  // + one warp for the block's cones
 constexpr int kStageFloats = kBoxX * kBoxY;                   // one plane tile (9,792 bytes)
@@ -211,13 +212,14 @@ __global__ void __launch_bounds__(CONES ? kLaunch3 : kThreads3, 4)
     const int gx = x0 + 4 * lane;
     const bool xin = gx < f.nx;
     const bool wl = gx == 0, wr = gx + 3 == f.nx - 1;
+    const float2 alpha2 = make_float2(f.alpha, f.alpha), beta2 = make_float2(f.beta, f.beta);
     const float4 *s4 = reinterpret_cast<const float4 *>(stage);
     bool tmo = false, bad = false;
     for (int p = plo; p <= zs; ++p)          // planes z-1 (if any) and z of the first step
         if (!wait(p)) tmo = true;
     for (int z = zs; z < ze; ++z) {
-        // keep two planes ahead: plane z+2 into the stage plane z-2 used
-        if (tid == 0 && z + 2 <= phi && z + 2 >= plo + kStages - 1) issue(z + 2);
+        // keep kAhead planes ahead: plane z+kAhead into the stage plane z-2 used
+        if (tid == 0 && z + kAhead <= phi && z + kAhead >= plo + kStages - 1) issue(z + kAhead);
         if (z + 1 <= phi && !wait(z + 1)) tmo = true;
         if (field_sync_or(tmo)) {
             if (tid == 0) {
@@ -250,11 +252,7 @@ __global__ void __launch_bounds__(CONES ? kLaunch3 : kThreads3, 4)
             if (wl) l = c.x;
             if (wr) rt = c.w;
             if (xin && gy < f.ny) {
-                float4 o;
-                o.x = node_update3(c.x, l, c.y, ym.x, yp.x, zm.x, zp.x, f.alpha, f.beta);
-                o.y = node_update3(c.y, c.x, c.z, ym.y, yp.y, zm.y, zp.y, f.alpha, f.beta);
-                o.z = node_update3(c.z, c.y, c.w, ym.z, yp.z, zm.z, zp.z, f.alpha, f.beta);
-                o.w = node_update3(c.w, c.z, rt, ym.w, yp.w, zm.w, zp.w, f.alpha, f.beta);
+                float4 o = node_update3_x4(c, l, rt, ym, yp, zm, zp, alpha2, beta2);
                 const size_t idx = ((size_t)z * f.ny + gy) * f.nx + gx;
                 if constexpr (MAP) {
                     const float4 m = __ldg(reinterpret_cast<const float4 *>(A.M + idx));

@@ -174,25 +174,6 @@ __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int x, i
                  : "memory");
 }
 
-// node_update3 on a float4 group, two nodes at a time with the packed FP32x2
-// instructions (each half of a pair rounds exactly like the scalar form):
-// ((x- + x+) + (y- + y+)) + (z- + z+), times alpha, plus beta c.
-__device__ __forceinline__ float4 upd4(const float4 &c, float xl, float xr, const float4 &ym, const float4 &yp,
-                                       const float4 &zm, const float4 &zp, float2 alpha2, float2 beta2)
-{
-    const float2 hx01 = __fadd2_rn(make_float2(xl, c.x), make_float2(c.y, c.z));
-    const float2 hx23 = __fadd2_rn(make_float2(c.y, c.z), make_float2(c.w, xr));
-    const float2 hy01 = __fadd2_rn(make_float2(ym.x, ym.y), make_float2(yp.x, yp.y));
-    const float2 hy23 = __fadd2_rn(make_float2(ym.z, ym.w), make_float2(yp.z, yp.w));
-    const float2 hz01 = __fadd2_rn(make_float2(zm.x, zm.y), make_float2(zp.x, zp.y));
-    const float2 hz23 = __fadd2_rn(make_float2(zm.z, zm.w), make_float2(zp.z, zp.w));
-    const float2 s01 = __fadd2_rn(__fadd2_rn(hx01, hy01), hz01);
-    const float2 s23 = __fadd2_rn(__fadd2_rn(hx23, hy23), hz23);
-    const float2 o01 = __ffma2_rn(alpha2, s01, __fmul2_rn(beta2, make_float2(c.x, c.y)));
-    const float2 o23 = __ffma2_rn(alpha2, s23, __fmul2_rn(beta2, make_float2(c.z, c.w)));
-    return make_float4(o01.x, o01.y, o23.x, o23.y);
-}
-
 // Wait for an input plane: one lane of the warp polls (bounded), then every lane
 // observes the completed phase itself (which returns at once).
 __device__ __forceinline__ bool warp_wait_plane(uint64_t *bar, unsigned phase, int lane)
@@ -653,7 +634,7 @@ __global__ void __launch_bounds__(CONES ? kAllT : kFT, kCtasPerSm)
                 if (F & (kE1 | kWr)) xr = c.w;
                 if (F & kYl) ym = c;
                 if (F & kYh) yp = c;
-                float4 o = upd4(c, xl, xr, ym, yp, zm, zp, alpha2, beta2);
+                float4 o = node_update3_x4(c, xl, xr, ym, yp, zm, zp, alpha2, beta2);
                 if (MAP && (F & kIng)) {
                     const float4 mv = __ldg(reinterpret_cast<const float4 *>(Mp + io[m]));
                     o.x = fmaf(f.dt, mv.x, o.x);
@@ -734,7 +715,7 @@ __global__ void __launch_bounds__(CONES ? kAllT : kFT, kCtasPerSm)
                     if (F & kWr) xr = c.w;
                     if (F & kYl) ym = c;
                     if (F & kYh) yp = c;
-                    float4 o = upd4(c, xl, xr, ym, yp, zm, zp, alpha2, beta2);
+                    float4 o = node_update3_x4(c, xl, xr, ym, yp, zm, zp, alpha2, beta2);
                     if (MAP) {
                         const float4 mv = __ldg(reinterpret_cast<const float4 *>(Mp + io[m]));
                         o.x = fmaf(f.dt, mv.x, o.x);
