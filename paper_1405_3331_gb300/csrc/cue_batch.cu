@@ -336,7 +336,9 @@ int stage_blocked(cue_batch *b, int K)
             // instruction fetch of eight unrolled sweeps being the first stall); then the
             // tile's expected cone load (the instance's cones over its tiles, in powers of
             // two), heaviest first so that no crowded tile is left for a group's last wave
-            // (-> 704)
+            // (-> 704).  Tiles whose cones take more than one round through global memory
+            // per sub-step (over 768) run longest: they go first, ahead of every group, so
+            // that none of them is left for the launch's tail (-> 752)
             const int tx = t % g.ntx, ty = t / g.ntx;
             const int ox = blocked_x(g, I.params.nx).origin(tx), oy = blocked_y(g, I.params.ny).origin(ty);
             const int nx = I.params.nx, ny = I.params.ny;
@@ -345,7 +347,8 @@ int stage_blocked(cue_batch *b, int K)
             const int load = std::max(I.n_axons, 0) / tiles;
             int lclass = 0;
             while ((1 << lclass) <= load && lclass < 30) ++lclass;
-            order_key.push_back((((I.src_map ? 4 : 0) | (wall ? 2 : 0) | (ragged ? 1 : 0)) << 8) | (30 - lclass));
+            const int cls = (I.src_map ? 4 : 0) | (wall ? 2 : 0) | (ragged ? 1 : 0);
+            order_key.push_back(load > kFusedBinCap + kBlockedThreads ? 30 - lclass : ((cls + 1) << 8) | (30 - lclass));
         }
         for (int a0 = 0; a0 < I.n_axons; a0 += 256) chunks.push_back(make_int2(i, a0));
         tile_base += tiles;

@@ -317,6 +317,7 @@ void timing_end(Sim &s);
 constexpr int kBlockedMaxSrc = 256;   // point sources per instance on this mode
 constexpr int kBlockedTileW = 256;    // loaded columns and rows of a blocked-mode tile
 constexpr int kBlockedTileRows = 96;
+constexpr int kBlockedThreads = 256;   // threads of a blocked-mode CTA
 // One instance of a batch in the blocked mode (device table; the tensor maps
 // give the struct their 128-byte alignment, which the workspace's 256-byte
 // offsets keep).

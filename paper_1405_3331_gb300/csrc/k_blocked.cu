@@ -45,7 +45,8 @@
 #include "cue_tile.cuh"
 
 namespace cue {
-static_assert(kBlockedTileW == tile::kW && kBlockedTileRows == tile::kRows, "blocked tile shape");
+static_assert(kBlockedTileW == tile::kW && kBlockedTileRows == tile::kRows && kBlockedThreads == tile::kThreads,
+              "blocked tile shape");
 
 namespace {
 
