@@ -57,6 +57,7 @@ struct ClusterArgs {
     uint32_t step0;              // Philox step of the first step
     int band;                    // rows per CTA (the last CTAs may own fewer, or none)
     int field_warps;             // warps 0 .. field_warps-1 update the band; the rest step cones
+    int pre_noise;               // 1: field warps without rows draw the cones' noise a step ahead
     int rows;                    // rows per work item of the band loop
     unsigned *status;
     unsigned long long *counter;
@@ -109,6 +110,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(const __gri
     int *s_cell = reinterpret_cast<int *>(smem + 2 * bsz);   // this band's sources, in source order
     float *s_emit = reinterpret_cast<float *>(s_cell + kClusterMaxSources);
     unsigned *s_rows = reinterpret_cast<unsigned *>(s_emit + kClusterMaxSources);
+    // the cones' noise of a step, drawn a step ahead by the field warps that have no
+    // rows: [2 steps][2 components][CL cone lanes]
+    const int CL = kClusterThreads - A.field_warps * 32;
+    float *s_noise = reinterpret_cast<float *>(s_rows + nrw);
     __shared__ int s_nsrc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -151,6 +156,21 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(const __gri
     const int ncb = (Q + 31) >> 5;
     const int R = A.rows;
     const int n_items = rows > 0 ? ncb * ((rows + R - 1) / R) : 0;
+    // field warps left without rows draw the noise of the next step (at most two draws a
+    // lane), which takes Philox and Box-Muller off the cones' dependent chain
+    const int idle = fw - min(n_items, fw);          // the host set pre_noise only where CL <= 64 idle
+    const bool pre_noise = A.pre_noise != 0 && idle > 0;
+    const bool noise_warp = pre_noise && field_warp && warp >= fw - idle;
+    auto draw_noise = [&](int step, int buf) {       // noise of step `step` into buffer buf
+        for (int i = (warp - (fw - idle)) * 32 + lane; i < CL; i += idle * 32) {
+            const int ai = i * G + rank;
+            float xi[2] = {0.f, 0.f};
+            if (ai < A.n_axons) cone_noise<2>(A.c.key0, A.c.key1, (uint32_t)ai, A.step0 + (uint32_t)step, xi);
+            s_noise[(2 * buf) * CL + i] = xi[0];
+            s_noise[(2 * buf + 1) * CL + i] = xi[1];
+        }
+    };
+    if (noise_warp) draw_noise(0, 0);
 
     // cone a = i * G + rank belongs to this CTA's cone lane i: its state stays in registers
     const int a = ((warp - fw) * 32 + lane) * G + rank;
@@ -250,9 +270,16 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(const __gri
                     vc = vp;
                 }
             }
+            if (noise_warp && s + 1 < A.nsteps) draw_noise(s + 1, (s + 1) & 1);
         } else if (has_cone) {
             float xi[2];
-            cone_noise<2>(A.c.key0, A.c.key1, (uint32_t)a, A.step0 + (uint32_t)s, xi);
+            if (pre_noise) {
+                const int i = (warp - fw) * 32 + lane;
+                xi[0] = s_noise[(2 * (s & 1)) * CL + i];
+                xi[1] = s_noise[(2 * (s & 1) + 1) * CL + i];
+            } else {
+                cone_noise<2>(A.c.key0, A.c.key1, (uint32_t)a, A.step0 + (uint32_t)s, xi);
+            }
             if (act) {
                 ++n_live;
                 // every node from its owner's buffer through the cluster's shared-memory window
@@ -304,11 +331,36 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(const __gri
 
 int cluster_band(const Sim &s, int G) { return (s.fd.ny + G - 1) / G; }
 
+// The launch's split of a CTA's warps: field warps, and runs of rows just tall
+// enough that every field warp has at most one work item; the cones' noise is
+// drawn a step ahead when the fullest band leaves field warps without rows
+// enough for at most two draws a lane.
+struct ClusterSplit {
+    int field_warps, rows, cone_lanes;
+    bool pre_noise;
+};
+
+ClusterSplit cluster_split(const Sim &s, int G)
+{
+    ClusterSplit k;
+    const int band = cluster_band(s, G);
+    const int cones_per_cta = (s.n_axons + G - 1) / G;
+    k.cone_lanes = (cones_per_cta + 31) / 32 * 32;
+    k.field_warps = kClusterThreads / 32 - k.cone_lanes / 32;
+    const int ncb = (s.fd.nx / 4 + 31) / 32;
+    k.rows = std::max(1, (band * ncb + k.field_warps - 1) / k.field_warps);
+    const int items = ncb * ((band + k.rows - 1) / k.rows);
+    const int idle = k.field_warps - std::min(items, k.field_warps);
+    k.pre_noise = k.cone_lanes > 0 && idle > 0 && k.cone_lanes <= 64 * idle;
+    return k;
+}
+
 size_t cluster_smem_bytes(const Sim &s, int G)
 {
     const int band = cluster_band(s, G);
+    const ClusterSplit k = cluster_split(s, G);
     return 2 * sizeof(float) * (size_t)(band + 2) * s.fd.nx + 8 * (size_t)kClusterMaxSources +
-           4 * (size_t)((band + 31) / 32);
+           4 * (size_t)((band + 31) / 32) + (k.pre_noise ? 4 * sizeof(float) * (size_t)k.cone_lanes : 0);
 }
 
 // Dynamic shared memory a CTA may ask for: the per-block opt-in maximum less
@@ -444,11 +496,10 @@ int run_cluster_if_supported(Sim &s, int nsteps)
     A.active = s.active;
     A.n_axons = s.n_axons;
     A.band = cluster_band(s, G);
-    const int cones_per_cta = (s.n_axons + G - 1) / G;
-    A.field_warps = kClusterThreads / 32 - (cones_per_cta + 31) / 32;
-    // runs just tall enough that every field warp has at most one work item
-    const int ncb = (s.fd.nx / 4 + 31) / 32;
-    A.rows = std::max(1, (A.band * ncb + A.field_warps - 1) / A.field_warps);
+    const ClusterSplit split = cluster_split(s, G);
+    A.field_warps = split.field_warps;
+    A.rows = split.rows;
+    A.pre_noise = split.pre_noise ? 1 : 0;
     A.status = s.status();
     A.counter = s.cone_counter();
     for (int done = 0; done < nsteps;) {              // launches of at most kPersistMaxSteps steps
