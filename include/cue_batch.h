@@ -75,8 +75,9 @@ cue_batch *cue_batch_create(int32_t n, const cue_instance *inst, void *d_ws, siz
  * C^n -> C^{n+1}).  One cooperative launch (CUE_BOPT_MODE 1), one or two
  * launches per step (mode 2), or (mode 3) the cones binned to field tiles and
  * then one temporally blocked launch per CUE_BOPT_DEPTH steps -- each field
- * tile of each instance loaded once into shared memory with its halo and
- * advanced that many steps there with its cones -- or one graph replay of
+ * tile of each instance loaded once into shared memory with its halo (tiles
+ * aligned to the instance's walls, no halo beyond a wall) and advanced that
+ * many steps there with its cones -- or one graph replay of
  * those when CUE_BOPT_GRAPH is on (the graph is captured at the first call
  * with a given nsteps and replayed afterwards; the step counter, buffer
  * parity and bin round live on the device, so a replay needs no new
